@@ -1,0 +1,237 @@
+"""FP64 CPU oracle (test infrastructure).
+
+Plain, slow, obviously-correct reference for the photo-switching
+optoacoustic hot path (arXiv 2510.23739): the switching matrix of
+Eq. (final-H)/(Sij-detailed), the forward H = W_tot S of Sec. 2.3 and
+Eq. (full-forward), its exact adjoint, the l1 and TV proximal maps of
+Eq. (prox)/(prox-dual) and Algorithm 2, FISTA (Algorithm 1), the power
+iteration for the step size, and the kappa/mu gradient of the data fit.
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline leg may import this package.  It shares no code with the CUDA
+library.  The arithmetic lives in ``swopt_oracle.c`` (plain C, FP64, optional
+OpenMP over independent outputs); this file only compiles it and marshals
+numpy arrays.
+
+Every function is pinned by ``tests/test_oracle_pins.py``; none is
+"parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "swopt_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MOMENTUM = {"beck_teboulle": 0, "paper_printed": 1, "none": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle into ``oracle/_build/liboracle.so``."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(base[:4] + ["-fopenmp"] + base[4:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            L.oracle_power.restype = ctypes.c_double
+            L.oracle_objective.restype = ctypes.c_double
+            L.oracle_tv.restype = ctypes.c_double
+            L.oracle_num_threads.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _dims(geom):
+    g = geom
+    return [ctypes.c_int(v) for v in (g.N, g.P, g.Y, g.X, g.Z, g.T, g.k)]
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+def fluence(geom, sw):
+    """Phi_j = exp(-mu j dz)."""
+    out = np.empty(geom.Z)
+    lib().oracle_fluence(ctypes.c_int(geom.Z), ctypes.c_double(sw.mu_per_mm),
+                         ctypes.c_double(geom.dz_mm), _p(out))
+    return out
+
+
+def switch_matrix(geom, sw):
+    """S[n][p][j] of Eq. (final-H)."""
+    phi = fluence(geom, sw)
+    kap = _f64(sw.kappa)
+    eb = _f64(sw.eps_bar)
+    eo = _f64(sw.eps_off)
+    S = np.empty((geom.N, geom.P, geom.Z))
+    lib().oracle_switch_matrix(ctypes.c_int(geom.N), ctypes.c_int(geom.P),
+                               ctypes.c_int(geom.Z), ctypes.c_int(geom.pulses_per_cycle),
+                               _p(phi), _p(kap), _p(eb), _p(eo), _p(S))
+    return S
+
+
+def forward(geom, sw, K, c, S=None):
+    """y = H c, y[N][Y][X][T]."""
+    S = switch_matrix(geom, sw) if S is None else _f64(S)
+    K = _f64(K)
+    c = _f64(c)
+    y = np.empty(geom.y_shape())
+    lib().oracle_forward(*_dims(geom), _p(S), _p(K), _p(c), _p(y))
+    return y
+
+
+def adjoint(geom, sw, K, y, S=None):
+    """c = H^T y, c[P][Y][X][Z]."""
+    S = switch_matrix(geom, sw) if S is None else _f64(S)
+    K = _f64(K)
+    y = _f64(y)
+    c = np.empty(geom.c_shape())
+    lib().oracle_adjoint(*_dims(geom), _p(S), _p(K), _p(y), _p(c))
+    return c
+
+
+def forward_at(geom, sw, K, c, nyx):
+    """(H c)[n, y, x, :] for each row of the int array ``nyx`` (count x 3)."""
+    S = switch_matrix(geom, sw)
+    idx = np.ascontiguousarray(nyx, dtype=np.int32)
+    out = np.empty((idx.shape[0], geom.T))
+    lib().oracle_forward_at(*_dims(geom), _p(S), _p(_f64(K)), _p(_f64(c)),
+                            ctypes.c_int(idx.shape[0]), _p(idx), _p(out))
+    return out
+
+
+def adjoint_at(geom, sw, K, y, pyxj):
+    """(H^T y)[p, y, x, j] for each row of ``pyxj`` (count x 4)."""
+    S = switch_matrix(geom, sw)
+    idx = np.ascontiguousarray(pyxj, dtype=np.int32)
+    out = np.empty(idx.shape[0])
+    lib().oracle_adjoint_at(*_dims(geom), _p(S), _p(_f64(K)), _p(_f64(y)),
+                            ctypes.c_int(idx.shape[0]), _p(idx), _p(out))
+    return out
+
+
+def grad3(v):
+    v = _f64(v)
+    Y, X, Z = v.shape
+    g = np.empty((3, Y, X, Z))
+    lib().oracle_grad3(ctypes.c_int(Y), ctypes.c_int(X), ctypes.c_int(Z), _p(v), _p(g))
+    return g
+
+
+def grad3T(g):
+    g = _f64(g)
+    _, Y, X, Z = g.shape
+    v = np.empty((Y, X, Z))
+    lib().oracle_grad3T(ctypes.c_int(Y), ctypes.c_int(X), ctypes.c_int(Z), _p(g), _p(v))
+    return v
+
+
+def tv(c):
+    c = _f64(c)
+    P, Y, X, Z = c.shape
+    return float(lib().oracle_tv(ctypes.c_int(P), ctypes.c_int(Y), ctypes.c_int(X),
+                                 ctypes.c_int(Z), _p(c)))
+
+
+def prox_l1(x, theta, nonneg=True):
+    x = _f64(x).copy()
+    lib().oracle_prox_l1(ctypes.c_size_t(x.size), _p(x), ctypes.c_double(theta),
+                         ctypes.c_int(1 if nonneg else 0))
+    return x
+
+
+def prox_tv(z, tau, iters, momentum="beck_teboulle"):
+    z = _f64(z)
+    P, Y, X, Z = z.shape
+    x = np.empty_like(z)
+    lib().oracle_prox_tv(ctypes.c_int(P), ctypes.c_int(Y), ctypes.c_int(X), ctypes.c_int(Z),
+                         _p(z), _p(x), ctypes.c_double(tau), ctypes.c_int(iters),
+                         ctypes.c_int(MOMENTUM[momentum]))
+    return x
+
+
+def prox(z, alpha, lam_l1, lam_tv, inner, momentum="beck_teboulle"):
+    z = _f64(z)
+    P, Y, X, Z = z.shape
+    x = np.empty_like(z)
+    lib().oracle_prox(ctypes.c_int(P), ctypes.c_int(Y), ctypes.c_int(X), ctypes.c_int(Z),
+                      _p(z), _p(x), ctypes.c_double(alpha), ctypes.c_double(lam_l1),
+                      ctypes.c_double(lam_tv), ctypes.c_int(inner),
+                      ctypes.c_int(MOMENTUM[momentum]))
+    return x
+
+
+def objective(geom, sw, K, c, y, lam_l1, lam_tv):
+    """Returns (F(c), data-fit 1/2||Hc - y||^2)."""
+    S = switch_matrix(geom, sw)
+    fit = ctypes.c_double(0.0)
+    F = lib().oracle_objective(*_dims(geom), _p(S), _p(_f64(K)), _p(_f64(c)), _p(_f64(y)),
+                               ctypes.c_double(lam_l1), ctypes.c_double(lam_tv),
+                               ctypes.byref(fit))
+    return float(F), float(fit.value)
+
+
+def fista(geom, sw, K, y, alpha, iters, lam_l1, lam_tv, inner,
+          momentum="beck_teboulle", inner_momentum="beck_teboulle", history=False):
+    """Algorithm 1 with a fixed iteration count; returns c (and F per iteration)."""
+    S = switch_matrix(geom, sw)
+    c = np.empty(geom.c_shape())
+    hist = np.empty(iters) if history else None
+    lib().oracle_fista(*_dims(geom), _p(S), _p(_f64(K)), _p(_f64(y)),
+                       ctypes.c_double(alpha), ctypes.c_int(iters),
+                       ctypes.c_double(lam_l1), ctypes.c_double(lam_tv), ctypes.c_int(inner),
+                       ctypes.c_int(MOMENTUM[momentum]), ctypes.c_int(MOMENTUM[inner_momentum]),
+                       _p(c), _p(hist) if history else ctypes.c_void_p(0))
+    return (c, hist) if history else c
+
+
+def power(geom, sw, K, v0, iters):
+    """Rayleigh-quotient estimate of eig_max(H^T H) after ``iters`` steps."""
+    S = switch_matrix(geom, sw)
+    return float(lib().oracle_power(*_dims(geom), _p(S), _p(_f64(K)), _p(_f64(v0)),
+                                    ctypes.c_int(iters)))
+
+
+def param_grad(geom, sw, K, c, y):
+    """(d/dkappa[P], d/dmu) of 1/2 ||H c - y||^2."""
+    dk = np.empty(geom.P)
+    dmu = ctypes.c_double(0.0)
+    lib().oracle_param_grad(*_dims(geom), ctypes.c_int(geom.pulses_per_cycle),
+                            ctypes.c_double(sw.mu_per_mm), ctypes.c_double(geom.dz_mm),
+                            _p(_f64(sw.kappa)), _p(_f64(sw.eps_bar)), _p(_f64(sw.eps_off)),
+                            _p(_f64(K)), _p(_f64(c)), _p(_f64(y)), _p(dk), ctypes.byref(dmu))
+    return dk, float(dmu.value)

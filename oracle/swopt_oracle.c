@@ -1,0 +1,533 @@
+/*
+ * FP64 CPU oracle for the one-step photo-switching optoacoustic reconstruction.
+ *
+ * TEST INFRASTRUCTURE.  This file is the plain, slow, obviously-correct
+ * reference against which the CUDA library is checked.  Only the test suite,
+ * the smoke check and the benchmark's CPU-baseline leg load it.  It shares no
+ * code, header, table or helper with the CUDA library.
+ *
+ * Every function follows a passage of the paper (arXiv 2510.23739):
+ *   switching matrix      Eq. (final-H) and Eq. (Sij-detailed), Sec. 2.3.1
+ *   forward  H = W_tot S  Eq. (q-above-final)/(q-below-final) read as a
+ *                         per-depth lateral correlation, Eq. (acoustic-full-
+ *                         forward), Eq. (full-forward)
+ *   adjoint  H^T          the exact transpose of the forward
+ *   TV / l1 prox          Eq. (prox), Eq. (prox-dual), Algorithm 2
+ *   FISTA                 Algorithm 1 with the objective of Eq. (one-step)
+ *                         and Eq. (reg-tv-l1-one) (lambda_3 = 0)
+ *   power iteration       the step size alpha_1 = 1/eig_max(A^T A) of
+ *                         Algorithm 1
+ *
+ * Layouts (row-major, C order):
+ *   c  [P][Y][X][Z]    concentrations
+ *   y  [N][Y][X][T]    measurements
+ *   K  [Z][k][k][T]    per-depth kernel, index [j][dy+r][dx+r][t]
+ *   S  [N][P][Z]       switching weights (depend on depth only)
+ *
+ * Parity is pinned for every function by the oracle test-suite (conv2d
+ * special case, point absorber, adjoint identity, closed forms, exact
+ * convex solutions computed by an independent solver, finite differences).
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define IDX4(a, b, c, d, B, C, D) ((((size_t)(a) * (B) + (b)) * (C) + (c)) * (D) + (d))
+
+/* ---------------------------------------------------------------------------
+ * Switching model, Eq. (final-H): per depth j and pulse n,
+ *   S[n][p][j] = Phi_j * (eps_bar_p * exp(-kappa_p * Phi_j * m) + eps_off_p),
+ * m = n mod pulses_per_cycle (switching time in pulse intervals since the
+ * start of the cycle) and Phi_j = exp(-mu * j * dz) (fluence from the top
+ * layer).  The background species has kappa = 0, eps_bar = 0.
+ * ------------------------------------------------------------------------- */
+void oracle_fluence(int Z, double mu_per_mm, double dz_mm, double* phi)
+{
+    for (int j = 0; j < Z; ++j) phi[j] = exp(-mu_per_mm * (double)j * dz_mm);
+}
+
+void oracle_switch_matrix(int N, int P, int Z, int pulses_per_cycle,
+                          const double* phi, const double* kappa,
+                          const double* eps_bar, const double* eps_off,
+                          double* S)
+{
+    for (int n = 0; n < N; ++n) {
+        int m = n % pulses_per_cycle;
+        for (int p = 0; p < P; ++p)
+            for (int j = 0; j < Z; ++j)
+                S[IDX4(0, n, p, j, N, P, Z)] =
+                    phi[j] * (eps_bar[p] * exp(-kappa[p] * phi[j] * (double)m) + eps_off[p]);
+    }
+}
+
+/* b[n][y][x][j] = sum_p S[n][p][j] c[p][y][x][j]   (Eq. Sij-detailed) */
+static void apply_S(int N, int P, int Y, int X, int Z, const double* S,
+                    const double* c, double* b)
+{
+    for (int n = 0; n < N; ++n)
+        for (int yy = 0; yy < Y; ++yy)
+            for (int xx = 0; xx < X; ++xx)
+                for (int j = 0; j < Z; ++j) {
+                    double acc = 0.0;
+                    for (int p = 0; p < P; ++p)
+                        acc += S[IDX4(0, n, p, j, N, P, Z)] * c[IDX4(p, yy, xx, j, Y, X, Z)];
+                    b[IDX4(n, yy, xx, j, Y, X, Z)] = acc;
+                }
+}
+
+/* ---------------------------------------------------------------------------
+ * Forward, y = W_tot S c.  For every pulse n and scan position (y, x):
+ *   y[n][y][x][t] = sum_j sum_{|dy|,|dx| <= r} b[n][y+dy][x+dx][j] K[j][dy][dx][t]
+ * with b = 0 outside the scan grid.  This is the paper's "correlate the OA
+ * image with the masked response and take the row at the focal plane"
+ * (Sec. 2.3.3), stacked over depths, with the electrical impulse response
+ * already folded into K along t; the same W is used for every pulse
+ * (Eq. acoustic-full-forward).
+ * ------------------------------------------------------------------------- */
+void oracle_forward(int N, int P, int Y, int X, int Z, int T, int k,
+                    const double* S, const double* K, const double* c, double* y)
+{
+    const int r = k / 2;
+    double* b = (double*)malloc(sizeof(double) * (size_t)N * Y * X * Z);
+    apply_S(N, P, Y, X, Z, S, c, b);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int n = 0; n < N; ++n)
+        for (int yy = 0; yy < Y; ++yy)
+            for (int xx = 0; xx < X; ++xx) {
+                double* out = y + IDX4(n, yy, xx, 0, Y, X, T);
+                for (int t = 0; t < T; ++t) out[t] = 0.0;
+                for (int dy = -r; dy <= r; ++dy) {
+                    int sy = yy + dy;
+                    if (sy < 0 || sy >= Y) continue;
+                    for (int dx = -r; dx <= r; ++dx) {
+                        int sx = xx + dx;
+                        if (sx < 0 || sx >= X) continue;
+                        for (int j = 0; j < Z; ++j) {
+                            double bv = b[IDX4(n, sy, sx, j, Y, X, Z)];
+                            const double* Kp = K + IDX4(j, dy + r, dx + r, 0, k, k, T);
+                            for (int t = 0; t < T; ++t) out[t] += bv * Kp[t];
+                        }
+                    }
+                }
+            }
+    free(b);
+}
+
+/* ---------------------------------------------------------------------------
+ * Adjoint, c = S^T W_tot^T y.  The transpose of the correlation above:
+ *   g[n][y][x][j] = sum_{dy,dx} sum_t y[n][y-dy][x-dx][t] K[j][dy][dx][t]
+ * then c[p][y][x][j] = sum_n S[n][p][j] g[n][y][x][j].
+ * ------------------------------------------------------------------------- */
+void oracle_adjoint(int N, int P, int Y, int X, int Z, int T, int k,
+                    const double* S, const double* K, const double* yv, double* c)
+{
+    const int r = k / 2;
+    double* g = (double*)malloc(sizeof(double) * (size_t)N * Y * X * Z);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int n = 0; n < N; ++n)
+        for (int yy = 0; yy < Y; ++yy)
+            for (int xx = 0; xx < X; ++xx)
+                for (int j = 0; j < Z; ++j) {
+                    double acc = 0.0;
+                    for (int dy = -r; dy <= r; ++dy) {
+                        int ty = yy - dy;
+                        if (ty < 0 || ty >= Y) continue;
+                        for (int dx = -r; dx <= r; ++dx) {
+                            int tx = xx - dx;
+                            if (tx < 0 || tx >= X) continue;
+                            const double* yp = yv + IDX4(n, ty, tx, 0, Y, X, T);
+                            const double* Kp = K + IDX4(j, dy + r, dx + r, 0, k, k, T);
+                            for (int t = 0; t < T; ++t) acc += yp[t] * Kp[t];
+                        }
+                    }
+                    g[IDX4(n, yy, xx, j, Y, X, Z)] = acc;
+                }
+    for (int p = 0; p < P; ++p)
+        for (int yy = 0; yy < Y; ++yy)
+            for (int xx = 0; xx < X; ++xx)
+                for (int j = 0; j < Z; ++j) {
+                    double acc = 0.0;
+                    for (int n = 0; n < N; ++n)
+                        acc += S[IDX4(0, n, p, j, N, P, Z)] * g[IDX4(n, yy, xx, j, Y, X, Z)];
+                    c[IDX4(p, yy, xx, j, Y, X, Z)] = acc;
+                }
+    free(g);
+}
+
+/* Forward at selected outputs: for each (n, y, x) triple, the T samples
+ * y[n][y][x][:] of the forward above (same definition, evaluated alone). */
+void oracle_forward_at(int N, int P, int Y, int X, int Z, int T, int k,
+                       const double* S, const double* K, const double* c,
+                       int count, const int* nyx, double* out)
+{
+    const int r = k / 2;
+    (void)N;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < count; ++i) {
+        int n = nyx[3 * i], yy = nyx[3 * i + 1], xx = nyx[3 * i + 2];
+        double* o = out + (size_t)i * T;
+        for (int t = 0; t < T; ++t) o[t] = 0.0;
+        for (int dy = -r; dy <= r; ++dy) {
+            int sy = yy + dy;
+            if (sy < 0 || sy >= Y) continue;
+            for (int dx = -r; dx <= r; ++dx) {
+                int sx = xx + dx;
+                if (sx < 0 || sx >= X) continue;
+                for (int j = 0; j < Z; ++j) {
+                    double bv = 0.0;
+                    for (int p = 0; p < P; ++p)
+                        bv += S[IDX4(0, n, p, j, N, P, Z)] * c[IDX4(p, sy, sx, j, Y, X, Z)];
+                    const double* Kp = K + IDX4(j, dy + r, dx + r, 0, k, k, T);
+                    for (int t = 0; t < T; ++t) o[t] += bv * Kp[t];
+                }
+            }
+        }
+    }
+}
+
+/* Adjoint at selected outputs: for each (p, y, x, j), c[p][y][x][j]. */
+void oracle_adjoint_at(int N, int P, int Y, int X, int Z, int T, int k,
+                       const double* S, const double* K, const double* yv,
+                       int count, const int* pyxj, double* out)
+{
+    const int r = k / 2;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < count; ++i) {
+        int p = pyxj[4 * i], yy = pyxj[4 * i + 1], xx = pyxj[4 * i + 2], j = pyxj[4 * i + 3];
+        double acc_c = 0.0;
+        for (int n = 0; n < N; ++n) {
+            double acc = 0.0;
+            for (int dy = -r; dy <= r; ++dy) {
+                int ty = yy - dy;
+                if (ty < 0 || ty >= Y) continue;
+                for (int dx = -r; dx <= r; ++dx) {
+                    int tx = xx - dx;
+                    if (tx < 0 || tx >= X) continue;
+                    const double* yp = yv + IDX4(n, ty, tx, 0, Y, X, T);
+                    const double* Kp = K + IDX4(j, dy + r, dx + r, 0, k, k, T);
+                    for (int t = 0; t < T; ++t) acc += yp[t] * Kp[t];
+                }
+            }
+            acc_c += S[IDX4(0, n, p, j, N, P, Z)] * acc;
+        }
+        out[i] = acc_c;
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Anisotropic TV (Sec. 2.4.1, extended to three axes): forward differences
+ * along y, x and z over interior edges only.  For one species volume
+ * v[Y][X][Z], the gradient g[3][Y][X][Z] has component a equal to
+ * v[i + e_a] - v[i] where i + e_a is inside the grid and 0 otherwise.
+ * ------------------------------------------------------------------------- */
+static void grad3(int Y, int X, int Z, const double* v, double* g)
+{
+    size_t L = (size_t)Y * X * Z;
+    for (int yy = 0; yy < Y; ++yy)
+        for (int xx = 0; xx < X; ++xx)
+            for (int j = 0; j < Z; ++j) {
+                size_t i = IDX4(0, yy, xx, j, Y, X, Z);
+                g[0 * L + i] = (yy + 1 < Y) ? v[IDX4(0, yy + 1, xx, j, Y, X, Z)] - v[i] : 0.0;
+                g[1 * L + i] = (xx + 1 < X) ? v[IDX4(0, yy, xx + 1, j, Y, X, Z)] - v[i] : 0.0;
+                g[2 * L + i] = (j + 1 < Z) ? v[IDX4(0, yy, xx, j + 1, Y, X, Z)] - v[i] : 0.0;
+            }
+}
+
+/* The transpose of grad3: (D^T g)[i] = sum_a (g_a[i - e_a] - g_a[i]) with the
+ * terms that involve edges outside the grid removed. */
+static void grad3T(int Y, int X, int Z, const double* g, double* v)
+{
+    size_t L = (size_t)Y * X * Z;
+    for (int yy = 0; yy < Y; ++yy)
+        for (int xx = 0; xx < X; ++xx)
+            for (int j = 0; j < Z; ++j) {
+                size_t i = IDX4(0, yy, xx, j, Y, X, Z);
+                double acc = 0.0;
+                if (yy + 1 < Y) acc -= g[0 * L + i];
+                if (yy > 0) acc += g[0 * L + IDX4(0, yy - 1, xx, j, Y, X, Z)];
+                if (xx + 1 < X) acc -= g[1 * L + i];
+                if (xx > 0) acc += g[1 * L + IDX4(0, yy, xx - 1, j, Y, X, Z)];
+                if (j + 1 < Z) acc -= g[2 * L + i];
+                if (j > 0) acc += g[2 * L + IDX4(0, yy, xx, j - 1, Y, X, Z)];
+                v[i] = acc;
+            }
+}
+
+void oracle_grad3(int Y, int X, int Z, const double* v, double* g) { grad3(Y, X, Z, v, g); }
+void oracle_grad3T(int Y, int X, int Z, const double* g, double* v) { grad3T(Y, X, Z, g, v); }
+
+double oracle_tv(int P, int Y, int X, int Z, const double* c)
+{
+    size_t L = (size_t)Y * X * Z;
+    double* g = (double*)malloc(sizeof(double) * 3 * L);
+    double s = 0.0;
+    for (int p = 0; p < P; ++p) {
+        grad3(Y, X, Z, c + p * L, g);
+        for (size_t i = 0; i < 3 * L; ++i) s += fabs(g[i]);
+    }
+    free(g);
+    return s;
+}
+
+/* l1 prox (closed form): sign(x) max(|x| - theta, 0); with the nonnegativity
+ * constraint of Eq. (one-step) it becomes max(x - theta, 0). */
+void oracle_prox_l1(size_t count, double* x, double theta, int nonneg)
+{
+    for (size_t i = 0; i < count; ++i) {
+        double v = x[i];
+        if (nonneg) x[i] = (v - theta > 0.0) ? v - theta : 0.0;
+        else x[i] = (v > theta) ? v - theta : ((v < -theta) ? v + theta : 0.0);
+    }
+}
+
+/* Momentum modes of Algorithms 1 and 2. */
+enum { MOM_BECK_TEBOULLE = 0, MOM_PAPER_PRINTED = 1, MOM_NONE = 2 };
+
+static double next_t(double t) { return 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t)); }
+
+static double momentum_coef(int mode, double t_k, double t_k1)
+{
+    if (mode == MOM_BECK_TEBOULLE) return (t_k - 1.0) / t_k1;
+    if (mode == MOM_PAPER_PRINTED) return (t_k - 1.0) / (t_k + 1.0);
+    return 0.0;
+}
+
+/* ---------------------------------------------------------------------------
+ * TV prox by Algorithm 2 with L = D (the 3D forward differences) applied per
+ * species: the dual u lives in the box |u| <= tau (tau = alpha * lambda_TV),
+ * the dual step is 1/12 (an upper bound of eig_max(D D^T) in 3D), the dual
+ * iterate starts at zero and the primal is recovered as z - D^T u.
+ *   for i = 1..iters:
+ *     x   = z - D^T r
+ *     u_i = clamp(r + (1/12) D x, -tau, tau)
+ *     t_{i+1} = (1 + sqrt(1 + 4 t_i^2)) / 2
+ *     r   = u_i + beta_i (u_i - u_{i-1})
+ *   x = z - D^T u_iters
+ * ------------------------------------------------------------------------- */
+void oracle_prox_tv(int P, int Y, int X, int Z, const double* z, double* x,
+                    double tau, int iters, int momentum)
+{
+    size_t L = (size_t)Y * X * Z;
+    double* u = (double*)calloc(3 * L, sizeof(double));
+    double* u_prev = (double*)calloc(3 * L, sizeof(double));
+    double* rr = (double*)calloc(3 * L, sizeof(double));
+    double* g = (double*)malloc(sizeof(double) * 3 * L);
+    double* xv = (double*)malloc(sizeof(double) * L);
+    double* dt = (double*)malloc(sizeof(double) * L);
+    for (int p = 0; p < P; ++p) {
+        const double* zp = z + p * L;
+        memset(u, 0, sizeof(double) * 3 * L);
+        memset(u_prev, 0, sizeof(double) * 3 * L);
+        memset(rr, 0, sizeof(double) * 3 * L);
+        double t = 1.0;
+        for (int it = 0; it < iters; ++it) {
+            grad3T(Y, X, Z, rr, dt);
+            for (size_t i = 0; i < L; ++i) xv[i] = zp[i] - dt[i];
+            grad3(Y, X, Z, xv, g);
+            for (size_t i = 0; i < 3 * L; ++i) {
+                double v = rr[i] + g[i] / 12.0;
+                u[i] = v > tau ? tau : (v < -tau ? -tau : v);
+            }
+            double t1 = next_t(t);
+            double beta = momentum_coef(momentum, t, t1);
+            for (size_t i = 0; i < 3 * L; ++i) {
+                rr[i] = u[i] + beta * (u[i] - u_prev[i]);
+                u_prev[i] = u[i];
+            }
+            t = t1;
+        }
+        grad3T(Y, X, Z, u, dt);
+        for (size_t i = 0; i < L; ++i) x[p * L + i] = zp[i] - dt[i];
+    }
+    free(u); free(u_prev); free(rr); free(g); free(xv); free(dt);
+}
+
+/* Full proximal map of w = lambda_TV TV + lambda_l1 ||.||_1 + indicator(>= 0)
+ * at step alpha: max(prox_TV(z) - alpha lambda_l1, 0). */
+void oracle_prox(int P, int Y, int X, int Z, const double* z, double* x,
+                 double alpha, double lam_l1, double lam_tv, int inner, int momentum)
+{
+    size_t n = (size_t)P * Y * X * Z;
+    if (lam_tv > 0.0 && inner > 0) {
+        oracle_prox_tv(P, Y, X, Z, z, x, alpha * lam_tv, inner, momentum);
+    } else {
+        memcpy(x, z, sizeof(double) * n);
+    }
+    oracle_prox_l1(n, x, alpha * lam_l1, 1);
+}
+
+/* F(c) = 1/2 ||Hc - y||^2 + lambda_TV sum_p TV(c_p) + lambda_l1 ||c||_1 for c >= 0
+ * (Eq. one-step with Eq. reg-tv-l1-one, lambda_3 = 0).  Returns also the
+ * data-fit term in *fit. */
+double oracle_objective(int N, int P, int Y, int X, int Z, int T, int k,
+                        const double* S, const double* K, const double* c,
+                        const double* yv, double lam_l1, double lam_tv, double* fit)
+{
+    size_t ny = (size_t)N * Y * X * T, nc = (size_t)P * Y * X * Z;
+    double* hc = (double*)malloc(sizeof(double) * ny);
+    oracle_forward(N, P, Y, X, Z, T, k, S, K, c, hc);
+    double f = 0.0;
+    for (size_t i = 0; i < ny; ++i) { double d = hc[i] - yv[i]; f += d * d; }
+    f *= 0.5;
+    double l1 = 0.0;
+    for (size_t i = 0; i < nc; ++i) l1 += fabs(c[i]);
+    double reg = lam_l1 * l1 + (lam_tv > 0.0 ? lam_tv * oracle_tv(P, Y, X, Z, c) : 0.0);
+    free(hc);
+    if (fit) *fit = f;
+    return f + reg;
+}
+
+/* ---------------------------------------------------------------------------
+ * Algorithm 1 (FISTA) with a fixed iteration count and a given step alpha:
+ *   c_0 = xi_0 = 0, t_0 = 1
+ *   for k = 0..iters-1:
+ *     c_{k+1} = prox(xi_k - alpha H^T (H xi_k - y))
+ *     t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
+ *     xi_{k+1} = c_{k+1} + beta_k (c_{k+1} - c_k)
+ * history (optional, length iters) receives F(c_{k+1}).
+ * ------------------------------------------------------------------------- */
+void oracle_fista(int N, int P, int Y, int X, int Z, int T, int k,
+                  const double* S, const double* K, const double* yv,
+                  double alpha, int iters, double lam_l1, double lam_tv,
+                  int inner, int momentum, int inner_momentum,
+                  double* c_out, double* history)
+{
+    size_t ny = (size_t)N * Y * X * T, nc = (size_t)P * Y * X * Z;
+    double* c = (double*)calloc(nc, sizeof(double));
+    double* c_new = (double*)malloc(sizeof(double) * nc);
+    double* xi = (double*)calloc(nc, sizeof(double));
+    double* zin = (double*)malloc(sizeof(double) * nc);
+    double* grad = (double*)malloc(sizeof(double) * nc);
+    double* res = (double*)malloc(sizeof(double) * ny);
+    double t = 1.0;
+    for (int it = 0; it < iters; ++it) {
+        oracle_forward(N, P, Y, X, Z, T, k, S, K, xi, res);
+        for (size_t i = 0; i < ny; ++i) res[i] -= yv[i];
+        oracle_adjoint(N, P, Y, X, Z, T, k, S, K, res, grad);
+        for (size_t i = 0; i < nc; ++i) zin[i] = xi[i] - alpha * grad[i];
+        if (lam_tv > 0.0 && inner > 0)
+            oracle_prox_tv(P, Y, X, Z, zin, c_new, alpha * lam_tv, inner, inner_momentum);
+        else
+            memcpy(c_new, zin, sizeof(double) * nc);
+        oracle_prox_l1(nc, c_new, alpha * lam_l1, 1);
+        double t1 = next_t(t);
+        double beta = momentum_coef(momentum, t, t1);
+        for (size_t i = 0; i < nc; ++i) {
+            xi[i] = c_new[i] + beta * (c_new[i] - c[i]);
+            c[i] = c_new[i];
+        }
+        t = t1;
+        if (history)
+            history[it] = oracle_objective(N, P, Y, X, Z, T, k, S, K, c, yv, lam_l1, lam_tv, NULL);
+    }
+    memcpy(c_out, c, sizeof(double) * nc);
+    free(c); free(c_new); free(xi); free(zin); free(grad); free(res);
+}
+
+/* Power iteration for eig_max(H^T H): v <- H^T H v / ||H^T H v|| from the
+ * given start vector; returns the Rayleigh quotient v^T H^T H v / v^T v. */
+double oracle_power(int N, int P, int Y, int X, int Z, int T, int k,
+                    const double* S, const double* K, const double* v0, int iters)
+{
+    size_t ny = (size_t)N * Y * X * T, nc = (size_t)P * Y * X * Z;
+    double* v = (double*)malloc(sizeof(double) * nc);
+    double* w = (double*)malloc(sizeof(double) * nc);
+    double* hv = (double*)malloc(sizeof(double) * ny);
+    double nrm = 0.0;
+    for (size_t i = 0; i < nc; ++i) nrm += v0[i] * v0[i];
+    nrm = sqrt(nrm);
+    for (size_t i = 0; i < nc; ++i) v[i] = v0[i] / nrm;
+    double rq = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        oracle_forward(N, P, Y, X, Z, T, k, S, K, v, hv);
+        oracle_adjoint(N, P, Y, X, Z, T, k, S, K, hv, w);
+        double vw = 0.0, ww = 0.0;
+        for (size_t i = 0; i < nc; ++i) { vw += v[i] * w[i]; ww += w[i] * w[i]; }
+        rq = vw; /* v has unit norm */
+        ww = sqrt(ww);
+        for (size_t i = 0; i < nc; ++i) v[i] = w[i] / ww;
+    }
+    free(v); free(w); free(hv);
+    return rq;
+}
+
+/* ---------------------------------------------------------------------------
+ * Gradient of f = 1/2 ||H c - y||^2 with respect to the kinetic constants
+ * kappa_p and the fluence decay mu, with c held fixed.  Writing
+ * b = S c and g = W_tot^T (H c - y):
+ *   df/dtheta = sum_{n,y,x,j} g[n][y][x][j] * sum_p dS[n][p][j]/dtheta c[p][y][x][j]
+ * where, from Eq. (final-H) with Phi_j = exp(-mu j dz) and e = exp(-kappa_p Phi_j m):
+ *   dS/dkappa_p = Phi_j * eps_bar_p * e * (-Phi_j m)
+ *   dS/dPhi     = eps_bar_p e + eps_off_p + Phi_j eps_bar_p e (-kappa_p m)
+ *   dS/dmu      = dS/dPhi * (-j dz Phi_j)
+ * ------------------------------------------------------------------------- */
+void oracle_param_grad(int N, int P, int Y, int X, int Z, int T, int k,
+                       int pulses_per_cycle, double mu_per_mm, double dz_mm,
+                       const double* kappa, const double* eps_bar, const double* eps_off,
+                       const double* K, const double* c, const double* yv,
+                       double* dkappa, double* dmu)
+{
+    const int r = k / 2;
+    size_t ny = (size_t)N * Y * X * T;
+    double* phi = (double*)malloc(sizeof(double) * Z);
+    double* S = (double*)malloc(sizeof(double) * (size_t)N * P * Z);
+    double* res = (double*)malloc(sizeof(double) * ny);
+    double* g = (double*)malloc(sizeof(double) * (size_t)N * Y * X * Z);
+    oracle_fluence(Z, mu_per_mm, dz_mm, phi);
+    oracle_switch_matrix(N, P, Z, pulses_per_cycle, phi, kappa, eps_bar, eps_off, S);
+    oracle_forward(N, P, Y, X, Z, T, k, S, K, c, res);
+    for (size_t i = 0; i < ny; ++i) res[i] -= yv[i];
+    /* g = W_tot^T res (acoustic adjoint only) */
+    for (int n = 0; n < N; ++n)
+        for (int yy = 0; yy < Y; ++yy)
+            for (int xx = 0; xx < X; ++xx)
+                for (int j = 0; j < Z; ++j) {
+                    double acc = 0.0;
+                    for (int dy = -r; dy <= r; ++dy) {
+                        int ty = yy - dy;
+                        if (ty < 0 || ty >= Y) continue;
+                        for (int dx = -r; dx <= r; ++dx) {
+                            int tx = xx - dx;
+                            if (tx < 0 || tx >= X) continue;
+                            const double* yp = res + IDX4(n, ty, tx, 0, Y, X, T);
+                            const double* Kp = K + IDX4(j, dy + r, dx + r, 0, k, k, T);
+                            for (int t = 0; t < T; ++t) acc += yp[t] * Kp[t];
+                        }
+                    }
+                    g[IDX4(n, yy, xx, j, Y, X, Z)] = acc;
+                }
+    for (int p = 0; p < P; ++p) dkappa[p] = 0.0;
+    *dmu = 0.0;
+    for (int n = 0; n < N; ++n) {
+        double m = (double)(n % pulses_per_cycle);
+        for (int j = 0; j < Z; ++j) {
+            double ph = phi[j];
+            double dphi_dmu = -(double)j * dz_mm * ph;
+            for (int p = 0; p < P; ++p) {
+                double e = exp(-kappa[p] * ph * m);
+                double dS_dk = ph * eps_bar[p] * e * (-ph * m);
+                double dS_dphi = eps_bar[p] * e + eps_off[p] + ph * eps_bar[p] * e * (-kappa[p] * m);
+                double dS_dmu = dS_dphi * dphi_dmu;
+                double acc = 0.0;
+                for (int yy = 0; yy < Y; ++yy)
+                    for (int xx = 0; xx < X; ++xx)
+                        acc += g[IDX4(n, yy, xx, j, Y, X, Z)] * c[IDX4(p, yy, xx, j, Y, X, Z)];
+                dkappa[p] += dS_dk * acc;
+                *dmu += dS_dmu * acc;
+            }
+        }
+    }
+    free(phi); free(S); free(res); free(g);
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,460 @@
+"""Pins of the FP64 oracle to things other than itself.
+
+Each test ties one oracle function to an independent fact: a library
+routine (torch conv2d / conv_transpose2d, numpy eigvalsh, scipy's L-BFGS-B
+on the exact convex problem), a mathematical identity (the adjoint
+identity, optimality conditions), a closed form or a finite difference.
+Chosen so that a dropped term, a wrong sign, a swapped index or a
+transposed operand in the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.optimize
+import torch
+
+import oracle
+import synth
+from synth import Geometry, Switching
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+
+def _geom(**kw):
+    base = dict(X=7, Y=6, Z=5, T=12, N=4, P=2, k=3, pulses_per_cycle=3)
+    base.update(kw)
+    return Geometry(**base)
+
+
+def _sw(P, kappa=None, mu=2.0):
+    kap = list(kappa) if kappa is not None else [0.3 * (p + 1) for p in range(P - 1)] + [0.0]
+    eb = [1.0] * (P - 1) + [0.0]
+    eo = [0.05] * (P - 1) + [1.0]
+    return Switching(kappa=tuple(kap), eps_bar=tuple(eb), eps_off=tuple(eo), mu_per_mm=mu)
+
+
+def _rand_kernel(g, seed):
+    # an asymmetric random kernel: catches dy/dx/t index swaps
+    return np.random.default_rng(seed).standard_normal(g.k_shape())
+
+
+def _dense_H(g, sw, K):
+    nc = int(np.prod(g.c_shape()))
+    cols = []
+    for i in range(nc):
+        e = np.zeros(nc)
+        e[i] = 1.0
+        cols.append(oracle.forward(g, sw, K, e.reshape(g.c_shape())).ravel())
+    return np.stack(cols, axis=1)
+
+
+# --------------------------------------------------------------------------
+# Forward / adjoint (Sec. 2.3.3, Eq. acoustic-full-forward, Eq. full-forward)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [1, 3, 5])
+def test_forward_is_conv2d_for_one_pulse_background(k):
+    """N=1, P=1 background, Phi=1: H is torch's conv2d (cross-correlation)
+    with C_in = Z depths, C_out = T samples, a k x k filter and zero padding."""
+    g = _geom(N=1, P=1, k=k, X=9, Y=8, Z=4, T=10, pulses_per_cycle=1)
+    sw = Switching(kappa=(0.0,), eps_bar=(0.0,), eps_off=(1.0,), mu_per_mm=0.0)
+    K = _rand_kernel(g, 1)
+    c = np.random.default_rng(2).standard_normal(g.c_shape())
+    y = oracle.forward(g, sw, K, c)
+    w = torch.from_numpy(K).permute(3, 0, 1, 2).contiguous()  # [T][Z][ky][kx]
+    inp = torch.from_numpy(c[0]).permute(2, 0, 1)[None]       # [1][Z][Y][X]
+    ref = torch.nn.functional.conv2d(inp, w, padding=k // 2)[0].permute(1, 2, 0).numpy()
+    np.testing.assert_allclose(y[0], ref, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("k", [1, 3, 5])
+def test_adjoint_is_conv_transpose2d_for_one_pulse_background(k):
+    g = _geom(N=1, P=1, k=k, X=9, Y=8, Z=4, T=10, pulses_per_cycle=1)
+    sw = Switching(kappa=(0.0,), eps_bar=(0.0,), eps_off=(1.0,), mu_per_mm=0.0)
+    K = _rand_kernel(g, 3)
+    yv = np.random.default_rng(4).standard_normal(g.y_shape())
+    c = oracle.adjoint(g, sw, K, yv)
+    w = torch.from_numpy(K).permute(3, 0, 1, 2).contiguous()
+    inp = torch.from_numpy(yv[0]).permute(2, 0, 1)[None]      # [1][T][Y][X]
+    ref = torch.nn.functional.conv_transpose2d(inp, w, padding=k // 2)[0].permute(1, 2, 0).numpy()
+    np.testing.assert_allclose(c[0], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_adjoint_identity_random_pairs():
+    """<Hx, y> = <x, H^T y> for 100 seeded N(0,1) pairs (full switching)."""
+    g = _geom()
+    sw = _sw(g.P)
+    K = _rand_kernel(g, 5)
+    rng = np.random.default_rng(6)
+    worst = 0.0
+    for _ in range(100):
+        x = rng.standard_normal(g.c_shape())
+        yv = rng.standard_normal(g.y_shape())
+        hx = oracle.forward(g, sw, K, x)
+        lhs = float(np.vdot(hx, yv))
+        rhs = float(np.vdot(x, oracle.adjoint(g, sw, K, yv)))
+        # scale: the Cauchy-Schwarz bound of either side
+        worst = max(worst, abs(lhs - rhs) / (np.linalg.norm(hx) * np.linalg.norm(yv)))
+    assert worst < 1e-13
+
+
+def test_adjoint_identity_tiny_workload_kernel():
+    prob = synth.workload("tiny_16x16x24_T64_k7_N8_P2")
+    g = prob.geom
+    K = synth.transducer_kernel(g)
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        x = rng.standard_normal(g.c_shape())
+        yv = rng.standard_normal(g.y_shape())
+        lhs = float(np.vdot(oracle.forward(g, prob.sw, K, x), yv))
+        rhs = float(np.vdot(x, oracle.adjoint(g, prob.sw, K, yv)))
+        assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_dense_adjoint_is_transpose():
+    g = _geom(X=4, Y=3, Z=3, T=6, N=3, P=2, k=3)
+    sw = _sw(g.P)
+    K = _rand_kernel(g, 8)
+    H = _dense_H(g, sw, K)
+    ny = int(np.prod(g.y_shape()))
+    rows = []
+    for i in range(ny):
+        e = np.zeros(ny)
+        e[i] = 1.0
+        rows.append(oracle.adjoint(g, sw, K, e.reshape(g.y_shape())).ravel())
+    HT = np.stack(rows, axis=1)
+    np.testing.assert_allclose(HT, H.T, rtol=0, atol=1e-13)
+
+
+def test_point_absorber_reproduces_kernel_background():
+    """A unit background absorber at (y0, x0, j) gives
+    y[n, y0-dy, x0-dx, t] = Phi_j K[j, dy, dx, t] for every pulse, and zero
+    elsewhere: pins the correlation sign and the fluence prefactor."""
+    g = _geom(X=9, Y=9, Z=4, T=8, N=5, P=2, k=5, pulses_per_cycle=5)
+    sw = _sw(g.P, mu=3.0)
+    K = _rand_kernel(g, 9)
+    y0, x0, j = 4, 3, 2
+    c = np.zeros(g.c_shape())
+    c[g.P - 1, y0, x0, j] = 1.0
+    y = oracle.forward(g, sw, K, c)
+    phi_j = math.exp(-sw.mu_per_mm * j * g.dz_mm)
+    expect = np.zeros(g.y_shape())
+    r = g.r
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            expect[:, y0 - dy, x0 - dx, :] = phi_j * K[j, dy + r, dx + r, :]
+    np.testing.assert_allclose(y, expect, rtol=0, atol=1e-14)
+
+
+def test_point_absorber_switching_decay():
+    """A switchable absorber decays geometrically within each cycle by the
+    factor exp(-kappa Phi_j) per pulse and restarts at each new cycle."""
+    g = _geom(X=5, Y=5, Z=6, T=8, N=9, P=2, k=3, pulses_per_cycle=3)
+    sw = Switching(kappa=(0.4, 0.0), eps_bar=(1.0, 0.0), eps_off=(0.0, 1.0), mu_per_mm=5.0)
+    K = np.abs(_rand_kernel(g, 10)) + 0.1
+    for j in (0, 3, 5):
+        c = np.zeros(g.c_shape())
+        c[0, 2, 2, j] = 1.0
+        y = oracle.forward(g, sw, K, c)[:, 2, 2, :]
+        phi = math.exp(-sw.mu_per_mm * j * g.dz_mm)
+        for n in range(g.N - 1):
+            ratio = y[n + 1] / y[n]
+            if (n + 1) % g.pulses_per_cycle == 0:
+                np.testing.assert_allclose(y[n + 1], y[n + 1 - g.pulses_per_cycle], rtol=1e-13)
+            else:
+                np.testing.assert_allclose(ratio, math.exp(-0.4 * phi), rtol=1e-12)
+    # background: constant over pulses, decays with depth by exp(-mu dz) per layer
+    ys = []
+    for j in range(g.Z):
+        c = np.zeros(g.c_shape())
+        c[1, 2, 2, j] = 1.0
+        y = oracle.forward(g, sw, K, c)[:, 2, 2, :]
+        np.testing.assert_allclose(y, np.broadcast_to(y[0], y.shape), rtol=1e-14)
+        ys.append(y[0] / K[j, 1, 1, :])
+    for j in range(g.Z - 1):
+        np.testing.assert_allclose(ys[j + 1] / ys[j], math.exp(-sw.mu_per_mm * g.dz_mm), rtol=1e-12)
+
+
+def test_linearity_and_shift_invariance():
+    g = _geom(X=10, Y=10, Z=3, T=6, N=3, P=2, k=3)
+    sw = _sw(g.P)
+    K = _rand_kernel(g, 11)
+    rng = np.random.default_rng(12)
+    a, b = 0.7, -1.3
+    x1 = rng.standard_normal(g.c_shape())
+    x2 = rng.standard_normal(g.c_shape())
+    lhs = oracle.forward(g, sw, K, a * x1 + b * x2)
+    rhs = a * oracle.forward(g, sw, K, x1) + b * oracle.forward(g, sw, K, x2)
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-12, atol=1e-12)
+    c = np.zeros(g.c_shape())
+    c[0, 4, 4, 1] = 1.0
+    c2 = np.zeros(g.c_shape())
+    c2[0, 5, 3, 1] = 1.0
+    y1 = oracle.forward(g, sw, K, c)
+    y2 = oracle.forward(g, sw, K, c2)
+    np.testing.assert_allclose(y2[:, 2:9, 0:7], y1[:, 1:8, 1:8], atol=1e-15)
+
+
+def test_sampled_forward_and_adjoint_match_full():
+    g = _geom(X=8, Y=7, Z=4, T=9, N=5, P=3, k=5, pulses_per_cycle=2)
+    sw = _sw(g.P)
+    K = _rand_kernel(g, 13)
+    rng = np.random.default_rng(14)
+    c = rng.standard_normal(g.c_shape())
+    yv = rng.standard_normal(g.y_shape())
+    y = oracle.forward(g, sw, K, c)
+    idx = np.array([[n, yy, xx] for n in range(g.N) for yy in (0, 3, 6) for xx in (0, 7)])
+    np.testing.assert_allclose(oracle.forward_at(g, sw, K, c, idx), y[idx[:, 0], idx[:, 1], idx[:, 2]],
+                               rtol=1e-13, atol=1e-13)
+    a = oracle.adjoint(g, sw, K, yv)
+    idx4 = np.array([[p, yy, xx, j] for p in range(g.P) for yy in (0, 6) for xx in (1, 7) for j in (0, 3)])
+    np.testing.assert_allclose(oracle.adjoint_at(g, sw, K, yv, idx4),
+                               a[idx4[:, 0], idx4[:, 1], idx4[:, 2], idx4[:, 3]], rtol=1e-13, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# TV, proximal maps (Eq. prox, Eq. prox-dual, Algorithm 2)
+# --------------------------------------------------------------------------
+
+def test_grad3_transpose_and_ramp():
+    rng = np.random.default_rng(15)
+    v = rng.standard_normal((4, 5, 6))
+    gg = rng.standard_normal((3, 4, 5, 6))
+    assert abs(np.vdot(oracle.grad3(v), gg) - np.vdot(v, oracle.grad3T(gg))) < 1e-12
+    yy, xx, zz = np.meshgrid(np.arange(4), np.arange(5), np.arange(6), indexing="ij")
+    ramp = 2.0 * yy - 3.0 * xx + 0.5 * zz
+    d = oracle.grad3(ramp)
+    assert np.allclose(d[0, :-1], 2.0) and np.allclose(d[0, -1], 0.0)
+    assert np.allclose(d[1, :, :-1], -3.0) and np.allclose(d[1, :, -1], 0.0)
+    assert np.allclose(d[2, :, :, :-1], 0.5) and np.allclose(d[2, :, :, -1], 0.0)
+
+
+def test_tv_of_step_is_jump_times_interface():
+    c = np.zeros((1, 4, 6, 5))
+    c[0, :, 3:, :] = 2.5
+    assert oracle.tv(c) == pytest.approx(2.5 * 4 * 5, rel=1e-15)
+
+
+def test_l1_prox_closed_form_against_scalar_minimiser():
+    rng = np.random.default_rng(16)
+    z = rng.standard_normal(40) * 2
+    theta = 0.7
+    for nonneg in (True, False):
+        x = oracle.prox_l1(z, theta, nonneg)
+        for zi, xi in zip(z, x):
+            lo = 0.0 if nonneg else -10.0
+            res = scipy.optimize.minimize_scalar(lambda t: 0.5 * (t - zi) ** 2 + theta * abs(t),
+                                                 bounds=(lo, 10.0), method="bounded",
+                                                 options={"xatol": 1e-12})
+            assert abs(res.x - xi) < 1e-6
+
+
+def _dual_tv_exact(z, tau, theta=None):
+    """Exact prox via the dual, solved by scipy's L-BFGS-B with box bounds.
+
+    TV only:         min_{|u|<=tau} 1/2 ||z - D^T u||^2,        x = z - D^T u
+    TV + l1 + (>=0): min_{|u|<=tau} 1/2 ||max(z - theta - D^T u, 0)||^2,
+                                                                  x = max(z - theta - D^T u, 0)
+    D is assembled here as an explicit sparse difference matrix.
+    """
+    import scipy.sparse as sp
+    Y, X, Z = z.shape
+    L = Y * X * Z
+    idx = np.arange(L).reshape(Y, X, Z)
+    rows, cols, vals = [], [], []
+    e = 0
+    blocks = []
+    for axis in range(3):
+        a = np.moveaxis(idx, axis, 0)
+        lo = a[:-1].ravel()
+        hi = a[1:].ravel()
+        m = lo.size
+        blocks.append((lo, hi, m))
+    # one dual entry per (axis, voxel); unused entries (last along the axis) have a zero row
+    D = sp.lil_matrix((3 * L, L))
+    for axis in range(3):
+        a = np.moveaxis(idx, axis, 0)
+        lo = a[:-1].ravel()
+        hi = a[1:].ravel()
+        for l_, h_ in zip(lo, hi):
+            D[axis * L + l_, h_] = 1.0
+            D[axis * L + l_, l_] = -1.0
+    D = D.tocsr()
+    zf = z.ravel()
+
+    if theta is None:
+        def fun(u):
+            w = zf - D.T @ u
+            return 0.5 * w @ w, -(D @ w)
+    else:
+        def fun(u):
+            w = np.maximum(zf - theta - D.T @ u, 0.0)
+            return 0.5 * w @ w, -(D @ w)
+    res = scipy.optimize.minimize(fun, np.zeros(3 * L), jac=True, method="L-BFGS-B",
+                                  bounds=[(-tau, tau)] * (3 * L),
+                                  options={"maxiter": 20000, "ftol": 1e-16, "gtol": 1e-13,
+                                           "maxcor": 50})
+    u = res.x
+    if theta is None:
+        return (zf - D.T @ u).reshape(z.shape)
+    return np.maximum(zf - theta - D.T @ u, 0.0).reshape(z.shape)
+
+
+def test_tv_prox_3d_matches_exact_dual_solution():
+    rng = np.random.default_rng(17)
+    z = rng.standard_normal((3, 4, 5))
+    tau = 0.3
+    exact = _dual_tv_exact(z, tau)
+    fgp = oracle.prox_tv(z[None], tau, 4000)[0]
+    np.testing.assert_allclose(fgp, exact, atol=2e-6)
+
+
+def test_tv_prox_1d_optimality_conditions():
+    """1D lines: x = prox_TV(z) iff z - x = tau D^T u with |u| <= 1 and
+    u_i = sign(x_{i+1} - x_i) wherever the jump is nonzero."""
+    rng = np.random.default_rng(18)
+    for trial in range(4):
+        Z = 14
+        z = np.cumsum(rng.standard_normal(Z)) + rng.standard_normal(Z)
+        tau = 0.4 + 0.3 * trial
+        x = oracle.prox_tv(z.reshape(1, 1, 1, Z), tau, 30000)[0, 0, 0]
+        w = (z - x) / tau
+        assert abs(w.sum()) < 1e-8
+        u = -np.cumsum(w)[:-1]  # (D^T u)_i = u_{i-1} - u_i
+        assert np.all(np.abs(u) <= 1 + 1e-6)
+        jump = np.diff(x)
+        big = np.abs(jump) > 1e-5
+        np.testing.assert_allclose(u[big], np.sign(jump[big]), atol=1e-5)
+
+
+def test_tv_prox_special_cases():
+    rng = np.random.default_rng(19)
+    z = rng.standard_normal((2, 3, 4, 5))
+    np.testing.assert_array_equal(oracle.prox_tv(z, 0.0, 10), z)  # tau = 0: identity
+    const = np.full((1, 3, 4, 5), 1.7)
+    np.testing.assert_array_equal(oracle.prox_tv(const, 0.5, 10), const)  # constant in, constant out
+    big = oracle.prox_tv(z, 1e3, 6000)  # large tau: the per-species mean
+    for p in range(2):
+        np.testing.assert_allclose(big[p], z[p].mean(), atol=1e-6)
+
+
+def test_composite_prox_equals_joint_prox():
+    """max(prox_TV(z) - theta, 0) is the exact prox of TV + l1 + indicator(>= 0)
+    (the joint dual of Eq. prox-dual solved to optimality)."""
+    rng = np.random.default_rng(20)
+    for trial in range(3):
+        z = rng.standard_normal((3, 3, 4)) + 0.3
+        tau, theta = 0.25 + 0.1 * trial, 0.2
+        joint = _dual_tv_exact(z, tau, theta)
+        comp = oracle.prox(z[None], 1.0, theta, tau, 4000)[0]
+        np.testing.assert_allclose(comp, joint, atol=2e-6)
+
+
+# --------------------------------------------------------------------------
+# FISTA (Algorithm 1), power iteration, objective, parameter gradient
+# --------------------------------------------------------------------------
+
+def _small_problem(seed=21):
+    """A small, reasonably conditioned problem (condition number ~1e3): a
+    dominant on-axis tap at a distinct time per depth plus a random blur."""
+    g = _geom(X=5, Y=4, Z=4, T=10, N=4, P=2, k=3, pulses_per_cycle=4)
+    sw = Switching(kappa=(1.5, 0.0), eps_bar=(1.0, 0.0), eps_off=(0.0, 1.0), mu_per_mm=2.0)
+    rng = np.random.default_rng(seed)
+    K = 0.2 * np.abs(rng.standard_normal(g.k_shape()))
+    for j in range(g.Z):
+        K[j, 1, 1, 2 * j] += 1.0
+    c_true = np.maximum(rng.standard_normal(g.c_shape()), 0)
+    y = oracle.forward(g, sw, K, c_true) + 0.05 * rng.standard_normal(g.y_shape())
+    return g, sw, K, y
+
+
+def test_power_iteration_matches_dense_eigenvalue():
+    g, sw, K, _ = _small_problem()
+    H = _dense_H(g, sw, K)
+    lam = np.linalg.eigvalsh(H.T @ H)[-1]
+    v0 = synth.gaussian(g.c_shape(), 3)
+    L = oracle.power(g, sw, K, v0, 3000)
+    assert abs(L - lam) <= 1e-10 * lam
+
+
+def test_objective_at_zero_and_components():
+    g, sw, K, y = _small_problem()
+    F, fit = oracle.objective(g, sw, K, np.zeros(g.c_shape()), y, 0.1, 0.2)
+    assert F == pytest.approx(0.5 * float(np.sum(y * y)), rel=1e-14)
+    c = np.zeros(g.c_shape())
+    c[1, :, 2:, :] = 1.5  # TV = 1.5 * Y * Z, l1 = 1.5 * count
+    F, fit = oracle.objective(g, sw, K, c, y, 0.1, 0.2)
+    hc = oracle.forward(g, sw, K, c)
+    exp_fit = 0.5 * float(np.sum((hc - y) ** 2))
+    assert fit == pytest.approx(exp_fit, rel=1e-13)
+    assert F - fit == pytest.approx(0.1 * 1.5 * c[1, :, 2:, :].size + 0.2 * 1.5 * g.Y * g.Z, rel=1e-13)
+
+
+def test_fista_reaches_bound_constrained_qp_optimum():
+    """lambda_TV = 0: min 1/2||Hc - y||^2 + lam sum(c), c >= 0 is a smooth
+    bound-constrained QP; L-BFGS-B on the explicit matrix gives its optimum."""
+    g, sw, K, y = _small_problem()
+    H = _dense_H(g, sw, K)
+    lam = 0.05
+    yf = y.ravel()
+
+    def fun(c):
+        r = H @ c - yf
+        return 0.5 * r @ r + lam * c.sum(), H.T @ r + lam
+
+    res = scipy.optimize.minimize(fun, np.zeros(H.shape[1]), jac=True, method="L-BFGS-B",
+                                  bounds=[(0, None)] * H.shape[1],
+                                  options={"maxiter": 50000, "ftol": 1e-16, "gtol": 1e-12})
+    Fstar = res.fun
+    L = np.linalg.eigvalsh(H.T @ H)[-1]
+    c = oracle.fista(g, sw, K, y, 1.0 / L, 3000, lam, 0.0, 0)
+    F, _ = oracle.objective(g, sw, K, c, y, lam, 0.0)
+    assert F - Fstar <= 1e-9 * abs(Fstar)
+    assert np.linalg.norm(c.ravel() - res.x) <= 1e-4 * np.linalg.norm(res.x)
+
+
+def test_ista_objective_is_monotone():
+    g, sw, K, y = _small_problem()
+    H = _dense_H(g, sw, K)
+    L = np.linalg.eigvalsh(H.T @ H)[-1]
+    _, hist = oracle.fista(g, sw, K, y, 1.0 / L, 60, 0.05, 0.0, 0, momentum="none", history=True)
+    assert np.all(np.diff(hist) <= 1e-12 * np.abs(hist[:-1]))
+    # with TV and a near-exact inner solve
+    _, hist = oracle.fista(g, sw, K, y, 1.0 / L, 25, 0.05, 0.05, 600, momentum="none", history=True)
+    assert np.all(np.diff(hist) <= 1e-7 * np.abs(hist[:-1]))
+
+
+def test_fista_momentum_modes_differ_and_first_step_is_prox_gradient():
+    g, sw, K, y = _small_problem()
+    alpha = 0.01
+    c1 = oracle.fista(g, sw, K, y, alpha, 1, 0.05, 0.02, 10)
+    # one step from zero: c_1 = prox(alpha H^T y)
+    z = alpha * oracle.adjoint(g, sw, K, y)
+    np.testing.assert_allclose(c1, oracle.prox(z, alpha, 0.05, 0.02, 10), atol=1e-15)
+    a = oracle.fista(g, sw, K, y, alpha, 5, 0.05, 0.02, 10, momentum="beck_teboulle")
+    b = oracle.fista(g, sw, K, y, alpha, 5, 0.05, 0.02, 10, momentum="paper_printed")
+    assert np.abs(a - b).max() > 0
+
+
+def test_param_grad_matches_central_differences():
+    g, sw, K, y = _small_problem(31)
+    c = np.maximum(np.random.default_rng(32).standard_normal(g.c_shape()), 0) + 0.1
+    dk, dmu = oracle.param_grad(g, sw, K, c, y)
+
+    def f(sw_):
+        _, fit = oracle.objective(g, sw_, K, c, y, 0.0, 0.0)
+        return fit
+
+    h = 1e-4
+    for p in range(g.P - 1):
+        kp = list(sw.kappa)
+        kp[p] += h
+        km = list(sw.kappa)
+        km[p] -= h
+        fd = (f(Switching(tuple(kp), sw.eps_bar, sw.eps_off, sw.mu_per_mm))
+              - f(Switching(tuple(km), sw.eps_bar, sw.eps_off, sw.mu_per_mm))) / (2 * h)
+        assert dk[p] == pytest.approx(fd, rel=1e-6)
+    fd = (f(Switching(sw.kappa, sw.eps_bar, sw.eps_off, sw.mu_per_mm + h))
+          - f(Switching(sw.kappa, sw.eps_bar, sw.eps_off, sw.mu_per_mm - h))) / (2 * h)
+    assert dmu == pytest.approx(fd, rel=1e-6)
