@@ -1,0 +1,400 @@
+"""Benchmark: FISTA iterations per second of the one-step reconstruction.
+
+One step = one FISTA iteration (Algorithm 1) of the whole hot path on the
+medium workload (64x64 scan, 64 depths, T=256, 15x15 lateral support,
+40 pulses in 4 cycles of 10, 2 species, 10 inner TV iterations): switching
+map P, acoustic forward A with the folded residual, adjoint A^T, P^T with
+the gradient step, the FGP TV prox, the l1/nonnegativity prox and the
+momentum update.  Inputs are synthetic and seeded (tube phantom, transducer
+kernel, 20 dB noise) and resident in HBM before the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl swopt|reference]
+For N > 1 it is launched by torch.distributed.run, one rank per GPU; each rank
+solves its own independent problem (replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOAD = "medium_64x64x64_T256_k15_N40_P2"
+METRIC = "FISTA iterations/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _smi_id(device) -> str:
+    """nvidia-smi --id for a torch device: its PCI bus id when torch exposes
+    it, else the physical index from CUDA_VISIBLE_DEVICES."""
+    import torch
+    props = torch.cuda.get_device_properties(device)
+    dom = getattr(props, "pci_domain_id", None)
+    bus = getattr(props, "pci_bus_id", None)
+    dv = getattr(props, "pci_device_id", None)
+    if bus is not None and dom is not None and dv is not None:
+        return f"{dom:08X}:{bus:02X}:{dv:02X}.0"
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    idx = device.index or 0
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if idx < len(ids):
+            return ids[idx]
+    return str(idx)
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("operator_simt.cu", "operator_tc.cu", "swopt_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2510_23739_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(kernel_name: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_name}_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"kernel_source_hash:\s*(\w+)", text)
+    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != _kernel_source_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+def make_problem(prob, seed: int, device):
+    """Seeded synthetic inputs on the device: kernel, phantom, measurements."""
+    import torch
+    import paper_2510_23739_gb300 as sw
+
+    g = prob.geom
+    K = synth.transducer_kernel(g, seed=0)
+    op = sw.Operator(g, K, prob.sw)
+    c_true = torch.tensor(synth.tube_phantom(g, prob.tubes, seed=seed,
+                                             per_species=prob.tubes_per_species),
+                          dtype=torch.float32, device=device)
+    clean = op.forward(c_true)
+    # noise power from the full clean signal (FP64 on the device)
+    sigma = math.sqrt(float(clean.double().pow(2).mean()) / 10 ** (prob.snr_db / 10))
+    noise = torch.tensor(synth.gaussian(g.y_shape(), seed + 1000), dtype=torch.float32,
+                         device=device)
+    y = clean + sigma * noise
+    del noise, clean
+    return op, K, c_true, y
+
+
+def run_swopt(args, rank, world, device):
+    import torch
+    import paper_2510_23739_gb300 as sw
+
+    prob = synth.workload(args.workload)
+    g = prob.geom
+    op, K, c_true, y = make_problem(prob, seed=rank, device=device)
+    if args.precision != "fp32":
+        op.set_precision(args.precision)
+    L = op.lipschitz(100)
+    alpha = 1.0 / L
+    params = sw.SolveParams(step=alpha, lambda_l1=prob.lam_l1, lambda_tv=prob.lam_tv,
+                            inner_iters=prob.inner, max_iters=args.steps)
+    stream = torch.cuda.current_stream()
+    op.fista_init(y, params)
+    for _ in range(args.warmup):
+        op.fista_step(1)
+    torch.cuda.synchronize()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    op.profile(True)
+    op.profile_read(0)
+    op.profile_read(1)
+    launches0 = op.launch_count()
+    clocks = ClockSampler(_smi_id(device))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))  # evict the working set from L2 between timed steps
+        starts[i].record(stream)
+        op.fista_step(1)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    launches = op.launch_count() - launches0
+    op.profile(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    kinfo = [op.profile_read(0), op.profile_read(1)]
+    avg = [ki["total_ms"] / max(ki["launches"], 1) for ki in kinfo]
+    dom = 0 if avg[0] >= avg[1] else 1
+    flops = kinfo[dom]["flops_per_launch"]
+
+    # e2e: a user call with host buffers (pinned), copies inside the timed region
+    y_host = y.cpu().pin_memory()
+    c_host = torch.empty(op.c_shape, dtype=torch.float32).pin_memory()
+    e2e_params = sw.SolveParams(step=alpha, lambda_l1=prob.lam_l1, lambda_tv=prob.lam_tv,
+                                inner_iters=prob.inner, max_iters=args.steps)
+    y_dev = torch.empty_like(y)
+    c_dev = torch.empty(op.c_shape, dtype=torch.float32, device=device)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    y_dev.copy_(y_host, non_blocking=True)
+    op.fista_init(y_dev, e2e_params)
+    op.fista_step(args.steps)
+    op.fista_get(c_dev)
+    c_host.copy_(c_dev, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+
+    result = {"total_ms": total_ms, "wall_s": wall, "dom": dom, "avg_ms": avg, "flops": flops,
+              "launches": launches, "clocks": clk, "e2e_ms": e2e_ms,
+              "h2d": y_host.numel() * 4, "d2h": c_host.numel() * 4, "info": op.info(),
+              "kinfo": kinfo}
+    op.close()
+    return result
+
+
+def cpu_oracle_iteration_ms(prob, sample_pulses: int):
+    """Time the FP64 oracle on a bounded sample of one FISTA iteration and
+    extrapolate to the full workload: forward + adjoint on `sample_pulses`
+    pulses (the per-pulse work is identical), the TV/l1 prox on the full
+    volume."""
+    import oracle
+    from dataclasses import replace
+
+    g = prob.geom
+    K = synth.transducer_kernel(g, seed=0)
+    gs = replace(g, N=sample_pulses)
+    c = synth.tube_phantom(g, prob.tubes, seed=0)
+    y = synth.gaussian(gs.y_shape(), 7) * 0.01
+    t0 = time.perf_counter()
+    yy = oracle.forward(gs, prob.sw, K, c)
+    t1 = time.perf_counter()
+    oracle.adjoint(gs, prob.sw, K, yy - y)
+    t2 = time.perf_counter()
+    oracle.prox(c, 1e-3, prob.lam_l1, prob.lam_tv, prob.inner)
+    t3 = time.perf_counter()
+    scale = g.N / sample_pulses
+    ms = ((t1 - t0) + (t2 - t1)) * scale * 1e3 + (t3 - t2) * 1e3
+    sample = (f"forward+adjoint on {sample_pulses} of {g.N} pulses, extrapolated x{scale:g}; "
+              f"TV+l1 prox ({prob.inner} inner) on the full volume")
+    return ms, sample, oracle.num_threads()
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle, each step a bounded sample of
+    one FISTA iteration extrapolated to the full workload."""
+    prob = synth.workload(args.workload)
+    times = []
+    sample = ""
+    cores = 1
+    for i in range(args.warmup + args.steps):
+        ms, sample, cores = cpu_oracle_iteration_ms(prob, args.ref_sample_pulses)
+        if i >= args.warmup:
+            times.append(ms)
+    ms = sum(times) / len(times)
+    value = 1000.0 / ms
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "it/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "impl": "FP64 CPU oracle (plain C, OpenMP)",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "it/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "it/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="swopt", choices=["swopt", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--cpu-sample-pulses", type=int, default=2)
+    ap.add_argument("--ref-sample-pulses", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=device)
+
+    import paper_2510_23739_gb300 as sw
+    sw.lib()
+    res = run_swopt(args, rank, world, device)
+
+    total_ms = res["total_ms"]
+    if world > 1:
+        t = torch.tensor([total_ms, res["e2e_ms"]], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms, e2e_ms = float(t[0]), float(t[1])
+    else:
+        e2e_ms = res["e2e_ms"]
+
+    if rank == 0:
+        peaks, peak_src = _peaks()
+        ms_step = total_ms / args.steps
+        value = world * args.steps / (total_ms / 1e3)
+        dom = res["dom"]
+        avg_ms = res["avg_ms"][dom]
+        achieved = res["flops"] / (avg_ms * 1e-3) / 1e12
+        clk = res["clocks"]
+        if args.precision == "fp32":
+            # FP32 FMA on the CUDA cores: 152 SMs x 128 lanes x 2 FLOP x max SM clock
+            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            bound, peak_note = "alu", f"FP32 FMA peak at {peaks.get('sm_max_mhz', 2070.0):g} MHz"
+        else:
+            peak = peaks["bf16_tflops_sustained"]
+            bound, peak_note = "tensor", f"bf16 sustained, {peak_src}"
+        kname = ["A_forward", "AT_adjoint"][dom]
+        traffic = _profiled_traffic(kname, args.workload)
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            ms_cpu, sample, cores = cpu_oracle_iteration_ms(synth.workload(args.workload),
+                                                            args.cpu_sample_pulses)
+            cpu = {"value": 1000.0 / ms_cpu, "unit": "it/s", "cores": cores, "kind": "oracle",
+                   "sample": sample}
+        line = {
+            "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else args.precision,
+            "data": "synthetic (seeded tube phantom, transducer kernel, 20 dB noise)",
+            "config": {"workload": args.workload, "precision": args.precision,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                       "time_window": res["info"], "inner_iters": 10},
+            "roofline": {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                         "avg_launch_ms": avg_ms, "flops_per_launch": res["flops"],
+                         "peak_source": peak_note,
+                         "other_kernel_avg_ms": res["avg_ms"][1 - dom]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": "it/s",
+                    "h2d_bytes_per_step": res["h2d"] / args.steps,
+                    "d2h_bytes_per_step": res["d2h"] / args.steps,
+                    "note": "one swopt solve of `steps` iterations from pinned host y to host c"},
+            "gpu_launches": res["launches"],
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,225 @@
+/*
+ * swopt: GB300-native (sm_103a) hot path of the one-step reconstruction for
+ * photo-switching optoacoustic mesoscopy (arXiv 2510.23739).
+ *
+ * The library applies the matrix-free forward operator H = A o P and its
+ * adjoint H^T (Sec. 2.3, Eq. full-forward), the l1 and TV proximal maps
+ * (Eq. prox, Eq. prox-dual, Algorithm 2) and the FISTA iteration of
+ * Algorithm 1 that combines them, all as CUDA kernels on one GPU.
+ *
+ * Conventions for every entry point:
+ *  - Array arguments named *_dev are DEVICE pointers owned by the caller
+ *    (for example PyTorch tensors), dense and row-major in the layouts
+ *    below; arguments named *_host are host pointers.  The library never
+ *    frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream unless they return
+ *    host scalars, which synchronise the stream before returning.
+ *  - Every call returns a swopt_status.  On failure the call leaves caller
+ *    buffers in an unspecified state and swopt_last_error() returns a
+ *    message (thread-local).  Arguments are validated on the host before any
+ *    GPU work is queued.
+ *  - A handle is not thread-safe: calls on one handle must not overlap in
+ *    time (host side) and share its workspaces (device side), so work on
+ *    one handle must be issued to one stream at a time.
+ *
+ * Layouts (C order), with S = Y*X scan positions:
+ *   concentrations c  float [P][Y][X][Z]   species, scan row, scan column, depth
+ *   measurements   y  float [N][Y][X][T]   pulse, scan row, scan column, time
+ *   kernel         K  double[Z][k][k][T]   depth j, dy+r, dx+r, time (r = k/2)
+ */
+#ifndef SWOPT_H
+#define SWOPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SWOPT_OK = 0,
+    SWOPT_ERR_INVALID_ARG = 1,  /* null pointer, bad enum or non-finite scalar */
+    SWOPT_ERR_SHAPE = 2,        /* geometry out of the supported range */
+    SWOPT_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    SWOPT_ERR_OOM = 4,          /* device allocation failed */
+    SWOPT_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+    SWOPT_ERR_DEVICE_CHECK = 6, /* a device-side consistency check failed */
+    SWOPT_ERR_UNSUPPORTED = 7   /* valid request the current build cannot serve */
+} swopt_status;
+
+typedef struct swopt_handle swopt_handle;
+
+/* Grid and pulse train.  Limits: 1 <= X, Y <= 4096; 1 <= Z <= 1024;
+ * 1 <= T <= 8192; 1 <= N <= 4096; 1 <= P <= 8; k odd, 1 <= k <= 63;
+ * 1 <= pulses_per_cycle.  dz_mm > 0 is the depth pitch used by the fluence
+ * model Phi_j = exp(-mu * j * dz_mm). */
+typedef struct {
+    int X, Y, Z, T, N, P, k;
+    int pulses_per_cycle;
+    double dz_mm;
+} swopt_geometry;
+
+/* Photo-switching parameters of Eq. (final-H), host arrays of length P.
+ * Pulse n of the train sits m = n mod pulses_per_cycle pulse intervals into
+ * its OFF-switching cycle, and depth j receives the weight
+ *   S[n][p][j] = Phi_j * (eps_bar[p] * exp(-kappa[p] * Phi_j * m) + eps_off[p]).
+ * The background species has kappa = 0, eps_bar = 0 (Sec. 2.1). */
+typedef struct {
+    const double* kappa_host;
+    const double* eps_bar_host;
+    const double* eps_off_host;
+    double mu_per_mm;
+} swopt_switching;
+
+/* Arithmetic of the A / A^T contractions.
+ *  SWOPT_PREC_FP32 : FP32 FMA on the CUDA cores (the accuracy reference).
+ *  SWOPT_PREC_BF16 : tcgen05 tensor cores, BF16 operands, FP32 accumulation.
+ *  SWOPT_PREC_BF16X3: tcgen05 tensor cores on a two-term BF16 split of both
+ *                    operands (hi*hi + hi*lo + lo*hi), FP32 accumulation. */
+typedef enum {
+    SWOPT_PREC_FP32 = 0,
+    SWOPT_PREC_BF16 = 1,
+    SWOPT_PREC_BF16X3 = 2
+} swopt_precision;
+
+/* Momentum of Algorithms 1 and 2: Beck-Teboulle (t_k - 1)/t_{k+1}, the
+ * coefficient as printed in the paper (t_k - 1)/(t_k + 1), or none. */
+typedef enum {
+    SWOPT_MOMENTUM_BECK_TEBOULLE = 0,
+    SWOPT_MOMENTUM_PAPER_PRINTED = 1,
+    SWOPT_MOMENTUM_NONE = 2
+} swopt_momentum;
+
+/* Settings of Algorithm 1 (FISTA) on Eq. (one-step) with Eq. (reg-tv-l1-one),
+ * lambda_3 = 0: w(c) = lambda_tv sum_p TV(c_p) + lambda_l1 ||c||_1 + indicator(c >= 0). */
+typedef struct {
+    double step;        /* alpha_1; <= 0 means 1/L with L from swopt_lipschitz */
+    double lambda_l1;   /* >= 0 */
+    double lambda_tv;   /* >= 0 */
+    int inner_iters;    /* K2 of Algorithm 2 (>= 0; 0 skips the TV prox) */
+    int max_iters;      /* K1 of Algorithm 1 (>= 0) */
+    double eps1;        /* relative objective change stop (<= 0: off) */
+    double eps2;        /* relative momentum-iterate change stop (<= 0: off) */
+    int momentum;       /* swopt_momentum of Algorithm 1 */
+    int inner_momentum; /* swopt_momentum of Algorithm 2 */
+    int power_iters;    /* power iterations when step <= 0 (>= 1) */
+    double* history_host; /* optional [max_iters]: F(c_{k+1}) per iteration */
+} swopt_solve_params;
+
+typedef struct {
+    int iters;          /* iterations run */
+    double step;        /* alpha_1 used */
+    double objective;   /* F(c) of the returned iterate (FP64) */
+    double data_fit;    /* 1/2 ||H c - y||^2 of the returned iterate (FP64) */
+} swopt_solve_stats;
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* swopt_last_error(void);
+
+/* Library version, "major.minor.patch". */
+const char* swopt_version(void);
+
+/* Create a handle on the current CUDA device.  K_host is the FP64 per-depth
+ * kernel K[Z][k][k][T] (copied; the caller may free it on return); it plays
+ * the part of the transducer response of Sec. 2.3 with the electrical
+ * impulse response of Eq. (acoustic-temporal-conv) folded in along t.
+ * Errors: INVALID_ARG (null pointers, non-finite values), SHAPE (limits
+ * above, or an all-zero kernel), OOM, CUDA. */
+swopt_status swopt_create(const swopt_geometry* geom, const double* K_host,
+                          const swopt_switching* sw, swopt_handle** out);
+
+/* Release a handle and all device memory it owns (NULL is a no-op). */
+swopt_status swopt_destroy(swopt_handle* h);
+
+/* Select the contraction arithmetic for later calls (swopt_precision). */
+swopt_status swopt_set_precision(swopt_handle* h, int precision);
+
+/* Forward operator, y = H c = W_tot S c (Eq. full-forward): for every pulse n
+ * and scan position (y, x),
+ *   y[n][y][x][t] = sum_j sum_{|dy|,|dx|<=r} b[n][y+dy][x+dx][j] K[j][dy+r][dx+r][t],
+ *   b[n][y][x][j] = sum_p S[n][p][j] c[p][y][x][j]      (Eq. Sij-detailed),
+ * with b = 0 outside the scan grid.  c_dev: [P][Y][X][Z]; y_dev: [N][Y][X][T]
+ * (fully overwritten). */
+swopt_status swopt_forward(swopt_handle* h, const float* c_dev, float* y_dev, void* stream);
+
+/* Adjoint operator, c = H^T y (the exact transpose of swopt_forward):
+ *   c[p][y][x][j] = sum_n S[n][p][j] sum_{dy,dx} sum_t y[n][y-dy][x-dx][t] K[j][dy+r][dx+r][t].
+ * y_dev: [N][Y][X][T]; c_dev: [P][Y][X][Z] (fully overwritten). */
+swopt_status swopt_adjoint(swopt_handle* h, const float* y_dev, float* c_dev, void* stream);
+
+/* l1 proximal map, in place on x_dev [P][Y][X][Z]: x <- sign(x) max(|x| - thresh, 0),
+ * or with nonneg != 0 (l1 plus the indicator of Eq. one-step) x <- max(x - thresh, 0).
+ * thresh >= 0. */
+swopt_status swopt_prox_l1(swopt_handle* h, float* x_dev, float thresh, int nonneg, void* stream);
+
+/* Anisotropic 3D TV proximal map of one volume per species by Algorithm 2
+ * with L = the forward differences along y, x and z (interior edges only),
+ * dual radius tau >= 0, dual step 1/12, zero dual start and inner_iters
+ * iterations with the given swopt_momentum; x = z - D^T u.
+ * z_dev, x_dev: [P][Y][X][Z] (may not alias). */
+swopt_status swopt_prox_tv(swopt_handle* h, const float* z_dev, float* x_dev, float tau,
+                           int inner_iters, int momentum, void* stream);
+
+/* Step-size estimate of Algorithm 1: L ~ eig_max(H^T H) by iters >= 1 power
+ * iterations v <- H^T H v / ||H^T H v|| (FP64 norms), returning the Rayleigh
+ * quotient in *L_out.  v0_dev ([P][Y][X][Z], optional): start vector; NULL
+ * starts from a fixed counter-based pseudo-random vector.  Synchronises. */
+swopt_status swopt_lipschitz(swopt_handle* h, const float* v0_dev, int iters, double* L_out,
+                             void* stream);
+
+/* Algorithm 1 in steps.  swopt_fista_init binds the measurements y_dev
+ * ([N][Y][X][T], read during this call only), sets c_0 = xi_0 = 0, t_0 = 1
+ * and fixes the settings (a step <= 0 runs swopt_lipschitz first, which
+ * synchronises).  swopt_fista_step runs `iters` iterations
+ *   c_{k+1} = prox_{alpha w}(xi_k - alpha H^T (H xi_k - y)),  t_{k+1}, xi_{k+1}
+ * asynchronously (no host synchronisation; the momentum scalars stay on the
+ * device in FP64; the eps1/eps2 tests and the history are not evaluated).
+ * swopt_fista_get copies the current c_k into c_dev [P][Y][X][Z]. */
+swopt_status swopt_fista_init(swopt_handle* h, const float* y_dev, const swopt_solve_params* prm,
+                              void* stream);
+swopt_status swopt_fista_step(swopt_handle* h, int iters, void* stream);
+swopt_status swopt_fista_get(swopt_handle* h, float* c_dev, void* stream);
+
+/* Complete solve (Algorithm 1): init, up to max_iters iterations with the
+ * eps1/eps2 stopping tests and the optional history, then c_dev <- c_K and
+ * the statistics (stats may be NULL).  Synchronises. */
+swopt_status swopt_solve(swopt_handle* h, const float* y_dev, float* c_dev,
+                         const swopt_solve_params* prm, swopt_solve_stats* stats, void* stream);
+
+/* Objective of Eq. (one-step), in FP64: *F = 1/2||H c - y||^2 + lambda_tv sum_p TV(c_p)
+ * + lambda_l1 ||c||_1, *fit = the data-fit term (either may be NULL).  c is not
+ * checked for nonnegativity.  Synchronises. */
+swopt_status swopt_objective(swopt_handle* h, const float* c_dev, const float* y_dev,
+                             double lambda_l1, double lambda_tv, double* F, double* fit,
+                             void* stream);
+
+/* Gradient of f = 1/2||H c - y||^2 with respect to the switching parameters
+ * with c held fixed (Eq. final-H differentiated): dkappa_host[p] = df/dkappa_p
+ * (length P) and *dmu = df/dmu.  FP64 accumulation.  Synchronises. */
+swopt_status swopt_param_grad(swopt_handle* h, const float* c_dev, const float* y_dev,
+                              double* dkappa_host, double* dmu, void* stream);
+
+/* Instrumentation.  swopt_profile_enable(h, 1) records CUDA events around
+ * every launch of the A and A^T contraction kernels on the launching
+ * stream; swopt_profile_read returns, for kernel_id 0 (A) or 1 (A^T), the
+ * summed device time in milliseconds, the number of launches and the
+ * algorithmic FLOPs of one launch (2 x multiply-adds of nonzero kernel taps).
+ * Reading synchronises on the recorded events and clears them.
+ * swopt_launch_count returns the number of kernels this handle launched. */
+swopt_status swopt_profile_enable(swopt_handle* h, int on);
+swopt_status swopt_profile_read(swopt_handle* h, int kernel_id, double* total_ms,
+                                int64_t* launches, double* flops_per_launch);
+swopt_status swopt_launch_count(swopt_handle* h, int64_t* count);
+
+/* Operator facts: the time window [t0, t0 + tw) that holds every nonzero
+ * kernel sample, the number of distinct switching states Q = min(N,
+ * pulses_per_cycle) and the number of nonzero kernel entries. */
+swopt_status swopt_info(swopt_handle* h, int* t0, int* tw, int* states, int64_t* kernel_nnz);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWOPT_H */

@@ -1,0 +1,380 @@
+"""Python binding of the swopt C-ABI (argument marshalling only).
+
+Every operation runs in the CUDA library ``_build/libswopt.so`` (built from
+``csrc/`` by ``build.py``); this module only converts PyTorch CUDA tensors to
+device pointers and the current CUDA stream to a ``cudaStream_t``.  There is
+no CPU path: if the library cannot be built or loaded, the import of
+:func:`lib` raises.
+
+The operator is H = A o P of arXiv 2510.23739 (Sec. 2.3, Eq. full-forward):
+P maps concentrations c[P][Y][X][Z] to per-pulse initial pressure through the
+switching law of Eq. (final-H), A is the lateral-shift-invariant per-depth
+acoustic kernel K[Z][k][k][T] that maps each pulse's pressure to
+measurements y[N][Y][X][T].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["lib", "Operator", "SolveParams", "SwoptError", "PRECISION", "MOMENTUM",
+           "HFunction"]
+
+PRECISION = {"fp32": 0, "bf16": 1, "bf16x3": 2}
+MOMENTUM = {"beck_teboulle": 0, "paper_printed": 1, "none": 2}
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "SHAPE", 3: "CUDA", 4: "OOM", 5: "TIMEOUT",
+           6: "DEVICE_CHECK", 7: "UNSUPPORTED"}
+
+
+class SwoptError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"swopt error {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Geometry(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_int), ("Y", ctypes.c_int), ("Z", ctypes.c_int),
+                ("T", ctypes.c_int), ("N", ctypes.c_int), ("P", ctypes.c_int),
+                ("k", ctypes.c_int), ("pulses_per_cycle", ctypes.c_int),
+                ("dz_mm", ctypes.c_double)]
+
+
+class _Switching(ctypes.Structure):
+    _fields_ = [("kappa_host", ctypes.POINTER(ctypes.c_double)),
+                ("eps_bar_host", ctypes.POINTER(ctypes.c_double)),
+                ("eps_off_host", ctypes.POINTER(ctypes.c_double)),
+                ("mu_per_mm", ctypes.c_double)]
+
+
+class _SolveParams(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_double), ("lambda_l1", ctypes.c_double),
+                ("lambda_tv", ctypes.c_double), ("inner_iters", ctypes.c_int),
+                ("max_iters", ctypes.c_int), ("eps1", ctypes.c_double),
+                ("eps2", ctypes.c_double), ("momentum", ctypes.c_int),
+                ("inner_momentum", ctypes.c_int), ("power_iters", ctypes.c_int),
+                ("history_host", ctypes.POINTER(ctypes.c_double))]
+
+
+class _SolveStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("step", ctypes.c_double),
+                ("objective", ctypes.c_double), ("data_fit", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# exported symbol -> argtypes (restype is swopt_status = int unless listed)
+_SIGS = {
+    "swopt_last_error": ([], ctypes.c_char_p),
+    "swopt_version": ([], ctypes.c_char_p),
+    "swopt_create": ([ctypes.POINTER(_Geometry), ctypes.c_void_p, ctypes.POINTER(_Switching),
+                      ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "swopt_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "swopt_set_precision": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "swopt_forward": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+                      ctypes.c_int),
+    "swopt_adjoint": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+                      ctypes.c_int),
+    "swopt_prox_l1": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int,
+                       ctypes.c_void_p], ctypes.c_int),
+    "swopt_prox_tv": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float,
+                       ctypes.c_int, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "swopt_lipschitz": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p], ctypes.c_int),
+    "swopt_fista_init": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_SolveParams),
+                          ctypes.c_void_p], ctypes.c_int),
+    "swopt_fista_step": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "swopt_fista_get": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "swopt_solve": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                     ctypes.POINTER(_SolveParams), ctypes.POINTER(_SolveStats), ctypes.c_void_p],
+                    ctypes.c_int),
+    "swopt_objective": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                         ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p], ctypes.c_int),
+    "swopt_param_grad": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                          ctypes.c_void_p], ctypes.c_int),
+    "swopt_profile_enable": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "swopt_profile_read": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
+                           ctypes.c_int),
+    "swopt_launch_count": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "swopt_info": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+}
+
+
+def lib():
+    """Load (building first if needed) the CUDA library.  Raises on failure."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(status: int):
+    if status != 0:
+        msg = lib().swopt_last_error().decode(errors="replace")
+        raise SwoptError(status, msg)
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class SolveParams:
+    """Settings of Algorithm 1 (see ``swopt_solve_params``)."""
+
+    def __init__(self, step=0.0, lambda_l1=1e-3, lambda_tv=1e-3, inner_iters=10, max_iters=100,
+                 eps1=0.0, eps2=0.0, momentum="beck_teboulle", inner_momentum="beck_teboulle",
+                 power_iters=100):
+        self.step = step
+        self.lambda_l1 = lambda_l1
+        self.lambda_tv = lambda_tv
+        self.inner_iters = inner_iters
+        self.max_iters = max_iters
+        self.eps1 = eps1
+        self.eps2 = eps2
+        self.momentum = momentum
+        self.inner_momentum = inner_momentum
+        self.power_iters = power_iters
+
+    def _c(self, history=None):
+        p = _SolveParams()
+        p.step = float(self.step)
+        p.lambda_l1 = float(self.lambda_l1)
+        p.lambda_tv = float(self.lambda_tv)
+        p.inner_iters = int(self.inner_iters)
+        p.max_iters = int(self.max_iters)
+        p.eps1 = float(self.eps1)
+        p.eps2 = float(self.eps2)
+        p.momentum = MOMENTUM[self.momentum] if isinstance(self.momentum, str) else int(self.momentum)
+        p.inner_momentum = (MOMENTUM[self.inner_momentum] if isinstance(self.inner_momentum, str)
+                            else int(self.inner_momentum))
+        p.power_iters = int(self.power_iters)
+        p.history_host = (history.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                          if history is not None else ctypes.POINTER(ctypes.c_double)())
+        return p
+
+
+class Operator:
+    """A handle: geometry, FP64 kernel and switching parameters on one GPU.
+
+    ``geom`` and ``sw`` are objects with the fields of ``synth.Geometry`` /
+    ``synth.Switching`` (X, Y, Z, T, N, P, k, pulses_per_cycle, dz_mm;
+    kappa, eps_bar, eps_off, mu_per_mm).  ``K`` is the FP64 kernel
+    [Z][k][k][T] (numpy), copied at creation.
+    """
+
+    def __init__(self, geom, K, sw, precision: str = "fp32"):
+        L = lib()
+        self.geom = geom
+        self.sw = sw
+        g = _Geometry(int(geom.X), int(geom.Y), int(geom.Z), int(geom.T), int(geom.N),
+                      int(geom.P), int(geom.k), int(geom.pulses_per_cycle), float(geom.dz_mm))
+        K = np.ascontiguousarray(K, dtype=np.float64)
+        if K.shape != (geom.Z, geom.k, geom.k, geom.T):
+            raise ValueError(f"kernel shape {K.shape} does not match the geometry")
+        self._kap = np.ascontiguousarray(sw.kappa, dtype=np.float64)
+        self._eb = np.ascontiguousarray(sw.eps_bar, dtype=np.float64)
+        self._eo = np.ascontiguousarray(sw.eps_off, dtype=np.float64)
+        for a in (self._kap, self._eb, self._eo):
+            if a.shape != (geom.P,):
+                raise ValueError("switching parameters must have one entry per species")
+        dp = ctypes.POINTER(ctypes.c_double)
+        s = _Switching(self._kap.ctypes.data_as(dp), self._eb.ctypes.data_as(dp),
+                       self._eo.ctypes.data_as(dp), float(sw.mu_per_mm))
+        h = ctypes.c_void_p()
+        _check(L.swopt_create(ctypes.byref(g), K.ctypes.data_as(ctypes.c_void_p), ctypes.byref(s),
+                              ctypes.byref(h)))
+        self._h = h
+        if precision != "fp32":
+            self.set_precision(precision)
+        self.precision = precision
+
+    # -- lifecycle --------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().swopt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, precision: str):
+        _check(lib().swopt_set_precision(self._h, PRECISION[precision]))
+        self.precision = precision
+
+    @property
+    def c_shape(self):
+        g = self.geom
+        return (g.P, g.Y, g.X, g.Z)
+
+    @property
+    def y_shape(self):
+        g = self.geom
+        return (g.N, g.Y, g.X, g.T)
+
+    def info(self):
+        t0, tw, q = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        nnz = ctypes.c_int64()
+        _check(lib().swopt_info(self._h, ctypes.byref(t0), ctypes.byref(tw), ctypes.byref(q),
+                                ctypes.byref(nnz)))
+        return {"t0": t0.value, "tw": tw.value, "states": q.value, "kernel_nnz": nnz.value}
+
+    # -- operators --------------------------------------------------------
+    def forward(self, c, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.y_shape, device=c.device, dtype=torch.float32)
+        _check(lib().swopt_forward(self._h, _ptr(c, self.c_shape, "c"),
+                                   _ptr(out, self.y_shape, "y"), _stream(stream)))
+        return out
+
+    def adjoint(self, y, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.c_shape, device=y.device, dtype=torch.float32)
+        _check(lib().swopt_adjoint(self._h, _ptr(y, self.y_shape, "y"),
+                                   _ptr(out, self.c_shape, "c"), _stream(stream)))
+        return out
+
+    def prox_l1(self, x, thresh, nonneg=True, stream=None):
+        _check(lib().swopt_prox_l1(self._h, _ptr(x, self.c_shape, "x"), float(thresh),
+                                   1 if nonneg else 0, _stream(stream)))
+        return x
+
+    def prox_tv(self, z, tau, inner_iters, momentum="beck_teboulle", out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(z)
+        _check(lib().swopt_prox_tv(self._h, _ptr(z, self.c_shape, "z"),
+                                   _ptr(out, self.c_shape, "x"), float(tau), int(inner_iters),
+                                   MOMENTUM[momentum], _stream(stream)))
+        return out
+
+    def lipschitz(self, iters=100, v0=None, stream=None):
+        L = ctypes.c_double()
+        v = _ptr(v0, self.c_shape, "v0") if v0 is not None else ctypes.c_void_p(0)
+        _check(lib().swopt_lipschitz(self._h, v, int(iters), ctypes.byref(L), _stream(stream)))
+        return L.value
+
+    # -- Algorithm 1 ------------------------------------------------------
+    def fista_init(self, y, params: SolveParams, stream=None):
+        p = params._c()
+        _check(lib().swopt_fista_init(self._h, _ptr(y, self.y_shape, "y"), ctypes.byref(p),
+                                      _stream(stream)))
+
+    def fista_step(self, iters=1, stream=None):
+        _check(lib().swopt_fista_step(self._h, int(iters), _stream(stream)))
+
+    def fista_get(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.c_shape, device="cuda", dtype=torch.float32)
+        _check(lib().swopt_fista_get(self._h, _ptr(out, self.c_shape, "c"), _stream(stream)))
+        return out
+
+    def solve(self, y, params: SolveParams, history=False, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.c_shape, device=y.device, dtype=torch.float32)
+        hist = np.zeros(params.max_iters) if history else None
+        p = params._c(hist)
+        st = _SolveStats()
+        _check(lib().swopt_solve(self._h, _ptr(y, self.y_shape, "y"), _ptr(out, self.c_shape, "c"),
+                                 ctypes.byref(p), ctypes.byref(st), _stream(stream)))
+        stats = {"iters": st.iters, "step": st.step, "objective": st.objective,
+                 "data_fit": st.data_fit}
+        if history:
+            stats["history"] = hist[: st.iters]
+        return out, stats
+
+    def objective(self, c, y, lambda_l1, lambda_tv, stream=None):
+        F, fit = ctypes.c_double(), ctypes.c_double()
+        _check(lib().swopt_objective(self._h, _ptr(c, self.c_shape, "c"),
+                                     _ptr(y, self.y_shape, "y"), float(lambda_l1),
+                                     float(lambda_tv), ctypes.byref(F), ctypes.byref(fit),
+                                     _stream(stream)))
+        return F.value, fit.value
+
+    def param_grad(self, c, y, stream=None):
+        dk = np.zeros(self.geom.P)
+        dmu = ctypes.c_double()
+        _check(lib().swopt_param_grad(self._h, _ptr(c, self.c_shape, "c"),
+                                      _ptr(y, self.y_shape, "y"),
+                                      dk.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      ctypes.byref(dmu), _stream(stream)))
+        return dk, dmu.value
+
+    # -- instrumentation --------------------------------------------------
+    def profile(self, on=True):
+        _check(lib().swopt_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, kernel_id):
+        ms, n, fl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().swopt_profile_read(self._h, int(kernel_id), ctypes.byref(ms), ctypes.byref(n),
+                                        ctypes.byref(fl)))
+        return {"total_ms": ms.value, "launches": n.value, "flops_per_launch": fl.value}
+
+    def launch_count(self):
+        n = ctypes.c_int64()
+        _check(lib().swopt_launch_count(self._h, ctypes.byref(n)))
+        return n.value
+
+
+def _make_hfunction():
+    import torch
+
+    class HFunction(torch.autograd.Function):
+        """y = H c with backward c_grad = H^T y_grad (hand-written adjoint)."""
+
+        @staticmethod
+        def forward(ctx, c, op):
+            ctx.op = op
+            return op.forward(c.contiguous())
+
+        @staticmethod
+        def backward(ctx, gy):
+            return ctx.op.adjoint(gy.contiguous()), None
+
+    return HFunction
+
+
+def __getattr__(name):
+    if name == "HFunction":
+        return _make_hfunction()
+    raise AttributeError(name)

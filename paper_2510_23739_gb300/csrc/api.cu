@@ -1,0 +1,812 @@
+// C-ABI entry points of swopt: argument validation, handle set-up (kernel
+// window, band masks, switching states) and the orchestration of each call
+// out of the kernels in operator_simt.cu, operator_tc.cu and prox.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <algorithm>
+
+#include "swopt_internal.cuh"
+
+namespace swopt {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_err[0] = 0; }
+
+// Slots of the FP64 device scalars.
+enum {
+    SC_T = 0,      // FISTA t_k
+    SC_BETA = 1,   // FISTA beta_k
+    SC_A = 2,      // reduction results
+    SC_B = 3,
+    SC_C = 4,
+    SC_D = 5,
+    SC_YSQ = 6,    // ||y||^2 of the measurements bound by fista_init
+    SC_COUNT = 16
+};
+
+void prof_begin(swopt_handle* h, int kernel, cudaStream_t st, ProfileRec* rec)
+{
+    rec->kernel = -1;
+    if (!h->profile) return;
+    cudaEvent_t a, b;
+    if (h->event_pool.size() >= 2) {
+        a = h->event_pool.back(); h->event_pool.pop_back();
+        b = h->event_pool.back(); h->event_pool.pop_back();
+    } else {
+        if (cudaEventCreate(&a) != cudaSuccess) return;
+        if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+    }
+    rec->a = a;
+    rec->b = b;
+    rec->kernel = kernel;
+    cudaEventRecord(a, st);
+}
+
+void prof_end(swopt_handle* h, ProfileRec* rec, cudaStream_t st)
+{
+    if (rec->kernel < 0) return;
+    cudaEventRecord(rec->b, st);
+    h->prof.push_back(*rec);
+}
+
+}  // namespace swopt
+
+using namespace swopt;
+
+namespace {
+
+bool is_fin(double v) { return std::isfinite(v); }
+
+swopt_status check_handle(swopt_handle* h)
+{
+    if (!h) {
+        set_error("null handle");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    return SWOPT_OK;
+}
+
+template <typename T>
+swopt_status dalloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? SWOPT_ERR_OOM : SWOPT_ERR_CUDA;
+    }
+    return SWOPT_OK;
+}
+
+template <typename T>
+void dfree(T*& p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void release_all(swopt_handle* h)
+{
+    tc_release(h);
+    dfree(h->Kf); dfree(h->Ka); dfree(h->fmask); dfree(h->amask); dfree(h->Sm); dfree(h->Cmf);
+    dfree(h->b); dfree(h->u); dfree(h->g); dfree(h->ytil); dfree(h->red); dfree(h->scal);
+    dfree(h->c); dfree(h->xi); dfree(h->zin); dfree(h->tvu); dfree(h->tvr0); dfree(h->tvr1);
+    dfree(h->tmp);
+    if (h->scal_host) cudaFreeHost(h->scal_host);
+    h->scal_host = nullptr;
+    for (auto& r : h->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    h->prof.clear();
+    for (auto e : h->event_pool) cudaEventDestroy(e);
+    h->event_pool.clear();
+}
+
+std::vector<double> momentum_betas(int iters, int mode)
+{
+    std::vector<double> out(std::max(iters, 1), 0.0);
+    double t = 1.0;
+    for (int i = 0; i < iters; ++i) {
+        const double t1 = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+        double b = 0.0;
+        if (mode == SWOPT_MOMENTUM_BECK_TEBOULLE) b = (t - 1.0) / t1;
+        else if (mode == SWOPT_MOMENTUM_PAPER_PRINTED) b = (t - 1.0) / (t + 1.0);
+        out[i] = b;
+        t = t1;
+    }
+    return out;
+}
+
+swopt_status ensure_tv_buffers(swopt_handle* h)
+{
+    const size_t n = nc_of(h);
+    if (!h->tvu) SW_TRY(dalloc(&h->tvu, 3 * n));
+    if (!h->tvr0) SW_TRY(dalloc(&h->tvr0, 3 * n));
+    if (!h->tvr1) SW_TRY(dalloc(&h->tvr1, 3 * n));
+    return SWOPT_OK;
+}
+
+swopt_status ensure_vectors(swopt_handle* h)
+{
+    const size_t n = nc_of(h);
+    if (!h->c) SW_TRY(dalloc(&h->c, n));
+    if (!h->xi) SW_TRY(dalloc(&h->xi, n));
+    if (!h->zin) SW_TRY(dalloc(&h->zin, n));
+    if (!h->tmp) SW_TRY(dalloc(&h->tmp, n));
+    return SWOPT_OK;
+}
+
+swopt_status ensure_ytil(swopt_handle* h)
+{
+    if (!h->ytil) SW_TRY(dalloc(&h->ytil, nu_of(h)));
+    return SWOPT_OK;
+}
+
+swopt_status read_scalars(swopt_handle* h, cudaStream_t st)
+{
+    SW_CUDA(cudaMemcpyAsync(h->scal_host, h->scal, SC_COUNT * sizeof(double),
+                            cudaMemcpyDeviceToHost, st));
+    SW_CUDA(cudaStreamSynchronize(st));
+    return SWOPT_OK;
+}
+
+bool use_tc(const swopt_handle* h) { return h->precision != SWOPT_PREC_FP32; }
+
+// u = (scale ? Cm : 1) * A b - ytil   (see simt_forward)
+swopt_status op_A(swopt_handle* h, const float* b, float* u, const float* ytil, double* partials,
+                  int scale, cudaStream_t st)
+{
+    if (use_tc(h)) return tc_forward(h, b, u, ytil, partials, scale, st);
+    return simt_forward(h, b, u, ytil, partials, scale, st);
+}
+
+swopt_status op_AT(swopt_handle* h, const float* u, float* g, cudaStream_t st)
+{
+    if (use_tc(h)) return tc_adjoint(h, u, g, st);
+    return simt_adjoint(h, u, g, st);
+}
+
+int forward_blocks(const swopt_handle* h)
+{
+    return use_tc(h) ? tc_forward_blocks(h) : simt_forward_blocks(h);
+}
+
+// w = H^T H v
+swopt_status normal_op(swopt_handle* h, const float* v, float* w, cudaStream_t st)
+{
+    SW_TRY(launch_states(h, v, h->b, st));
+    SW_TRY(op_A(h, h->b, h->u, nullptr, nullptr, 1, st));
+    SW_TRY(op_AT(h, h->u, h->g, st));
+    return launch_pt(h, h->g, nullptr, 0.f, w, 0, st);
+}
+
+swopt_status lipschitz_impl(swopt_handle* h, const float* v0, int iters, double* L,
+                            cudaStream_t st)
+{
+    SW_TRY(ensure_vectors(h));
+    const size_t n = nc_of(h);
+    float* v = h->tmp;
+    float* w = h->zin;
+    if (v0) SW_CUDA(cudaMemcpyAsync(v, v0, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    else SW_TRY(fill_counter_random(h, v, n, 0x5eed5eedull, st));
+    SW_TRY(reduce_sumsq(h, v, n, SC_A, st));
+    SW_TRY(scale_by_inv_sqrt(h, v, v, n, SC_A, st));
+    for (int it = 0; it < iters; ++it) {
+        SW_TRY(normal_op(h, v, w, st));
+        SW_TRY(reduce_dot(h, v, w, n, SC_B, st));   // Rayleigh quotient (||v|| = 1)
+        SW_TRY(reduce_sumsq(h, w, n, SC_A, st));
+        SW_TRY(scale_by_inv_sqrt(h, w, v, n, SC_A, st));
+    }
+    SW_TRY(read_scalars(h, st));
+    *L = h->scal_host[SC_B];
+    return SWOPT_OK;
+}
+
+swopt_status validate_params(const swopt_solve_params* p)
+{
+    if (!p) {
+        set_error("null solve parameters");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    if (!is_fin(p->step) || !is_fin(p->lambda_l1) || !is_fin(p->lambda_tv) || !is_fin(p->eps1) ||
+        !is_fin(p->eps2) || p->lambda_l1 < 0 || p->lambda_tv < 0 || p->inner_iters < 0 ||
+        p->inner_iters > 100000 || p->max_iters < 0 || p->momentum < 0 || p->momentum > 2 ||
+        p->inner_momentum < 0 || p->inner_momentum > 2 ||
+        (p->step <= 0 && (p->power_iters < 1 || p->power_iters > 100000))) {
+        set_error("invalid solve parameters");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    return SWOPT_OK;
+}
+
+// One FISTA iteration on the bound measurements (all on `st`, no host sync).
+swopt_status fista_iteration(swopt_handle* h, cudaStream_t st)
+{
+    const float alpha = (float)h->step;
+    const bool tv = h->prm.lambda_tv > 0 && h->prm.inner_iters > 0;
+    SW_TRY(launch_states(h, h->xi, h->b, st));                        // P
+    SW_TRY(op_A(h, h->b, h->u, h->ytil, nullptr, 1, st));             // A, folded residual
+    SW_TRY(op_AT(h, h->u, h->g, st));                                 // A^T
+    SW_TRY(launch_pt(h, h->g, h->xi, alpha, h->zin, 1, st));          // P^T, gradient step
+    if (tv)
+        SW_TRY(prox_tv_iters(h, h->zin, (float)(h->step * h->prm.lambda_tv),
+                             h->prm.inner_iters, h->inner_beta.data(), st));
+    SW_TRY(fista_scalars(h, h->prm.momentum, st));
+    return fista_finish(h, h->zin, tv, (float)(h->step * h->prm.lambda_l1), st);
+}
+
+// F(c) and the data fit on measurements y (FP64; slots SC_A..SC_D).
+swopt_status objective_impl(swopt_handle* h, const float* c, const float* y, double lam_l1,
+                            double lam_tv, double* F, double* fit, cudaStream_t st)
+{
+    SW_TRY(launch_states(h, c, h->b, st));
+    SW_TRY(op_A(h, h->b, h->u, nullptr, nullptr, 0, st));
+    SW_TRY(ensure_vectors(h));
+    // expand H c into the y layout chunk by chunk is avoided: the data fit is
+    // the sum over pulses of ||u[m(n)] - y[n]||^2 including the samples
+    // outside the window, computed as ||y||^2 + sum_m Cm ||u_m||^2 - 2 <u, ytil>.
+    float* yt = nullptr;
+    SW_TRY(dalloc(&yt, nu_of(h)));
+    swopt_status s = launch_fold(h, y, yt, st);
+    if (s == SWOPT_OK) s = reduce_sumsq(h, y, (size_t)h->N * h->S * h->T, SC_A, st);
+    if (s == SWOPT_OK) s = reduce_dot(h, h->u, yt, nu_of(h), SC_B, st);
+    // sum_m Cm ||u_m||^2 : one reduction per state
+    double cu = 0.0;
+    if (s == SWOPT_OK) s = read_scalars(h, st);
+    double ysq = h->scal_host[SC_A], uy = h->scal_host[SC_B];
+    for (int m = 0; m < h->Q && s == SWOPT_OK; ++m) {
+        s = reduce_sumsq(h, h->u + (size_t)m * h->S * h->Twp, (size_t)h->S * h->Twp, SC_C, st);
+        if (s == SWOPT_OK) s = read_scalars(h, st);
+        cu += h->Cm[m] * h->scal_host[SC_C];
+    }
+    if (s == SWOPT_OK) s = reduce_abs(h, c, nc_of(h), SC_C, st);
+    if (s == SWOPT_OK) s = reduce_tv(h, c, SC_D, st);
+    if (s == SWOPT_OK) s = read_scalars(h, st);
+    cudaFree(yt);
+    SW_TRY(s);
+    const double df = 0.5 * (ysq + cu - 2.0 * uy);
+    if (fit) *fit = df;
+    if (F) *F = df + lam_l1 * h->scal_host[SC_C] + lam_tv * h->scal_host[SC_D];
+    return SWOPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* swopt_last_error(void) { return g_err; }
+
+const char* swopt_version(void) { return "0.1.0"; }
+
+swopt_status swopt_create(const swopt_geometry* geom, const double* K_host,
+                          const swopt_switching* sw, swopt_handle** out)
+{
+    clear_error();
+    if (!out) {
+        set_error("null output pointer");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!geom || !K_host || !sw || !sw->kappa_host || !sw->eps_bar_host || !sw->eps_off_host) {
+        set_error("null geometry, kernel or switching pointer");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    const swopt_geometry& g = *geom;
+    if (g.X < 1 || g.X > 4096 || g.Y < 1 || g.Y > 4096 || g.Z < 1 || g.Z > 1024 || g.T < 1 ||
+        g.T > 8192 || g.N < 1 || g.N > 4096 || g.P < 1 || g.P > 8 || g.k < 1 || g.k > 63 ||
+        (g.k % 2) == 0 || g.pulses_per_cycle < 1) {
+        set_error("geometry out of range (X=%d Y=%d Z=%d T=%d N=%d P=%d k=%d cycle=%d)", g.X, g.Y,
+                  g.Z, g.T, g.N, g.P, g.k, g.pulses_per_cycle);
+        return SWOPT_ERR_SHAPE;
+    }
+    if (!is_fin(g.dz_mm) || g.dz_mm <= 0 || !is_fin(sw->mu_per_mm)) {
+        set_error("invalid dz_mm or mu_per_mm");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    for (int p = 0; p < g.P; ++p)
+        if (!is_fin(sw->kappa_host[p]) || !is_fin(sw->eps_bar_host[p]) ||
+            !is_fin(sw->eps_off_host[p])) {
+            set_error("non-finite switching parameter for species %d", p);
+            return SWOPT_ERR_INVALID_ARG;
+        }
+    const size_t kn = (size_t)g.Z * g.k * g.k * g.T;
+    int tmin = g.T, tmax = -1;
+    int64_t nnz = 0;
+    for (size_t i = 0; i < kn; ++i) {
+        const double v = K_host[i];
+        if (!is_fin(v)) {
+            set_error("non-finite kernel entry at %zu", i);
+            return SWOPT_ERR_INVALID_ARG;
+        }
+        if (v != 0.0) {
+            const int t = (int)(i % g.T);
+            tmin = std::min(tmin, t);
+            tmax = std::max(tmax, t);
+            ++nnz;
+        }
+    }
+    if (nnz == 0) {
+        set_error("the kernel is identically zero");
+        return SWOPT_ERR_SHAPE;
+    }
+
+    swopt_handle* h = new swopt_handle();
+    h->X = g.X; h->Y = g.Y; h->Z = g.Z; h->T = g.T; h->N = g.N; h->P = g.P; h->k = g.k;
+    h->r = g.k / 2; h->ncyc = g.pulses_per_cycle; h->dz_mm = g.dz_mm; h->mu = sw->mu_per_mm;
+    h->kappa.assign(sw->kappa_host, sw->kappa_host + g.P);
+    h->eps_bar.assign(sw->eps_bar_host, sw->eps_bar_host + g.P);
+    h->eps_off.assign(sw->eps_off_host, sw->eps_off_host + g.P);
+    h->S = g.X * g.Y;
+    h->Q = std::min(g.N, g.pulses_per_cycle);
+    h->nnz = nnz;
+    h->t0 = tmin & ~3;
+    h->tw = tmax - h->t0 + 1;
+    h->Twp = ((h->tw + TCHUNK - 1) / TCHUNK) * TCHUNK;
+    h->nTc = h->Twp / TCHUNK;
+    h->Zp = ((g.Z + JCHUNK - 1) / JCHUNK) * JCHUNK;
+    h->nJc = h->Zp / JCHUNK;
+    h->K64.assign(K_host, K_host + kn);
+    cudaGetDevice(&h->device);
+
+    // switching states: S[m][p][j] for m < Q (Eq. final-H)
+    h->phi.resize(g.Z);
+    for (int j = 0; j < g.Z; ++j) h->phi[j] = std::exp(-h->mu * j * h->dz_mm);
+    h->Sm64.resize((size_t)h->Q * g.P * g.Z);
+    h->Cm.assign(h->Q, 0);
+    for (int n = 0; n < g.N; ++n) h->Cm[n % h->ncyc]++;
+    for (int m = 0; m < h->Q; ++m)
+        for (int p = 0; p < g.P; ++p)
+            for (int j = 0; j < g.Z; ++j) {
+                const double ph = h->phi[j];
+                h->Sm64[((size_t)m * g.P + p) * g.Z + j] =
+                    ph * (h->eps_bar[p] * std::exp(-h->kappa[p] * ph * m) + h->eps_off[p]);
+            }
+
+    // FP32 kernel copies and band masks
+    const int kk = g.k * g.k;
+    std::vector<float> Kf((size_t)g.Z * kk * h->Twp, 0.f);
+    for (int j = 0; j < g.Z; ++j)
+        for (int d = 0; d < kk; ++d)
+            for (int w = 0; w < h->Twp; ++w) {
+                const int t = h->t0 + w;
+                if (t < g.T)
+                    Kf[((size_t)j * kk + d) * h->Twp + w] =
+                        (float)K_host[((size_t)j * kk + d) * g.T + t];
+            }
+    std::vector<uint8_t> fm((size_t)g.Z * kk * h->nTc, 0);
+    for (size_t jd = 0; jd < (size_t)g.Z * kk; ++jd)
+        for (int tc = 0; tc < h->nTc; ++tc) {
+            uint8_t msk = 0;
+            for (int q = 0; q < 4; ++q)
+                for (int i = 0; i < 8; ++i)
+                    if (Kf[jd * h->Twp + tc * TCHUNK + 8 * q + i] != 0.f) msk |= (uint8_t)(1u << q);
+            fm[jd * h->nTc + tc] = msk;
+        }
+    std::vector<float> Ka((size_t)kk * h->Twp * h->Zp, 0.f);
+    for (int j = 0; j < g.Z; ++j)
+        for (int d = 0; d < kk; ++d)
+            for (int w = 0; w < h->Twp; ++w)
+                Ka[((size_t)d * h->Twp + w) * h->Zp + j] = Kf[((size_t)j * kk + d) * h->Twp + w];
+    std::vector<uint8_t> am((size_t)kk * h->Twp * h->nJc, 0);
+    for (size_t dw = 0; dw < (size_t)kk * h->Twp; ++dw)
+        for (int jz = 0; jz < h->nJc; ++jz) {
+            uint8_t msk = 0;
+            for (int q = 0; q < 4; ++q)
+                for (int i = 0; i < 8; ++i)
+                    if (Ka[dw * h->Zp + jz * JCHUNK + 8 * q + i] != 0.f) msk |= (uint8_t)(1u << q);
+            am[dw * h->nJc + jz] = msk;
+        }
+    std::vector<float> Smf(h->Sm64.begin(), h->Sm64.end());
+    std::vector<float> Cmf(h->Cm.begin(), h->Cm.end());
+
+    swopt_status s = SWOPT_OK;
+    auto step = [&](swopt_status v) { if (s == SWOPT_OK) s = v; };
+    step(dalloc(&h->Kf, Kf.size()));
+    step(dalloc(&h->Ka, Ka.size()));
+    step(dalloc(&h->fmask, fm.size()));
+    step(dalloc(&h->amask, am.size()));
+    step(dalloc(&h->Sm, Smf.size()));
+    step(dalloc(&h->Cmf, Cmf.size()));
+    step(dalloc(&h->b, nb_of(h)));
+    step(dalloc(&h->u, nu_of(h)));
+    step(dalloc(&h->g, nb_of(h)));
+    h->red_cap = std::max({4096, simt_forward_blocks(h) + 64, h->Q * h->P * h->Z + 64});
+    step(dalloc(&h->red, (size_t)h->red_cap));
+    step(dalloc(&h->scal, (size_t)SC_COUNT));
+    if (s == SWOPT_OK) {
+        cudaError_t e = cudaMallocHost((void**)&h->scal_host, SC_COUNT * sizeof(double));
+        if (e != cudaSuccess) {
+            set_error("cudaMallocHost failed: %s", cudaGetErrorString(e));
+            s = SWOPT_ERR_OOM;
+        }
+    }
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        if (s != SWOPT_OK) return;
+        cudaError_t e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            set_error("cudaMemcpy failed: %s", cudaGetErrorString(e));
+            s = SWOPT_ERR_CUDA;
+        }
+    };
+    up(h->Kf, Kf.data(), Kf.size() * sizeof(float));
+    up(h->Ka, Ka.data(), Ka.size() * sizeof(float));
+    up(h->fmask, fm.data(), fm.size());
+    up(h->amask, am.data(), am.size());
+    up(h->Sm, Smf.data(), Smf.size() * sizeof(float));
+    up(h->Cmf, Cmf.data(), Cmf.size() * sizeof(float));
+    if (s == SWOPT_OK) {
+        cudaError_t e = cudaMemset(h->scal, 0, SC_COUNT * sizeof(double));
+        if (e != cudaSuccess) {
+            set_error("cudaMemset failed: %s", cudaGetErrorString(e));
+            s = SWOPT_ERR_CUDA;
+        }
+    }
+    if (s != SWOPT_OK) {
+        release_all(h);
+        delete h;
+        return s;
+    }
+    *out = h;
+    return SWOPT_OK;
+}
+
+swopt_status swopt_destroy(swopt_handle* h)
+{
+    clear_error();
+    if (!h) return SWOPT_OK;
+    release_all(h);
+    delete h;
+    return SWOPT_OK;
+}
+
+swopt_status swopt_set_precision(swopt_handle* h, int precision)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (precision < SWOPT_PREC_FP32 || precision > SWOPT_PREC_BF16X3) {
+        set_error("unknown precision %d", precision);
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    if (precision != SWOPT_PREC_FP32) {
+        const int prev = h->precision;
+        h->precision = precision;
+        swopt_status s = tc_prepare(h);
+        if (s != SWOPT_OK) {
+            h->precision = prev;
+            return s;
+        }
+    }
+    h->precision = precision;
+    return SWOPT_OK;
+}
+
+swopt_status swopt_forward(swopt_handle* h, const float* c_dev, float* y_dev, void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!c_dev || !y_dev) {
+        set_error("null c or y");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    SW_TRY(launch_states(h, c_dev, h->b, st));
+    SW_TRY(op_A(h, h->b, h->u, nullptr, nullptr, 0, st));
+    return launch_expand(h, h->u, y_dev, st);
+}
+
+swopt_status swopt_adjoint(swopt_handle* h, const float* y_dev, float* c_dev, void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!c_dev || !y_dev) {
+        set_error("null c or y");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    SW_TRY(launch_fold(h, y_dev, h->u, st));
+    SW_TRY(op_AT(h, h->u, h->g, st));
+    return launch_pt(h, h->g, nullptr, 0.f, c_dev, 0, st);
+}
+
+swopt_status swopt_prox_l1(swopt_handle* h, float* x_dev, float thresh, int nonneg, void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!x_dev || !std::isfinite(thresh) || thresh < 0) {
+        set_error("null x or invalid threshold");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    return prox_l1(h, x_dev, thresh, nonneg, (cudaStream_t)stream);
+}
+
+swopt_status swopt_prox_tv(swopt_handle* h, const float* z_dev, float* x_dev, float tau,
+                           int inner_iters, int momentum, void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!z_dev || !x_dev || z_dev == x_dev || !std::isfinite(tau) || tau < 0 || inner_iters < 0 ||
+        inner_iters > 1000000 || momentum < 0 || momentum > 2) {
+        set_error("invalid prox_tv arguments");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (inner_iters == 0) {
+        SW_CUDA(cudaMemcpyAsync(x_dev, z_dev, nc_of(h) * sizeof(float), cudaMemcpyDeviceToDevice,
+                                st));
+        return SWOPT_OK;
+    }
+    SW_TRY(ensure_tv_buffers(h));
+    const std::vector<double> betas = momentum_betas(inner_iters, momentum);
+    SW_TRY(prox_tv_iters(h, z_dev, tau, inner_iters, betas.data(), st));
+    return prox_tv_finish(h, z_dev, x_dev, st);
+}
+
+swopt_status swopt_lipschitz(swopt_handle* h, const float* v0_dev, int iters, double* L_out,
+                             void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!L_out || iters < 1 || iters > 1000000) {
+        set_error("invalid lipschitz arguments");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    return lipschitz_impl(h, v0_dev, iters, L_out, (cudaStream_t)stream);
+}
+
+swopt_status swopt_fista_init(swopt_handle* h, const float* y_dev, const swopt_solve_params* prm,
+                              void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!y_dev) {
+        set_error("null y");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    SW_TRY(validate_params(prm));
+    cudaStream_t st = (cudaStream_t)stream;
+    h->fista_ready = false;
+    SW_TRY(ensure_vectors(h));
+    SW_TRY(ensure_ytil(h));
+    if (prm->lambda_tv > 0 && prm->inner_iters > 0) SW_TRY(ensure_tv_buffers(h));
+    h->prm = *prm;
+    h->inner_beta = momentum_betas(prm->inner_iters, prm->inner_momentum);
+    SW_TRY(launch_fold(h, y_dev, h->ytil, st));
+    SW_TRY(reduce_sumsq(h, y_dev, (size_t)h->N * h->S * h->T, SC_YSQ, st));
+    if (prm->step > 0) {
+        h->step = prm->step;
+    } else {
+        double L = 0.0;
+        SW_TRY(lipschitz_impl(h, nullptr, prm->power_iters, &L, st));
+        if (!(L > 0) || !std::isfinite(L)) {
+            set_error("power iteration gave a non-positive estimate %g", L);
+            return SWOPT_ERR_DEVICE_CHECK;
+        }
+        h->step = 1.0 / L;
+    }
+    SW_CUDA(cudaMemsetAsync(h->c, 0, nc_of(h) * sizeof(float), st));
+    SW_CUDA(cudaMemsetAsync(h->xi, 0, nc_of(h) * sizeof(float), st));
+    SW_TRY(fista_reset_scalars(h, st));
+    h->fista_ready = true;
+    return SWOPT_OK;
+}
+
+swopt_status swopt_fista_step(swopt_handle* h, int iters, void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!h->fista_ready) {
+        set_error("swopt_fista_init has not been called");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    if (iters < 0) {
+        set_error("negative iteration count");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < iters; ++i) SW_TRY(fista_iteration(h, st));
+    return SWOPT_OK;
+}
+
+swopt_status swopt_fista_get(swopt_handle* h, float* c_dev, void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!c_dev || !h->fista_ready) {
+        set_error("null c or no FISTA state");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    SW_CUDA(cudaMemcpyAsync(c_dev, h->c, nc_of(h) * sizeof(float), cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)stream));
+    return SWOPT_OK;
+}
+
+swopt_status swopt_solve(swopt_handle* h, const float* y_dev, float* c_dev,
+                         const swopt_solve_params* prm, swopt_solve_stats* stats, void* stream)
+{
+    SW_TRY(swopt_fista_init(h, y_dev, prm, stream));
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool tests = prm->eps1 > 0 || prm->eps2 > 0 || prm->history_host;
+    int it = 0;
+    double f_prev = INFINITY;
+    for (; it < prm->max_iters; ++it) {
+        if (tests && prm->eps2 > 0)
+            SW_CUDA(cudaMemcpyAsync(h->tmp, h->xi, nc_of(h) * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, st));
+        SW_TRY(fista_iteration(h, st));
+        if (!tests) continue;
+        double F = 0.0;
+        if (prm->eps1 > 0 || prm->history_host)
+            SW_TRY(objective_impl(h, h->c, y_dev, prm->lambda_l1, prm->lambda_tv, &F, nullptr, st));
+        if (prm->history_host) prm->history_host[it] = F;
+        bool stop = false;
+        if (it >= 1 && prm->eps1 > 0 && std::fabs(F - f_prev) < prm->eps1 * std::fabs(f_prev))
+            stop = true;
+        if (it >= 1 && prm->eps2 > 0) {
+            // ||xi_{k+1} - xi_k|| / ||xi_k||
+            SW_TRY(reduce_sumsq(h, h->tmp, nc_of(h), SC_C, st));
+            SW_TRY(reduce_sumsq(h, h->xi, nc_of(h), SC_D, st));
+            SW_TRY(reduce_dot(h, h->xi, h->tmp, nc_of(h), SC_A, st));
+            SW_TRY(read_scalars(h, st));
+            const double a = h->scal_host[SC_D], b = h->scal_host[SC_C], ab = h->scal_host[SC_A];
+            const double diff = std::sqrt(std::max(0.0, a + b - 2.0 * ab));
+            if (b > 0 && diff < prm->eps2 * std::sqrt(b)) stop = true;
+        }
+        f_prev = F;
+        if (stop) {
+            ++it;
+            break;
+        }
+    }
+    SW_CUDA(cudaMemcpyAsync(c_dev, h->c, nc_of(h) * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (stats) {
+        stats->iters = it;
+        stats->step = h->step;
+        SW_TRY(objective_impl(h, h->c, y_dev, prm->lambda_l1, prm->lambda_tv, &stats->objective,
+                              &stats->data_fit, st));
+    } else {
+        SW_CUDA(cudaStreamSynchronize(st));
+    }
+    return SWOPT_OK;
+}
+
+swopt_status swopt_objective(swopt_handle* h, const float* c_dev, const float* y_dev,
+                             double lambda_l1, double lambda_tv, double* F, double* fit,
+                             void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!c_dev || !y_dev || !is_fin(lambda_l1) || !is_fin(lambda_tv)) {
+        set_error("invalid objective arguments");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    return objective_impl(h, c_dev, y_dev, lambda_l1, lambda_tv, F, fit, (cudaStream_t)stream);
+}
+
+swopt_status swopt_param_grad(swopt_handle* h, const float* c_dev, const float* y_dev,
+                              double* dkappa_host, double* dmu, void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!c_dev || !y_dev || !dkappa_host || !dmu) {
+        set_error("null argument");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // residual folded over equal states: C_m (A P c)_m - sum_{n=m mod cycle} y_n
+    float* yt = nullptr;
+    SW_TRY(dalloc(&yt, nu_of(h)));
+    swopt_status s = launch_fold(h, y_dev, yt, st);
+    if (s == SWOPT_OK) s = launch_states(h, c_dev, h->b, st);
+    if (s == SWOPT_OK) s = op_A(h, h->b, h->u, yt, nullptr, 1, st);
+    if (s == SWOPT_OK) s = op_AT(h, h->u, h->g, st);
+    if (s == SWOPT_OK) s = param_weights(h, h->g, c_dev, 0, st);
+    const size_t nw = (size_t)h->Q * h->P * h->Z;
+    std::vector<double> W(nw);
+    if (s == SWOPT_OK) {
+        cudaError_t e = cudaMemcpyAsync(W.data(), h->red, nw * sizeof(double),
+                                        cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_error("param_grad copy failed: %s", cudaGetErrorString(e));
+            s = SWOPT_ERR_CUDA;
+        }
+    }
+    cudaFree(yt);
+    SW_TRY(s);
+    // d/dtheta of S[m][p][j] = Phi_j (eps_bar_p e^{-kappa_p Phi_j m} + eps_off_p),
+    // Phi_j = exp(-mu j dz)
+    double dm = 0.0;
+    for (int p = 0; p < h->P; ++p) dkappa_host[p] = 0.0;
+    for (int m = 0; m < h->Q; ++m)
+        for (int p = 0; p < h->P; ++p)
+            for (int j = 0; j < h->Z; ++j) {
+                const double ph = h->phi[j];
+                const double e = std::exp(-h->kappa[p] * ph * m);
+                const double w = W[((size_t)m * h->P + p) * h->Z + j];
+                const double dS_dk = ph * h->eps_bar[p] * e * (-ph * m);
+                const double dS_dphi =
+                    h->eps_bar[p] * e + h->eps_off[p] + ph * h->eps_bar[p] * e * (-h->kappa[p] * m);
+                const double dphi_dmu = -(double)j * h->dz_mm * ph;
+                dkappa_host[p] += w * dS_dk;
+                dm += w * dS_dphi * dphi_dmu;
+            }
+    *dmu = dm;
+    return SWOPT_OK;
+}
+
+swopt_status swopt_profile_enable(swopt_handle* h, int on)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    h->profile = on != 0;
+    return SWOPT_OK;
+}
+
+swopt_status swopt_profile_read(swopt_handle* h, int kernel_id, double* total_ms,
+                                int64_t* launches, double* flops_per_launch)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (kernel_id < 0 || kernel_id > 1) {
+        set_error("kernel_id must be 0 (A) or 1 (A^T)");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    for (auto& r : h->prof) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) {
+            set_error("cudaEventSynchronize failed: %s", cudaGetErrorString(e));
+            return SWOPT_ERR_CUDA;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        h->prof_ms[r.kernel] += ms;
+        h->prof_n[r.kernel] += 1;
+        h->event_pool.push_back(r.a);
+        h->event_pool.push_back(r.b);
+    }
+    h->prof.clear();
+    if (total_ms) *total_ms = h->prof_ms[kernel_id];
+    if (launches) *launches = h->prof_n[kernel_id];
+    if (flops_per_launch) *flops_per_launch = 2.0 * (double)h->Q * h->S * (double)h->nnz;
+    h->prof_ms[kernel_id] = 0;
+    h->prof_n[kernel_id] = 0;
+    return SWOPT_OK;
+}
+
+swopt_status swopt_launch_count(swopt_handle* h, int64_t* count)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!count) {
+        set_error("null count");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    *count = h->launches;
+    return SWOPT_OK;
+}
+
+swopt_status swopt_info(swopt_handle* h, int* t0, int* tw, int* states, int64_t* kernel_nnz)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (t0) *t0 = h->t0;
+    if (tw) *tw = h->tw;
+    if (states) *states = h->Q;
+    if (kernel_nnz) *kernel_nnz = h->nnz;
+    return SWOPT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,197 @@
+// Internal declarations shared by the swopt CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "swopt.h"
+
+namespace swopt {
+
+// ---------------------------------------------------------------------------
+// Error reporting (thread-local message of the last failed call).
+// ---------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define SW_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            ::swopt::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                               __FILE__, __LINE__);                                \
+            return e_ == cudaErrorMemoryAllocation ? SWOPT_ERR_OOM : SWOPT_ERR_CUDA; \
+        }                                                                          \
+    } while (0)
+
+#define SW_LAUNCHED(h)                                                             \
+    do {                                                                           \
+        cudaError_t e_ = cudaGetLastError();                                       \
+        if (e_ != cudaSuccess) {                                                   \
+            ::swopt::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), \
+                               __FILE__, __LINE__);                                \
+            return SWOPT_ERR_CUDA;                                                 \
+        }                                                                          \
+        (h)->launches++;                                                           \
+    } while (0)
+
+#define SW_TRY(expr)                                                               \
+    do {                                                                           \
+        swopt_status s_ = (expr);                                                  \
+        if (s_ != SWOPT_OK) return s_;                                             \
+    } while (0)
+
+// Time samples are processed in chunks of 32 (a warp's worth of outputs in
+// the FP32 kernels, two 16-wide N tiles on the tensor cores).
+constexpr int TCHUNK = 32;
+// Depths are processed in chunks of 32 by the FP32 adjoint.
+constexpr int JCHUNK = 32;
+// Lateral tile of the FP32 contraction kernels: 16 x 16 scan positions.
+constexpr int TILE = 16;
+
+struct DeviceBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// Tensor-core operator data (built lazily on first BF16 use).
+struct TcOperator;
+
+struct ProfileRec {
+    cudaEvent_t a, b;
+    int kernel;
+};
+
+}  // namespace swopt
+
+struct swopt_handle {
+    // geometry
+    int X, Y, Z, T, N, P, k, r, ncyc;
+    double dz_mm, mu;
+    std::vector<double> kappa, eps_bar, eps_off;
+    int S;       // X * Y
+    int Q;       // distinct switching states min(N, ncyc)
+    int t0;      // first sample of the time window
+    int tw;      // nonzero extent of the window (t0 + tw - 1 = last nonzero sample)
+    int Twp;     // padded window length, multiple of TCHUNK
+    int nTc;     // Twp / TCHUNK
+    int Zp;      // Z padded to a multiple of JCHUNK
+    int nJc;     // Zp / JCHUNK
+    int64_t nnz; // nonzero kernel entries
+    std::vector<double> K64;      // host copy [Z][k][k][T]
+    std::vector<double> phi;      // [Z]
+    std::vector<double> Sm64;     // [Q][P][Z] switching weights of the states
+    std::vector<int> Cm;          // [Q] pulses per state
+    int precision = SWOPT_PREC_FP32;
+    int device = 0;
+
+    // FP32 operator data
+    float* Kf = nullptr;          // [Z][k][k][Twp] forward kernel, window-padded
+    float* Ka = nullptr;          // [k*k][Twp][Zp] adjoint kernel (depth fastest)
+    uint8_t* fmask = nullptr;     // [Z*k*k][nTc] 8-sample nonzero sub-block masks
+    uint8_t* amask = nullptr;     // [k*k][Twp][nJc] 8-depth nonzero sub-block masks
+    float* Sm = nullptr;          // [Q][P][Z]
+    float* Cmf = nullptr;         // [Q]
+
+    // operator workspaces
+    float* b = nullptr;           // [Q][Y][X][Z] state images (input of A)
+    float* u = nullptr;           // [Q][Y][X][Twp] A output / folded residual
+    float* g = nullptr;           // [Q][Y][X][Z] A^T output (before P^T)
+    float* ytil = nullptr;        // [Q][Y][X][Twp] pulse-folded measurements
+    double* red = nullptr;        // reduction partials
+    int red_cap = 0;              // capacity in doubles
+    double* scal = nullptr;       // small FP64 device scalars
+    double* scal_host = nullptr;  // pinned host mirror
+
+    // FISTA state
+    bool fista_ready = false;
+    swopt_solve_params prm{};
+    double step = 0.0;
+    double y_sq = 0.0;            // ||y||^2 of the bound measurements
+    float* c = nullptr;           // [P][Y][X][Z] current c_k
+    float* xi = nullptr;          // momentum iterate
+    float* zin = nullptr;         // gradient-step output (prox input)
+    float* tvu = nullptr;         // [3][P][Y][X][Z] dual iterate
+    float* tvr0 = nullptr;        // [3][..] extrapolated dual (ping)
+    float* tvr1 = nullptr;        // [3][..] (pong)
+    float* tmp = nullptr;         // [P][Y][X][Z] scratch
+    std::vector<double> inner_beta; // momentum coefficients of Algorithm 2
+
+    // tensor-core path
+    swopt::TcOperator* tc = nullptr;
+
+    // instrumentation
+    bool profile = false;
+    std::vector<swopt::ProfileRec> prof;
+    std::vector<cudaEvent_t> event_pool;
+    double prof_ms[2] = {0, 0};
+    int64_t prof_n[2] = {0, 0};
+    int64_t launches = 0;
+};
+
+namespace swopt {
+
+inline size_t nc_of(const swopt_handle* h) { return (size_t)h->P * h->S * h->Z; }
+inline size_t nb_of(const swopt_handle* h) { return (size_t)h->Q * h->S * h->Z; }
+inline size_t nu_of(const swopt_handle* h) { return (size_t)h->Q * h->S * h->Twp; }
+inline int grid_for(size_t n, int block) {
+    size_t g = (n + block - 1) / block;
+    return (int)(g > 2147483647ull ? 2147483647ull : g);
+}
+
+// FP32 contraction kernels (operator_simt.cu).
+// out = (scale ? Cm[m] : 1) * (A b)[m] - (ytil ? ytil[m] : 0); partials (optional):
+// per-block FP64 sums of Cm*(Ab)^2 - 2*(Ab)*ytil.
+swopt_status simt_forward(swopt_handle* h, const float* b, float* u, const float* ytil,
+                          double* partials, int scale, cudaStream_t st);
+swopt_status simt_adjoint(swopt_handle* h, const float* u, float* g, cudaStream_t st);
+int simt_forward_blocks(const swopt_handle* h);
+
+// Tensor-core contraction kernels (operator_tc.cu).
+swopt_status tc_prepare(swopt_handle* h);
+void tc_release(swopt_handle* h);
+swopt_status tc_forward(swopt_handle* h, const float* b, float* u, const float* ytil,
+                        double* partials, int scale, cudaStream_t st);
+swopt_status tc_adjoint(swopt_handle* h, const float* u, float* g, cudaStream_t st);
+int tc_forward_blocks(const swopt_handle* h);
+
+// Elementwise / layout kernels (operator_simt.cu).
+swopt_status launch_states(swopt_handle* h, const float* c, float* b, cudaStream_t st);
+swopt_status launch_expand(swopt_handle* h, const float* u, float* y, cudaStream_t st);
+swopt_status launch_fold(swopt_handle* h, const float* y, float* ytil, cudaStream_t st);
+// out = sum_m Sm[m][p][j] g[m] (mode 0); out = xi - alpha * that (mode 1)
+swopt_status launch_pt(swopt_handle* h, const float* g, const float* xi, float alpha,
+                       float* out, int mode, cudaStream_t st);
+
+// Proximal / FISTA / reduction kernels (prox.cu).
+swopt_status prox_l1(swopt_handle* h, float* x, float thresh, int nonneg, cudaStream_t st);
+swopt_status prox_tv_iters(swopt_handle* h, const float* z, float tau, int iters,
+                           const double* betas, cudaStream_t st);
+swopt_status prox_tv_finish(swopt_handle* h, const float* z, float* x, cudaStream_t st);
+swopt_status fista_finish(swopt_handle* h, const float* z, bool use_tv, float theta,
+                          cudaStream_t st);
+swopt_status fista_scalars(swopt_handle* h, int momentum, cudaStream_t st);
+swopt_status fista_reset_scalars(swopt_handle* h, cudaStream_t st);
+// FP64 reductions, result written to h->scal[slot]
+swopt_status reduce_sumsq(swopt_handle* h, const float* x, size_t n, int slot, cudaStream_t st);
+swopt_status reduce_dot(swopt_handle* h, const float* x, const float* y, size_t n, int slot,
+                        cudaStream_t st);
+swopt_status reduce_abs(swopt_handle* h, const float* x, size_t n, int slot, cudaStream_t st);
+swopt_status reduce_tv(swopt_handle* h, const float* x, int slot, cudaStream_t st);
+swopt_status reduce_partials(swopt_handle* h, const double* parts, int count, int slot,
+                             cudaStream_t st);
+swopt_status scale_by_inv_sqrt(swopt_handle* h, const float* in, float* out, size_t n, int slot,
+                               cudaStream_t st);
+swopt_status fill_counter_random(swopt_handle* h, float* x, size_t n, uint64_t seed,
+                                 cudaStream_t st);
+swopt_status param_weights(swopt_handle* h, const float* g, const float* c, int slot0,
+                           cudaStream_t st);
+
+// Instrumentation
+void prof_begin(swopt_handle* h, int kernel, cudaStream_t st, ProfileRec* rec);
+void prof_end(swopt_handle* h, ProfileRec* rec, cudaStream_t st);
+
+}  // namespace swopt

@@ -1,0 +1,96 @@
+"""The C-ABI library: it builds for sm_103a, loads, exports every entry point
+declared in include/swopt.h, and rejects bad arguments on the host before
+any GPU work (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2510_23739_gb300 as sw
+from paper_2510_23739_gb300 import build as swbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "swopt.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|swopt_status)\s+(swopt_\w+)\s*\(",
+                                 text, re.M)))
+
+
+def test_library_targets_sm_103a_and_loads():
+    path = swbuild.build()
+    assert os.path.exists(path)
+    assert any("arch=compute_103a,code=sm_103a" in a for a in swbuild.ARCH)
+    sw.lib()
+
+
+def test_every_declared_symbol_is_exported():
+    names = _declared()
+    assert len(names) >= 20
+    L = ctypes.CDLL(swbuild.build())
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # and the binding knows every one of them
+    assert set(names) <= set(sw._SIGS)
+
+
+def _geom(**kw):
+    g = sw._Geometry(8, 8, 4, 16, 4, 2, 3, 2, 0.01)
+    for k, v in kw.items():
+        setattr(g, k, v)
+    return g
+
+
+def _switching(P=2):
+    arrs = [np.array([0.1, 0.0][:P]), np.array([1.0, 0.0][:P]), np.array([0.0, 1.0][:P])]
+    dp = ctypes.POINTER(ctypes.c_double)
+    return sw._Switching(*(a.ctypes.data_as(dp) for a in arrs), 2.0), arrs
+
+
+def _create(g, K, s):
+    h = ctypes.c_void_p()
+    st = sw.lib().swopt_create(ctypes.byref(g) if g is not None else None,
+                               K.ctypes.data_as(ctypes.c_void_p) if K is not None else None,
+                               ctypes.byref(s) if s is not None else None, ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("field,value", [("k", 4), ("k", 0), ("X", 0), ("P", 9), ("T", 0),
+                                         ("pulses_per_cycle", 0), ("N", 0)])
+def test_create_rejects_bad_shapes(field, value):
+    s, keep = _switching()
+    g = _geom(**{field: value})
+    K = np.ones((max(g.Z, 1), max(g.k, 1), max(g.k, 1), max(g.T, 1)))
+    st, h = _create(g, K, s)
+    assert st == 2 and not h.value  # SWOPT_ERR_SHAPE
+    assert b"range" in sw.lib().swopt_last_error()
+
+
+def test_create_rejects_null_and_nonfinite():
+    s, keep = _switching()
+    g = _geom()
+    K = np.ones((4, 3, 3, 16))
+    assert _create(None, K, s)[0] == 1
+    assert _create(g, None, s)[0] == 1
+    assert _create(g, K, None)[0] == 1
+    K2 = K.copy()
+    K2[1, 1, 1, 3] = np.nan
+    assert _create(g, K2, s)[0] == 1
+    assert _create(_geom(dz_mm=-1.0), K, s)[0] == 1
+    # an all-zero kernel has no time window
+    st, _ = _create(g, np.zeros_like(K), s)
+    assert st == 2 and b"zero" in sw.lib().swopt_last_error()
+
+
+def test_null_handle_calls_fail_cleanly():
+    L = sw.lib()
+    assert L.swopt_destroy(None) == 0
+    assert L.swopt_forward(None, None, None, None) == 1
+    assert L.swopt_adjoint(None, None, None, None) == 1
+    assert L.swopt_set_precision(None, 0) == 1
+    assert L.swopt_fista_step(None, 1, None) == 1
+    assert b"null handle" in L.swopt_last_error()
+    assert L.swopt_version().decode().count(".") == 2

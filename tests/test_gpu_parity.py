@@ -1,0 +1,328 @@
+"""GPU parity: the CUDA library, called through the C-ABI, against the FP64
+oracle on the same seeded inputs.
+
+Tolerances (relative L2 unless stated): the FP32 operator <= 1e-5, proximal
+maps <= 1e-5, FISTA iterates after a fixed number of iterations <= 1e-4
+(all with the same step alpha on both sides).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2510_23739_gb300 as sw
+import synth
+from synth import Geometry, Switching
+
+pytestmark = pytest.mark.gpu
+
+TINY = synth.workload("tiny_16x16x24_T64_k7_N8_P2")
+MEDIUM = synth.workload("medium_64x64x64_T256_k15_N40_P2")
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float32, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+# ragged and degenerate shapes: tiles, depth chunks and windows with tails
+CASES = {
+    "tiny": (TINY.geom, TINY.sw, 0),
+    "ragged": (Geometry(X=13, Y=11, Z=37, T=57, N=7, P=3, k=5, pulses_per_cycle=3),
+               Switching((0.04, 0.09, 0.0), (1.0, 0.8, 0.0), (0.0, 0.1, 1.0), 3.0), 1),
+    "k1_one_pulse": (Geometry(X=17, Y=5, Z=3, T=20, N=1, P=1, k=1, pulses_per_cycle=5),
+                     Switching((0.0,), (0.0,), (1.0,), 0.0), 2),
+    "pulses_below_cycle": (Geometry(X=6, Y=9, Z=33, T=40, N=3, P=2, k=9, pulses_per_cycle=10),
+                           Switching((0.2, 0.0), (1.0, 0.0), (0.0, 1.0), 2.0), 3),
+    "single_column": (Geometry(X=1, Y=1, Z=5, T=33, N=4, P=2, k=3, pulses_per_cycle=2),
+                      Switching((0.3, 0.0), (1.0, 0.0), (0.0, 1.0), 1.0), 4),
+    "support_wider_than_grid": (Geometry(X=4, Y=3, Z=8, T=48, N=5, P=2, k=11, pulses_per_cycle=5),
+                                Switching((0.1, 0.0), (1.0, 0.0), (0.0, 1.0), 2.0), 5),
+}
+
+
+def _kernel(g, seed):
+    if g.k >= 3 and g.T >= 32:
+        try:
+            return synth.transducer_kernel(g, seed=seed)
+        except Exception:
+            pass
+    rng = np.random.default_rng(seed)
+    K = rng.standard_normal(g.k_shape())
+    K[..., : g.T // 4] = 0.0  # a window that does not start at 0
+    return K
+
+
+@pytest.fixture(scope="module")
+def cases():
+    out = {}
+    for name, (g, s, seed) in CASES.items():
+        K = _kernel(g, seed)
+        if not np.any(K):
+            K = np.random.default_rng(seed).standard_normal(g.k_shape())
+        out[name] = (g, s, K, sw.Operator(g, K, s))
+    yield out
+    for v in out.values():
+        v[3].close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_forward_matches_oracle(cases, name):
+    g, s, K, op = cases[name]
+    c = np.random.default_rng(10).standard_normal(g.c_shape())
+    got = host(op.forward(dev(c)))
+    ref = oracle.forward(g, s, K, c)
+    assert rel(got, ref) <= 1e-5
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max() * 10
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_matches_oracle(cases, name):
+    g, s, K, op = cases[name]
+    yv = np.random.default_rng(11).standard_normal(g.y_shape())
+    got = host(op.adjoint(dev(yv)))
+    ref = oracle.adjoint(g, s, K, yv)
+    assert rel(got, ref) <= 1e-5
+
+
+def test_forward_of_phantom_matches_oracle(cases):
+    g, s, K, op = cases["tiny"]
+    c = synth.tube_phantom(g, TINY.tubes, seed=0, per_species=True)
+    assert rel(host(op.forward(dev(c))), oracle.forward(g, s, K, c)) <= 1e-5
+
+
+def test_adjoint_identity_on_gpu(cases):
+    g, s, K, op = cases["ragged"]
+    rng = np.random.default_rng(12)
+    for _ in range(20):
+        x = dev(rng.standard_normal(g.c_shape()))
+        y = dev(rng.standard_normal(g.y_shape()))
+        hx = op.forward(x)
+        lhs = float(torch.sum(hx.double() * y.double()))
+        rhs = float(torch.sum(x.double() * op.adjoint(y).double()))
+        scale = float(hx.double().norm() * y.double().norm())
+        assert abs(lhs - rhs) <= 1e-6 * scale
+
+
+def test_operator_is_deterministic(cases):
+    g, s, K, op = cases["tiny"]
+    c = dev(np.random.default_rng(13).standard_normal(g.c_shape()))
+    a = op.forward(c)
+    b = op.forward(c)
+    assert torch.equal(a, b)
+    y = dev(np.random.default_rng(14).standard_normal(g.y_shape()))
+    assert torch.equal(op.adjoint(y), op.adjoint(y))
+
+
+@pytest.mark.parametrize("nonneg", [True, False])
+def test_prox_l1_matches_oracle(cases, nonneg):
+    g, s, K, op = cases["ragged"]
+    z = np.random.default_rng(15).standard_normal(g.c_shape())
+    x = dev(z)
+    op.prox_l1(x, 0.3, nonneg)
+    ref = oracle.prox_l1(z, 0.3, nonneg)
+    np.testing.assert_allclose(host(x), ref, atol=1e-6)
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged", "single_column"])
+@pytest.mark.parametrize("momentum", ["beck_teboulle", "paper_printed", "none"])
+def test_prox_tv_matches_oracle(cases, name, momentum):
+    g, s, K, op = cases[name]
+    z = np.random.default_rng(16).standard_normal(g.c_shape())
+    got = host(op.prox_tv(dev(z), 0.2, 10, momentum))
+    ref = oracle.prox_tv(z, 0.2, 10, momentum)
+    assert rel(got, ref) <= 1e-5
+
+
+def test_prox_tv_zero_iterations_and_zero_tau(cases):
+    g, s, K, op = cases["tiny"]
+    z = dev(np.random.default_rng(17).standard_normal(g.c_shape()))
+    assert torch.equal(op.prox_tv(z, 0.5, 0), z)
+    assert torch.equal(op.prox_tv(z, 0.0, 10), z)
+
+
+def _tiny_measurements(g, s, K, seed=0):
+    c_true = synth.tube_phantom(g, TINY.tubes, seed=seed, per_species=True)
+    clean = oracle.forward(g, s, K, c_true)
+    sigma = synth.noise_sigma(clean, TINY.snr_db)
+    return clean + sigma * synth.gaussian(g.y_shape(), seed + 100)
+
+
+@pytest.mark.parametrize("momentum", ["beck_teboulle", "paper_printed"])
+def test_fista_tiny_workload_matches_oracle(cases, momentum):
+    """The tiny workload's plain solve: 20 iterations, lambda_l1 = lambda_TV =
+    1e-3, 10 inner iterations, the same alpha on both sides."""
+    g, s, K, op = cases["tiny"]
+    y = _tiny_measurements(g, s, K)
+    L = oracle.power(g, s, K, synth.gaussian(g.c_shape(), 1), 100)
+    alpha = 1.0 / L
+    params = sw.SolveParams(step=alpha, lambda_l1=TINY.lam_l1, lambda_tv=TINY.lam_tv,
+                            inner_iters=TINY.inner, max_iters=TINY.iters, momentum=momentum,
+                            inner_momentum=momentum)
+    got, stats = op.solve(dev(y), params)
+    ref = oracle.fista(g, s, K, y, alpha, TINY.iters, TINY.lam_l1, TINY.lam_tv, TINY.inner,
+                       momentum=momentum, inner_momentum=momentum)
+    assert stats["iters"] == TINY.iters
+    assert rel(host(got), ref) <= 1e-4
+    F_ref, fit_ref = oracle.objective(g, s, K, ref, y, TINY.lam_l1, TINY.lam_tv)
+    assert stats["objective"] == pytest.approx(F_ref, rel=1e-4)
+
+
+def test_fista_ragged_matches_oracle(cases):
+    g, s, K, op = cases["ragged"]
+    rng = np.random.default_rng(18)
+    y = oracle.forward(g, s, K, np.maximum(rng.standard_normal(g.c_shape()), 0))
+    L = oracle.power(g, s, K, synth.gaussian(g.c_shape(), 2), 60)
+    params = sw.SolveParams(step=1.0 / L, lambda_l1=0.01, lambda_tv=0.02, inner_iters=5,
+                            max_iters=8)
+    got, _ = op.solve(dev(y), params)
+    ref = oracle.fista(g, s, K, y, 1.0 / L, 8, 0.01, 0.02, 5)
+    assert rel(host(got), ref) <= 1e-4
+
+
+def test_fista_steps_equal_solve(cases):
+    g, s, K, op = cases["tiny"]
+    y = dev(_tiny_measurements(g, s, K, 3))
+    params = sw.SolveParams(step=0.5 / oracle.power(g, s, K, synth.gaussian(g.c_shape(), 1), 50),
+                            max_iters=6)
+    a, _ = op.solve(y, params)
+    op.fista_init(y, params)
+    op.fista_step(2)
+    op.fista_step(4)
+    b = op.fista_get()
+    assert torch.equal(a, b)
+
+
+def test_lipschitz_matches_dense_eigenvalue():
+    g = Geometry(X=5, Y=4, Z=4, T=20, N=4, P=2, k=3, pulses_per_cycle=2)
+    s = Switching((0.5, 0.0), (1.0, 0.0), (0.0, 1.0), 2.0)
+    K = np.random.default_rng(19).standard_normal(g.k_shape())
+    nc = int(np.prod(g.c_shape()))
+    H = np.stack([oracle.forward(g, s, K, e.reshape(g.c_shape())).ravel()
+                  for e in np.eye(nc)], axis=1)
+    lam = np.linalg.eigvalsh(H.T @ H)[-1]
+    op = sw.Operator(g, K, s)
+    v0 = synth.gaussian(g.c_shape(), 4)
+    L_gpu = op.lipschitz(500, dev(v0))
+    assert L_gpu == pytest.approx(lam, rel=1e-4)
+    assert op.lipschitz(500) == pytest.approx(lam, rel=1e-4)  # built-in start vector
+    assert L_gpu == pytest.approx(oracle.power(g, s, K, v0, 500), rel=1e-5)
+    op.close()
+
+
+def test_objective_matches_oracle(cases):
+    g, s, K, op = cases["ragged"]
+    rng = np.random.default_rng(20)
+    c = np.maximum(rng.standard_normal(g.c_shape()), 0)
+    y = rng.standard_normal(g.y_shape())
+    F, fit = op.objective(dev(c), dev(y), 0.05, 0.07)
+    F_ref, fit_ref = oracle.objective(g, s, K, c, y, 0.05, 0.07)
+    assert F == pytest.approx(F_ref, rel=1e-6)
+    assert fit == pytest.approx(fit_ref, rel=1e-6)
+
+
+def test_param_grad_matches_oracle(cases):
+    g, s, K, op = cases["ragged"]
+    rng = np.random.default_rng(21)
+    c = np.maximum(rng.standard_normal(g.c_shape()), 0)
+    y = oracle.forward(g, s, K, c * 1.1) + 0.01 * rng.standard_normal(g.y_shape())
+    dk, dmu = op.param_grad(dev(c), dev(y))
+    dk_ref, dmu_ref = oracle.param_grad(g, s, K, c, y)
+    for p in range(g.P):
+        if dk_ref[p] != 0:
+            assert dk[p] == pytest.approx(dk_ref[p], rel=1e-4)
+    assert dmu == pytest.approx(dmu_ref, rel=1e-4)
+
+
+def test_solve_stops_on_eps2(cases):
+    g, s, K, op = cases["tiny"]
+    y = dev(_tiny_measurements(g, s, K, 5))
+    params = sw.SolveParams(step=0.0, power_iters=50, max_iters=300, eps2=0.05)
+    _, stats = op.solve(y, params, history=True)
+    assert 1 < stats["iters"] < 300
+    assert len(stats["history"]) == stats["iters"]
+    assert np.all(np.isfinite(stats["history"]))
+    params = sw.SolveParams(step=0.0, power_iters=50, max_iters=300, eps1=1e-3)
+    _, stats = op.solve(y, params, history=True)
+    assert 1 < stats["iters"] < 300
+    h = stats["history"]
+    assert abs(h[-1] - h[-2]) < 1e-3 * abs(h[-2])
+
+
+def test_invalid_arguments_raise(cases):
+    g, s, K, op = cases["tiny"]
+    with pytest.raises(ValueError):
+        op.forward(torch.zeros((1, 2, 3), device="cuda"))
+    with pytest.raises(sw.SwoptError):
+        sw._check(sw.lib().swopt_prox_l1(op._h, None, 0.1, 1, None))
+    with pytest.raises(sw.SwoptError):
+        op.prox_l1(dev(np.zeros(g.c_shape())), -1.0)
+
+
+# ---------------------------------------------------------------------------
+# Full size: the medium workload (64x64 scan, 64 depths, T=256, 15x15 support,
+# 40 pulses in 4 cycles, 2 species) in the launch configuration the benchmark
+# times, checked on sampled outputs that the oracle evaluates one by one.
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def medium():
+    g, s = MEDIUM.geom, MEDIUM.sw
+    K = synth.transducer_kernel(g, seed=0)
+    op = sw.Operator(g, K, s)
+    yield g, s, K, op
+    op.close()
+
+
+def test_medium_forward_sampled(medium):
+    g, s, K, op = medium
+    c = synth.tube_phantom(g, MEDIUM.tubes, seed=0)
+    y = host(op.forward(dev(c)))
+    rng = np.random.default_rng(22)
+    idx = np.stack([rng.integers(0, g.N, 48), rng.integers(0, g.Y, 48), rng.integers(0, g.X, 48)], 1)
+    idx[:4] = [[0, 0, 0], [g.N - 1, g.Y - 1, g.X - 1], [5, 0, g.X - 1], [39, g.Y - 1, 7]]
+    ref = oracle.forward_at(g, s, K, c, idx)
+    got = y[idx[:, 0], idx[:, 1], idx[:, 2]]
+    assert rel(got, ref) <= 1e-5
+
+
+def test_medium_adjoint_sampled(medium):
+    g, s, K, op = medium
+    yv = synth.gaussian(g.y_shape(), 23)
+    c = host(op.adjoint(dev(yv)))
+    rng = np.random.default_rng(24)
+    idx = np.stack([rng.integers(0, g.P, 48), rng.integers(0, g.Y, 48), rng.integers(0, g.X, 48),
+                    rng.integers(0, g.Z, 48)], 1)
+    idx[:2] = [[0, 0, 0, 0], [g.P - 1, g.Y - 1, g.X - 1, g.Z - 1]]
+    ref = oracle.adjoint_at(g, s, K, yv, idx)
+    got = c[idx[:, 0], idx[:, 1], idx[:, 2], idx[:, 3]]
+    assert rel(got, ref) <= 1e-5
+
+
+def test_medium_adjoint_identity_and_descent(medium):
+    g, s, K, op = medium
+    rng = np.random.default_rng(25)
+    x = dev(rng.standard_normal(g.c_shape()))
+    y = dev(rng.standard_normal(g.y_shape()))
+    hx = op.forward(x)
+    lhs = float(torch.sum(hx.double() * y.double()))
+    rhs = float(torch.sum(x.double() * op.adjoint(y).double()))
+    assert abs(lhs - rhs) <= 1e-6 * float(hx.double().norm() * y.double().norm())
+    # a few FISTA iterations on a noisy phantom lower the objective
+    c_true = dev(synth.tube_phantom(g, MEDIUM.tubes, seed=0))
+    ym = op.forward(c_true)
+    params = sw.SolveParams(step=0.0, power_iters=30, lambda_l1=MEDIUM.lam_l1,
+                            lambda_tv=MEDIUM.lam_tv, inner_iters=MEDIUM.inner, max_iters=5)
+    _, stats = op.solve(ym, params, history=True)
+    h = stats["history"]
+    F0 = 0.5 * float(ym.double().pow(2).sum())
+    assert h[-1] < h[0] < F0
