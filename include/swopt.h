@@ -218,6 +218,37 @@ swopt_status swopt_launch_count(swopt_handle* h, int64_t* count);
  * pulses_per_cycle) and the number of nonzero kernel entries. */
 swopt_status swopt_info(swopt_handle* h, int* t0, int* tw, int* states, int64_t* kernel_nnz);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free TV proximal map.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory themselves
+ * or through the library -- for example a host framework whose caching
+ * allocator owns all of the GPU's memory and forbids outside cudaMalloc, or
+ * a real-time loop that cannot afford cudaMalloc's implicit device-wide
+ * synchronisation after start-up.  It needs no handle.
+ *
+ * It computes the same map as swopt_prox_tv (same kernels, same arguments
+ * apart from the volume shape P x Y x X x Z given directly): z_dev and x_dev
+ * are caller-owned device arrays [P][Y][X][Z] that may not alias.  Its
+ * scratch (the three FGP dual arrays, 9 floats per volume element) is a
+ * file-scope static device array sized for SWOPT_PROX_TV_STATIC_MAX_ELEMS
+ * elements (18 MiB); every GPU that loads the library holds that array until
+ * the process exits.  Volumes with P*Y*X*Z above the limit are rejected with
+ * SWOPT_ERR_SHAPE and a message; the call never allocates (no cudaMalloc,
+ * cudaFree or allocating library routine).
+ *
+ * The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls in the process share the one array:
+ * calls whose GPU work overlaps in time (different streams, or host threads
+ * using the same device) race on it, so serialise them.  The array keeps
+ * the last call's contents, but nothing in it needs clearing: each call
+ * writes every scratch element before reading it.
+ * ------------------------------------------------------------------------- */
+#define SWOPT_PROX_TV_STATIC_MAX_ELEMS ((size_t)1 << 19)
+
+swopt_status swopt_prox_tv_static(int P, int Y, int X, int Z, const float* z_dev, float* x_dev,
+                                  float tau, int inner_iters, int momentum, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -106,6 +106,9 @@ _SIGS = {
     "swopt_launch_count": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "swopt_info": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "swopt_prox_tv_static": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int,
+                              ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
 }
 
 

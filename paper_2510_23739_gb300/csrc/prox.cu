@@ -413,4 +413,26 @@ swopt_status param_weights(swopt_handle* h, const float* g, const float* c, int 
     return SWOPT_OK;
 }
 
+// Launchers on caller-given buffers, without a handle (used by the
+// allocation-free entry point in noalloc.cu).
+cudaError_t fgp_iter_on(const float* z, const float* rin, float* rout, float* u, int P, int Y,
+                        int X, int Z, float tau, float beta, int first, cudaStream_t st)
+{
+    Vol v;
+    v.P = P; v.Y = Y; v.X = X; v.Z = Z;
+    v.L = (size_t)P * Y * X * Z;
+    fgp_iter_kernel<<<ew_grid(v.L), 256, 0, st>>>(z, rin, rout, u, v, tau, beta, first);
+    return cudaGetLastError();
+}
+
+cudaError_t fgp_finish_on(const float* z, const float* u, float* x, int P, int Y, int X, int Z,
+                          cudaStream_t st)
+{
+    Vol v;
+    v.P = P; v.Y = Y; v.X = X; v.Z = Z;
+    v.L = (size_t)P * Y * X * Z;
+    fgp_finish_kernel<<<ew_grid(v.L), 256, 0, st>>>(z, u, x, v);
+    return cudaGetLastError();
+}
+
 }  // namespace swopt

@@ -190,6 +190,13 @@ swopt_status fill_counter_random(swopt_handle* h, float* x, size_t n, uint64_t s
 swopt_status param_weights(swopt_handle* h, const float* g, const float* c, int slot0,
                            cudaStream_t st);
 
+// Handle-free launchers of one FGP iteration / the primal recovery on
+// caller-given buffers (prox.cu); the duals u, rin, rout have 3 components.
+cudaError_t fgp_iter_on(const float* z, const float* rin, float* rout, float* u, int P, int Y,
+                        int X, int Z, float tau, float beta, int first, cudaStream_t st);
+cudaError_t fgp_finish_on(const float* z, const float* u, float* x, int P, int Y, int X, int Z,
+                          cudaStream_t st);
+
 // Instrumentation
 void prof_begin(swopt_handle* h, int kernel, cudaStream_t st, ProfileRec* rec);
 void prof_end(swopt_handle* h, ProfileRec* rec, cudaStream_t st);
