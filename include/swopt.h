@@ -77,7 +77,9 @@ typedef struct {
  *  SWOPT_PREC_FP32 : FP32 FMA on the CUDA cores (the accuracy reference).
  *  SWOPT_PREC_BF16 : tcgen05 tensor cores, BF16 operands, FP32 accumulation.
  *  SWOPT_PREC_BF16X3: tcgen05 tensor cores on a two-term BF16 split of both
- *                    operands (hi*hi + hi*lo + lo*hi), FP32 accumulation. */
+ *                    operands (hi*hi + hi*lo + lo*hi), FP32 accumulation:
+ *                    about 16 significant bits per product (relative error
+ *                    of the operator ~1e-5). */
 typedef enum {
     SWOPT_PREC_FP32 = 0,
     SWOPT_PREC_BF16 = 1,
@@ -212,6 +214,18 @@ swopt_status swopt_profile_enable(swopt_handle* h, int on);
 swopt_status swopt_profile_read(swopt_handle* h, int kernel_id, double* total_ms,
                                 int64_t* launches, double* flops_per_launch);
 swopt_status swopt_launch_count(swopt_handle* h, int64_t* count);
+
+/* Synchronises `stream` and reports device-side failures of earlier calls on
+ * this handle: SWOPT_ERR_TIMEOUT if a tensor-core kernel gave up one of its
+ * bounded waits (the word is then cleared), else SWOPT_OK.  Calls that
+ * synchronise anyway (lipschitz, solve, objective, param_grad) check it too. */
+swopt_status swopt_check_device(swopt_handle* h, void* stream);
+
+/* FLOPs issued by one launch of the A (kernel_id 0) or A^T (1) contraction in
+ * the current precision: 2 x the multiply-adds the kernel executes,
+ * including the zero-padded parts of the kernel band it does not skip (for
+ * the split BF16 mode, all three products). */
+swopt_status swopt_issued_flops(swopt_handle* h, int kernel_id, double* flops);
 
 /* Operator facts: the time window [t0, t0 + tw) that holds every nonzero
  * kernel sample, the number of distinct switching states Q = min(N,

@@ -106,6 +106,9 @@ _SIGS = {
     "swopt_launch_count": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "swopt_info": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "swopt_check_device": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "swopt_issued_flops": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
+                           ctypes.c_int),
     "swopt_prox_tv_static": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int,
                               ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
@@ -352,6 +355,14 @@ class Operator:
         _check(lib().swopt_profile_read(self._h, int(kernel_id), ctypes.byref(ms), ctypes.byref(n),
                                         ctypes.byref(fl)))
         return {"total_ms": ms.value, "launches": n.value, "flops_per_launch": fl.value}
+
+    def check_device(self, stream=None):
+        _check(lib().swopt_check_device(self._h, _stream(stream)))
+
+    def issued_flops(self, kernel_id):
+        f = ctypes.c_double()
+        _check(lib().swopt_issued_flops(self._h, int(kernel_id), ctypes.byref(f)))
+        return f.value
 
     def launch_count(self):
         n = ctypes.c_int64()

@@ -155,41 +155,64 @@ swopt_status ensure_ytil(swopt_handle* h)
     return SWOPT_OK;
 }
 
+// Device-side failures recorded by the kernels (a bounded wait that gave up).
+swopt_status device_errors(swopt_handle* h)
+{
+    const int w = tc_error_word(h);
+    if (w > 0) {
+        set_error("a tensor-core kernel gave up a bounded wait (code %d)", w);
+        return SWOPT_ERR_TIMEOUT;
+    }
+    if (w < 0) {
+        set_error("reading the device error word failed");
+        return SWOPT_ERR_CUDA;
+    }
+    return SWOPT_OK;
+}
+
 swopt_status read_scalars(swopt_handle* h, cudaStream_t st)
 {
     SW_CUDA(cudaMemcpyAsync(h->scal_host, h->scal, SC_COUNT * sizeof(double),
                             cudaMemcpyDeviceToHost, st));
     SW_CUDA(cudaStreamSynchronize(st));
-    return SWOPT_OK;
+    return device_errors(h);
 }
 
 bool use_tc(const swopt_handle* h) { return h->precision != SWOPT_PREC_FP32; }
 
-// u = (scale ? Cm : 1) * A b - ytil   (see simt_forward)
-swopt_status op_A(swopt_handle* h, const float* b, float* u, const float* ytil, double* partials,
-                  int scale, cudaStream_t st)
+// P then A.  out = A_OUT_U writes h->u (FP32 [Q][S][Twp]); out = A_OUT_R writes
+// the input format of apply_AT (h->u for the FP32 kernels, the padded BF16
+// residual images for the tensor-core kernels).  The result is
+// (scale ? Cm : 1) * (A P c) - ytil  (see simt_forward).
+enum { A_OUT_U = 0, A_OUT_R = 1 };
+
+swopt_status apply_A(swopt_handle* h, const float* c, int out, const float* ytil,
+                     double* partials, int scale, cudaStream_t st)
 {
-    if (use_tc(h)) return tc_forward(h, b, u, ytil, partials, scale, st);
-    return simt_forward(h, b, u, ytil, partials, scale, st);
+    if (use_tc(h)) {
+        SW_TRY(tc_states(h, c, st));
+        return tc_forward(h, out == A_OUT_R, ytil, partials, scale, st);
+    }
+    SW_TRY(launch_states(h, c, h->b, st));
+    return simt_forward(h, h->b, h->u, ytil, partials, scale, st);
 }
 
-swopt_status op_AT(swopt_handle* h, const float* u, float* g, cudaStream_t st)
+// A^T into h->g.  from_u: the input is h->u (FP32) rather than the output of
+// apply_A(A_OUT_R).
+swopt_status apply_AT(swopt_handle* h, bool from_u, cudaStream_t st)
 {
-    if (use_tc(h)) return tc_adjoint(h, u, g, st);
-    return simt_adjoint(h, u, g, st);
-}
-
-int forward_blocks(const swopt_handle* h)
-{
-    return use_tc(h) ? tc_forward_blocks(h) : simt_forward_blocks(h);
+    if (use_tc(h)) {
+        if (from_u) SW_TRY(tc_pack_u(h, st));
+        return tc_adjoint(h, st);
+    }
+    return simt_adjoint(h, h->u, h->g, st);
 }
 
 // w = H^T H v
 swopt_status normal_op(swopt_handle* h, const float* v, float* w, cudaStream_t st)
 {
-    SW_TRY(launch_states(h, v, h->b, st));
-    SW_TRY(op_A(h, h->b, h->u, nullptr, nullptr, 1, st));
-    SW_TRY(op_AT(h, h->u, h->g, st));
+    SW_TRY(apply_A(h, v, A_OUT_R, nullptr, nullptr, 1, st));
+    SW_TRY(apply_AT(h, false, st));
     return launch_pt(h, h->g, nullptr, 0.f, w, 0, st);
 }
 
@@ -237,9 +260,8 @@ swopt_status fista_iteration(swopt_handle* h, cudaStream_t st)
 {
     const float alpha = (float)h->step;
     const bool tv = h->prm.lambda_tv > 0 && h->prm.inner_iters > 0;
-    SW_TRY(launch_states(h, h->xi, h->b, st));                        // P
-    SW_TRY(op_A(h, h->b, h->u, h->ytil, nullptr, 1, st));             // A, folded residual
-    SW_TRY(op_AT(h, h->u, h->g, st));                                 // A^T
+    SW_TRY(apply_A(h, h->xi, A_OUT_R, h->ytil, nullptr, 1, st));     // P, A, folded residual
+    SW_TRY(apply_AT(h, false, st));                                   // A^T
     SW_TRY(launch_pt(h, h->g, h->xi, alpha, h->zin, 1, st));          // P^T, gradient step
     if (tv)
         SW_TRY(prox_tv_iters(h, h->zin, (float)(h->step * h->prm.lambda_tv),
@@ -252,8 +274,7 @@ swopt_status fista_iteration(swopt_handle* h, cudaStream_t st)
 swopt_status objective_impl(swopt_handle* h, const float* c, const float* y, double lam_l1,
                             double lam_tv, double* F, double* fit, cudaStream_t st)
 {
-    SW_TRY(launch_states(h, c, h->b, st));
-    SW_TRY(op_A(h, h->b, h->u, nullptr, nullptr, 0, st));
+    SW_TRY(apply_A(h, c, A_OUT_U, nullptr, nullptr, 0, st));
     SW_TRY(ensure_vectors(h));
     // expand H c into the y layout chunk by chunk is avoided: the data fit is
     // the sum over pulses of ||u[m(n)] - y[n]||^2 including the samples
@@ -423,7 +444,8 @@ swopt_status swopt_create(const swopt_geometry* geom, const double* K_host,
     step(dalloc(&h->b, nb_of(h)));
     step(dalloc(&h->u, nu_of(h)));
     step(dalloc(&h->g, nb_of(h)));
-    h->red_cap = std::max({4096, simt_forward_blocks(h) + 64, h->Q * h->P * h->Z + 64});
+    h->red_cap = std::max({4096, simt_forward_blocks(h) + 64, tc_forward_blocks(h) + 64,
+                           h->Q * h->P * h->Z + 64});
     step(dalloc(&h->red, (size_t)h->red_cap));
     step(dalloc(&h->scal, (size_t)SC_COUNT));
     if (s == SWOPT_OK) {
@@ -502,8 +524,7 @@ swopt_status swopt_forward(swopt_handle* h, const float* c_dev, float* y_dev, vo
         return SWOPT_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    SW_TRY(launch_states(h, c_dev, h->b, st));
-    SW_TRY(op_A(h, h->b, h->u, nullptr, nullptr, 0, st));
+    SW_TRY(apply_A(h, c_dev, A_OUT_U, nullptr, nullptr, 0, st));
     return launch_expand(h, h->u, y_dev, st);
 }
 
@@ -517,7 +538,7 @@ swopt_status swopt_adjoint(swopt_handle* h, const float* y_dev, float* c_dev, vo
     }
     cudaStream_t st = (cudaStream_t)stream;
     SW_TRY(launch_fold(h, y_dev, h->u, st));
-    SW_TRY(op_AT(h, h->u, h->g, st));
+    SW_TRY(apply_AT(h, true, st));
     return launch_pt(h, h->g, nullptr, 0.f, c_dev, 0, st);
 }
 
@@ -709,9 +730,8 @@ swopt_status swopt_param_grad(swopt_handle* h, const float* c_dev, const float* 
     float* yt = nullptr;
     SW_TRY(dalloc(&yt, nu_of(h)));
     swopt_status s = launch_fold(h, y_dev, yt, st);
-    if (s == SWOPT_OK) s = launch_states(h, c_dev, h->b, st);
-    if (s == SWOPT_OK) s = op_A(h, h->b, h->u, yt, nullptr, 1, st);
-    if (s == SWOPT_OK) s = op_AT(h, h->u, h->g, st);
+    if (s == SWOPT_OK) s = apply_A(h, c_dev, A_OUT_R, yt, nullptr, 1, st);
+    if (s == SWOPT_OK) s = apply_AT(h, false, st);
     if (s == SWOPT_OK) s = param_weights(h, h->g, c_dev, 0, st);
     const size_t nw = (size_t)h->Q * h->P * h->Z;
     std::vector<double> W(nw);
@@ -783,6 +803,38 @@ swopt_status swopt_profile_read(swopt_handle* h, int kernel_id, double* total_ms
     if (flops_per_launch) *flops_per_launch = 2.0 * (double)h->Q * h->S * (double)h->nnz;
     h->prof_ms[kernel_id] = 0;
     h->prof_n[kernel_id] = 0;
+    return SWOPT_OK;
+}
+
+swopt_status swopt_check_device(swopt_handle* h, void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    SW_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return device_errors(h);
+}
+
+swopt_status swopt_issued_flops(swopt_handle* h, int kernel_id, double* flops)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!flops || kernel_id < 0 || kernel_id > 1) {
+        set_error("invalid arguments");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    if (use_tc(h)) {
+        *flops = 2.0 * tc_issued_macs(h, kernel_id);
+        return SWOPT_OK;
+    }
+    // FP32 kernels: every nonzero 8-sample (8-depth) sub-block is issued for
+    // every position of every state
+    std::vector<uint8_t> m(kernel_id == 0 ? (size_t)h->Z * h->k * h->k * h->nTc
+                                          : (size_t)h->k * h->k * h->Twp * h->nJc);
+    SW_CUDA(cudaMemcpy(m.data(), kernel_id == 0 ? h->fmask : h->amask, m.size(),
+                       cudaMemcpyDeviceToHost));
+    double blocks = 0;
+    for (uint8_t v : m) blocks += __builtin_popcount(v);
+    *flops = 2.0 * blocks * 8.0 * (double)h->S * h->Q;
     return SWOPT_OK;
 }
 

@@ -151,12 +151,25 @@ swopt_status simt_adjoint(swopt_handle* h, const float* u, float* g, cudaStream_
 int simt_forward_blocks(const swopt_handle* h);
 
 // Tensor-core contraction kernels (operator_tc.cu).
+// tc_prepare builds the BF16 operator data for h->precision (idempotent).
 swopt_status tc_prepare(swopt_handle* h);
 void tc_release(swopt_handle* h);
-swopt_status tc_forward(swopt_handle* h, const float* b, float* u, const float* ytil,
-                        double* partials, int scale, cudaStream_t st);
-swopt_status tc_adjoint(swopt_handle* h, const float* u, float* g, cudaStream_t st);
+// P: c [P][Y][X][Z] -> padded BF16 state images (hi, and lo for the split mode)
+swopt_status tc_states(swopt_handle* h, const float* c, cudaStream_t st);
+// A on the state images.  to_r: write the padded BF16 residual images that
+// tc_adjoint reads; else write h->u (FP32 [Q][S][Twp]).  Value:
+// (scale ? Cm : 1) * acc - (ytil ? ytil : 0); partials as in simt_forward.
+swopt_status tc_forward(swopt_handle* h, bool to_r, const float* ytil, double* partials,
+                        int scale, cudaStream_t st);
+// h->u (FP32) -> padded BF16 residual images
+swopt_status tc_pack_u(swopt_handle* h, cudaStream_t st);
+// A^T of the padded residual images into h->g (FP32 [Q][S][Z])
+swopt_status tc_adjoint(swopt_handle* h, cudaStream_t st);
 int tc_forward_blocks(const swopt_handle* h);
+// Reads and clears the tensor-core kernels' device error word (0 = none).
+int tc_error_word(swopt_handle* h);
+// MMA multiply-adds issued by one launch of the forward (0) / adjoint (1)
+double tc_issued_macs(const swopt_handle* h, int kernel);
 
 // Elementwise / layout kernels (operator_simt.cu).
 swopt_status launch_states(swopt_handle* h, const float* c, float* b, cudaStream_t st);

@@ -326,3 +326,106 @@ def test_medium_adjoint_identity_and_descent(medium):
     h = stats["history"]
     F0 = 0.5 * float(ym.double().pow(2).sum())
     assert h[-1] < h[0] < F0
+
+
+# ---------------------------------------------------------------------------
+# Tensor-core precisions.  Tolerances (relative L2).  BF16 keeps 8
+# significant bits (unit roundoff u = 2^-8).  The split mode writes each
+# operand as v = hi + lo with |v - hi - lo| <= u^2 |v| = 2^-16 |v| and
+# accumulates hi*hi + hi*lo + lo*hi in FP32, so each product carries at most
+# about 3 * 2^-16 = 4.6e-5 relative error (two representation errors and the
+# dropped lo*lo, each <= 2^-16): held to 4e-5 (measured 0.5-2.3e-5).  Plain
+# BF16: two roundings of <= 2^-8 per product (7.8e-3 worst, about 2.3e-3
+# measured): held to 5e-3.
+# ---------------------------------------------------------------------------
+TC_TOL = {"bf16x3": 4e-5, "bf16": 5e-3}
+
+
+@pytest.fixture(scope="module")
+def tc_cases():
+    out = {}
+    for name in ("tiny", "ragged", "k1_one_pulse", "pulses_below_cycle", "single_column",
+                 "support_wider_than_grid"):
+        g, s, seed = CASES[name]
+        K = _kernel(g, seed)
+        out[name] = (g, s, K)
+    return out
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("name", ["tiny", "ragged", "k1_one_pulse", "pulses_below_cycle",
+                                  "single_column", "support_wider_than_grid"])
+def test_tensor_core_operator_matches_oracle(tc_cases, name, prec):
+    g, s, K = tc_cases[name]
+    op = sw.Operator(g, K, s, precision=prec)
+    c = np.random.default_rng(30).standard_normal(g.c_shape())
+    yv = np.random.default_rng(31).standard_normal(g.y_shape())
+    f = host(op.forward(dev(c)))
+    a = host(op.adjoint(dev(yv)))
+    op.check_device()
+    assert rel(f, oracle.forward(g, s, K, c)) <= TC_TOL[prec]
+    assert rel(a, oracle.adjoint(g, s, K, yv)) <= TC_TOL[prec]
+    op.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_tensor_core_medium_sampled(medium, prec):
+    g, s, K, op = medium
+    op.set_precision(prec)
+    try:
+        c = synth.tube_phantom(g, MEDIUM.tubes, seed=1)
+        y = host(op.forward(dev(c)))
+        rng = np.random.default_rng(32)
+        idx = np.stack([rng.integers(0, g.N, 32), rng.integers(0, g.Y, 32),
+                        rng.integers(0, g.X, 32)], 1)
+        assert rel(y[idx[:, 0], idx[:, 1], idx[:, 2]], oracle.forward_at(g, s, K, c, idx)) \
+            <= TC_TOL[prec]
+        yv = synth.gaussian(g.y_shape(), 33)
+        cg = host(op.adjoint(dev(yv)))
+        idx4 = np.stack([rng.integers(0, g.P, 32), rng.integers(0, g.Y, 32),
+                         rng.integers(0, g.X, 32), rng.integers(0, g.Z, 32)], 1)
+        assert rel(cg[idx4[:, 0], idx4[:, 1], idx4[:, 2], idx4[:, 3]],
+                   oracle.adjoint_at(g, s, K, yv, idx4)) <= TC_TOL[prec]
+        op.check_device()
+    finally:
+        op.set_precision("fp32")
+
+
+def test_tensor_core_fista_split_matches_oracle(tc_cases):
+    g, s, K = tc_cases["tiny"]
+    op = sw.Operator(g, K, s, precision="bf16x3")
+    y = _tiny_measurements(g, s, K)
+    alpha = 1.0 / oracle.power(g, s, K, synth.gaussian(g.c_shape(), 1), 100)
+    params = sw.SolveParams(step=alpha, lambda_l1=TINY.lam_l1, lambda_tv=TINY.lam_tv,
+                            inner_iters=TINY.inner, max_iters=TINY.iters)
+    got, stats = op.solve(dev(y), params)
+    ref = oracle.fista(g, s, K, y, alpha, TINY.iters, TINY.lam_l1, TINY.lam_tv, TINY.inner)
+    assert rel(host(got), ref) <= 1e-4
+    op.close()
+
+
+def test_tensor_core_lipschitz_and_param_grad(tc_cases):
+    g, s, K = tc_cases["ragged"]
+    op = sw.Operator(g, K, s, precision="bf16x3")
+    v0 = synth.gaussian(g.c_shape(), 5)
+    assert op.lipschitz(50, dev(v0)) == pytest.approx(oracle.power(g, s, K, v0, 50), rel=1e-5)
+    rng = np.random.default_rng(34)
+    c = np.maximum(rng.standard_normal(g.c_shape()), 0)
+    y = oracle.forward(g, s, K, c * 1.1) + 0.01 * rng.standard_normal(g.y_shape())
+    dk, dmu = op.param_grad(dev(c), dev(y))
+    dk_ref, dmu_ref = oracle.param_grad(g, s, K, c, y)
+    assert dmu == pytest.approx(dmu_ref, rel=1e-4)
+    for p in range(g.P):
+        if dk_ref[p] != 0:
+            assert dk[p] == pytest.approx(dk_ref[p], rel=1e-4)
+    op.close()
+
+
+def test_tensor_core_operator_is_deterministic(tc_cases):
+    g, s, K = tc_cases["tiny"]
+    op = sw.Operator(g, K, s, precision="bf16")
+    c = dev(np.random.default_rng(35).standard_normal(g.c_shape()))
+    assert torch.equal(op.forward(c), op.forward(c))
+    y = dev(np.random.default_rng(36).standard_normal(g.y_shape()))
+    assert torch.equal(op.adjoint(y), op.adjoint(y))
+    op.close()
