@@ -227,6 +227,22 @@ swopt_status swopt_check_device(swopt_handle* h, void* stream);
  * the split BF16 mode, all three products). */
 swopt_status swopt_issued_flops(swopt_handle* h, int kernel_id, double* flops);
 
+/* Tensor-core tile configuration (autotuner).  When a BF16 precision is
+ * selected, the library times each candidate configuration of the A (0) and
+ * A^T (1) kernels on the handle's geometry and keeps the fastest.  A
+ * configuration is: 1, 2 or 4 tiles of 16 x 8 positions per CTA; 1-8
+ * accumulator replicas per tile (successive taps rotate over them, which
+ * keeps independent MMA chains in flight; the epilogue sums them); one or
+ * two CTAs per SM.  swopt_tc_configure pins tiles_per_cta (1, 2, 4),
+ * ctas_per_sm (1, 2) and replicas (1-8) instead, 0 leaving a field tuned,
+ * and rebuilds the operator if one is active (synchronises).  swopt_tc_config
+ * reports the configuration in use (INVALID_ARG if no BF16 precision is
+ * selected). */
+swopt_status swopt_tc_configure(swopt_handle* h, int kernel_id, int tiles_per_cta, int ctas_per_sm,
+                                int replicas);
+swopt_status swopt_tc_config(swopt_handle* h, int kernel_id, int* tiles_per_cta, int* ctas_per_sm,
+                             int* stages, int* groups, int* replicas);
+
 /* Operator facts: the time window [t0, t0 + tw) that holds every nonzero
  * kernel sample, the number of distinct switching states Q = min(N,
  * pulses_per_cycle) and the number of nonzero kernel entries. */

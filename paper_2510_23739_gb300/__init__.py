@@ -109,6 +109,10 @@ _SIGS = {
     "swopt_check_device": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "swopt_issued_flops": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
                            ctypes.c_int),
+    "swopt_tc_configure": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                            ctypes.c_int], ctypes.c_int),
+    "swopt_tc_config": ([ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 5,
+                        ctypes.c_int),
     "swopt_prox_tv_static": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int,
                               ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
@@ -363,6 +367,16 @@ class Operator:
         f = ctypes.c_double()
         _check(lib().swopt_issued_flops(self._h, int(kernel_id), ctypes.byref(f)))
         return f.value
+
+    def tc_configure(self, kernel_id, tiles_per_cta=0, ctas_per_sm=0, replicas=0):
+        _check(lib().swopt_tc_configure(self._h, int(kernel_id), int(tiles_per_cta),
+                                        int(ctas_per_sm), int(replicas)))
+
+    def tc_config(self, kernel_id):
+        v = [ctypes.c_int() for _ in range(5)]
+        _check(lib().swopt_tc_config(self._h, int(kernel_id), *[ctypes.byref(x) for x in v]))
+        return {"tiles_per_cta": v[0].value, "ctas_per_sm": v[1].value, "stages": v[2].value,
+                "groups": v[3].value, "replicas": v[4].value}
 
     def launch_count(self):
         n = ctypes.c_int64()

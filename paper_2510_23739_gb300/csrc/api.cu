@@ -838,6 +838,45 @@ swopt_status swopt_issued_flops(swopt_handle* h, int kernel_id, double* flops)
     return SWOPT_OK;
 }
 
+swopt_status swopt_tc_configure(swopt_handle* h, int kernel_id, int tiles_per_cta,
+                                int ctas_per_sm, int replicas)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (kernel_id < 0 || kernel_id > 1 || tiles_per_cta < 0 || tiles_per_cta > 4 ||
+        tiles_per_cta == 3 || ctas_per_sm < 0 || ctas_per_sm > 2 || replicas < 0 ||
+        replicas > 8) {
+        set_error("invalid tensor-core configuration");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    h->tc_force_mt[kernel_id] = tiles_per_cta;
+    h->tc_force_ctas[kernel_id] = ctas_per_sm;
+    h->tc_force_ra[kernel_id] = replicas;
+    if (h->tc) {
+        tc_release(h);
+        if (use_tc(h)) return tc_prepare(h);
+    }
+    return SWOPT_OK;
+}
+
+swopt_status swopt_tc_config(swopt_handle* h, int kernel_id, int* tiles_per_cta,
+                             int* ctas_per_sm, int* stages, int* groups, int* replicas)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (kernel_id < 0 || kernel_id > 1 || !tiles_per_cta || !ctas_per_sm || !stages || !groups ||
+        !replicas) {
+        set_error("invalid arguments");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    if (!h->tc) {
+        set_error("no tensor-core precision selected");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    tc_config(h, kernel_id, tiles_per_cta, ctas_per_sm, stages, groups, replicas);
+    return SWOPT_OK;
+}
+
 swopt_status swopt_launch_count(swopt_handle* h, int64_t* count)
 {
     clear_error();

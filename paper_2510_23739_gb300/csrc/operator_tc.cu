@@ -1,19 +1,29 @@
 // Tensor-core (tcgen05, sm_103a) kernels for the acoustic correlation A and
 // its transpose A^T (Sec. 2.3.3, Eq. acoustic-full-forward).
 //
-// Both are implicit GEMMs over a 16 x 8 tile of scan positions (M = 128, one
+// Both are implicit GEMMs over tiles of 16 x 8 scan positions (M = 128, one
 // TMEM lane per position):
 //   A  : D[pos][t] += sum_j b[pos + d][j] K[j][d][t]     (K-dim: depth j)
 //   A^T: D[pos][j] += sum_t r[pos - d][t] K[j][d][t]     (K-dim: window sample t)
-// for every lateral tap d.  Operands live in shared memory in the
-// no-swizzle K-major core-matrix layout: the A operand is a halo of the tile
-// stored as [8-element slice][halo row][halo column][8 elements], so the
-// operand of tap d is the same buffer at a byte offset (rows of 8 consecutive
-// x are 16 B apart; 8-row groups are one halo row apart).  The B operand
-// (the kernel) is pre-packed per tap in the same layout.  Each MMA covers
-// K = 16 (two slices) and only the band of output columns where the kernel
-// is nonzero (N = the band width rounded to 16, at a TMEM column offset), so
-// the zero parts of the banded kernel cost nothing.
+// for every lateral tap d.  One CTA owns MT tiles side by side (16 x 8 MT
+// positions) for one switching state, so every staged block of the kernel
+// feeds MT MMAs.  Operands live in shared memory in the no-swizzle K-major
+// core-matrix layout: the A operand is a halo of the CTA's tiles stored as
+// [8-element slice][halo row][halo column][8 elements], so the operand of
+// tap d and tile i is the same buffer at a byte offset (rows of 8
+// consecutive x are 16 B apart; 8-row groups are one halo row apart).
+//
+// Measured on GB300, an M = 128, K = 16 MMA costs max(96, N/2) cycles, and
+// switching the accumulator between consecutive MMAs adds about 150 cycles.
+// So every MMA covers the whole output range (N = the time window for A, the
+// padded depth count for A^T) at TMEM column 0 of its tile, and the issue
+// order keeps one accumulator for as long as possible (tiles outermost within
+// a stage).  Trailing pairs of slices whose kernel is zero for every tap are
+// dropped.  The kernel is pre-packed per tap as [pair][slice][N rows][8]
+// (leading offset N x 16 B), so every descriptor of the MMA loop is uniform
+// arithmetic on loop counters and one elected lane issues MMAs back to back.
+// Consecutive taps are grouped into runs of one stage of shared memory (several
+// taps per stage), each arriving with one bulk asynchronous copy.
 //
 // Roles (192 threads): warp 0 stages operands with bulk asynchronous copies
 // (the TMA engine) on mbarriers, one lane of warp 1 issues tcgen05.mma and
@@ -24,8 +34,7 @@
 //
 // Precisions: BF16 operands with FP32 accumulation, or a two-term BF16 split
 // of both operands (v = hi + lo) with the three products hi*hi + hi*lo +
-// lo*hi accumulated in FP32 (relative error ~2^-16 per product instead of
-// ~2^-8).
+// lo*hi accumulated in FP32 (about 16 significant bits instead of 8).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -36,29 +45,39 @@
 
 namespace swopt {
 
+// Operator data of one direction (forward or adjoint).
+struct TcDir {
+    int GA = 0, NG = 0, KS = 0;   // A slices per group, groups, padded slices
+    int NB = 0;                   // accumulator columns per tile
+    int MT = 1;                   // tiles per CTA
+    int RA = 1;                   // accumulator replicas per tile (taps rotate over them)
+    int NS = 4;                   // stages of the B ring
+    uint32_t stage_bytes = 0;     // bytes of one stage (hi part; lo is as large)
+    int HX = 0, npos = 0;         // halo width and positions
+    int cols = 0;                 // TMEM columns allocated
+    size_t smem = 0;              // dynamic shared memory requested
+    int groupsX = 0;              // CTAs along x
+    __nv_bfloat16 *Bhi = nullptr, *Blo = nullptr;  // banded kernel, [group][tap][pair][2][N_p][8]
+    uint32_t* tab = nullptr;      // per group: header + pair table (see TcArgs)
+    int tab_words = 0;
+    double macs = 0;              // issued MACs per launch
+};
+
 struct TcOperator {
     int split = 0;
-    int tilesX = 0, tilesY = 0, Yp = 0, Xp = 0, HY = 0, HX = 0, npos = 0;
+    int tilesX = 0, tilesY = 0, Yp = 0, Xp = 0, HY = 0;
     int Zp16 = 0;
-    // forward: slices of 8 depths
-    int KSf = 0, GAf = 0, NGf = 0, NSf = 4;
-    // adjoint: slices of 8 window samples
-    int KSa = 0, GAa = 0, NGa = 0, NSa = 4;
-    int colsF = 0, colsA = 0;
-    size_t smemF = 0, smemA = 0;
-    __nv_bfloat16 *bpad_hi = nullptr, *bpad_lo = nullptr;  // [Q][KSf][Yp][Xp][8]
-    __nv_bfloat16 *rpad_hi = nullptr, *rpad_lo = nullptr;  // [Q][KSa][Yp][Xp][8]
-    __nv_bfloat16 *Bf_hi = nullptr, *Bf_lo = nullptr;      // [NGf][kk][GAf][Twp][8]
-    __nv_bfloat16 *Ba_hi = nullptr, *Ba_lo = nullptr;      // [NGa][kk][GAa][Zp16][8]
-    uint32_t *band_f = nullptr, *band_a = nullptr;         // [NG][kk][GA/2] = lo | n << 16
+    TcDir F, A;
+    __nv_bfloat16 *bpad_hi = nullptr, *bpad_lo = nullptr;  // [Q][F.KS][Yp][Xp][8]
+    __nv_bfloat16 *rpad_hi = nullptr, *rpad_lo = nullptr;  // [Q][A.KS][Yp][Xp][8]
     int* err = nullptr;
-    double macs_f = 0, macs_a = 0;                         // issued MACs per launch
 };
 
 namespace {
 
 constexpr int kTcThreads = 192;
 constexpr int kMaxStages = 8;
+constexpr int kMaxTapsPerStage = 8;  // taps per stage of the B ring (host-side cap)
 constexpr uint32_t kWaitPolls = 1u << 22;  // x 256 ns back-off: about one second
 
 // ---------------------------------------------------------------------------
@@ -109,6 +128,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     return false;
 }
 
+// Bounded wait by a whole converged warp: every lane gets the same answer.
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity,
+                                               volatile int* abort_flag)
+{
+    const bool ok = mbar_wait(bar, parity, abort_flag);
+    return __all_sync(0xffffffffu, ok);
+}
+
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
 {
     asm volatile(
@@ -116,6 +143,18 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
             dst),
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
+}
+
+// One lane of a converged warp (the lowest) returns true.
+__device__ __forceinline__ bool elect_one()
+{
+    uint32_t pred = 0;
+    asm volatile(
+        "{\n\t.reg .b32 rx;\n\t.reg .pred px;\n\t"
+        "elect.sync rx|px, 0xffffffff;\n\t"
+        "@px mov.s32 %0, 1;\n\t}"
+        : "+r"(pred));
+    return pred != 0;
 }
 
 __device__ __forceinline__ void tc_fence_before()
@@ -135,7 +174,10 @@ __device__ __forceinline__ void tc_commit(uint32_t bar)
                  : "memory");
 }
 
-// D[tmem] (+)= A[smem desc] * B[smem desc]^T, kind::f16 (BF16 in, FP32 accumulate)
+// D[tmem] (+)= A[smem desc] * B[smem desc]^T, kind::f16 (BF16 in, FP32 accumulate).
+// No memory clobber: the operands are read by the asynchronous proxy after
+// the mbarrier waits (which are compiler barriers), so plain loads of the
+// next items may be scheduled around the issue.
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                        uint32_t idesc, uint32_t accumulate)
 {
@@ -143,27 +185,7 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// Shared-memory matrix descriptor, no swizzle: start, leading-dimension byte
-// offset (K direction), stride-dimension byte offset (M/N direction), all in
-// 16-byte units; bits 46-48 hold the fixed value 0b001.
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
-    d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// Instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9,
-// 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-__device__ __forceinline__ uint32_t make_idesc(uint32_t n)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
@@ -213,12 +235,16 @@ __device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo)
                     pack_bf16x2(l[6], l[7]));
 }
 
+
 struct TcArgs {
     const __nv_bfloat16* a_hi;  // [Q][KS][Yp][Xp][8]
     const __nv_bfloat16* a_lo;
-    const __nv_bfloat16* b_hi;  // [NG][kk][GA][NB][8]
-    const __nv_bfloat16* b_lo;
-    const uint32_t* band;       // [NG][kk][GA/2]
+    const __nv_bfloat16* b_hi;  // banded kernel, [group][tap][pair][2][N_p][8]
+    const __nv_bfloat16* b_lo;  // (split mode: the lo halves, same layout)
+    const uint4* tab;           // per group g: {base (16 B units), tap bytes, taps per
+                                // run, pairs}, then per run of taps (groups in order)
+                                // eight 16-bit A offsets of its taps in 16-B units
+    int tab_n;                  // uint4 entries in tab
     float* out_f;               // forward mode 0: [Q][S][Twp]; adjoint: [Q][S][Z]
     __nv_bfloat16* out_hi;      // forward mode 1: [Q][KSo][Yp][Xp][8]
     __nv_bfloat16* out_lo;
@@ -226,8 +252,9 @@ struct TcArgs {
     const float* Cmf;           // [Q]
     double* partials;           // per block, or null
     int* err;
-    int Y, X, Yp, Xp, Z, k, r, HY, HX, tilesX;
+    int Y, X, Yp, Xp, Z, k, r, HY, HX, groupsX, MT, RA;
     int KS, GA, NG, NS, NB;
+    uint32_t stage_bytes;
     int Twp, KSo;
     int adj, split, scale, mode;
     uint32_t tcols;
@@ -235,7 +262,7 @@ struct TcArgs {
 
 // ---------------------------------------------------------------------------
 // The contraction kernel (forward or adjoint, see the file comment).
-// grid = (tiles, Q); block = 192 threads.
+// grid = (CTAs over the scan plane, Q); block = 192 threads.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
 {
@@ -249,17 +276,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m = blockIdx.y;
-    const int x0 = (blockIdx.x % a.tilesX) * 8, y0 = (blockIdx.x / a.tilesX) * 16;
+    const int x0 = (blockIdx.x % a.groupsX) * 8 * a.MT, y0 = (blockIdx.x / a.groupsX) * 16;
     const int kk = a.k * a.k;
     const uint32_t npos = (uint32_t)(a.HY * a.HX);
     const uint32_t a_slice = npos * 16u;                       // bytes of one A slice
     const uint32_t a_part = (uint32_t)a.GA * a_slice;          // hi (or lo) A bytes
-    const uint32_t sA = smem_u32(smem);
+    const uint32_t sA = __shfl_sync(0xffffffffu, smem_u32(smem), 0);
     const uint32_t sA_lo = sA + a_part;
-    const uint32_t sB = sA + a_part * (a.split ? 2u : 1u);
-    const uint32_t b_part = (uint32_t)a.GA * (uint32_t)a.NB * 16u;  // hi (or lo) B bytes
-    const uint32_t stage_bytes = b_part * (a.split ? 2u : 1u);
+    const uint32_t b_region = a_part * (a.split ? 2u : 1u);
+    const uint32_t sB = sA + b_region;
+    const uint32_t stage_total = a.stage_bytes * (a.split ? 2u : 1u);
+    const uint32_t tab_region = b_region + (uint32_t)a.NS * stage_total;
+    const uint4* s_tab = reinterpret_cast<const uint4*>(smem + tab_region);
 
+    // the group / pair table is small: stage it once
+    for (int i = threadIdx.x; i < a.tab_n; i += kTcThreads)
+        reinterpret_cast<uint4*>(smem + tab_region)[i] = a.tab[i];
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.NS; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
@@ -269,6 +301,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         mbar_init(smem_u32(&bar_aempty), 1);
         mbar_init(smem_u32(&bar_acc), 1);
         s_abort = 0;
+        s_red[0] = s_red[1] = s_red[2] = s_red[3] = 0.0;
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -281,12 +314,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = s_tmem;
+    // warp-uniform by construction (MMA operands must be uniform values)
+    const uint32_t tmem = __shfl_sync(0xffffffffu, s_tmem, 0);
 
-    // zero the accumulator columns that the epilogue reads
+    // zero the accumulator columns of all tiles
     if (warp >= 2) {
         const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-        for (int cb = 0; cb < a.NB / 16; ++cb) tmem_zero16(tmem + lanes + (uint32_t)cb * 16u);
+        for (int cb = 0; cb < a.MT * a.RA * a.NB / 16; ++cb)
+            tmem_zero16(tmem + lanes + (uint32_t)cb * 16u);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
@@ -302,7 +337,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         int a_fills = 0;
         bool ok = true;
         for (int g = 0; g < a.NG && ok; ++g) {
-            if (g > 0 && !mbar_wait(smem_u32(&bar_aempty), (uint32_t)(g - 1) & 1u, &s_abort)) {
+            const uint4 hd = s_tab[g];  // {base16, tap bytes, taps per run, pairs}
+            if (g > 0 &&
+                !mbar_wait_warp(smem_u32(&bar_aempty), (uint32_t)(a_fills - 1) & 1u, &s_abort)) {
                 ok = false;
                 break;
             }
@@ -319,18 +356,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                     bulk_g2s(sA_lo + soff, a.a_lo + goff, (uint32_t)a.HX * 16u,
                              smem_u32(&bar_afull));
             }
-            for (int d = 0; d < kk; ++d) {
-                if (!mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1u, &s_abort)) {
+            for (int d0 = 0; d0 < kk && ok; d0 += (int)hd.z) {
+                const int nt = min((int)hd.z, kk - d0);
+                if (!mbar_wait_warp(smem_u32(&bar_empty[stage]), phase ^ 1u, &s_abort)) {
                     ok = false;
                     break;
                 }
                 if (lane == 0) {
                     const uint32_t bar = smem_u32(&bar_full[stage]);
-                    mbar_expect_tx(bar, stage_bytes);
-                    const size_t boff = ((size_t)g * kk + d) * (size_t)a.GA * a.NB * 8;
-                    const uint32_t dst = sB + (uint32_t)stage * stage_bytes;
-                    bulk_g2s(dst, a.b_hi + boff, b_part, bar);
-                    if (a.split) bulk_g2s(dst + b_part, a.b_lo + boff, b_part, bar);
+                    const uint32_t dst = sB + (uint32_t)stage * stage_total;
+                    const uint32_t bytes = (uint32_t)nt * hd.y;
+                    const size_t src = ((size_t)hd.x * 16 + (size_t)d0 * hd.y) / 2;  // elements
+                    mbar_expect_tx(bar, bytes * (a.split ? 2u : 1u));
+                    if (bytes) {
+                        bulk_g2s(dst, a.b_hi + src, bytes, bar);
+                        if (a.split) bulk_g2s(dst + a.stage_bytes, a.b_lo + src, bytes, bar);
+                    }
                 }
                 fills[stage]++;
                 __syncwarp();
@@ -346,111 +387,147 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         }
         // drain: every copy this warp issued has landed before the CTA exits
         if (lane == 0) {
+            volatile int never = 0;
             for (int s = 0; s < a.NS; ++s)
-                if (fills[s] > 0) {
-                    volatile int never = 0;
-                    if (!mbar_wait(smem_u32(&bar_full[s]), (uint32_t)(fills[s] - 1) & 1u, &never))
-                        atomicExch(a.err, 2);
-                }
-            if (a_fills > 0) {
-                volatile int never = 0;
-                if (!mbar_wait(smem_u32(&bar_afull), (uint32_t)(a_fills - 1) & 1u, &never))
+                if (fills[s] > 0 &&
+                    !mbar_wait(smem_u32(&bar_full[s]), (uint32_t)(fills[s] - 1) & 1u, &never))
                     atomicExch(a.err, 2);
-            }
+            if (a_fills > 0 &&
+                !mbar_wait(smem_u32(&bar_afull), (uint32_t)(a_fills - 1) & 1u, &never))
+                atomicExch(a.err, 2);
         }
     } else if (warp == 1) {
         // ------------------------------ MMA issuer ----------------------------
-        if (lane == 0) {
-            const uint32_t lbo_a = a_slice, sbo_a = (uint32_t)a.HX * 16u;
-            const uint32_t lbo_b = (uint32_t)a.NB * 16u, sbo_b = 128u;
-            int stage = 0;
-            uint32_t phase = 0;
-            bool ok = true;
-            for (int g = 0; g < a.NG && ok; ++g) {
-                if (!mbar_wait(smem_u32(&bar_afull), (uint32_t)g & 1u, &s_abort)) {
+        // The whole warp walks groups, runs, pairs and taps in step, so all
+        // descriptors are warp-uniform arithmetic; one elected lane issues
+        // the MMAs and the commits.
+        const bool leader = elect_one();
+        const uint64_t lbo_a16 = (uint64_t)(a_slice >> 4), sbo_a16 = (uint64_t)(a.HX);
+        // descriptor constant parts: LBO, SBO and the fixed bits 46-48
+        const uint64_t adesc_c = (lbo_a16 << 16) | (sbo_a16 << 32) | ((uint64_t)1 << 46);
+        const uint64_t bdesc_c = ((uint64_t)(128u >> 4) << 32) | ((uint64_t)1 << 46);  // SBO 128 B
+        const uint64_t alo16 = (uint64_t)(a_part >> 4), blo16 = (uint64_t)(a.stage_bytes >> 4);
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                               (((uint32_t)a.NB >> 3) << 17) | ((128u >> 4) << 24);
+        const uint64_t bdesc = bdesc_c | ((uint64_t)a.NB << 16);  // LBO = N x 16 B
+        const uint32_t pair_b = 2u * (uint32_t)a.NB * 16u;         // B bytes of one pair
+        const int MT = a.MT, NBc = a.NB;
+        const bool split = a.split != 0;
+        int run = 0;
+        for (int g = 0; g < a.NG && ok; ++g) {
+            const uint4 hd = s_tab[g];
+            const int tpr = __shfl_sync(0xffffffffu, (int)hd.z, 0);
+            const uint32_t tapb = __shfl_sync(0xffffffffu, hd.y, 0);
+            const int np = __shfl_sync(0xffffffffu, (int)hd.w, 0);
+            if (g > 0 && leader) tc_commit(smem_u32(&bar_aempty));
+            __syncwarp();
+            if (!mbar_wait_warp(smem_u32(&bar_afull), (uint32_t)g & 1u, &s_abort)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            for (int d0 = 0; d0 < kk; d0 += tpr) {
+                const int nt = min(tpr, kk - d0);
+                if (!mbar_wait_warp(smem_u32(&bar_full[stage]), phase, &s_abort)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                for (int d = 0; d < kk; ++d) {
-                    if (!mbar_wait(smem_u32(&bar_full[stage]), phase, &s_abort)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const int dy = d / a.k, dx = d - dy * a.k;
-                    const uint32_t tap =
-                        a.adj ? (uint32_t)((2 * a.r - dy) * a.HX + (2 * a.r - dx)) * 16u
-                              : (uint32_t)(dy * a.HX + dx) * 16u;
-                    const uint32_t* bandp = a.band + ((size_t)g * kk + d) * (size_t)(a.GA / 2);
-                    const uint32_t bst = sB + (uint32_t)stage * stage_bytes;
-                    for (int p = 0; p < a.GA / 2; ++p) {
-                        const uint32_t e = __ldg(bandp + p);
-                        const uint32_t n = e >> 16;
-                        if (n == 0) continue;
-                        const uint32_t lo = e & 0xFFFFu;
-                        const uint32_t idesc = make_idesc(n);
-                        const uint32_t aoff = 2u * (uint32_t)p * lbo_a + tap;
-                        const uint32_t boff = 2u * (uint32_t)p * lbo_b + lo * 16u;
-                        const uint64_t ad = make_desc(sA + aoff, lbo_a, sbo_a);
-                        const uint64_t bd = make_desc(bst + boff, lbo_b, sbo_b);
-                        const uint32_t dt = tmem + lo;
-                        tc_mma(dt, ad, bd, idesc, 1u);
-                        if (a.split) {
-                            tc_mma(dt, ad, make_desc(bst + b_part + boff, lbo_b, sbo_b), idesc, 1u);
-                            tc_mma(dt, make_desc(sA_lo + aoff, lbo_a, sbo_a), bd, idesc, 1u);
+                const uint32_t bst = sB + (uint32_t)stage * stage_total;
+                // A offsets of this stage's taps (16-B units), from the run table
+                const uint4 ro = s_tab[a.NG + run];
+                const uint32_t ow[4] = {__shfl_sync(0xffffffffu, ro.x, 0),
+                                        __shfl_sync(0xffffffffu, ro.y, 0),
+                                        __shfl_sync(0xffffffffu, ro.z, 0),
+                                        __shfl_sync(0xffffffffu, ro.w, 0)};
+                ++run;
+                const uint64_t tapb16 = tapb >> 4;
+                for (int i = 0; i < MT; ++i) {
+                    const uint32_t dt = tmem + (uint32_t)(i * NBc);
+                    for (int p = 0; p < np; ++p) {
+                        const uint64_t adp = adesc_c | (uint64_t)((sA + 2u * (uint32_t)p * a_slice +
+                                                                   (uint32_t)i * 128u) >> 4);
+                        const uint64_t bdp = bdesc | (uint64_t)((bst + (uint32_t)p * pair_b) >> 4);
+                        if (leader) {
+#pragma unroll
+                            for (int t = 0; t < kMaxTapsPerStage; ++t) {
+                                if (t < nt) {
+                                    const uint64_t ad =
+                                        adp + (uint64_t)((ow[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
+                                    const uint64_t bd = bdp + (uint64_t)t * tapb16;
+                                    tc_mma(dt, ad, bd, idesc, 1u);
+                                    if (split) {
+                                        tc_mma(dt, ad, bd + blo16, idesc, 1u);
+                                        tc_mma(dt, ad + alo16, bd, idesc, 1u);
+                                    }
+                                }
+                            }
                         }
                     }
-                    tc_commit(smem_u32(&bar_empty[stage]));
-                    if (++stage == a.NS) {
-                        stage = 0;
-                        phase ^= 1u;
-                    }
                 }
-                if (ok) tc_commit(smem_u32(&bar_aempty));
-            }
-            // signals the epilogue; also covers every MMA issued above
-            tc_commit(smem_u32(&bar_acc));
-            if (!ok) {
-                s_abort = 1;
-                atomicExch(a.err, 1);
-                volatile int never = 0;
-                if (!mbar_wait(smem_u32(&bar_acc), 0u, &never)) atomicExch(a.err, 2);
+                __syncwarp();
+                if (leader) tc_commit(smem_u32(&bar_empty[stage]));
+                __syncwarp();
+                if (++stage == a.NS) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
             }
         }
+        // signals the epilogue; also covers every MMA issued above
+        if (leader) tc_commit(smem_u32(&bar_acc));
         __syncwarp();
+        if (!ok) {
+            if (leader) {
+                s_abort = 1;
+                atomicExch(a.err, 1);
+            }
+            volatile int never = 0;
+            if (!mbar_wait(smem_u32(&bar_acc), 0u, &never) && leader) atomicExch(a.err, 2);
+        }
     } else {
         // ------------------------------ epilogue ------------------------------
         const int q = warp & 3;
-        const int i = q * 32 + lane;
-        const int yl = i >> 3, xl = i & 7;
-        const int y = y0 + yl, x = x0 + xl;
-        const bool valid = (y < a.Y) && (x < a.X);
-        bool ok = mbar_wait(smem_u32(&bar_acc), 0u, &s_abort);
-        ok = __all_sync(0xffffffffu, ok);
+        const int li = q * 32 + lane;
+        const int yl = li >> 3, xl = li & 7;
+        const bool ok = mbar_wait_warp(smem_u32(&bar_acc), 0u, &s_abort);
         tc_fence_after();
         double part = 0.0;
         if (ok) {
             const uint32_t lanes = (uint32_t)(q * 32) << 16;
-            const size_t pos = (size_t)y * a.X + x;
             const size_t S = (size_t)a.Y * a.X;
             const float cm = a.scale ? a.Cmf[m] : 1.f;
-            for (int cb = 0; cb < a.NB / 16; ++cb) {
-                float v[16];
-                tmem_ld16(tmem + lanes + (uint32_t)cb * 16u, v);
-                if (!valid) continue;
-                if (a.adj) {
-                    float* out = a.out_f + ((size_t)m * S + pos) * a.Z + cb * 16;
-                    const int nz = min(16, a.Z - cb * 16);
-                    if (nz == 16 && (a.Z & 3) == 0) {
+            const int y = y0 + yl;
+            for (int ti = 0; ti < a.MT; ++ti) {
+                const int x = x0 + 8 * ti + xl;
+                const bool valid = (y < a.Y) && (x < a.X);
+                const size_t pos = (size_t)y * a.X + x;
+                for (int cb = 0; cb < a.NB / 16; ++cb) {
+                    float v[16];
+                    tmem_ld16(tmem + lanes + (uint32_t)(ti * a.RA * a.NB + cb * 16), v);
+                    for (int rp = 1; rp < a.RA; ++rp) {
+                        float w[16];
+                        tmem_ld16(tmem + lanes + (uint32_t)((ti * a.RA + rp) * a.NB + cb * 16), w);
 #pragma unroll
-                        for (int e = 0; e < 16; e += 4)
-                            *reinterpret_cast<float4*>(out + e) =
-                                make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
-                    } else {
-                        for (int e = 0; e < nz; ++e) out[e] = v[e];
+                        for (int e = 0; e < 16; ++e) v[e] += w[e];
                     }
-                } else {
+                    if (!valid) continue;
+                    if (a.adj) {
+                        float* out = a.out_f + ((size_t)m * S + pos) * a.Z + cb * 16;
+                        const int nz = min(16, a.Z - cb * 16);
+                        if (nz == 16 && (a.Z & 3) == 0) {
+#pragma unroll
+                            for (int e = 0; e < 16; e += 4)
+                                *reinterpret_cast<float4*>(out + e) =
+                                    make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                        } else {
+                            for (int e = 0; e < nz; ++e) out[e] = v[e];
+                        }
+                        continue;
+                    }
                     const size_t ub = ((size_t)m * S + pos) * a.Twp + cb * 16;
                     float o[16];
                     if (a.ytil) {
@@ -611,25 +688,6 @@ swopt_status tc_upload(T** p, const std::vector<T>& v)
     return SWOPT_OK;
 }
 
-// Slices per group so that the operands of one CTA fit `budget` bytes.
-bool pick_groups(int slices_min, int npos, int NB, int split, int NS, size_t budget, int* GA,
-                 int* NG, size_t* smem)
-{
-    const size_t mult = split ? 2 : 1;
-    for (int ng = 1; ng <= slices_min; ++ng) {
-        int ga = (slices_min + ng - 1) / ng;
-        ga += ga & 1;  // K = 16 per MMA: slices come in pairs
-        const size_t bytes = mult * ((size_t)ga * npos * 16 + (size_t)NS * ga * NB * 16);
-        if (bytes <= budget) {
-            *GA = ga;
-            *NG = (slices_min + ga - 1) / ga;
-            *smem = bytes;
-            return true;
-        }
-    }
-    return false;
-}
-
 uint32_t pow2_cols(int n)
 {
     uint32_t c = 32;
@@ -639,138 +697,322 @@ uint32_t pow2_cols(int n)
 
 }  // namespace
 
+
+namespace {
+
+void free_dir(TcDir& D)
+{
+    cudaFree(D.Bhi); cudaFree(D.Blo); cudaFree(D.tab);
+    D.Bhi = D.Blo = nullptr;
+    D.tab = nullptr;
+}
+
+// Host image of one direction's packed operator.
+struct DirHost {
+    TcDir cfg;
+    std::vector<uint16_t> hi, lo;   // banded kernel
+    std::vector<uint32_t> tab;      // group headers and pair tables (uint4 entries)
+};
+
+// Builds the banded kernel of one direction for MT tiles per CTA within a
+// shared-memory budget.  Returns false if it does not fit.
+bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int RA,
+              size_t budget, DirHost* out)
+{
+    const int kk = h->k * h->k;
+    const int split = t->split;
+    TcDir D;
+    D.MT = MT;
+    D.RA = RA;
+    D.NB = adj ? t->Zp16 : h->Twp;
+    const int ks_min = adj ? h->Twp / 8 : t->Zp16 / 8;  // both even
+    const int npairs = ks_min / 2;
+    D.HX = 8 * MT + 2 * h->r;
+    D.npos = t->HY * D.HX;
+    D.cols = (int)pow2_cols(MT * RA * D.NB);
+    if (D.cols > 512) return false;
+    D.groupsX = (t->tilesX + MT - 1) / MT;
+
+    // value of the kernel at output column `row` and contraction index `kidx`
+    auto kv = [&](int row, int kidx, int d) -> float {
+        const int j = adj ? row : kidx, w = adj ? kidx : row;
+        const int tt = h->t0 + w;
+        if (j >= h->Z || w >= h->Twp || tt >= h->T) return 0.f;
+        return (float)h->K64[((size_t)j * kk + d) * h->T + tt];
+    };
+    // pairs with any nonzero kernel entry; trailing all-zero pairs are dropped
+    int npe = 0;
+    for (int gp = 0; gp < npairs; ++gp) {
+        bool any = false;
+        for (int d = 0; d < kk && !any; ++d)
+            for (int row = 0; row < D.NB && !any; ++row)
+                for (int e = 0; e < 16; ++e)
+                    if (kv(row, 16 * gp + e, d) != 0.f) {
+                        any = true;
+                        break;
+                    }
+        if (any) npe = gp + 1;
+    }
+    if (npe == 0) npe = 1;
+    const size_t pair_b = 2 * (size_t)D.NB * 16;
+    // smallest number of groups whose A slices and B ring fit the budget;
+    // prefer stages that hold several taps
+    const size_t mult = split ? 2 : 1;
+    bool found = false;
+    for (int ng = 1; ng <= npe && !found; ++ng) {
+        const int gpairs = (npe + ng - 1) / ng;
+        const int GA = 2 * gpairs;
+        const int NG = (npe + gpairs - 1) / gpairs;
+        const size_t tapb = (size_t)gpairs * pair_b;
+        const size_t a_bytes = mult * (size_t)GA * D.npos * 16;
+        // group headers plus one entry per run of at most kMaxTapsPerStage taps
+        const size_t tab = ((size_t)NG + (size_t)NG * kk) * 16;
+        if (a_bytes + tab + 3 * tapb * mult > budget) continue;
+        // largest stage (in whole taps, up to kMaxTapsPerStage) with at least 3 stages
+        for (int tps = kMaxTapsPerStage; tps >= 1 && !found; --tps) {
+            const size_t stage = tapb * (size_t)std::min(tps, kk);
+            const size_t tabr = ((size_t)NG + (size_t)NG * ((kk + tps - 1) / tps)) * 16;
+            for (int ns = kMaxStages; ns >= 3; --ns) {
+                const size_t total = a_bytes + (size_t)ns * stage * mult + tabr;
+                if (total <= budget) {
+                    D.GA = GA;
+                    D.NG = NG;
+                    // slice stride of the image: at least every slice that the
+                    // state / pack kernels and the forward epilogue write
+                    D.KS = std::max(NG * GA, ks_min);
+                    D.NS = ns;
+                    D.stage_bytes = (uint32_t)stage;
+                    D.smem = total;
+                    found = true;
+                    break;
+                }
+            }
+        }
+    }
+    if (!found) return false;
+    // At most 512 / cols CTAs may share an SM's 512 TMEM columns: request
+    // enough shared memory that no more can be resident (233472 B per SM,
+    // so more than 233472 / (512 / cols + 1) bytes per CTA).
+    D.smem = std::max(D.smem, (size_t)233472 / (512 / D.cols + 1) + 1024);
+    if (D.smem > 225 * 1024) return false;
+
+    // pack [group][tap][pair][2 slices][NB rows][8] and the group headers
+    const int gpairs = D.GA / 2;
+    out->hi.clear();
+    out->lo.clear();
+    out->tab.clear();
+    std::vector<uint32_t> runtab;
+    double macs = 0;
+    for (int g = 0; g < D.NG; ++g) {
+        const int np = std::min(gpairs, npe - g * gpairs);
+        const uint32_t tapb = (uint32_t)(np * pair_b);
+        const uint32_t base16 = (uint32_t)(out->hi.size() / 8);
+        const uint32_t tpr = std::min<uint32_t>(
+            kMaxTapsPerStage, std::max<uint32_t>(1, D.stage_bytes / tapb));
+        out->tab.insert(out->tab.end(), {base16, tapb, tpr, (uint32_t)np});
+        // runs of tpr taps: A offsets (16-B units) of each tap of the run
+        for (int d0 = 0; d0 < kk; d0 += (int)tpr) {
+            uint32_t w[4] = {0, 0, 0, 0};
+            for (int tt = 0; tt < (int)tpr && d0 + tt < kk; ++tt) {
+                const int d = d0 + tt, dy = d / h->k, dx = d - dy * h->k;
+                const int off = adj ? (2 * h->r - dy) * D.HX + (2 * h->r - dx) : dy * D.HX + dx;
+                w[tt >> 1] |= (uint32_t)(off & 0xFFFF) << (16 * (tt & 1));
+            }
+            runtab.insert(runtab.end(), {w[0], w[1], w[2], w[3]});
+        }
+        for (int d = 0; d < kk; ++d)
+            for (int p = 0; p < np; ++p) {
+                const int gp = g * gpairs + p;
+                for (int s2 = 0; s2 < 2; ++s2)
+                    for (int row = 0; row < D.NB; ++row)
+                        for (int e = 0; e < 8; ++e) {
+                            const float v = kv(row, 16 * gp + 8 * s2 + e, d);
+                            const uint16_t hb = f2bf(v);
+                            out->hi.push_back(hb);
+                            out->lo.push_back(f2bf(v - bf2f(hb)));
+                        }
+                macs += 128.0 * D.NB * 16;
+            }
+    }
+    if (out->hi.empty()) {
+        out->hi.assign(8, 0);
+        out->lo.assign(8, 0);
+    }
+    out->tab.insert(out->tab.end(), runtab.begin(), runtab.end());
+    D.tab_words = (int)out->tab.size();
+    const double ctas = (double)D.groupsX * t->tilesY * h->Q;
+    D.macs = macs * MT * (split ? 3 : 1) * ctas;
+    out->cfg = D;
+    return true;
+}
+
+swopt_status upload_dir(const DirHost& H, int split, TcDir* D)
+{
+    *D = H.cfg;
+    D->Bhi = D->Blo = nullptr;
+    D->tab = nullptr;
+    auto up16 = [&](__nv_bfloat16** dst, const std::vector<uint16_t>& v) -> swopt_status {
+        SW_TRY(tc_alloc(dst, v.size()));
+        SW_CUDA(cudaMemcpy(*dst, v.data(), v.size() * 2, cudaMemcpyHostToDevice));
+        return SWOPT_OK;
+    };
+    swopt_status s = up16(&D->Bhi, H.hi);
+    if (s == SWOPT_OK && split) s = up16(&D->Blo, H.lo);
+    if (s == SWOPT_OK) s = tc_upload(&D->tab, H.tab);
+    if (s != SWOPT_OK) free_dir(*D);
+    return s;
+}
+
+TcArgs dir_args(const swopt_handle* h, const TcOperator* t, const TcDir& D, bool adj)
+{
+    TcArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.Cmf = h->Cmf;
+    a.err = t->err;
+    a.Y = h->Y; a.X = h->X; a.Yp = t->Yp; a.Xp = t->Xp; a.Z = h->Z; a.k = h->k; a.r = h->r;
+    a.HY = t->HY; a.HX = D.HX; a.groupsX = D.groupsX; a.MT = D.MT; a.RA = D.RA;
+    a.KS = D.KS; a.GA = D.GA; a.NG = D.NG; a.NS = D.NS; a.NB = D.NB;
+    a.stage_bytes = D.stage_bytes;
+    a.Twp = h->Twp;
+    a.KSo = t->A.KS;
+    a.split = t->split;
+    a.adj = adj ? 1 : 0;
+    a.b_hi = D.Bhi; a.b_lo = D.Blo;
+    a.tab = reinterpret_cast<const uint4*>(D.tab);
+    a.tab_n = D.tab_words / 4;
+    a.tcols = (uint32_t)D.cols;
+    if (adj) {
+        a.a_hi = t->rpad_hi; a.a_lo = t->rpad_lo;
+    } else {
+        a.a_hi = t->bpad_hi; a.a_lo = t->bpad_lo;
+    }
+    return a;
+}
+
+swopt_status launch_conv(swopt_handle* h, const TcDir& D, const TcArgs& a, cudaStream_t st)
+{
+    if (D.smem > 48 * 1024)
+        SW_CUDA(cudaFuncSetAttribute(tc_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)D.smem));
+    dim3 grid(D.groupsX * h->tc->tilesY, h->Q);
+    tc_conv_kernel<<<grid, kTcThreads, D.smem, st>>>(a);
+    SW_LAUNCHED(h);
+    return SWOPT_OK;
+}
+
+// Candidate configurations: tiles per CTA, accumulator replicas per tile
+// (independent accumulation chains keep more MMAs in flight) and the
+// shared-memory budget (two CTAs per SM, or one).
+struct Cand {
+    int MT, RA;
+    size_t budget;
+};
+const Cand kCands[] = {{1, 1, 110 * 1024}, {2, 1, 110 * 1024}, {1, 1, 220 * 1024},
+                       {2, 1, 220 * 1024}, {4, 1, 220 * 1024}};
+
+}  // namespace
+
 void tc_release(swopt_handle* h)
 {
     TcOperator* t = h->tc;
     if (!t) return;
+    free_dir(t->F);
+    free_dir(t->A);
     cudaFree(t->bpad_hi); cudaFree(t->bpad_lo); cudaFree(t->rpad_hi); cudaFree(t->rpad_lo);
-    cudaFree(t->Bf_hi); cudaFree(t->Bf_lo); cudaFree(t->Ba_hi); cudaFree(t->Ba_lo);
-    cudaFree(t->band_f); cudaFree(t->band_a); cudaFree(t->err);
+    cudaFree(t->err);
     delete t;
     h->tc = nullptr;
+}
+
+// Chooses, for one direction, the fastest candidate configuration (timed
+// with CUDA events on zeroed operands) unless `force_mt` > 0 pins the tiles
+// per CTA.  The padded images must already be sized for max_ks slices.
+static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_ctas,
+                             int force_ra, TcDir* best)
+{
+    TcOperator* t = h->tc;
+    std::vector<DirHost> plans;
+    for (const Cand& c : kCands) {
+        if (force_mt > 0 && c.MT != force_mt) continue;
+        if (force_ctas > 0 && (force_ctas == 2) != (c.budget < 200 * 1024)) continue;
+        if (force_ra > 0 && c.RA != force_ra) continue;
+        DirHost H;
+        if (plan_dir(h, t, adj, c.MT, c.RA, c.budget, &H)) plans.push_back(std::move(H));
+    }
+    if (plans.empty()) {
+        set_error("no tensor-core configuration fits this geometry (k=%d, window %d, depths %d)",
+                  h->k, h->Twp, h->Z);
+        return SWOPT_ERR_UNSUPPORTED;
+    }
+    int best_i = 0;
+    if (plans.size() > 1) {
+        cudaEvent_t e0, e1;
+        SW_CUDA(cudaEventCreate(&e0));
+        SW_CUDA(cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        for (size_t i = 0; i < plans.size(); ++i) {
+            TcDir D;
+            SW_TRY(upload_dir(plans[i], t->split, &D));
+            TcArgs a = dir_args(h, t, D, adj);
+            a.out_f = adj ? h->g : h->u;
+            a.mode = 0;
+            swopt_status s = launch_conv(h, D, a, 0);  // warm-up
+            float ms = 0.f;
+            if (s == SWOPT_OK) {
+                cudaEventRecord(e0, 0);
+                for (int rep = 0; rep < 3 && s == SWOPT_OK; ++rep) s = launch_conv(h, D, a, 0);
+                cudaEventRecord(e1, 0);
+                if (cudaEventSynchronize(e1) != cudaSuccess) s = SWOPT_ERR_CUDA;
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            free_dir(D);
+            if (s != SWOPT_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return s;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_i = (int)i;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (tc_error_word(h) != 0) {
+            set_error("a tensor-core kernel gave up a bounded wait while tuning");
+            return SWOPT_ERR_TIMEOUT;
+        }
+    }
+    return upload_dir(plans[best_i], t->split, best);
 }
 
 swopt_status tc_prepare(swopt_handle* h)
 {
     const int split = h->precision == SWOPT_PREC_BF16X3 ? 1 : 0;
     if (h->tc && h->tc->split == split) return SWOPT_OK;
+    const int keep_f = h->tc ? h->tc->F.MT : 0;
+    (void)keep_f;
     tc_release(h);
-    const int kk = h->k * h->k;
     TcOperator* t = new TcOperator();
     t->split = split;
     t->tilesX = (h->X + 7) / 8;
     t->tilesY = (h->Y + 15) / 16;
-    t->Xp = t->tilesX * 8 + 2 * h->r;
+    t->Xp = ((t->tilesX + 3) / 4) * 32 + 2 * h->r;  // room for up to 4 tiles per CTA
     t->Yp = t->tilesY * 16 + 2 * h->r;
-    t->HX = 8 + 2 * h->r;
     t->HY = 16 + 2 * h->r;
-    t->npos = t->HX * t->HY;
     t->Zp16 = ((h->Z + 15) / 16) * 16;
+    h->tc = t;
     if (h->Twp > 256 || t->Zp16 > 256) {
-        delete t;
         set_error("tensor-core path supports a time window and a depth count up to 256 "
                   "(window %d, depths %d)", h->Twp, h->Z);
+        tc_release(h);
         return SWOPT_ERR_UNSUPPORTED;
     }
-    // two CTAs per SM: operands within ~110 KB, accumulator within 256 TMEM columns
-    const size_t budget = 110 * 1024;
-    if (!pick_groups(t->Zp16 / 8, t->npos, h->Twp, split, t->NSf, budget, &t->GAf, &t->NGf,
-                     &t->smemF) ||
-        !pick_groups(h->Twp / 8, t->npos, t->Zp16, split, t->NSa, budget, &t->GAa, &t->NGa,
-                     &t->smemA)) {
-        delete t;
-        set_error("lateral support k=%d too large for the tensor-core tile", h->k);
-        return SWOPT_ERR_UNSUPPORTED;
-    }
-    t->KSf = t->NGf * t->GAf;
-    t->KSa = t->NGa * t->GAa;
-    t->colsF = (int)pow2_cols(h->Twp);
-    t->colsA = (int)pow2_cols(t->Zp16);
-
-    // FP32 values of the windowed kernel
-    auto kval = [&](int j, int d, int w) -> float {
-        const int tt = h->t0 + w;
-        if (j >= h->Z || w >= h->Twp || tt >= h->T) return 0.f;
-        return (float)h->K64[((size_t)j * kk + d) * h->T + tt];
-    };
-    // forward B blocks and bands
-    std::vector<uint16_t> bfh((size_t)t->NGf * kk * t->GAf * h->Twp * 8, 0), bfl(bfh.size(), 0);
-    std::vector<uint32_t> bandf((size_t)t->NGf * kk * (t->GAf / 2), 0);
-    double macs_f = 0;
-    for (int g = 0; g < t->NGf; ++g)
-        for (int d = 0; d < kk; ++d) {
-            for (int sl = 0; sl < t->GAf; ++sl)
-                for (int w = 0; w < h->Twp; ++w)
-                    for (int e = 0; e < 8; ++e) {
-                        const float v = kval(8 * (g * t->GAf + sl) + e, d, w);
-                        const uint16_t hb = f2bf(v);
-                        const size_t o = ((((size_t)g * kk + d) * t->GAf + sl) * h->Twp + w) * 8 + e;
-                        bfh[o] = hb;
-                        bfl[o] = f2bf(v - bf2f(hb));
-                    }
-            for (int p = 0; p < t->GAf / 2; ++p) {
-                int lo = -1, hi = -1;
-                for (int e = 0; e < 16; ++e) {
-                    const int j = 16 * (g * t->GAf / 2 + p) + e;
-                    for (int w = 0; w < h->Twp; ++w)
-                        if (kval(j, d, w) != 0.f) {
-                            if (lo < 0 || w < lo) lo = w;
-                            if (w > hi) hi = w;
-                        }
-                }
-                uint32_t ent = 0;
-                if (lo >= 0) {
-                    const int l16 = lo & ~15;
-                    const int n16 = ((hi + 1 - l16 + 15) / 16) * 16;
-                    ent = (uint32_t)l16 | ((uint32_t)n16 << 16);
-                    macs_f += 128.0 * n16 * 16 * (split ? 3 : 1);
-                }
-                bandf[((size_t)g * kk + d) * (t->GAf / 2) + p] = ent;
-            }
-        }
-    // adjoint B blocks and bands
-    std::vector<uint16_t> bah((size_t)t->NGa * kk * t->GAa * t->Zp16 * 8, 0), bal(bah.size(), 0);
-    std::vector<uint32_t> banda((size_t)t->NGa * kk * (t->GAa / 2), 0);
-    double macs_a = 0;
-    for (int g = 0; g < t->NGa; ++g)
-        for (int d = 0; d < kk; ++d) {
-            for (int sl = 0; sl < t->GAa; ++sl)
-                for (int j = 0; j < t->Zp16; ++j)
-                    for (int e = 0; e < 8; ++e) {
-                        const float v = kval(j, d, 8 * (g * t->GAa + sl) + e);
-                        const uint16_t hb = f2bf(v);
-                        const size_t o =
-                            ((((size_t)g * kk + d) * t->GAa + sl) * t->Zp16 + j) * 8 + e;
-                        bah[o] = hb;
-                        bal[o] = f2bf(v - bf2f(hb));
-                    }
-            for (int p = 0; p < t->GAa / 2; ++p) {
-                int lo = -1, hi = -1;
-                for (int e = 0; e < 16; ++e) {
-                    const int w = 16 * (g * t->GAa / 2 + p) + e;
-                    for (int j = 0; j < t->Zp16; ++j)
-                        if (kval(j, d, w) != 0.f) {
-                            if (lo < 0 || j < lo) lo = j;
-                            if (j > hi) hi = j;
-                        }
-                }
-                uint32_t ent = 0;
-                if (lo >= 0) {
-                    const int l16 = lo & ~15;
-                    const int n16 = ((hi + 1 - l16 + 15) / 16) * 16;
-                    ent = (uint32_t)l16 | ((uint32_t)n16 << 16);
-                    macs_a += 128.0 * n16 * 16 * (split ? 3 : 1);
-                }
-                banda[((size_t)g * kk + d) * (t->GAa / 2) + p] = ent;
-            }
-        }
-    const double ctas = (double)t->tilesX * t->tilesY * h->Q;
-    t->macs_f = macs_f * ctas;
-    t->macs_a = macs_a * ctas;
-
-    h->tc = t;
-    const size_t nb = (size_t)h->Q * t->KSf * t->Yp * t->Xp * 8;
-    const size_t nr = (size_t)h->Q * t->KSa * t->Yp * t->Xp * 8;
+    // padded images sized for the largest slice count any candidate may use
+    // (NG groups of 2 ceil(pairs / NG) slices never exceed twice the pairs' slices)
+    const int ksf_max = 2 * (t->Zp16 / 8), ksa_max = 2 * (h->Twp / 8);
+    const size_t plane = (size_t)t->Yp * t->Xp * 8;
+    const size_t nb = (size_t)h->Q * ksf_max * plane, nr = (size_t)h->Q * ksa_max * plane;
     swopt_status s = SWOPT_OK;
     auto step = [&](swopt_status v) { if (s == SWOPT_OK) s = v; };
     step(tc_alloc(&t->bpad_hi, nb));
@@ -779,45 +1021,32 @@ swopt_status tc_prepare(swopt_handle* h)
         step(tc_alloc(&t->bpad_lo, nb));
         step(tc_alloc(&t->rpad_lo, nr));
     }
-    std::vector<__nv_bfloat16> tmp;
-    auto up16 = [&](__nv_bfloat16** dst, const std::vector<uint16_t>& v) {
-        if (s != SWOPT_OK) return;
-        s = tc_alloc(dst, v.size());
-        if (s != SWOPT_OK) return;
-        if (cudaMemcpy(*dst, v.data(), v.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
-            set_error("cudaMemcpy of the tensor-core kernel failed");
-            s = SWOPT_ERR_CUDA;
-        }
-    };
-    up16(&t->Bf_hi, bfh);
-    up16(&t->Ba_hi, bah);
-    if (split) {
-        up16(&t->Bf_lo, bfl);
-        up16(&t->Ba_lo, bal);
-    }
-    if (s == SWOPT_OK) step(tc_upload(&t->band_f, bandf));
-    if (s == SWOPT_OK) step(tc_upload(&t->band_a, banda));
-    if (s == SWOPT_OK) step(tc_alloc(&t->err, 1));
-    // zero borders and padded slices once; kernels only write the interior
+    step(tc_alloc(&t->err, 1));
     auto zero = [&](void* p, size_t bytes) {
         if (s == SWOPT_OK && p && cudaMemset(p, 0, bytes) != cudaSuccess) {
             set_error("cudaMemset failed");
             s = SWOPT_ERR_CUDA;
         }
     };
+    // borders and padded slices stay zero; kernels only write the interior
     zero(t->bpad_hi, nb * 2); zero(t->bpad_lo, nb * 2);
     zero(t->rpad_hi, nr * 2); zero(t->rpad_lo, nr * 2);
     zero(t->err, sizeof(int));
-    // At most 512 / cols CTAs may share an SM's 512 TMEM columns: request
-    // enough shared memory that no more can be resident (233472 B per SM).
-    const size_t per_sm = 233472;
-    t->smemF = std::max(t->smemF, per_sm / (512 / t->colsF) + 1024);
-    t->smemA = std::max(t->smemA, per_sm / (512 / t->colsA) + 1024);
+    // the adjoint's slice count fixes the layout the forward epilogue writes
+    if (s == SWOPT_OK)
+        s = tune_dir(h, true, h->tc_force_mt[1], h->tc_force_ctas[1], h->tc_force_ra[1], &t->A);
+    if (s == SWOPT_OK)
+        s = tune_dir(h, false, h->tc_force_mt[0], h->tc_force_ctas[0], h->tc_force_ra[0], &t->F);
+    if (s == SWOPT_OK && (t->F.KS > ksf_max || t->A.KS > ksa_max)) {
+        set_error("internal: padded slice count exceeds the allocation");
+        s = SWOPT_ERR_DEVICE_CHECK;
+    }
     if (s == SWOPT_OK) {
-        const size_t mx = std::max(t->smemF, t->smemA);
-        if (cudaFuncSetAttribute(tc_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)mx) != cudaSuccess) {
-            set_error("cudaFuncSetAttribute failed for the tensor-core kernel");
+        // the tuning launches left data in the workspaces; clear the images
+        zero(t->bpad_hi, nb * 2); zero(t->bpad_lo, nb * 2);
+        zero(t->rpad_hi, nr * 2); zero(t->rpad_lo, nr * 2);
+        if (s == SWOPT_OK && cudaDeviceSynchronize() != cudaSuccess) {
+            set_error("synchronisation after tensor-core set-up failed");
             s = SWOPT_ERR_CUDA;
         }
     }
@@ -838,7 +1067,7 @@ swopt_status tc_states(swopt_handle* h, const float* c, cudaStream_t st)
     int grid = grid_for(n, 256);
     if (grid > 152 * 16) grid = 152 * 16;
     tc_states_kernel<<<grid, 256, 0, st>>>(c, h->Sm, t->bpad_hi, t->split ? t->bpad_lo : nullptr,
-                                           h->Q, h->P, h->Y, h->X, h->Z, slices, t->KSf, t->Yp,
+                                           h->Q, h->P, h->Y, h->X, h->Z, slices, t->F.KS, t->Yp,
                                            t->Xp, h->r);
     SW_LAUNCHED(h);
     return SWOPT_OK;
@@ -851,36 +1080,16 @@ swopt_status tc_pack_u(swopt_handle* h, cudaStream_t st)
     int grid = grid_for(n, 256);
     if (grid > 152 * 16) grid = 152 * 16;
     tc_pack_kernel<<<grid, 256, 0, st>>>(h->u, t->rpad_hi, t->split ? t->rpad_lo : nullptr, h->Q,
-                                         h->Y, h->X, h->Twp, t->KSa, t->Yp, t->Xp, h->r);
+                                         h->Y, h->X, h->Twp, t->A.KS, t->Yp, t->Xp, h->r);
     SW_LAUNCHED(h);
     return SWOPT_OK;
-}
-
-static TcArgs base_args(swopt_handle* h)
-{
-    TcOperator* t = h->tc;
-    TcArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.Cmf = h->Cmf;
-    a.err = t->err;
-    a.Y = h->Y; a.X = h->X; a.Yp = t->Yp; a.Xp = t->Xp; a.Z = h->Z; a.k = h->k; a.r = h->r;
-    a.HY = t->HY; a.HX = t->HX; a.tilesX = t->tilesX;
-    a.Twp = h->Twp;
-    a.KSo = t->KSa;
-    a.split = t->split;
-    return a;
 }
 
 swopt_status tc_forward(swopt_handle* h, bool to_r, const float* ytil, double* partials,
                         int scale, cudaStream_t st)
 {
     TcOperator* t = h->tc;
-    TcArgs a = base_args(h);
-    a.a_hi = t->bpad_hi; a.a_lo = t->bpad_lo;
-    a.b_hi = t->Bf_hi; a.b_lo = t->Bf_lo;
-    a.band = t->band_f;
-    a.KS = t->KSf; a.GA = t->GAf; a.NG = t->NGf; a.NS = t->NSf; a.NB = h->Twp;
-    a.adj = 0;
+    TcArgs a = dir_args(h, t, t->F, false);
     a.scale = scale;
     a.ytil = ytil;
     a.partials = partials;
@@ -888,12 +1097,9 @@ swopt_status tc_forward(swopt_handle* h, bool to_r, const float* ytil, double* p
     a.out_f = to_r ? nullptr : h->u;
     a.out_hi = to_r ? t->rpad_hi : nullptr;
     a.out_lo = to_r ? t->rpad_lo : nullptr;
-    a.tcols = (uint32_t)t->colsF;
-    dim3 grid(t->tilesX * t->tilesY, h->Q);
     ProfileRec rec;
     prof_begin(h, 0, st, &rec);
-    tc_conv_kernel<<<grid, kTcThreads, t->smemF, st>>>(a);
-    SW_LAUNCHED(h);
+    SW_TRY(launch_conv(h, t->F, a, st));
     prof_end(h, &rec, st);
     return SWOPT_OK;
 }
@@ -901,19 +1107,11 @@ swopt_status tc_forward(swopt_handle* h, bool to_r, const float* ytil, double* p
 swopt_status tc_adjoint(swopt_handle* h, cudaStream_t st)
 {
     TcOperator* t = h->tc;
-    TcArgs a = base_args(h);
-    a.a_hi = t->rpad_hi; a.a_lo = t->rpad_lo;
-    a.b_hi = t->Ba_hi; a.b_lo = t->Ba_lo;
-    a.band = t->band_a;
-    a.KS = t->KSa; a.GA = t->GAa; a.NG = t->NGa; a.NS = t->NSa; a.NB = t->Zp16;
-    a.adj = 1;
+    TcArgs a = dir_args(h, t, t->A, true);
     a.out_f = h->g;
-    a.tcols = (uint32_t)t->colsA;
-    dim3 grid(t->tilesX * t->tilesY, h->Q);
     ProfileRec rec;
     prof_begin(h, 1, st, &rec);
-    tc_conv_kernel<<<grid, kTcThreads, t->smemA, st>>>(a);
-    SW_LAUNCHED(h);
+    SW_TRY(launch_conv(h, t->A, a, st));
     prof_end(h, &rec, st);
     return SWOPT_OK;
 }
@@ -930,7 +1128,19 @@ int tc_error_word(swopt_handle* h)
 double tc_issued_macs(const swopt_handle* h, int kernel)
 {
     if (!h->tc) return 0;
-    return kernel == 0 ? h->tc->macs_f : h->tc->macs_a;
+    return kernel == 0 ? h->tc->F.macs : h->tc->A.macs;
+}
+
+void tc_config(const swopt_handle* h, int kernel, int* mt, int* ctas_per_sm, int* stages,
+               int* groups, int* replicas)
+{
+    const TcDir& D = kernel == 0 ? h->tc->F : h->tc->A;
+    *mt = D.MT;
+    *replicas = D.RA;
+    *ctas_per_sm = (int)(233472 / (D.smem + 1024));
+    if (*ctas_per_sm > 512 / D.cols) *ctas_per_sm = 512 / D.cols;
+    *stages = D.NS;
+    *groups = D.NG;
 }
 
 }  // namespace swopt

@@ -122,6 +122,9 @@ struct swopt_handle {
 
     // tensor-core path
     swopt::TcOperator* tc = nullptr;
+    int tc_force_mt[2] = {0, 0};     // tiles per CTA of A / A^T (0: tuned)
+    int tc_force_ctas[2] = {0, 0};   // CTAs per SM of A / A^T (0: tuned)
+    int tc_force_ra[2] = {0, 0};     // accumulator replicas of A / A^T (0: tuned)
 
     // instrumentation
     bool profile = false;
@@ -170,6 +173,9 @@ int tc_forward_blocks(const swopt_handle* h);
 int tc_error_word(swopt_handle* h);
 // MMA multiply-adds issued by one launch of the forward (0) / adjoint (1)
 double tc_issued_macs(const swopt_handle* h, int kernel);
+// configuration chosen for the forward (0) / adjoint (1)
+void tc_config(const swopt_handle* h, int kernel, int* mt, int* ctas_per_sm, int* stages,
+               int* groups, int* replicas);
 
 // Elementwise / layout kernels (operator_simt.cu).
 swopt_status launch_states(swopt_handle* h, const float* c, float* b, cudaStream_t st);
