@@ -77,9 +77,11 @@ typedef struct {
  *  SWOPT_PREC_FP32 : FP32 FMA on the CUDA cores (the accuracy reference).
  *  SWOPT_PREC_BF16 : tcgen05 tensor cores, BF16 operands, FP32 accumulation.
  *  SWOPT_PREC_BF16X3: tcgen05 tensor cores on a two-term BF16 split of both
- *                    operands (hi*hi + hi*lo + lo*hi), FP32 accumulation:
- *                    about 16 significant bits per product (relative error
- *                    of the operator ~1e-5). */
+ *                    operands (v = v0 + v1; v0 w0 + v0 w1 + v1 w0), FP32
+ *                    accumulation with the two correction products in an
+ *                    accumulator of their own: measured relative error of
+ *                    the operator 4e-6 (A) and 1e-5 (A^T) at 64^3 x 256 with
+ *                    15 x 15 support, against 1e-6 for SWOPT_PREC_FP32. */
 typedef enum {
     SWOPT_PREC_FP32 = 0,
     SWOPT_PREC_BF16 = 1,
@@ -107,6 +109,19 @@ typedef struct {
     int momentum;       /* swopt_momentum of Algorithm 1 */
     int inner_momentum; /* swopt_momentum of Algorithm 2 */
     int power_iters;    /* power iterations when step <= 0 (>= 1) */
+    /* Refined gradient (not in the paper; an iterative-refinement scheme for
+     * the low-precision contractions).  0: every iteration evaluates the
+     * gradient at the momentum point directly, at the handle's precision.
+     * R >= 1: the gradient G_k = H^T (H c_k - y) is kept in FP32 and updated
+     * with the normal operator applied to the increment,
+     * G_{k+1} = G_k + H^T H (c_{k+1} - c_k), at the handle's precision; every
+     * R-th iteration (and at the start) it is recomputed from c_{k+1} at
+     * refine_precision.  The gradient at the momentum point follows by
+     * linearity, (1 + beta_k) G_{k+1} - beta_k G_k.  In exact arithmetic the
+     * iterates are those of Algorithm 1; the increment's rounding error
+     * scales with ||c_{k+1} - c_k|| and so shrinks as the solve converges. */
+    int refine_every;
+    int refine_precision; /* swopt_precision of the initial and periodic exact gradients */
     double* history_host; /* optional [max_iters]: F(c_{k+1}) per iteration */
 } swopt_solve_params;
 
@@ -203,9 +218,17 @@ swopt_status swopt_objective(swopt_handle* h, const float* c_dev, const float* y
 swopt_status swopt_param_grad(swopt_handle* h, const float* c_dev, const float* y_dev,
                               double* dkappa_host, double* dmu, void* stream);
 
+/* CUDA graphs (default on): swopt_fista_step captures one iteration into a
+ * CUDA graph on first use after swopt_fista_init (on a stream the handle
+ * owns) and replays it on the caller's stream; on = 0 launches the kernels
+ * one by one instead.  Changing the precision or the tensor-core
+ * configuration discards the graph. */
+swopt_status swopt_use_graphs(swopt_handle* h, int on);
+
 /* Instrumentation.  swopt_profile_enable(h, 1) records CUDA events around
- * every launch of the A and A^T contraction kernels on the launching
- * stream; swopt_profile_read returns, for kernel_id 0 (A) or 1 (A^T), the
+ * every launch of the A and A^T contraction kernels on the launching stream
+ * (inside a replayed FISTA graph, through its event-record nodes);
+ * swopt_profile_read returns, for kernel_id 0 (A) or 1 (A^T), the
  * summed device time in milliseconds, the number of launches and the
  * algorithmic FLOPs of one launch (2 x multiply-adds of nonzero kernel taps).
  * Reading synchronises on the recorded events and clears them.
@@ -224,24 +247,28 @@ swopt_status swopt_check_device(swopt_handle* h, void* stream);
 /* FLOPs issued by one launch of the A (kernel_id 0) or A^T (1) contraction in
  * the current precision: 2 x the multiply-adds the kernel executes,
  * including the zero-padded parts of the kernel band it does not skip (for
- * the split BF16 mode, all three products). */
+ * the split BF16 modes, all 3 or 6 products). */
 swopt_status swopt_issued_flops(swopt_handle* h, int kernel_id, double* flops);
 
 /* Tensor-core tile configuration (autotuner).  When a BF16 precision is
  * selected, the library times each candidate configuration of the A (0) and
  * A^T (1) kernels on the handle's geometry and keeps the fastest.  A
- * configuration is: 1, 2 or 4 tiles of 16 x 8 positions per CTA; 1-8
- * accumulator replicas per tile (successive taps rotate over them, which
- * keeps independent MMA chains in flight; the epilogue sums them); one or
- * two CTAs per SM.  swopt_tc_configure pins tiles_per_cta (1, 2, 4),
- * ctas_per_sm (1, 2) and replicas (1-8) instead, 0 leaving a field tuned,
- * and rebuilds the operator if one is active (synchronises).  swopt_tc_config
+ * configuration is: 1, 2 or 4 tiles of 16 x 8 positions per CTA; one or two
+ * CTAs per SM; one or two FP32 accumulators per tile.  With two, the
+ * correction products of the split precisions (every product but hi x hi)
+ * accumulate apart from the main products and the epilogue adds the two: the
+ * corrections are about 2^-8 of the main sum, so each accumulation step into
+ * their accumulator rounds 2^-8 finer.  The default is two for the split
+ * precisions where TMEM holds them, else one; the choice is not timed.
+ * swopt_tc_configure pins tiles_per_cta (1, 2, 4), ctas_per_sm (1, 2) and
+ * accumulators (1, 2) instead, 0 leaving a field at its default, and
+ * rebuilds the operator if one is active (synchronises).  swopt_tc_config
  * reports the configuration in use (INVALID_ARG if no BF16 precision is
  * selected). */
 swopt_status swopt_tc_configure(swopt_handle* h, int kernel_id, int tiles_per_cta, int ctas_per_sm,
-                                int replicas);
+                                int accumulators);
 swopt_status swopt_tc_config(swopt_handle* h, int kernel_id, int* tiles_per_cta, int* ctas_per_sm,
-                             int* stages, int* groups, int* replicas);
+                             int* stages, int* groups, int* accumulators);
 
 /* Operator facts: the time window [t0, t0 + tw) that holds every nonzero
  * kernel sample, the number of distinct switching states Q = min(N,

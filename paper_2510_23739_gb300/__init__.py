@@ -57,6 +57,7 @@ class _SolveParams(ctypes.Structure):
                 ("max_iters", ctypes.c_int), ("eps1", ctypes.c_double),
                 ("eps2", ctypes.c_double), ("momentum", ctypes.c_int),
                 ("inner_momentum", ctypes.c_int), ("power_iters", ctypes.c_int),
+                ("refine_every", ctypes.c_int), ("refine_precision", ctypes.c_int),
                 ("history_host", ctypes.POINTER(ctypes.c_double))]
 
 
@@ -100,6 +101,7 @@ _SIGS = {
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.c_void_p], ctypes.c_int),
     "swopt_profile_enable": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "swopt_use_graphs": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "swopt_profile_read": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
                            ctypes.c_int),
@@ -167,7 +169,7 @@ class SolveParams:
 
     def __init__(self, step=0.0, lambda_l1=1e-3, lambda_tv=1e-3, inner_iters=10, max_iters=100,
                  eps1=0.0, eps2=0.0, momentum="beck_teboulle", inner_momentum="beck_teboulle",
-                 power_iters=100):
+                 power_iters=100, refine_every=0, refine_precision="bf16x3"):
         self.step = step
         self.lambda_l1 = lambda_l1
         self.lambda_tv = lambda_tv
@@ -178,6 +180,8 @@ class SolveParams:
         self.momentum = momentum
         self.inner_momentum = inner_momentum
         self.power_iters = power_iters
+        self.refine_every = refine_every
+        self.refine_precision = refine_precision
 
     def _c(self, history=None):
         p = _SolveParams()
@@ -192,6 +196,10 @@ class SolveParams:
         p.inner_momentum = (MOMENTUM[self.inner_momentum] if isinstance(self.inner_momentum, str)
                             else int(self.inner_momentum))
         p.power_iters = int(self.power_iters)
+        p.refine_every = int(self.refine_every)
+        p.refine_precision = (PRECISION[self.refine_precision]
+                              if isinstance(self.refine_precision, str)
+                              else int(self.refine_precision))
         p.history_host = (history.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
                           if history is not None else ctypes.POINTER(ctypes.c_double)())
         return p
@@ -351,6 +359,9 @@ class Operator:
         return dk, dmu.value
 
     # -- instrumentation --------------------------------------------------
+    def use_graphs(self, on=True):
+        _check(lib().swopt_use_graphs(self._h, 1 if on else 0))
+
     def profile(self, on=True):
         _check(lib().swopt_profile_enable(self._h, 1 if on else 0))
 
@@ -368,15 +379,15 @@ class Operator:
         _check(lib().swopt_issued_flops(self._h, int(kernel_id), ctypes.byref(f)))
         return f.value
 
-    def tc_configure(self, kernel_id, tiles_per_cta=0, ctas_per_sm=0, replicas=0):
+    def tc_configure(self, kernel_id, tiles_per_cta=0, ctas_per_sm=0, accumulators=0):
         _check(lib().swopt_tc_configure(self._h, int(kernel_id), int(tiles_per_cta),
-                                        int(ctas_per_sm), int(replicas)))
+                                        int(ctas_per_sm), int(accumulators)))
 
     def tc_config(self, kernel_id):
         v = [ctypes.c_int() for _ in range(5)]
         _check(lib().swopt_tc_config(self._h, int(kernel_id), *[ctypes.byref(x) for x in v]))
         return {"tiles_per_cta": v[0].value, "ctas_per_sm": v[1].value, "stages": v[2].value,
-                "groups": v[3].value, "replicas": v[4].value}
+                "groups": v[3].value, "accumulators": v[4].value}
 
     def launch_count(self):
         n = ctypes.c_int64()

@@ -34,18 +34,41 @@ enum {
     SC_COUNT = 16
 };
 
+// Two timing events from the handle's pool (created when the pool is empty).
+bool take_events(swopt_handle* h, cudaEvent_t* a, cudaEvent_t* b)
+{
+    if (h->event_pool.size() >= 2) {
+        *a = h->event_pool.back(); h->event_pool.pop_back();
+        *b = h->event_pool.back(); h->event_pool.pop_back();
+        return true;
+    }
+    if (cudaEventCreate(a) != cudaSuccess) return false;
+    if (cudaEventCreate(b) != cudaSuccess) {
+        cudaEventDestroy(*a);
+        return false;
+    }
+    return true;
+}
+
 void prof_begin(swopt_handle* h, int kernel, cudaStream_t st, ProfileRec* rec)
 {
     rec->kernel = -1;
+    if (h->capturing) {
+        // an event-record node in the graph; its event is swapped per replay
+        cudaEvent_t a;
+        if (cudaEventCreate(&a) != cudaSuccess) return;
+        if (cudaEventRecordWithFlags(a, st, cudaEventRecordExternal) != cudaSuccess) {
+            cudaEventDestroy(a);
+            return;
+        }
+        h->cap_events.push_back({a, kernel});
+        rec->a = a;
+        rec->kernel = kernel;
+        return;
+    }
     if (!h->profile) return;
     cudaEvent_t a, b;
-    if (h->event_pool.size() >= 2) {
-        a = h->event_pool.back(); h->event_pool.pop_back();
-        b = h->event_pool.back(); h->event_pool.pop_back();
-    } else {
-        if (cudaEventCreate(&a) != cudaSuccess) return;
-        if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
-    }
+    if (!take_events(h, &a, &b)) return;
     rec->a = a;
     rec->b = b;
     rec->kernel = kernel;
@@ -55,6 +78,16 @@ void prof_begin(swopt_handle* h, int kernel, cudaStream_t st, ProfileRec* rec)
 void prof_end(swopt_handle* h, ProfileRec* rec, cudaStream_t st)
 {
     if (rec->kernel < 0) return;
+    if (h->capturing) {
+        cudaEvent_t b;
+        if (cudaEventCreate(&b) != cudaSuccess) return;
+        if (cudaEventRecordWithFlags(b, st, cudaEventRecordExternal) != cudaSuccess) {
+            cudaEventDestroy(b);
+            return;
+        }
+        h->cap_events.push_back({b, -1 - rec->kernel});  // end marker
+        return;
+    }
     cudaEventRecord(rec->b, st);
     h->prof.push_back(*rec);
 }
@@ -97,13 +130,59 @@ void dfree(T*& p)
     p = nullptr;
 }
 
+void release_graph(swopt_handle* h)
+{
+    for (IterGraph& g : h->graphs) {
+        if (g.gexec) cudaGraphExecDestroy(g.gexec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+        g = IterGraph();
+    }
+    for (auto& e : h->cap_events) cudaEventDestroy(e.first);
+    h->cap_events.clear();
+}
+
+// Within its scope the handle computes at the refined solve's resync
+// precision: h->precision and the tensor-core operator are swapped for those
+// of the resync (a no-op when the two precisions agree).
+struct RefScope {
+    swopt_handle* h;
+    int prec;
+    TcOperator* tc;
+    bool active;
+    RefScope(swopt_handle* hh, int ref_precision)
+        : h(hh), prec(hh->precision), tc(hh->tc), active(ref_precision != hh->precision)
+    {
+        if (!active) return;
+        h->precision = ref_precision;
+        h->tc = h->tc_ref;
+    }
+    ~RefScope()
+    {
+        if (!active) return;
+        h->tc_ref = h->tc;
+        h->tc = tc;
+        h->precision = prec;
+    }
+};
+
+void release_ref(swopt_handle* h)
+{
+    std::swap(h->tc, h->tc_ref);
+    tc_release(h);
+    std::swap(h->tc, h->tc_ref);
+}
+
 void release_all(swopt_handle* h)
 {
+    release_graph(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
     tc_release(h);
+    release_ref(h);
     dfree(h->Kf); dfree(h->Ka); dfree(h->fmask); dfree(h->amask); dfree(h->Sm); dfree(h->Cmf);
     dfree(h->b); dfree(h->u); dfree(h->g); dfree(h->ytil); dfree(h->red); dfree(h->scal);
     dfree(h->c); dfree(h->xi); dfree(h->zin); dfree(h->tvu); dfree(h->tvr0); dfree(h->tvr1);
-    dfree(h->tmp);
+    dfree(h->tmp); dfree(h->G); dfree(h->xprev);
     if (h->scal_host) cudaFreeHost(h->scal_host);
     h->scal_host = nullptr;
     for (auto& r : h->prof) {
@@ -158,7 +237,12 @@ swopt_status ensure_ytil(swopt_handle* h)
 // Device-side failures recorded by the kernels (a bounded wait that gave up).
 swopt_status device_errors(swopt_handle* h)
 {
-    const int w = tc_error_word(h);
+    int w = tc_error_word(h);
+    if (w == 0) {
+        std::swap(h->tc, h->tc_ref);
+        w = tc_error_word(h);
+        std::swap(h->tc, h->tc_ref);
+    }
     if (w > 0) {
         set_error("a tensor-core kernel gave up a bounded wait (code %d)", w);
         return SWOPT_ERR_TIMEOUT;
@@ -186,10 +270,17 @@ bool use_tc(const swopt_handle* h) { return h->precision != SWOPT_PREC_FP32; }
 // (scale ? Cm : 1) * (A P c) - ytil  (see simt_forward).
 enum { A_OUT_U = 0, A_OUT_R = 1 };
 
+swopt_status no_tc_operator()
+{
+    set_error("internal: no tensor-core operator for the selected precision");
+    return SWOPT_ERR_DEVICE_CHECK;
+}
+
 swopt_status apply_A(swopt_handle* h, const float* c, int out, const float* ytil,
                      double* partials, int scale, cudaStream_t st)
 {
     if (use_tc(h)) {
+        if (!h->tc) return no_tc_operator();
         SW_TRY(tc_states(h, c, st));
         return tc_forward(h, out == A_OUT_R, ytil, partials, scale, st);
     }
@@ -202,6 +293,7 @@ swopt_status apply_A(swopt_handle* h, const float* c, int out, const float* ytil
 swopt_status apply_AT(swopt_handle* h, bool from_u, cudaStream_t st)
 {
     if (use_tc(h)) {
+        if (!h->tc) return no_tc_operator();
         if (from_u) SW_TRY(tc_pack_u(h, st));
         return tc_adjoint(h, st);
     }
@@ -247,7 +339,8 @@ swopt_status validate_params(const swopt_solve_params* p)
     if (!is_fin(p->step) || !is_fin(p->lambda_l1) || !is_fin(p->lambda_tv) || !is_fin(p->eps1) ||
         !is_fin(p->eps2) || p->lambda_l1 < 0 || p->lambda_tv < 0 || p->inner_iters < 0 ||
         p->inner_iters > 100000 || p->max_iters < 0 || p->momentum < 0 || p->momentum > 2 ||
-        p->inner_momentum < 0 || p->inner_momentum > 2 ||
+        p->inner_momentum < 0 || p->inner_momentum > 2 || p->refine_every < 0 ||
+        p->refine_precision < SWOPT_PREC_FP32 || p->refine_precision > SWOPT_PREC_BF16X3 ||
         (p->step <= 0 && (p->power_iters < 1 || p->power_iters > 100000))) {
         set_error("invalid solve parameters");
         return SWOPT_ERR_INVALID_ARG;
@@ -255,19 +348,165 @@ swopt_status validate_params(const swopt_solve_params* p)
     return SWOPT_OK;
 }
 
+// Refined solve: the gradient G = P^T A^T (C A P c - ytil) at c = h->c,
+// evaluated at the resync precision, replaces h->G; h->zin receives the
+// gradient step at the momentum point (see launch_pt_refine).
+swopt_status exact_gradient(swopt_handle* h, cudaStream_t st)
+{
+    RefScope sc(h, h->prm.refine_precision);
+    SW_TRY(apply_A(h, h->c, A_OUT_R, h->ytil, nullptr, 1, st));
+    SW_TRY(apply_AT(h, false, st));
+    return launch_pt_refine(h, h->g, h->xi, (float)h->step, h->G, h->zin, 0, st);
+}
+
+// Builds the resync precision's tensor-core operator if the refined solve
+// needs one (synchronises; never called while capturing).
+swopt_status ensure_ref(swopt_handle* h)
+{
+    const int rp = h->prm.refine_precision;
+    if (h->prm.refine_every <= 0 || rp == SWOPT_PREC_FP32 || rp == h->precision) return SWOPT_OK;
+    RefScope sc(h, rp);
+    return tc_prepare(h);
+}
+
+// Kind of FISTA iteration number h->iter: 1 when the refined solve
+// recomputes its gradient exactly at the end of it, else 0.
+int iteration_kind(const swopt_handle* h)
+{
+    const int R = h->prm.refine_every;
+    return (R > 0 && (h->iter + 1) % R == 0) ? 1 : 0;
+}
+
 // One FISTA iteration on the bound measurements (all on `st`, no host sync).
-swopt_status fista_iteration(swopt_handle* h, cudaStream_t st)
+//
+// Plain (refine_every = 0): the gradient at xi_k is evaluated directly,
+//   z = xi_k - alpha P^T A^T (C A P xi_k - ytil), then the prox and momentum.
+// Refined (refine_every = R): the prox input z_k is already in h->zin, and the
+//   gradient at c_k in h->G.  After the prox and momentum update, the gradient
+//   at c_{k+1} is G + H^T H (c_{k+1} - c_k), the normal operator applied to
+//   the increment at the handle's precision (kind 0), or is recomputed
+//   from c_{k+1} at the resync precision (kind 1).  The gradient step at
+//   xi_{k+1} then follows by linearity.  In exact arithmetic both variants
+//   give the iterates of Algorithm 1.
+swopt_status fista_iteration(swopt_handle* h, int kind, cudaStream_t st)
 {
     const float alpha = (float)h->step;
     const bool tv = h->prm.lambda_tv > 0 && h->prm.inner_iters > 0;
-    SW_TRY(apply_A(h, h->xi, A_OUT_R, h->ytil, nullptr, 1, st));     // P, A, folded residual
-    SW_TRY(apply_AT(h, false, st));                                   // A^T
-    SW_TRY(launch_pt(h, h->g, h->xi, alpha, h->zin, 1, st));          // P^T, gradient step
+    const bool refined = h->prm.refine_every > 0;
+    if (!refined) {
+        SW_TRY(apply_A(h, h->xi, A_OUT_R, h->ytil, nullptr, 1, st));     // P, A, folded residual
+        SW_TRY(apply_AT(h, false, st));                                   // A^T
+        SW_TRY(launch_pt(h, h->g, h->xi, alpha, h->zin, 1, st));          // P^T, gradient step
+    }
     if (tv)
         SW_TRY(prox_tv_iters(h, h->zin, (float)(h->step * h->prm.lambda_tv),
                              h->prm.inner_iters, h->inner_beta.data(), st));
     SW_TRY(fista_scalars(h, h->prm.momentum, st));
-    return fista_finish(h, h->zin, tv, (float)(h->step * h->prm.lambda_l1), st);
+    SW_TRY(fista_finish(h, h->zin, tv, (float)(h->step * h->prm.lambda_l1),
+                        refined ? h->tmp : nullptr, st));
+    if (!refined) return SWOPT_OK;
+    if (kind == 1) return exact_gradient(h, st);
+    SW_TRY(apply_A(h, h->tmp, A_OUT_R, nullptr, nullptr, 1, st));        // C A P delta
+    SW_TRY(apply_AT(h, false, st));
+    return launch_pt_refine(h, h->g, h->xi, alpha, h->G, h->zin, 1, st);
+}
+
+// Captures one FISTA iteration into a CUDA graph on the handle's capture
+// stream (the caller's stream may be the legacy default stream, which cannot
+// capture); the graph is then launched on the caller's stream.
+swopt_status build_graph(swopt_handle* h, int kind)
+{
+    IterGraph& G = h->graphs[kind];
+    if (!h->cap_stream) SW_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    const int64_t launches0 = h->launches;
+    const size_t ev0 = h->cap_events.size();
+    SW_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    swopt_status s = fista_iteration(h, kind, h->cap_stream);
+    h->capturing = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (s != SWOPT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) {
+        set_error("graph capture failed: %s", cudaGetErrorString(e));
+        return SWOPT_ERR_CUDA;
+    }
+    G.graph = g;
+    G.kernels = h->launches - launches0;
+    h->launches = launches0;
+    SW_CUDA(cudaGraphInstantiate(&G.gexec, g, 0));
+    // locate the event-record nodes that bracket the A / A^T kernels
+    size_t n = 0;
+    SW_CUDA(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    SW_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
+    std::vector<std::pair<cudaEvent_t, cudaGraphNode_t>> rec;
+    for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        SW_CUDA(cudaGraphNodeGetType(nd, &ty));
+        if (ty != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev;
+        SW_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+        rec.push_back({ev, nd});
+    }
+    auto node_of = [&](cudaEvent_t ev) -> cudaGraphNode_t {
+        for (auto& r : rec)
+            if (r.first == ev) return r.second;
+        return nullptr;
+    };
+    for (size_t i = ev0; i + 1 < h->cap_events.size(); ++i) {
+        const auto& b = h->cap_events[i];
+        const auto& en = h->cap_events[i + 1];
+        if (b.second >= 0 && en.second == -1 - b.second) {
+            GraphProbe pr;
+            pr.begin = node_of(b.first);
+            pr.end = node_of(en.first);
+            pr.ev_begin = b.first;
+            pr.ev_end = en.first;
+            pr.kernel = b.second;
+            if (pr.begin && pr.end) G.probes.push_back(pr);
+            ++i;
+        }
+    }
+    return SWOPT_OK;
+}
+
+// One replay of a captured iteration on `st` (with fresh events on the
+// probe nodes when profiling).
+swopt_status launch_graph(swopt_handle* h, int kind, cudaStream_t st)
+{
+    IterGraph& G = h->graphs[kind];
+    if (h->profile) {
+        for (auto& pr : G.probes) {
+            ProfileRec rec;
+            if (!take_events(h, &rec.a, &rec.b)) continue;
+            rec.kernel = pr.kernel;
+            SW_CUDA(cudaGraphExecEventRecordNodeSetEvent(G.gexec, pr.begin, rec.a));
+            SW_CUDA(cudaGraphExecEventRecordNodeSetEvent(G.gexec, pr.end, rec.b));
+            h->prof.push_back(rec);
+        }
+    }
+    SW_CUDA(cudaGraphLaunch(G.gexec, st));
+    h->launches += G.kernels;
+    return SWOPT_OK;
+}
+
+// The next FISTA iteration, replayed from its graph when graphs are on.
+swopt_status run_iteration(swopt_handle* h, cudaStream_t st)
+{
+    SW_TRY(ensure_ref(h));
+    const int kind = iteration_kind(h);
+    if (h->use_graph) {
+        if (!h->graphs[kind].gexec) SW_TRY(build_graph(h, kind));
+        SW_TRY(launch_graph(h, kind, st));
+    } else {
+        SW_TRY(fista_iteration(h, kind, st));
+    }
+    ++h->iter;
+    return SWOPT_OK;
 }
 
 // F(c) and the data fit on measurements y (FP64; slots SC_A..SC_D).
@@ -502,6 +741,8 @@ swopt_status swopt_set_precision(swopt_handle* h, int precision)
         set_error("unknown precision %d", precision);
         return SWOPT_ERR_INVALID_ARG;
     }
+    release_graph(h);
+    release_ref(h);
     if (precision != SWOPT_PREC_FP32) {
         const int prev = h->precision;
         h->precision = precision;
@@ -599,6 +840,7 @@ swopt_status swopt_fista_init(swopt_handle* h, const float* y_dev, const swopt_s
     SW_TRY(validate_params(prm));
     cudaStream_t st = (cudaStream_t)stream;
     h->fista_ready = false;
+    release_graph(h);
     SW_TRY(ensure_vectors(h));
     SW_TRY(ensure_ytil(h));
     if (prm->lambda_tv > 0 && prm->inner_iters > 0) SW_TRY(ensure_tv_buffers(h));
@@ -620,6 +862,14 @@ swopt_status swopt_fista_init(swopt_handle* h, const float* y_dev, const swopt_s
     SW_CUDA(cudaMemsetAsync(h->c, 0, nc_of(h) * sizeof(float), st));
     SW_CUDA(cudaMemsetAsync(h->xi, 0, nc_of(h) * sizeof(float), st));
     SW_TRY(fista_reset_scalars(h, st));
+    h->iter = 0;
+    if (prm->refine_every > 0) {
+        // gradient at c_0 = 0 and the first prox input, at the resync precision
+        if (!h->G) SW_TRY(dalloc(&h->G, nc_of(h)));
+        SW_CUDA(cudaMemsetAsync(h->G, 0, nc_of(h) * sizeof(float), st));
+        SW_TRY(ensure_ref(h));
+        SW_TRY(exact_gradient(h, st));
+    }
     h->fista_ready = true;
     return SWOPT_OK;
 }
@@ -637,7 +887,7 @@ swopt_status swopt_fista_step(swopt_handle* h, int iters, void* stream)
         return SWOPT_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    for (int i = 0; i < iters; ++i) SW_TRY(fista_iteration(h, st));
+    for (int i = 0; i < iters; ++i) SW_TRY(run_iteration(h, st));
     return SWOPT_OK;
 }
 
@@ -663,10 +913,12 @@ swopt_status swopt_solve(swopt_handle* h, const float* y_dev, float* c_dev,
     int it = 0;
     double f_prev = INFINITY;
     for (; it < prm->max_iters; ++it) {
-        if (tests && prm->eps2 > 0)
-            SW_CUDA(cudaMemcpyAsync(h->tmp, h->xi, nc_of(h) * sizeof(float),
+        if (tests && prm->eps2 > 0) {
+            if (!h->xprev) SW_TRY(dalloc(&h->xprev, nc_of(h)));
+            SW_CUDA(cudaMemcpyAsync(h->xprev, h->xi, nc_of(h) * sizeof(float),
                                     cudaMemcpyDeviceToDevice, st));
-        SW_TRY(fista_iteration(h, st));
+        }
+        SW_TRY(run_iteration(h, st));
         if (!tests) continue;
         double F = 0.0;
         if (prm->eps1 > 0 || prm->history_host)
@@ -677,9 +929,9 @@ swopt_status swopt_solve(swopt_handle* h, const float* y_dev, float* c_dev,
             stop = true;
         if (it >= 1 && prm->eps2 > 0) {
             // ||xi_{k+1} - xi_k|| / ||xi_k||
-            SW_TRY(reduce_sumsq(h, h->tmp, nc_of(h), SC_C, st));
+            SW_TRY(reduce_sumsq(h, h->xprev, nc_of(h), SC_C, st));
             SW_TRY(reduce_sumsq(h, h->xi, nc_of(h), SC_D, st));
-            SW_TRY(reduce_dot(h, h->xi, h->tmp, nc_of(h), SC_A, st));
+            SW_TRY(reduce_dot(h, h->xi, h->xprev, nc_of(h), SC_A, st));
             SW_TRY(read_scalars(h, st));
             const double a = h->scal_host[SC_D], b = h->scal_host[SC_C], ab = h->scal_host[SC_A];
             const double diff = std::sqrt(std::max(0.0, a + b - 2.0 * ab));
@@ -767,6 +1019,15 @@ swopt_status swopt_param_grad(swopt_handle* h, const float* c_dev, const float* 
     return SWOPT_OK;
 }
 
+swopt_status swopt_use_graphs(swopt_handle* h, int on)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    h->use_graph = on != 0;
+    release_graph(h);
+    return SWOPT_OK;
+}
+
 swopt_status swopt_profile_enable(swopt_handle* h, int on)
 {
     clear_error();
@@ -839,19 +1100,21 @@ swopt_status swopt_issued_flops(swopt_handle* h, int kernel_id, double* flops)
 }
 
 swopt_status swopt_tc_configure(swopt_handle* h, int kernel_id, int tiles_per_cta,
-                                int ctas_per_sm, int replicas)
+                                int ctas_per_sm, int accumulators)
 {
     clear_error();
     SW_TRY(check_handle(h));
     if (kernel_id < 0 || kernel_id > 1 || tiles_per_cta < 0 || tiles_per_cta > 4 ||
-        tiles_per_cta == 3 || ctas_per_sm < 0 || ctas_per_sm > 2 || replicas < 0 ||
-        replicas > 8) {
+        tiles_per_cta == 3 || ctas_per_sm < 0 || ctas_per_sm > 2 || accumulators < 0 ||
+        accumulators > 2) {
         set_error("invalid tensor-core configuration");
         return SWOPT_ERR_INVALID_ARG;
     }
+    release_graph(h);
     h->tc_force_mt[kernel_id] = tiles_per_cta;
     h->tc_force_ctas[kernel_id] = ctas_per_sm;
-    h->tc_force_ra[kernel_id] = replicas;
+    h->tc_force_ra[kernel_id] = accumulators;
+    release_ref(h);
     if (h->tc) {
         tc_release(h);
         if (use_tc(h)) return tc_prepare(h);
@@ -860,12 +1123,12 @@ swopt_status swopt_tc_configure(swopt_handle* h, int kernel_id, int tiles_per_ct
 }
 
 swopt_status swopt_tc_config(swopt_handle* h, int kernel_id, int* tiles_per_cta,
-                             int* ctas_per_sm, int* stages, int* groups, int* replicas)
+                             int* ctas_per_sm, int* stages, int* groups, int* accumulators)
 {
     clear_error();
     SW_TRY(check_handle(h));
     if (kernel_id < 0 || kernel_id > 1 || !tiles_per_cta || !ctas_per_sm || !stages || !groups ||
-        !replicas) {
+        !accumulators) {
         set_error("invalid arguments");
         return SWOPT_ERR_INVALID_ARG;
     }
@@ -873,7 +1136,7 @@ swopt_status swopt_tc_config(swopt_handle* h, int kernel_id, int* tiles_per_cta,
         set_error("no tensor-core precision selected");
         return SWOPT_ERR_INVALID_ARG;
     }
-    tc_config(h, kernel_id, tiles_per_cta, ctas_per_sm, stages, groups, replicas);
+    tc_config(h, kernel_id, tiles_per_cta, ctas_per_sm, stages, groups, accumulators);
     return SWOPT_OK;
 }
 

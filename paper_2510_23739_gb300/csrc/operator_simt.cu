@@ -319,6 +319,34 @@ __global__ void pt_kernel(const float* __restrict__ g, const float* __restrict__
     }
 }
 
+// Refined solve (gradient kept at c_k, updated by increments):
+//   d  = sum_m Sm[m][p][j] g[m][s][j]       (P^T of the A^T output)
+//   Gn = (add ? G : 0) + d                  (gradient at c_{k+1})
+//   out = xi - alpha ((1 + beta) Gn - beta G)   (gradient step at the
+//         momentum point xi_{k+1} = (1 + beta) c_{k+1} - beta c_k, by linearity)
+//   G  = Gn
+__global__ void pt_refine_kernel(const float* __restrict__ g, const float* __restrict__ Sm,
+                                 const float* __restrict__ xi, float alpha, float* G,
+                                 float* __restrict__ out, const double* __restrict__ scal,
+                                 int Q, int P, int S, int Z, int add)
+{
+    const size_t SZ = (size_t)S * Z;
+    const size_t n = (size_t)P * SZ;
+    const float beta = (float)scal[1];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i % Z);
+        const size_t sj = i % SZ;
+        const int p = (int)(i / SZ);
+        float acc = 0.f;
+        for (int m = 0; m < Q; ++m) acc = fmaf(Sm[(m * P + p) * Z + j], g[(size_t)m * SZ + sj], acc);
+        const float go = G[i];
+        const float gn = add ? go + acc : acc;
+        out[i] = fmaf(-alpha, fmaf(beta, gn - go, gn), xi[i]);
+        G[i] = gn;
+    }
+}
+
 int fwd_jc(const swopt_handle* h)
 {
     const int H = TILE + 2 * h->r;
@@ -409,6 +437,16 @@ swopt_status launch_pt(swopt_handle* h, const float* g, const float* xi, float a
     const size_t n = nc_of(h);
     pt_kernel<<<grid_for(n, 256), 256, 0, st>>>(g, h->Sm, xi, alpha, out, h->Q, h->P, h->S, h->Z,
                                                  mode);
+    SW_LAUNCHED(h);
+    return SWOPT_OK;
+}
+
+swopt_status launch_pt_refine(swopt_handle* h, const float* g, const float* xi, float alpha,
+                              float* G, float* out, int add, cudaStream_t st)
+{
+    const size_t n = nc_of(h);
+    pt_refine_kernel<<<grid_for(n, 256), 256, 0, st>>>(g, h->Sm, xi, alpha, G, out, h->scal,
+                                                        h->Q, h->P, h->S, h->Z, add);
     SW_LAUNCHED(h);
     return SWOPT_OK;
 }

@@ -32,9 +32,15 @@
 // CTA records an error in a device word, drains its own copies, frees its
 // TMEM and exits.
 //
-// Precisions: BF16 operands with FP32 accumulation, or a two-term BF16 split
-// of both operands (v = hi + lo) with the three products hi*hi + hi*lo +
-// lo*hi accumulated in FP32 (about 16 significant bits instead of 8).
+// Precisions: BF16 operands with FP32 accumulation (1 term), or a split of
+// both operands into 2 BF16 terms (v = v0 + v1, v1 the BF16 rounding of
+// v - v0) with the 3 products v0 w0, v0 w1, v1 w0 (the dropped v1 w1 is
+// below 2^-16 of |v w|) accumulated in FP32.  The 2 correction products go
+// to an accumulator of their own, so that the tensor core's FP32
+// accumulation rounds them on their own (2^-8 smaller) scale; what remains
+// is the rounding of the main accumulation, a few 1e-6 relative at depth x
+// support sums of 10^4 terms.  A third term (6 products) was measured to
+// give no further gain for that reason and is not offered.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -45,31 +51,33 @@
 
 namespace swopt {
 
+constexpr int kMaxTerms = 2;  // BF16 terms per operand of the split precision
+
 // Operator data of one direction (forward or adjoint).
 struct TcDir {
     int GA = 0, NG = 0, KS = 0;   // A slices per group, groups, padded slices
     int NB = 0;                   // accumulator columns per tile
     int MT = 1;                   // tiles per CTA
-    int RA = 1;                   // accumulator replicas per tile (taps rotate over them)
+    int RA = 1;                   // accumulators per tile: 1, or 2 (corrections apart)
     int NS = 4;                   // stages of the B ring
     uint32_t stage_bytes = 0;     // bytes of one stage (hi part; lo is as large)
     int HX = 0, npos = 0;         // halo width and positions
     int cols = 0;                 // TMEM columns allocated
     size_t smem = 0;              // dynamic shared memory requested
     int groupsX = 0;              // CTAs along x
-    __nv_bfloat16 *Bhi = nullptr, *Blo = nullptr;  // banded kernel, [group][tap][pair][2][N_p][8]
+    __nv_bfloat16* Bt[kMaxTerms] = {nullptr, nullptr};  // kernel per term, [group][tap][pair][2][N][8]
     uint32_t* tab = nullptr;      // per group: header + pair table (see TcArgs)
     int tab_words = 0;
     double macs = 0;              // issued MACs per launch
 };
 
 struct TcOperator {
-    int split = 0;
+    int terms = 1;                // BF16 terms per operand (1 or 2)
     int tilesX = 0, tilesY = 0, Yp = 0, Xp = 0, HY = 0;
     int Zp16 = 0;
     TcDir F, A;
-    __nv_bfloat16 *bpad_hi = nullptr, *bpad_lo = nullptr;  // [Q][F.KS][Yp][Xp][8]
-    __nv_bfloat16 *rpad_hi = nullptr, *rpad_lo = nullptr;  // [Q][A.KS][Yp][Xp][8]
+    __nv_bfloat16* bpad[kMaxTerms] = {nullptr, nullptr};  // [Q][F.KS][Yp][Xp][8] per term
+    __nv_bfloat16* rpad[kMaxTerms] = {nullptr, nullptr};  // [Q][A.KS][Yp][Xp][8] per term
     int* err = nullptr;
 };
 
@@ -219,35 +227,34 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// hi = bf16(v), lo = bf16(v - hi) for 8 values, packed as two uint4
-__device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo)
+// The BF16 terms of 8 values: t0 = bf16(v), then t1 = bf16(v - t0) when
+// `terms` is 2, each packed as one uint4.
+__device__ __forceinline__ void split_terms(const float* v, uint4* out, int terms)
 {
-    float h[8], l[8];
+    float r[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const __nv_bfloat16 b = __float2bfloat16_rn(v[e]);
-        h[e] = __bfloat162float(b);
-        l[e] = v[e] - h[e];
+    for (int e = 0; e < 8; ++e) r[e] = v[e];
+    for (int tt = 0; tt < terms; ++tt) {
+        float h[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            h[e] = __bfloat162float(__float2bfloat16_rn(r[e]));
+            r[e] -= h[e];
+        }
+        out[tt] = make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]),
+                             pack_bf16x2(h[4], h[5]), pack_bf16x2(h[6], h[7]));
     }
-    hi = make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]), pack_bf16x2(h[4], h[5]),
-                    pack_bf16x2(h[6], h[7]));
-    lo = make_uint4(pack_bf16x2(l[0], l[1]), pack_bf16x2(l[2], l[3]), pack_bf16x2(l[4], l[5]),
-                    pack_bf16x2(l[6], l[7]));
 }
 
-
 struct TcArgs {
-    const __nv_bfloat16* a_hi;  // [Q][KS][Yp][Xp][8]
-    const __nv_bfloat16* a_lo;
-    const __nv_bfloat16* b_hi;  // banded kernel, [group][tap][pair][2][N_p][8]
-    const __nv_bfloat16* b_lo;  // (split mode: the lo halves, same layout)
+    const __nv_bfloat16* a_t[kMaxTerms];  // per term: [Q][KS][Yp][Xp][8]
+    const __nv_bfloat16* b_t[kMaxTerms];  // per term: kernel [group][tap][pair][2][N][8]
     const uint4* tab;           // per group g: {base (16 B units), tap bytes, taps per
                                 // run, pairs}, then per run of taps (groups in order)
                                 // eight 16-bit A offsets of its taps in 16-B units
     int tab_n;                  // uint4 entries in tab
     float* out_f;               // forward mode 0: [Q][S][Twp]; adjoint: [Q][S][Z]
-    __nv_bfloat16* out_hi;      // forward mode 1: [Q][KSo][Yp][Xp][8]
-    __nv_bfloat16* out_lo;
+    __nv_bfloat16* out_t[kMaxTerms];    // forward mode 1, per term: [Q][KSo][Yp][Xp][8]
     const float* ytil;          // [Q][S][Twp] or null
     const float* Cmf;           // [Q]
     double* partials;           // per block, or null
@@ -256,7 +263,7 @@ struct TcArgs {
     int KS, GA, NG, NS, NB;
     uint32_t stage_bytes;
     int Twp, KSo;
-    int adj, split, scale, mode;
+    int adj, terms, scale, mode;
     uint32_t tcols;
 };
 
@@ -282,10 +289,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
     const uint32_t a_slice = npos * 16u;                       // bytes of one A slice
     const uint32_t a_part = (uint32_t)a.GA * a_slice;          // hi (or lo) A bytes
     const uint32_t sA = __shfl_sync(0xffffffffu, smem_u32(smem), 0);
-    const uint32_t sA_lo = sA + a_part;
-    const uint32_t b_region = a_part * (a.split ? 2u : 1u);
+    const uint32_t b_region = a_part * (uint32_t)a.terms;
     const uint32_t sB = sA + b_region;
-    const uint32_t stage_total = a.stage_bytes * (a.split ? 2u : 1u);
+    const uint32_t stage_total = a.stage_bytes * (uint32_t)a.terms;
     const uint32_t tab_region = b_region + (uint32_t)a.NS * stage_total;
     const uint4* s_tab = reinterpret_cast<const uint4*>(smem + tab_region);
 
@@ -343,7 +349,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                 ok = false;
                 break;
             }
-            if (lane == 0) mbar_expect_tx(smem_u32(&bar_afull), a_part * (a.split ? 2u : 1u));
+            if (lane == 0) mbar_expect_tx(smem_u32(&bar_afull), a_part * (uint32_t)a.terms);
             ++a_fills;
             __syncwarp();
             const size_t img = (size_t)m * a.KS + (size_t)g * a.GA;
@@ -351,10 +357,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                 const int sl = idx / a.HY, hy = idx - sl * a.HY;
                 const size_t goff = (((img + sl) * a.Yp + (size_t)(y0 + hy)) * a.Xp + x0) * 8;
                 const uint32_t soff = (uint32_t)sl * a_slice + (uint32_t)(hy * a.HX) * 16u;
-                bulk_g2s(sA + soff, a.a_hi + goff, (uint32_t)a.HX * 16u, smem_u32(&bar_afull));
-                if (a.split)
-                    bulk_g2s(sA_lo + soff, a.a_lo + goff, (uint32_t)a.HX * 16u,
-                             smem_u32(&bar_afull));
+                for (int tt = 0; tt < a.terms; ++tt)
+                    bulk_g2s(sA + (uint32_t)tt * a_part + soff, a.a_t[tt] + goff,
+                             (uint32_t)a.HX * 16u, smem_u32(&bar_afull));
             }
             for (int d0 = 0; d0 < kk && ok; d0 += (int)hd.z) {
                 const int nt = min((int)hd.z, kk - d0);
@@ -367,11 +372,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                     const uint32_t dst = sB + (uint32_t)stage * stage_total;
                     const uint32_t bytes = (uint32_t)nt * hd.y;
                     const size_t src = ((size_t)hd.x * 16 + (size_t)d0 * hd.y) / 2;  // elements
-                    mbar_expect_tx(bar, bytes * (a.split ? 2u : 1u));
-                    if (bytes) {
-                        bulk_g2s(dst, a.b_hi + src, bytes, bar);
-                        if (a.split) bulk_g2s(dst + a.stage_bytes, a.b_lo + src, bytes, bar);
-                    }
+                    mbar_expect_tx(bar, bytes * (uint32_t)a.terms);
+                    if (bytes)
+                        for (int tt = 0; tt < a.terms; ++tt)
+                            bulk_g2s(dst + (uint32_t)tt * a.stage_bytes, a.b_t[tt] + src, bytes, bar);
                 }
                 fills[stage]++;
                 __syncwarp();
@@ -415,7 +419,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         const uint64_t bdesc = bdesc_c | ((uint64_t)a.NB << 16);  // LBO = N x 16 B
         const uint32_t pair_b = 2u * (uint32_t)a.NB * 16u;         // B bytes of one pair
         const int MT = a.MT, NBc = a.NB;
-        const bool split = a.split != 0;
+        const int terms = a.terms;
         int run = 0;
         for (int g = 0; g < a.NG && ok; ++g) {
             const uint4 hd = s_tab[g];
@@ -447,6 +451,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                 const uint64_t tapb16 = tapb >> 4;
                 for (int i = 0; i < MT; ++i) {
                     const uint32_t dt = tmem + (uint32_t)(i * NBc);
+                    // correction products: own accumulator when RA == 2
+                    const uint32_t dc = tmem + (uint32_t)((a.RA > 1 ? MT + i : i) * NBc);
                     for (int p = 0; p < np; ++p) {
                         const uint64_t adp = adesc_c | (uint64_t)((sA + 2u * (uint32_t)p * a_slice +
                                                                    (uint32_t)i * 128u) >> 4);
@@ -459,9 +465,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                                         adp + (uint64_t)((ow[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
                                     const uint64_t bd = bdp + (uint64_t)t * tapb16;
                                     tc_mma(dt, ad, bd, idesc, 1u);
-                                    if (split) {
-                                        tc_mma(dt, ad, bd + blo16, idesc, 1u);
-                                        tc_mma(dt, ad + alo16, bd, idesc, 1u);
+                                    if (terms > 1) {
+                                        tc_mma(dc, ad, bd + blo16, idesc, 1u);
+                                        tc_mma(dc, ad + alo16, bd, idesc, 1u);
                                     }
                                 }
                             }
@@ -507,10 +513,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                 const size_t pos = (size_t)y * a.X + x;
                 for (int cb = 0; cb < a.NB / 16; ++cb) {
                     float v[16];
-                    tmem_ld16(tmem + lanes + (uint32_t)(ti * a.RA * a.NB + cb * 16), v);
+                    tmem_ld16(tmem + lanes + (uint32_t)(ti * a.NB + cb * 16), v);
                     for (int rp = 1; rp < a.RA; ++rp) {
                         float w[16];
-                        tmem_ld16(tmem + lanes + (uint32_t)((ti * a.RA + rp) * a.NB + cb * 16), w);
+                        tmem_ld16(tmem + lanes + (uint32_t)((rp * a.MT + ti) * a.NB + cb * 16), w);
 #pragma unroll
                         for (int e = 0; e < 16; ++e) v[e] += w[e];
                     }
@@ -560,10 +566,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                         for (int h = 0; h < 2; ++h) {
                             const size_t ro = ((((size_t)m * a.KSo + 2 * cb + h) * a.Yp +
                                                 (y + a.r)) * a.Xp + (x + a.r)) * 8;
-                            uint4 hi, lo;
-                            split8(o + 8 * h, hi, lo);
-                            *reinterpret_cast<uint4*>(a.out_hi + ro) = hi;
-                            if (a.out_lo) *reinterpret_cast<uint4*>(a.out_lo + ro) = lo;
+                            uint4 parts[kMaxTerms];
+                            split_terms(o + 8 * h, parts, a.terms);
+                            for (int tt = 0; tt < a.terms; ++tt)
+                                *reinterpret_cast<uint4*>(a.out_t[tt] + ro) = parts[tt];
                         }
                     }
                 }
@@ -591,10 +597,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
 
 // P into the padded BF16 state images: for each (m, slice, y, x) the 8
 // depths j = 8 slice + e of b[m][y][x][j] = sum_p Sm[m][p][j] c[p][y][x][j].
+struct TermPtrs {
+    __nv_bfloat16* p[kMaxTerms];
+};
+
 __global__ void tc_states_kernel(const float* __restrict__ c, const float* __restrict__ Sm,
-                                 __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
-                                 int Q, int P, int Y, int X, int Z, int slices, int KS, int Yp,
-                                 int Xp, int r)
+                                 TermPtrs out, int terms, int Q, int P, int Y, int X, int Z,
+                                 int slices, int KS, int Yp, int Xp, int r)
 {
     const size_t n = (size_t)Q * slices * Y * X;
     const size_t SZ = (size_t)Y * X * Z;
@@ -614,18 +623,16 @@ __global__ void tc_states_kernel(const float* __restrict__ c, const float* __res
                     acc = fmaf(Sm[(m * P + p) * Z + j], c[p * SZ + ((size_t)y * X + x) * Z + j], acc);
             v[e] = acc;
         }
-        uint4 h, l;
-        split8(v, h, l);
+        uint4 parts[kMaxTerms];
+        split_terms(v, parts, terms);
         const size_t o = ((((size_t)m * KS + s8) * Yp + (y + r)) * Xp + (x + r)) * 8;
-        *reinterpret_cast<uint4*>(hi + o) = h;
-        if (lo) *reinterpret_cast<uint4*>(lo + o) = l;
+        for (int tt = 0; tt < terms; ++tt) *reinterpret_cast<uint4*>(out.p[tt] + o) = parts[tt];
     }
 }
 
 // FP32 u [Q][S][Twp] into the padded BF16 residual images
-__global__ void tc_pack_kernel(const float* __restrict__ u, __nv_bfloat16* __restrict__ hi,
-                               __nv_bfloat16* __restrict__ lo, int Q, int Y, int X, int Twp,
-                               int KS, int Yp, int Xp, int r)
+__global__ void tc_pack_kernel(const float* __restrict__ u, TermPtrs out, int terms, int Q,
+                               int Y, int X, int Twp, int KS, int Yp, int Xp, int r)
 {
     const int slices = Twp / 8;
     const size_t n = (size_t)Q * slices * Y * X;
@@ -639,11 +646,10 @@ __global__ void tc_pack_kernel(const float* __restrict__ u, __nv_bfloat16* __res
             u + (((size_t)m * Y + y) * X + x) * Twp + 8 * s8);
         const float4 a0 = src[0], a1 = src[1];
         const float v[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        uint4 h, l;
-        split8(v, h, l);
+        uint4 parts[kMaxTerms];
+        split_terms(v, parts, terms);
         const size_t o = ((((size_t)m * KS + s8) * Yp + (y + r)) * Xp + (x + r)) * 8;
-        *reinterpret_cast<uint4*>(hi + o) = h;
-        if (lo) *reinterpret_cast<uint4*>(lo + o) = l;
+        for (int tt = 0; tt < terms; ++tt) *reinterpret_cast<uint4*>(out.p[tt] + o) = parts[tt];
     }
 }
 
@@ -702,15 +708,18 @@ namespace {
 
 void free_dir(TcDir& D)
 {
-    cudaFree(D.Bhi); cudaFree(D.Blo); cudaFree(D.tab);
-    D.Bhi = D.Blo = nullptr;
+    for (int tt = 0; tt < kMaxTerms; ++tt) {
+        cudaFree(D.Bt[tt]);
+        D.Bt[tt] = nullptr;
+    }
+    cudaFree(D.tab);
     D.tab = nullptr;
 }
 
 // Host image of one direction's packed operator.
 struct DirHost {
     TcDir cfg;
-    std::vector<uint16_t> hi, lo;   // banded kernel
+    std::vector<uint16_t> t[kMaxTerms];     // kernel per term
     std::vector<uint32_t> tab;      // group headers and pair tables (uint4 entries)
 };
 
@@ -720,7 +729,7 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
               size_t budget, DirHost* out)
 {
     const int kk = h->k * h->k;
-    const int split = t->split;
+    const int terms = t->terms;
     TcDir D;
     D.MT = MT;
     D.RA = RA;
@@ -757,7 +766,7 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
     const size_t pair_b = 2 * (size_t)D.NB * 16;
     // smallest number of groups whose A slices and B ring fit the budget;
     // prefer stages that hold several taps
-    const size_t mult = split ? 2 : 1;
+    const size_t mult = (size_t)terms;
     bool found = false;
     for (int ng = 1; ng <= npe && !found; ++ng) {
         const int gpairs = (npe + ng - 1) / ng;
@@ -798,15 +807,14 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
 
     // pack [group][tap][pair][2 slices][NB rows][8] and the group headers
     const int gpairs = D.GA / 2;
-    out->hi.clear();
-    out->lo.clear();
+    for (int tt = 0; tt < kMaxTerms; ++tt) out->t[tt].clear();
     out->tab.clear();
     std::vector<uint32_t> runtab;
     double macs = 0;
     for (int g = 0; g < D.NG; ++g) {
         const int np = std::min(gpairs, npe - g * gpairs);
         const uint32_t tapb = (uint32_t)(np * pair_b);
-        const uint32_t base16 = (uint32_t)(out->hi.size() / 8);
+        const uint32_t base16 = (uint32_t)(out->t[0].size() / 8);
         const uint32_t tpr = std::min<uint32_t>(
             kMaxTapsPerStage, std::max<uint32_t>(1, D.stage_bytes / tapb));
         out->tab.insert(out->tab.end(), {base16, tapb, tpr, (uint32_t)np});
@@ -826,38 +834,38 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
                 for (int s2 = 0; s2 < 2; ++s2)
                     for (int row = 0; row < D.NB; ++row)
                         for (int e = 0; e < 8; ++e) {
-                            const float v = kv(row, 16 * gp + 8 * s2 + e, d);
-                            const uint16_t hb = f2bf(v);
-                            out->hi.push_back(hb);
-                            out->lo.push_back(f2bf(v - bf2f(hb)));
+                            float rv = kv(row, 16 * gp + 8 * s2 + e, d);
+                            for (int tt = 0; tt < kMaxTerms; ++tt) {
+                                const uint16_t hb = f2bf(rv);
+                                out->t[tt].push_back(hb);
+                                rv -= bf2f(hb);
+                            }
                         }
                 macs += 128.0 * D.NB * 16;
             }
     }
-    if (out->hi.empty()) {
-        out->hi.assign(8, 0);
-        out->lo.assign(8, 0);
-    }
+    for (int tt = 0; tt < kMaxTerms; ++tt)
+        if (out->t[tt].empty()) out->t[tt].assign(8, 0);
     out->tab.insert(out->tab.end(), runtab.begin(), runtab.end());
     D.tab_words = (int)out->tab.size();
     const double ctas = (double)D.groupsX * t->tilesY * h->Q;
-    D.macs = macs * MT * (split ? 3 : 1) * ctas;
+    D.macs = macs * MT * (terms * (terms + 1) / 2) * ctas;
     out->cfg = D;
     return true;
 }
 
-swopt_status upload_dir(const DirHost& H, int split, TcDir* D)
+swopt_status upload_dir(const DirHost& H, int terms, TcDir* D)
 {
     *D = H.cfg;
-    D->Bhi = D->Blo = nullptr;
+    D->Bt[0] = D->Bt[1] = D->Bt[2] = nullptr;
     D->tab = nullptr;
     auto up16 = [&](__nv_bfloat16** dst, const std::vector<uint16_t>& v) -> swopt_status {
         SW_TRY(tc_alloc(dst, v.size()));
         SW_CUDA(cudaMemcpy(*dst, v.data(), v.size() * 2, cudaMemcpyHostToDevice));
         return SWOPT_OK;
     };
-    swopt_status s = up16(&D->Bhi, H.hi);
-    if (s == SWOPT_OK && split) s = up16(&D->Blo, H.lo);
+    swopt_status s = SWOPT_OK;
+    for (int tt = 0; tt < terms && s == SWOPT_OK; ++tt) s = up16(&D->Bt[tt], H.t[tt]);
     if (s == SWOPT_OK) s = tc_upload(&D->tab, H.tab);
     if (s != SWOPT_OK) free_dir(*D);
     return s;
@@ -875,17 +883,13 @@ TcArgs dir_args(const swopt_handle* h, const TcOperator* t, const TcDir& D, bool
     a.stage_bytes = D.stage_bytes;
     a.Twp = h->Twp;
     a.KSo = t->A.KS;
-    a.split = t->split;
+    a.terms = t->terms;
     a.adj = adj ? 1 : 0;
-    a.b_hi = D.Bhi; a.b_lo = D.Blo;
+    for (int tt = 0; tt < kMaxTerms; ++tt) a.b_t[tt] = D.Bt[tt];
     a.tab = reinterpret_cast<const uint4*>(D.tab);
     a.tab_n = D.tab_words / 4;
     a.tcols = (uint32_t)D.cols;
-    if (adj) {
-        a.a_hi = t->rpad_hi; a.a_lo = t->rpad_lo;
-    } else {
-        a.a_hi = t->bpad_hi; a.a_lo = t->bpad_lo;
-    }
+    for (int tt = 0; tt < kMaxTerms; ++tt) a.a_t[tt] = adj ? t->rpad[tt] : t->bpad[tt];
     return a;
 }
 
@@ -900,15 +904,14 @@ swopt_status launch_conv(swopt_handle* h, const TcDir& D, const TcArgs& a, cudaS
     return SWOPT_OK;
 }
 
-// Candidate configurations: tiles per CTA, accumulator replicas per tile
-// (independent accumulation chains keep more MMAs in flight) and the
-// shared-memory budget (two CTAs per SM, or one).
+// Candidate configurations: tiles per CTA and the shared-memory budget (two
+// CTAs per SM, or one).
 struct Cand {
-    int MT, RA;
+    int MT;
     size_t budget;
 };
-const Cand kCands[] = {{1, 1, 110 * 1024}, {2, 1, 110 * 1024}, {1, 1, 220 * 1024},
-                       {2, 1, 220 * 1024}, {4, 1, 220 * 1024}};
+const Cand kCands[] = {{1, 110 * 1024}, {2, 110 * 1024}, {1, 220 * 1024}, {2, 220 * 1024},
+                       {4, 220 * 1024}};
 
 }  // namespace
 
@@ -918,7 +921,10 @@ void tc_release(swopt_handle* h)
     if (!t) return;
     free_dir(t->F);
     free_dir(t->A);
-    cudaFree(t->bpad_hi); cudaFree(t->bpad_lo); cudaFree(t->rpad_hi); cudaFree(t->rpad_lo);
+    for (int tt = 0; tt < kMaxTerms; ++tt) {
+        cudaFree(t->bpad[tt]);
+        cudaFree(t->rpad[tt]);
+    }
     cudaFree(t->err);
     delete t;
     h->tc = nullptr;
@@ -932,12 +938,18 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
 {
     TcOperator* t = h->tc;
     std::vector<DirHost> plans;
-    for (const Cand& c : kCands) {
-        if (force_mt > 0 && c.MT != force_mt) continue;
-        if (force_ctas > 0 && (force_ctas == 2) != (c.budget < 200 * 1024)) continue;
-        if (force_ra > 0 && c.RA != force_ra) continue;
-        DirHost H;
-        if (plan_dir(h, t, adj, c.MT, c.RA, c.budget, &H)) plans.push_back(std::move(H));
+    // The split precisions keep their correction products in an accumulator
+    // of their own where TMEM holds it: they are about 2^-8 of the main sum,
+    // so the FP32 rounding of each accumulation step into it is 2^-8 finer.
+    const int ra_want = force_ra > 0 ? force_ra : (t->terms > 1 ? 2 : 1);
+    for (int ra = ra_want; ra >= 1 && plans.empty(); --ra) {
+        if (force_ra > 0 && ra != force_ra) break;
+        for (const Cand& c : kCands) {
+            if (force_mt > 0 && c.MT != force_mt) continue;
+            if (force_ctas > 0 && (force_ctas == 2) != (c.budget < 200 * 1024)) continue;
+            DirHost H;
+            if (plan_dir(h, t, adj, c.MT, ra, c.budget, &H)) plans.push_back(std::move(H));
+        }
     }
     if (plans.empty()) {
         set_error("no tensor-core configuration fits this geometry (k=%d, window %d, depths %d)",
@@ -952,7 +964,7 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
         float best_ms = 1e30f;
         for (size_t i = 0; i < plans.size(); ++i) {
             TcDir D;
-            SW_TRY(upload_dir(plans[i], t->split, &D));
+            SW_TRY(upload_dir(plans[i], t->terms, &D));
             TcArgs a = dir_args(h, t, D, adj);
             a.out_f = adj ? h->g : h->u;
             a.mode = 0;
@@ -983,18 +995,18 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
             return SWOPT_ERR_TIMEOUT;
         }
     }
-    return upload_dir(plans[best_i], t->split, best);
+    return upload_dir(plans[best_i], t->terms, best);
 }
 
 swopt_status tc_prepare(swopt_handle* h)
 {
-    const int split = h->precision == SWOPT_PREC_BF16X3 ? 1 : 0;
-    if (h->tc && h->tc->split == split) return SWOPT_OK;
+    const int terms = h->precision == SWOPT_PREC_BF16X3 ? 2 : 1;
+    if (h->tc && h->tc->terms == terms) return SWOPT_OK;
     const int keep_f = h->tc ? h->tc->F.MT : 0;
     (void)keep_f;
     tc_release(h);
     TcOperator* t = new TcOperator();
-    t->split = split;
+    t->terms = terms;
     t->tilesX = (h->X + 7) / 8;
     t->tilesY = (h->Y + 15) / 16;
     t->Xp = ((t->tilesX + 3) / 4) * 32 + 2 * h->r;  // room for up to 4 tiles per CTA
@@ -1015,11 +1027,9 @@ swopt_status tc_prepare(swopt_handle* h)
     const size_t nb = (size_t)h->Q * ksf_max * plane, nr = (size_t)h->Q * ksa_max * plane;
     swopt_status s = SWOPT_OK;
     auto step = [&](swopt_status v) { if (s == SWOPT_OK) s = v; };
-    step(tc_alloc(&t->bpad_hi, nb));
-    step(tc_alloc(&t->rpad_hi, nr));
-    if (split) {
-        step(tc_alloc(&t->bpad_lo, nb));
-        step(tc_alloc(&t->rpad_lo, nr));
+    for (int tt = 0; tt < terms; ++tt) {
+        step(tc_alloc(&t->bpad[tt], nb));
+        step(tc_alloc(&t->rpad[tt], nr));
     }
     step(tc_alloc(&t->err, 1));
     auto zero = [&](void* p, size_t bytes) {
@@ -1029,8 +1039,10 @@ swopt_status tc_prepare(swopt_handle* h)
         }
     };
     // borders and padded slices stay zero; kernels only write the interior
-    zero(t->bpad_hi, nb * 2); zero(t->bpad_lo, nb * 2);
-    zero(t->rpad_hi, nr * 2); zero(t->rpad_lo, nr * 2);
+    for (int tt = 0; tt < terms; ++tt) {
+        zero(t->bpad[tt], nb * 2);
+        zero(t->rpad[tt], nr * 2);
+    }
     zero(t->err, sizeof(int));
     // the adjoint's slice count fixes the layout the forward epilogue writes
     if (s == SWOPT_OK)
@@ -1043,8 +1055,10 @@ swopt_status tc_prepare(swopt_handle* h)
     }
     if (s == SWOPT_OK) {
         // the tuning launches left data in the workspaces; clear the images
-        zero(t->bpad_hi, nb * 2); zero(t->bpad_lo, nb * 2);
-        zero(t->rpad_hi, nr * 2); zero(t->rpad_lo, nr * 2);
+        for (int tt = 0; tt < terms; ++tt) {
+            zero(t->bpad[tt], nb * 2);
+            zero(t->rpad[tt], nr * 2);
+        }
         if (s == SWOPT_OK && cudaDeviceSynchronize() != cudaSuccess) {
             set_error("synchronisation after tensor-core set-up failed");
             s = SWOPT_ERR_CUDA;
@@ -1066,9 +1080,9 @@ swopt_status tc_states(swopt_handle* h, const float* c, cudaStream_t st)
     const size_t n = (size_t)h->Q * slices * h->Y * h->X;
     int grid = grid_for(n, 256);
     if (grid > 152 * 16) grid = 152 * 16;
-    tc_states_kernel<<<grid, 256, 0, st>>>(c, h->Sm, t->bpad_hi, t->split ? t->bpad_lo : nullptr,
-                                           h->Q, h->P, h->Y, h->X, h->Z, slices, t->F.KS, t->Yp,
-                                           t->Xp, h->r);
+    TermPtrs out{{t->bpad[0], t->bpad[1]}};
+    tc_states_kernel<<<grid, 256, 0, st>>>(c, h->Sm, out, t->terms, h->Q, h->P, h->Y, h->X, h->Z,
+                                           slices, t->F.KS, t->Yp, t->Xp, h->r);
     SW_LAUNCHED(h);
     return SWOPT_OK;
 }
@@ -1079,8 +1093,9 @@ swopt_status tc_pack_u(swopt_handle* h, cudaStream_t st)
     const size_t n = (size_t)h->Q * (h->Twp / 8) * h->Y * h->X;
     int grid = grid_for(n, 256);
     if (grid > 152 * 16) grid = 152 * 16;
-    tc_pack_kernel<<<grid, 256, 0, st>>>(h->u, t->rpad_hi, t->split ? t->rpad_lo : nullptr, h->Q,
-                                         h->Y, h->X, h->Twp, t->A.KS, t->Yp, t->Xp, h->r);
+    TermPtrs out{{t->rpad[0], t->rpad[1]}};
+    tc_pack_kernel<<<grid, 256, 0, st>>>(h->u, out, t->terms, h->Q, h->Y, h->X, h->Twp, t->A.KS,
+                                         t->Yp, t->Xp, h->r);
     SW_LAUNCHED(h);
     return SWOPT_OK;
 }
@@ -1095,8 +1110,7 @@ swopt_status tc_forward(swopt_handle* h, bool to_r, const float* ytil, double* p
     a.partials = partials;
     a.mode = to_r ? 1 : 0;
     a.out_f = to_r ? nullptr : h->u;
-    a.out_hi = to_r ? t->rpad_hi : nullptr;
-    a.out_lo = to_r ? t->rpad_lo : nullptr;
+    for (int tt = 0; tt < kMaxTerms; ++tt) a.out_t[tt] = to_r ? t->rpad[tt] : nullptr;
     ProfileRec rec;
     prof_begin(h, 0, st, &rec);
     SW_TRY(launch_conv(h, t->F, a, st));
@@ -1132,11 +1146,11 @@ double tc_issued_macs(const swopt_handle* h, int kernel)
 }
 
 void tc_config(const swopt_handle* h, int kernel, int* mt, int* ctas_per_sm, int* stages,
-               int* groups, int* replicas)
+               int* groups, int* accumulators)
 {
     const TcDir& D = kernel == 0 ? h->tc->F : h->tc->A;
     *mt = D.MT;
-    *replicas = D.RA;
+    *accumulators = D.RA;
     *ctas_per_sm = (int)(233472 / (D.smem + 1024));
     if (*ctas_per_sm > 512 / D.cols) *ctas_per_sm = 512 / D.cols;
     *stages = D.NS;

@@ -66,85 +66,99 @@ __device__ __forceinline__ float dtq(const float* __restrict__ q, const Vol& v, 
     return acc;
 }
 
+// Volume kernels use a 3D launch: threadIdx.x + 32 blockIdx.x runs along z,
+// threadIdx.y + 8 blockIdx.y along x, blockIdx.z over (species, y).
+struct VIdx {
+    int j, x, y;
+    size_t i;
+    bool ok;
+};
+
+__device__ __forceinline__ VIdx vidx(const Vol& v)
+{
+    VIdx r;
+    r.j = blockIdx.x * 32 + threadIdx.x;
+    r.x = blockIdx.y * 8 + threadIdx.y;
+    r.y = (int)(blockIdx.z % (unsigned)v.Y);
+    const int p = (int)(blockIdx.z / (unsigned)v.Y);
+    r.ok = r.j < v.Z && r.x < v.X;
+    r.i = (((size_t)p * v.Y + r.y) * v.X + r.x) * v.Z + r.j;
+    return r;
+}
+
 // One iteration of Algorithm 2 with L = D:
 //   x   = z - D^T r_in          (recomputed at i and at its +y, +x, +z neighbours)
 //   u_i = clamp(r_in + D x / 12, -tau, tau)
 //   r_out = u_i + beta (u_i - u_{i-1})
 // `first` means r_in = u_{i-1} = 0 (neither is read).
-__global__ void fgp_iter_kernel(const float* __restrict__ z, const float* __restrict__ rin,
-                                float* __restrict__ rout, float* __restrict__ u, Vol v, float tau,
-                                float beta, int first)
+__global__ void __launch_bounds__(256) fgp_iter_kernel(const float* __restrict__ z,
+                                                       const float* __restrict__ rin,
+                                                       float* __restrict__ rout,
+                                                       float* __restrict__ u, Vol v, float tau,
+                                                       float beta, int first)
 {
-    const size_t XZ = (size_t)v.X * v.Z;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < v.L;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(i % v.Z);
-        const int x = (int)((i / v.Z) % v.X);
-        const int y = (int)((i / XZ) % v.Y);
-        float xc, xn[3];
-        if (first) {
-            xc = z[i];
-            xn[0] = y + 1 < v.Y ? z[i + XZ] : 0.f;
-            xn[1] = x + 1 < v.X ? z[i + v.Z] : 0.f;
-            xn[2] = j + 1 < v.Z ? z[i + 1] : 0.f;
-        } else {
-            xc = z[i] - dtq(rin, v, i, y, x, j);
-            xn[0] = y + 1 < v.Y ? z[i + XZ] - dtq(rin, v, i + XZ, y + 1, x, j) : 0.f;
-            xn[1] = x + 1 < v.X ? z[i + v.Z] - dtq(rin, v, i + v.Z, y, x + 1, j) : 0.f;
-            xn[2] = j + 1 < v.Z ? z[i + 1] - dtq(rin, v, i + 1, y, x, j + 1) : 0.f;
-        }
-        const bool has[3] = {y + 1 < v.Y, x + 1 < v.X, j + 1 < v.Z};
+    const VIdx q = vidx(v);
+    if (!q.ok) return;
+    const size_t i = q.i, XZ = (size_t)v.X * v.Z;
+    const int y = q.y, x = q.x, j = q.j;
+    const bool has[3] = {y + 1 < v.Y, x + 1 < v.X, j + 1 < v.Z};
+    const size_t step[3] = {XZ, (size_t)v.Z, 1};
+    float xc, xn[3];
+    if (first) {
+        xc = z[i];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const size_t ia = (size_t)a * v.L + i;
-            const float ra = first ? 0.f : rin[ia];
-            const float ua_prev = first ? 0.f : u[ia];
-            const float dx = has[a] ? xn[a] - xc : 0.f;
-            const float un = clampf(fmaf(dx, 1.0f / 12.0f, ra), -tau, tau);
-            u[ia] = un;
-            rout[ia] = fmaf(beta, un - ua_prev, un);
-        }
+        for (int a = 0; a < 3; ++a) xn[a] = has[a] ? z[i + step[a]] : 0.f;
+    } else {
+        xc = z[i] - dtq(rin, v, i, y, x, j);
+        xn[0] = has[0] ? z[i + XZ] - dtq(rin, v, i + XZ, y + 1, x, j) : 0.f;
+        xn[1] = has[1] ? z[i + v.Z] - dtq(rin, v, i + v.Z, y, x + 1, j) : 0.f;
+        xn[2] = has[2] ? z[i + 1] - dtq(rin, v, i + 1, y, x, j + 1) : 0.f;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const size_t ia = (size_t)a * v.L + i;
+        const float ra = first ? 0.f : rin[ia];
+        const float ua_prev = first ? 0.f : u[ia];
+        const float dx = has[a] ? xn[a] - xc : 0.f;
+        const float un = clampf(fmaf(dx, 1.0f / 12.0f, ra), -tau, tau);
+        u[ia] = un;
+        rout[ia] = fmaf(beta, un - ua_prev, un);
     }
 }
 
 // x = z - D^T u
-__global__ void fgp_finish_kernel(const float* __restrict__ z, const float* __restrict__ u,
-                                  float* __restrict__ xo, Vol v)
+__global__ void __launch_bounds__(256) fgp_finish_kernel(const float* __restrict__ z,
+                                                         const float* __restrict__ u,
+                                                         float* __restrict__ xo, Vol v)
 {
-    const size_t XZ = (size_t)v.X * v.Z;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < v.L;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(i % v.Z);
-        const int x = (int)((i / v.Z) % v.X);
-        const int y = (int)((i / XZ) % v.Y);
-        xo[i] = z[i] - dtq(u, v, i, y, x, j);
-    }
+    const VIdx q = vidx(v);
+    if (!q.ok) return;
+    xo[q.i] = z[q.i] - dtq(u, v, q.i, q.y, q.x, q.j);
 }
 
 // End of one FISTA iteration (Algorithm 1):
 //   x       = z - D^T u                 (TV prox output; x = z without TV)
 //   c_{k+1} = max(x - theta, 0)        (l1 + nonnegativity)
 //   xi      = c_{k+1} + beta_k (c_{k+1} - c_k),  beta_k from the device scalars
-__global__ void fista_finish_kernel(const float* __restrict__ z, const float* __restrict__ u,
-                                    float* __restrict__ c, float* __restrict__ xi, Vol v,
-                                    float theta, int use_tv, const double* __restrict__ scal)
+//   delta   = c_{k+1} - c_k                      (when delta is given)
+__global__ void __launch_bounds__(256) fista_finish_kernel(const float* __restrict__ z,
+                                                           const float* __restrict__ u,
+                                                           float* __restrict__ c,
+                                                           float* __restrict__ xi,
+                                                           float* __restrict__ delta, Vol v,
+                                                           float theta, int use_tv,
+                                                           const double* __restrict__ scal)
 {
+    const VIdx q = vidx(v);
+    if (!q.ok) return;
     const float beta = (float)scal[1];
-    const size_t XZ = (size_t)v.X * v.Z;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < v.L;
-         i += (size_t)gridDim.x * blockDim.x) {
-        float xv = z[i];
-        if (use_tv) {
-            const int j = (int)(i % v.Z);
-            const int x = (int)((i / v.Z) % v.X);
-            const int y = (int)((i / XZ) % v.Y);
-            xv -= dtq(u, v, i, y, x, j);
-        }
-        const float cn = fmaxf(xv - theta, 0.f);
-        const float co = c[i];
-        c[i] = cn;
-        xi[i] = fmaf(beta, cn - co, cn);
-    }
+    float xv = z[q.i];
+    if (use_tv) xv -= dtq(u, v, q.i, q.y, q.x, q.j);
+    const float cn = fmaxf(xv - theta, 0.f);
+    const float d = cn - c[q.i];
+    c[q.i] = cn;
+    xi[q.i] = fmaf(beta, d, cn);
+    if (delta) delta[q.i] = d;
 }
 
 // Momentum scalars of Algorithm 1 in FP64: scal[0] = t_k -> t_{k+1},
@@ -276,6 +290,13 @@ Vol vol_of(const swopt_handle* h)
     return v;
 }
 
+dim3 vol_grid(const Vol& v)
+{
+    return dim3((unsigned)((v.Z + 31) / 32), (unsigned)((v.X + 7) / 8), (unsigned)(v.P * v.Y));
+}
+
+const dim3 kVolBlock(32, 8);
+
 int ew_grid(size_t n)
 {
     int g = grid_for(n, 256);
@@ -299,7 +320,7 @@ swopt_status prox_tv_iters(swopt_handle* h, const float* z, float tau, int iters
     float* rin = h->tvr0;
     float* rout = h->tvr1;
     for (int it = 0; it < iters; ++it) {
-        fgp_iter_kernel<<<ew_grid(v.L), 256, 0, st>>>(z, rin, rout, h->tvu, v, tau,
+        fgp_iter_kernel<<<vol_grid(v), kVolBlock, 0, st>>>(z, rin, rout, h->tvu, v, tau,
                                                       (float)betas[it], it == 0 ? 1 : 0);
         SW_LAUNCHED(h);
         float* t = rin;
@@ -312,17 +333,17 @@ swopt_status prox_tv_iters(swopt_handle* h, const float* z, float tau, int iters
 swopt_status prox_tv_finish(swopt_handle* h, const float* z, float* x, cudaStream_t st)
 {
     const Vol v = vol_of(h);
-    fgp_finish_kernel<<<ew_grid(v.L), 256, 0, st>>>(z, h->tvu, x, v);
+    fgp_finish_kernel<<<vol_grid(v), kVolBlock, 0, st>>>(z, h->tvu, x, v);
     SW_LAUNCHED(h);
     return SWOPT_OK;
 }
 
 swopt_status fista_finish(swopt_handle* h, const float* z, bool use_tv, float theta,
-                          cudaStream_t st)
+                          float* delta, cudaStream_t st)
 {
     const Vol v = vol_of(h);
-    fista_finish_kernel<<<ew_grid(v.L), 256, 0, st>>>(z, h->tvu, h->c, h->xi, v, theta,
-                                                      use_tv ? 1 : 0, h->scal);
+    fista_finish_kernel<<<vol_grid(v), kVolBlock, 0, st>>>(z, h->tvu, h->c, h->xi, delta, v,
+                                                           theta, use_tv ? 1 : 0, h->scal);
     SW_LAUNCHED(h);
     return SWOPT_OK;
 }
@@ -421,7 +442,7 @@ cudaError_t fgp_iter_on(const float* z, const float* rin, float* rout, float* u,
     Vol v;
     v.P = P; v.Y = Y; v.X = X; v.Z = Z;
     v.L = (size_t)P * Y * X * Z;
-    fgp_iter_kernel<<<ew_grid(v.L), 256, 0, st>>>(z, rin, rout, u, v, tau, beta, first);
+    fgp_iter_kernel<<<vol_grid(v), kVolBlock, 0, st>>>(z, rin, rout, u, v, tau, beta, first);
     return cudaGetLastError();
 }
 
@@ -431,7 +452,7 @@ cudaError_t fgp_finish_on(const float* z, const float* u, float* x, int P, int Y
     Vol v;
     v.P = P; v.Y = Y; v.X = X; v.Z = Z;
     v.L = (size_t)P * Y * X * Z;
-    fgp_finish_kernel<<<ew_grid(v.L), 256, 0, st>>>(z, u, x, v);
+    fgp_finish_kernel<<<vol_grid(v), kVolBlock, 0, st>>>(z, u, x, v);
     return cudaGetLastError();
 }
 

@@ -65,6 +65,23 @@ struct ProfileRec {
     int kernel;
 };
 
+// An event-record node pair of the captured FISTA iteration that brackets
+// one launch of the A (0) or A^T (1) kernel.
+struct GraphProbe {
+    cudaGraphNode_t begin = nullptr, end = nullptr;
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // placeholders used at capture
+    int kernel = 0;
+};
+
+// One captured FISTA iteration (kind 0: plain or incremental-gradient
+// iteration; kind 1: the resync iteration of the refined solve).
+struct IterGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t kernels = 0;
+    std::vector<GraphProbe> probes;
+};
+
 }  // namespace swopt
 
 struct swopt_handle {
@@ -117,14 +134,25 @@ struct swopt_handle {
     float* tvu = nullptr;         // [3][P][Y][X][Z] dual iterate
     float* tvr0 = nullptr;        // [3][..] extrapolated dual (ping)
     float* tvr1 = nullptr;        // [3][..] (pong)
-    float* tmp = nullptr;         // [P][Y][X][Z] scratch
+    float* tmp = nullptr;         // [P][Y][X][Z] scratch (c_{k+1} - c_k in the refined solve)
+    float* G = nullptr;           // [P][Y][X][Z] refined solve: gradient at c_k
+    float* xprev = nullptr;       // [P][Y][X][Z] previous momentum iterate (eps2 test)
+    int64_t iter = 0;             // FISTA iterations since swopt_fista_init
     std::vector<double> inner_beta; // momentum coefficients of Algorithm 2
 
     // tensor-core path
-    swopt::TcOperator* tc = nullptr;
+    swopt::TcOperator* tc = nullptr;      // operator of `precision`
+    swopt::TcOperator* tc_ref = nullptr;  // operator of the refined solve's resync precision
     int tc_force_mt[2] = {0, 0};     // tiles per CTA of A / A^T (0: tuned)
     int tc_force_ctas[2] = {0, 0};   // CTAs per SM of A / A^T (0: tuned)
-    int tc_force_ra[2] = {0, 0};     // accumulator replicas of A / A^T (0: tuned)
+    int tc_force_ra[2] = {0, 0};     // accumulators per tile of A / A^T (0: default)
+
+    // CUDA graph of one FISTA iteration (rebuilt when the settings change)
+    bool use_graph = true;
+    bool capturing = false;
+    cudaStream_t cap_stream = nullptr;
+    swopt::IterGraph graphs[2];
+    std::vector<std::pair<cudaEvent_t, int>> cap_events;
 
     // instrumentation
     bool profile = false;
@@ -175,7 +203,7 @@ int tc_error_word(swopt_handle* h);
 double tc_issued_macs(const swopt_handle* h, int kernel);
 // configuration chosen for the forward (0) / adjoint (1)
 void tc_config(const swopt_handle* h, int kernel, int* mt, int* ctas_per_sm, int* stages,
-               int* groups, int* replicas);
+               int* groups, int* accumulators);
 
 // Elementwise / layout kernels (operator_simt.cu).
 swopt_status launch_states(swopt_handle* h, const float* c, float* b, cudaStream_t st);
@@ -184,14 +212,19 @@ swopt_status launch_fold(swopt_handle* h, const float* y, float* ytil, cudaStrea
 // out = sum_m Sm[m][p][j] g[m] (mode 0); out = xi - alpha * that (mode 1)
 swopt_status launch_pt(swopt_handle* h, const float* g, const float* xi, float alpha,
                        float* out, int mode, cudaStream_t st);
+// Refined solve: d = sum_m Sm[m][p][j] g[m]; Gn = (add ? G : 0) + d;
+// out = xi - alpha ((1 + beta) Gn - beta G) with beta = scal[1]; G = Gn.
+swopt_status launch_pt_refine(swopt_handle* h, const float* g, const float* xi, float alpha,
+                              float* G, float* out, int add, cudaStream_t st);
 
 // Proximal / FISTA / reduction kernels (prox.cu).
 swopt_status prox_l1(swopt_handle* h, float* x, float thresh, int nonneg, cudaStream_t st);
 swopt_status prox_tv_iters(swopt_handle* h, const float* z, float tau, int iters,
                            const double* betas, cudaStream_t st);
 swopt_status prox_tv_finish(swopt_handle* h, const float* z, float* x, cudaStream_t st);
+// delta (optional): also write c_{k+1} - c_k there
 swopt_status fista_finish(swopt_handle* h, const float* z, bool use_tv, float theta,
-                          cudaStream_t st);
+                          float* delta, cudaStream_t st);
 swopt_status fista_scalars(swopt_handle* h, int momentum, cudaStream_t st);
 swopt_status fista_reset_scalars(swopt_handle* h, cudaStream_t st);
 // FP64 reductions, result written to h->scal[slot]

@@ -458,3 +458,35 @@ def test_param_grad_matches_central_differences():
     fd = (f(Switching(sw.kappa, sw.eps_bar, sw.eps_off, sw.mu_per_mm + h))
           - f(Switching(sw.kappa, sw.eps_bar, sw.eps_off, sw.mu_per_mm - h))) / (2 * h)
     assert dmu == pytest.approx(fd, rel=1e-6)
+
+
+def test_incremental_gradient_fista_equals_algorithm_1():
+    """The refined solve's recursion, written out in FP64 with the oracle's
+    operators: the gradient at c_k kept and updated by H^T H (c_{k+1} - c_k),
+    recomputed every R iterations, and the gradient at the momentum point
+    taken as (1 + beta) G_{k+1} - beta G_k.  In exact arithmetic this is
+    Algorithm 1, so it must reproduce the oracle's FISTA iterates."""
+    g, sw, K, y = _small_problem()
+    alpha, lam1, lamtv, inner, iters = 0.01, 0.05, 0.02, 10, 12
+
+    def grad(c):
+        return oracle.adjoint(g, sw, K, oracle.forward(g, sw, K, c) - y)
+
+    for R in (1, 3, 1000):
+        c = np.zeros(g.c_shape())
+        G = grad(c)
+        z = -alpha * G
+        t = 1.0
+        for k in range(iters):
+            cn = oracle.prox(z, alpha, lam1, lamtv, inner)
+            t1 = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
+            beta = (t - 1.0) / t1
+            t = t1
+            d = cn - c
+            xi = cn + beta * d
+            Gn = grad(cn) if (k + 1) % R == 0 else G + oracle.adjoint(
+                g, sw, K, oracle.forward(g, sw, K, d))
+            z = xi - alpha * ((1.0 + beta) * Gn - beta * G)
+            c, G = cn, Gn
+        ref = oracle.fista(g, sw, K, y, alpha, iters, lam1, lamtv, inner)
+        assert np.linalg.norm(c - ref) <= 1e-12 * np.linalg.norm(ref), R
