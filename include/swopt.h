@@ -230,7 +230,9 @@ swopt_status swopt_use_graphs(swopt_handle* h, int on);
  * (inside a replayed FISTA graph, through its event-record nodes);
  * swopt_profile_read returns, for kernel_id 0 (A) or 1 (A^T), the
  * summed device time in milliseconds, the number of launches and the
- * algorithmic FLOPs of one launch (2 x multiply-adds of nonzero kernel taps).
+ * algorithmic FLOPs of one launch (2 x multiply-adds of nonzero kernel taps);
+ * kernel_id 2 and 3 report the launches of A and A^T that the refined solve
+ * makes at its resync precision (the initial and periodic exact gradients).
  * Reading synchronises on the recorded events and clears them.
  * swopt_launch_count returns the number of kernels this handle launched. */
 swopt_status swopt_profile_enable(swopt_handle* h, int on);

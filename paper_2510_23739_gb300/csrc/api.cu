@@ -53,6 +53,7 @@ bool take_events(swopt_handle* h, cudaEvent_t* a, cudaEvent_t* b)
 void prof_begin(swopt_handle* h, int kernel, cudaStream_t st, ProfileRec* rec)
 {
     rec->kernel = -1;
+    if (h->in_ref) kernel += 2;  // launches at the refined solve's resync precision
     if (h->capturing) {
         // an event-record node in the graph; its event is swapped per replay
         cudaEvent_t a;
@@ -152,12 +153,14 @@ struct RefScope {
     RefScope(swopt_handle* hh, int ref_precision)
         : h(hh), prec(hh->precision), tc(hh->tc), active(ref_precision != hh->precision)
     {
+        h->in_ref = true;
         if (!active) return;
         h->precision = ref_precision;
         h->tc = h->tc_ref;
     }
     ~RefScope()
     {
+        h->in_ref = false;
         if (!active) return;
         h->tc_ref = h->tc;
         h->tc = tc;
@@ -182,6 +185,7 @@ void release_all(swopt_handle* h)
     dfree(h->Kf); dfree(h->Ka); dfree(h->fmask); dfree(h->amask); dfree(h->Sm); dfree(h->Cmf);
     dfree(h->b); dfree(h->u); dfree(h->g); dfree(h->ytil); dfree(h->red); dfree(h->scal);
     dfree(h->c); dfree(h->xi); dfree(h->zin); dfree(h->tvu); dfree(h->tvr0); dfree(h->tvr1);
+    dfree(h->tvx); dfree(h->coop_bar);
     dfree(h->tmp); dfree(h->G); dfree(h->xprev);
     if (h->scal_host) cudaFreeHost(h->scal_host);
     h->scal_host = nullptr;
@@ -194,27 +198,14 @@ void release_all(swopt_handle* h)
     h->event_pool.clear();
 }
 
-std::vector<double> momentum_betas(int iters, int mode)
-{
-    std::vector<double> out(std::max(iters, 1), 0.0);
-    double t = 1.0;
-    for (int i = 0; i < iters; ++i) {
-        const double t1 = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
-        double b = 0.0;
-        if (mode == SWOPT_MOMENTUM_BECK_TEBOULLE) b = (t - 1.0) / t1;
-        else if (mode == SWOPT_MOMENTUM_PAPER_PRINTED) b = (t - 1.0) / (t + 1.0);
-        out[i] = b;
-        t = t1;
-    }
-    return out;
-}
-
 swopt_status ensure_tv_buffers(swopt_handle* h)
 {
     const size_t n = nc_of(h);
     if (!h->tvu) SW_TRY(dalloc(&h->tvu, 3 * n));
     if (!h->tvr0) SW_TRY(dalloc(&h->tvr0, 3 * n));
     if (!h->tvr1) SW_TRY(dalloc(&h->tvr1, 3 * n));
+    if (!h->tvx) SW_TRY(dalloc(&h->tvx, n));
+    SW_TRY(coop_prepare(h));
     return SWOPT_OK;
 }
 
@@ -242,6 +233,14 @@ swopt_status device_errors(swopt_handle* h)
         std::swap(h->tc, h->tc_ref);
         w = tc_error_word(h);
         std::swap(h->tc, h->tc_ref);
+    }
+    if (w == 0) {
+        const int c = coop_error_word(h);
+        if (c > 0) {
+            set_error("the TV prox kernel gave up a bounded grid barrier");
+            return SWOPT_ERR_TIMEOUT;
+        }
+        if (c < 0) w = -1;
     }
     if (w > 0) {
         set_error("a tensor-core kernel gave up a bounded wait (code %d)", w);
@@ -398,12 +397,16 @@ swopt_status fista_iteration(swopt_handle* h, int kind, cudaStream_t st)
         SW_TRY(apply_AT(h, false, st));                                   // A^T
         SW_TRY(launch_pt(h, h->g, h->xi, alpha, h->zin, 1, st));          // P^T, gradient step
     }
-    if (tv)
-        SW_TRY(prox_tv_iters(h, h->zin, (float)(h->step * h->prm.lambda_tv),
-                             h->prm.inner_iters, h->inner_beta.data(), st));
-    SW_TRY(fista_scalars(h, h->prm.momentum, st));
-    SW_TRY(fista_finish(h, h->zin, tv, (float)(h->step * h->prm.lambda_l1),
-                        refined ? h->tmp : nullptr, st));
+    const float theta = (float)(h->step * h->prm.lambda_l1);
+    if (tv) {
+        // TV prox, momentum scalars, l1 prox and momentum step: one launch
+        SW_TRY(fista_prox_finish(h, h->zin, (float)(h->step * h->prm.lambda_tv),
+                                 h->prm.inner_iters, h->prm.inner_momentum, theta,
+                                 refined ? h->tmp : nullptr, st));
+    } else {
+        SW_TRY(fista_scalars(h, h->prm.momentum, st));
+        SW_TRY(fista_finish(h, h->zin, false, theta, refined ? h->tmp : nullptr, st));
+    }
     if (!refined) return SWOPT_OK;
     if (kind == 1) return exact_gradient(h, st);
     SW_TRY(apply_A(h, h->tmp, A_OUT_R, nullptr, nullptr, 1, st));        // C A P delta
@@ -811,9 +814,7 @@ swopt_status swopt_prox_tv(swopt_handle* h, const float* z_dev, float* x_dev, fl
         return SWOPT_OK;
     }
     SW_TRY(ensure_tv_buffers(h));
-    const std::vector<double> betas = momentum_betas(inner_iters, momentum);
-    SW_TRY(prox_tv_iters(h, z_dev, tau, inner_iters, betas.data(), st));
-    return prox_tv_finish(h, z_dev, x_dev, st);
+    return prox_tv_coop(h, z_dev, tau, inner_iters, momentum, x_dev, st);
 }
 
 swopt_status swopt_lipschitz(swopt_handle* h, const float* v0_dev, int iters, double* L_out,
@@ -845,7 +846,6 @@ swopt_status swopt_fista_init(swopt_handle* h, const float* y_dev, const swopt_s
     SW_TRY(ensure_ytil(h));
     if (prm->lambda_tv > 0 && prm->inner_iters > 0) SW_TRY(ensure_tv_buffers(h));
     h->prm = *prm;
-    h->inner_beta = momentum_betas(prm->inner_iters, prm->inner_momentum);
     SW_TRY(launch_fold(h, y_dev, h->ytil, st));
     SW_TRY(reduce_sumsq(h, y_dev, (size_t)h->N * h->S * h->T, SC_YSQ, st));
     if (prm->step > 0) {
@@ -1041,8 +1041,8 @@ swopt_status swopt_profile_read(swopt_handle* h, int kernel_id, double* total_ms
 {
     clear_error();
     SW_TRY(check_handle(h));
-    if (kernel_id < 0 || kernel_id > 1) {
-        set_error("kernel_id must be 0 (A) or 1 (A^T)");
+    if (kernel_id < 0 || kernel_id > 3) {
+        set_error("kernel_id must be 0 (A), 1 (A^T), 2 or 3 (A, A^T at the resync precision)");
         return SWOPT_ERR_INVALID_ARG;
     }
     for (auto& r : h->prof) {

@@ -371,9 +371,18 @@ swopt_status simt_forward(swopt_handle* h, const float* b, float* u, const float
     const int jc = fwd_jc(h);
     const int H = TILE + 2 * h->r;
     const size_t smem = (size_t)jc * H * H * sizeof(float);
-    if (smem > 48 * 1024)
+    if (smem > 48 * 1024) {
+        // a function attribute shared by all handles and captured launches:
+        // raised to the device maximum, never lowered
+        const int dmax = max_dynamic_smem(h, (const void*)fwd_simt_kernel);
+        if (dmax <= 0 || smem > (size_t)dmax) {
+            set_error("FP32 forward needs %zu bytes of shared memory (device limit %d)", smem,
+                      dmax);
+            return SWOPT_ERR_UNSUPPORTED;
+        }
         SW_CUDA(cudaFuncSetAttribute(fwd_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+                                     dmax));
+    }
     dim3 grid(tiles, h->Q, h->nTc);
     ProfileRec rec;
     prof_begin(h, 0, st, &rec);

@@ -895,9 +895,17 @@ TcArgs dir_args(const swopt_handle* h, const TcOperator* t, const TcDir& D, bool
 
 swopt_status launch_conv(swopt_handle* h, const TcDir& D, const TcArgs& a, cudaStream_t st)
 {
-    if (D.smem > 48 * 1024)
-        SW_CUDA(cudaFuncSetAttribute(tc_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)D.smem));
+    // The dynamic shared-memory limit is an attribute of the function, shared
+    // by every handle and by every launch already captured in a graph: it is
+    // raised once to the device maximum and never lowered.
+    const int dmax = max_dynamic_smem(h, (const void*)tc_conv_kernel);
+    if (dmax <= 0 || D.smem > (size_t)dmax) {
+        set_error("tensor-core kernel needs %zu bytes of shared memory (device limit %d)", D.smem,
+                  dmax);
+        return SWOPT_ERR_UNSUPPORTED;
+    }
+    SW_CUDA(cudaFuncSetAttribute(tc_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 dmax));
     dim3 grid(D.groupsX * h->tc->tilesY, h->Q);
     tc_conv_kernel<<<grid, kTcThreads, D.smem, st>>>(a);
     SW_LAUNCHED(h);

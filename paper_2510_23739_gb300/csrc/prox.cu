@@ -6,6 +6,7 @@
 // Layouts: volumes [P][Y][X][Z]; TV duals [3][P][Y][X][Z] with component 0
 // along y, 1 along x, 2 along z (the entry of the last layer along an axis
 // has no edge and stays zero).
+#include <algorithm>
 #include <cmath>
 
 #include "swopt_internal.cuh"
@@ -161,6 +162,448 @@ __global__ void __launch_bounds__(256) fista_finish_kernel(const float* __restri
     if (delta) delta[q.i] = d;
 }
 
+// ---------------------------------------------------------------------------
+// The whole TV prox in one cooperative launch: every block of a grid sized to
+// be co-resident loops over the volume, and the phases of Algorithm 2 are
+// separated by a grid-wide barrier.  Per inner iteration i:
+//   phase A:  x = z - D^T r_{i-1}            (skipped for i = 1, where r = 0)
+//   phase B:  u_i = clamp(r_{i-1} + D x / 12, -tau, tau)
+//             r_i = u_i + beta_i (u_i - u_{i-1})
+// and after the last: x = z - D^T u_K written out (mode 0), or the end of the
+// FISTA iteration with the momentum scalars updated here (mode 1, as
+// fista_finish_kernel).  The inner coefficients beta_i follow Algorithm 2's
+// t recursion in FP64 in every thread.
+// ---------------------------------------------------------------------------
+constexpr int kCoopThreads = 256;
+constexpr uint32_t kBarrierPolls = 1u << 25;  // x 32 ns back-off: about a second
+
+// Grid barrier over all blocks of a cooperative launch.  bar[0] counts
+// arrivals, bar[1] is the generation, bar[2] an error word: a block that polls
+// kBarrierPolls times without seeing the generation advance sets it, and from
+// then on every barrier returns at once (the results are then invalid and the
+// host reports a timeout).
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// The arrival is an acquire-release atomic and the generation bump a release
+// reduction, so the block's writes before the barrier are visible to every
+// block that has observed the new generation with an acquire load; the CTA
+// barriers extend that to all threads of the block.
+__device__ __forceinline__ void grid_sync(unsigned* bar, unsigned nblocks)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vb = bar;
+        if (vb[2] == 0u) {
+            const unsigned gen = ld_acquire(bar + 1);
+            unsigned arrived;
+            asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;"
+                         : "=r"(arrived) : "l"(bar) : "memory");
+            if (arrived == nblocks - 1) {
+                atomicExch(&bar[0], 0u);
+                asm volatile("red.release.gpu.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
+            } else {
+                uint32_t polls = 0;
+                while (ld_acquire(bar + 1) == gen && vb[2] == 0u) {
+                    if (++polls > kBarrierPolls) {
+                        atomicExch(&bar[2], 1u);
+                        break;
+                    }
+                    if (polls > 256) __nanosleep(32);
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// 4-byte asynchronous global -> shared copy (completed by cp_async_wait).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+// 16-byte asynchronous copy through L2 only (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(float* dst, const float* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+// One column of Z floats, global -> shared, asynchronously by one warp:
+// 16-byte copies when `vec` (Z a multiple of 4 and every source array 16-byte
+// aligned, so that each column starts on a 16-byte boundary in both spaces),
+// else 4-byte copies.
+__device__ __forceinline__ void copy_column(float* dst, const float* src, int Z, int lane,
+                                            bool vec)
+{
+    if (vec) {
+        for (int j = 4 * lane; j < Z; j += 128) cp_async16(dst + j, src + j);
+    } else {
+        for (int j = lane; j < Z; j += 32) cp_async4(dst + j, src + j);
+    }
+}
+
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+struct FgpCoop {
+    const float* z;  // prox input
+    float* xb;       // x scratch
+    float* u;        // dual iterate [3][L]
+    float* r0;       // extrapolated duals (ping-pong) [3][L]
+    float* r1;
+    Vol v;
+    float tau;
+    int iters;       // >= 1
+    int inner_momentum;
+    int mode;        // 0: out = z - D^T u;  1: FISTA finish
+    float* out;
+    float* c;
+    float* xi;
+    float* delta;    // optional (mode 1)
+    double* scal;    // FISTA t_k, beta_k (mode 1)
+    int momentum;
+    float theta;
+    unsigned* bar;
+    int TY, TX;      // shared-memory variant: tile of TY x TX columns of all z
+    int tilesY, tilesX;
+    bool vec;        // 16-byte column copies allowed (see copy_column)
+};
+
+__device__ __forceinline__ double momentum_coef(double t, double t1, int mode)
+{
+    if (mode == SWOPT_MOMENTUM_BECK_TEBOULLE) return (t - 1.0) / t1;
+    if (mode == SWOPT_MOMENTUM_PAPER_PRINTED) return (t - 1.0) / (t + 1.0);
+    return 0.0;
+}
+
+// Work split of the cooperative kernel: warp w of the grid takes the rows
+// (p, y, x) = w, w + warps, ...; its lanes run along z (coalesced).  `body`
+// is called with the row's coordinates and the linear index of its z = 0.
+template <typename F>
+__device__ __forceinline__ void for_rows(const Vol& v, F body)
+{
+    const unsigned warps = gridDim.x * (blockDim.x >> 5);
+    const unsigned w0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const unsigned rows = (unsigned)v.P * v.Y * v.X;
+    for (unsigned row = w0; row < rows; row += warps) {
+        const int x = (int)(row % (unsigned)v.X);
+        const int y = (int)((row / (unsigned)v.X) % (unsigned)v.Y);
+        body(y, x, (size_t)row * v.Z);
+    }
+}
+
+__global__ void __launch_bounds__(kCoopThreads) fgp_coop_kernel(const FgpCoop a)
+{
+    const Vol v = a.v;
+    const size_t L = v.L, XZ = (size_t)v.X * v.Z;
+    const int lane = threadIdx.x & 31;
+    const unsigned nb = gridDim.x;
+    if (a.mode == 1 && blockIdx.x == 0 && threadIdx.x == 0) {
+        // Algorithm 1's t_k -> t_{k+1} and beta_k, read after the barriers below
+        const double t = a.scal[0];
+        const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        a.scal[1] = momentum_coef(t, t1, a.momentum);
+        a.scal[0] = t1;
+    }
+    const float* rin = a.r0;
+    float* rout = a.r1;
+    // Algorithm 2's t recursion runs in FP64 in one thread per block (FP64
+    // arithmetic is scarce on this GPU) and reaches the block through shared
+    // memory
+    __shared__ float s_beta;
+    double t = 1.0;
+    for (int it = 0; it < a.iters; ++it) {
+        if (threadIdx.x == 0) {
+            const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+            s_beta = (float)momentum_coef(t, t1, a.inner_momentum);
+            t = t1;
+        }
+        __syncthreads();
+        const float beta = s_beta;
+        if (it > 0) {
+            for_rows(v, [&](int y, int x, size_t base) {
+                for (int j = lane; j < v.Z; j += 32) {
+                    const size_t e = base + j;
+                    a.xb[e] = a.z[e] - dtq(rin, v, e, y, x, j);
+                }
+            });
+            grid_sync(a.bar, nb);
+        }
+        const float* xs = it == 0 ? a.z : a.xb;
+        const float* ri = rin;
+        float* ro = rout;
+        for_rows(v, [&](int y, int x, size_t base) {
+            const bool hy = y + 1 < v.Y, hx = x + 1 < v.X;
+            for (int j = lane; j < v.Z; j += 32) {
+                const size_t e = base + j;
+                const float xc = xs[e];
+                const float d[3] = {hy ? xs[e + XZ] - xc : 0.f, hx ? xs[e + v.Z] - xc : 0.f,
+                                    j + 1 < v.Z ? xs[e + 1] - xc : 0.f};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const size_t ia = (size_t)c * L + e;
+                    const float ra = it == 0 ? 0.f : ri[ia];
+                    const float up = it == 0 ? 0.f : a.u[ia];
+                    const float un = clampf(fmaf(d[c], 1.0f / 12.0f, ra), -a.tau, a.tau);
+                    a.u[ia] = un;
+                    ro[ia] = fmaf(beta, un - up, un);
+                }
+            }
+        });
+        grid_sync(a.bar, nb);  // also orders s_beta's next write after every read
+        const float* tmp = rin;
+        rin = rout;
+        rout = const_cast<float*>(tmp);
+    }
+    const float fb = a.mode == 1 ? (float)a.scal[1] : 0.f;
+    for_rows(v, [&](int y, int x, size_t base) {
+        for (int j = lane; j < v.Z; j += 32) {
+            const size_t e = base + j;
+            const float xv = a.z[e] - dtq(a.u, v, e, y, x, j);
+            if (a.mode == 0) {
+                a.out[e] = xv;
+            } else {
+                const float cn = fmaxf(xv - a.theta, 0.f);
+                const float dd = cn - a.c[e];
+                a.c[e] = cn;
+                a.xi[e] = fmaf(fb, dd, cn);
+                if (a.delta) a.delta[e] = dd;
+            }
+        }
+    });
+}
+
+// Shared-memory-resident variant of fgp_coop_kernel.  Block b owns the
+// columns (p, y0 .. y0+TY-1, x0 .. x0+TX-1) over all z and keeps z, x, the
+// duals u and r of its tile in shared memory for all inner iterations, with
+// a ring of ghost columns around the tile (ghosted index (gy, gx) is the
+// column (y0 + gy - 1, x0 + gx - 1)).  Only the tile's boundary columns of r
+// go through global memory: after phase B each block publishes them (into
+// r0 / r1 by iteration parity, so that a neighbour still reading the previous
+// values is never overwritten), one grid barrier, then every block reads its
+// ghost ring.  Phase A computes x on the tile and on the ghost row below and
+// the ghost column to its right, which is where phase B's forward
+// differences reach.  The arithmetic per entry is that of fgp_iter_kernel.
+constexpr int kTileThreads = 1024;
+
+// x = z - D^T q at ghosted shared index i of the column (y, x), depth j; q has
+// three components at stride G; the terms are summed in dtq's order.
+__device__ __forceinline__ float tile_x(const float* q, const float* sz, int i, int G, int GXZ,
+                                        int Z, int j, bool ylo, bool yhi, bool xlo, bool xhi)
+{
+    float acc = 0.f;
+    if (yhi) acc -= q[i];
+    if (ylo) acc += q[i - GXZ];
+    if (xhi) acc -= q[G + i];
+    if (xlo) acc += q[G + i - Z];
+    if (j + 1 < Z) acc -= q[2 * G + i];
+    if (j > 0) acc += q[2 * G + i - 1];
+    return sz[i] - acc;
+}
+
+__global__ void __launch_bounds__(kTileThreads) fgp_tile_kernel(const FgpCoop a)
+{
+    extern __shared__ __align__(16) float sm[];
+    const Vol v = a.v;
+    const int Z = v.Z;
+    const size_t L = v.L;
+    const int GY = a.TY + 2, GX = a.TX + 2;
+    const int G = GY * GX * Z, GXZ = GX * Z;
+    float* sz = sm;          // [GY][GX][Z]   z
+    float* sx = sz + G;      // [GY][GX][Z]   x = z - D^T r
+    float* sr = sx + G;      // [3][GY][GX][Z] r (then u with ghosts, for the output)
+    float* su = sr + 3 * G;  // [3][TY][TX][Z] u
+    const int T = a.TY * a.TX * Z;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned nb = gridDim.x;
+    const int b = blockIdx.x;
+    const int tx = b % a.tilesX, ty = (b / a.tilesX) % a.tilesY;
+    const int p = b / (a.tilesX * a.tilesY);
+    const int y0 = ty * a.TY, x0 = tx * a.TX;
+    const int ny = min(a.TY, v.Y - y0), nx = min(a.TX, v.X - x0);
+    auto gidx = [&](int gy, int gx) -> size_t {  // global index of column (gy, gx), z = 0
+        return (((size_t)p * v.Y + (y0 + gy - 1)) * v.X + (x0 + gx - 1)) * Z;
+    };
+    auto sidx = [&](int gy, int gx) -> int { return (gy * GX + gx) * Z; };
+    auto inside = [&](int gy, int gx) -> bool {
+        const int y = y0 + gy - 1, x = x0 + gx - 1;
+        return y >= 0 && y < v.Y && x >= 0 && x < v.X;
+    };
+    if (a.mode == 1 && b == 0 && threadIdx.x == 0) {
+        const double t = a.scal[0];
+        const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        a.scal[1] = momentum_coef(t, t1, a.momentum);
+        a.scal[0] = t1;
+    }
+    // x on one column (gy, gx); lanes take the depths j and j + 32 together
+    auto phase_a = [&](int gy, int gx) {
+        const int y = y0 + gy - 1, x = x0 + gx - 1;
+        const bool ylo = y > 0, yhi = y + 1 < v.Y, xlo = x > 0, xhi = x + 1 < v.X;
+        const int s0 = sidx(gy, gx);
+        for (int j = lane; j < Z; j += 64) {
+            const int j2 = j + 32;
+            const float v1 = tile_x(sr, sz, s0 + j, G, GXZ, Z, j, ylo, yhi, xlo, xhi);
+            const float v2 = j2 < Z ? tile_x(sr, sz, s0 + j2, G, GXZ, Z, j2, ylo, yhi, xlo, xhi)
+                                    : 0.f;
+            sx[s0 + j] = v1;
+            if (j2 < Z) sx[s0 + j2] = v2;
+        }
+    };
+    // the ghost ring of r, asynchronously, from the published boundary columns
+    auto load_ghosts = [&](const float* pub) {
+        const int ring = 2 * (nx + 2) + 2 * ny;
+        for (int k = warp; k < ring; k += nw) {
+            int gy, gx;
+            if (k < nx + 2) {
+                gy = 0;
+                gx = k;
+            } else if (k < 2 * (nx + 2)) {
+                gy = ny + 1;
+                gx = k - (nx + 2);
+            } else {
+                const int q = k - 2 * (nx + 2);
+                gy = 1 + (q >> 1);
+                gx = (q & 1) ? nx + 1 : 0;
+            }
+            if (!inside(gy, gx)) continue;
+            const size_t g0 = gidx(gy, gx);
+            const int s0 = sidx(gy, gx);
+            for (int c = 0; c < 3; ++c)
+                copy_column(&sr[c * G + s0], &pub[(size_t)c * L + g0], Z, lane, a.vec);
+        }
+    };
+    // r = u = 0; z on the tile, the ghost row below and the ghost column right
+    for (int i = threadIdx.x; i < 3 * G; i += blockDim.x) sr[i] = 0.f;
+    for (int i = threadIdx.x; i < 3 * T; i += blockDim.x) su[i] = 0.f;
+    for (int cidx = warp; cidx < (ny + 1) * (nx + 1); cidx += nw) {
+        const int gy = 1 + cidx / (nx + 1), gx = 1 + cidx % (nx + 1);
+        if (!inside(gy, gx)) continue;
+        copy_column(&sz[sidx(gy, gx)], &a.z[gidx(gy, gx)], Z, lane, a.vec);
+    }
+    cp_async_wait();
+    __syncthreads();
+    // Algorithm 2's t recursion: FP64 in one thread (FP64 arithmetic is scarce
+    // on this GPU), published in shared memory before the barrier after phase A
+    __shared__ float s_beta;
+    double t = 1.0;
+    for (int it = 0; it < a.iters; ++it) {
+        if (threadIdx.x == 0) {
+            const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+            s_beta = (float)momentum_coef(t, t1, a.inner_momentum);
+            t = t1;
+        }
+        const bool last = it + 1 == a.iters;
+        // ghosts of the previous iteration in flight while the interior columns
+        // (whose D^T r stays inside the tile) compute x
+        if (it > 0) load_ghosts(((it - 1) & 1) ? a.r1 : a.r0);
+        for (int cidx = warp; cidx < (ny - 1) * (nx - 1); cidx += nw)
+            phase_a(2 + cidx / (nx - 1), 2 + cidx % (nx - 1));
+        cp_async_wait();
+        __syncthreads();
+        // phase A on the remaining columns: the tile's first row and column, the
+        // ghost row below and the ghost column right
+        for (int cidx = warp; cidx < (ny + 1) * (nx + 1); cidx += nw) {
+            const int gy = 1 + cidx / (nx + 1), gx = 1 + cidx % (nx + 1);
+            const bool interior = gy >= 2 && gy <= ny && gx >= 2 && gx <= nx;
+            if (interior || (gy == ny + 1 && gx == nx + 1) || !inside(gy, gx)) continue;
+            phase_a(gy, gx);
+        }
+        __syncthreads();
+        const float beta = s_beta;
+        // phase B on the tile; boundary columns published
+        float* pub = (it & 1) ? a.r1 : a.r0;
+        for (int cidx = warp; cidx < ny * nx; cidx += nw) {
+            const int gy = 1 + cidx / nx, gx = 1 + cidx % nx;
+            const int y = y0 + gy - 1, x = x0 + gx - 1;
+            const bool hy = y + 1 < v.Y, hx = x + 1 < v.X;
+            const int s0 = sidx(gy, gx), u0 = ((gy - 1) * a.TX + (gx - 1)) * Z;
+            const bool edge = gy == 1 || gy == ny || gx == 1 || gx == nx;
+            const size_t g0 = gidx(gy, gx);
+            for (int j = lane; j < Z; j += 32) {
+                const int i = s0 + j;
+                const float xc = sx[i];
+                const float d[3] = {hy ? sx[i + GXZ] - xc : 0.f, hx ? sx[i + Z] - xc : 0.f,
+                                    j + 1 < Z ? sx[i + 1] - xc : 0.f};
+                float ra[3], up[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    ra[c] = sr[c * G + i];
+                    up[c] = su[c * T + u0 + j];
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float un = clampf(fmaf(d[c], 1.0f / 12.0f, ra[c]), -a.tau, a.tau);
+                    const float rn = fmaf(beta, un - up[c], un);
+                    su[c * T + u0 + j] = un;
+                    sr[c * G + i] = rn;
+                    if (edge) {
+                        if (last) a.u[(size_t)c * L + g0 + j] = un;
+                        else pub[(size_t)c * L + g0 + j] = rn;
+                    }
+                }
+            }
+        }
+        grid_sync(a.bar, nb);
+    }
+    // u with the ghost row above and column left (all that D^T u reads)
+    for (int cidx = warp; cidx < ny * nx; cidx += nw) {
+        const int gy = 1 + cidx / nx, gx = 1 + cidx % nx;
+        const int s0 = sidx(gy, gx), u0 = ((gy - 1) * a.TX + (gx - 1)) * Z;
+        for (int c = 0; c < 3; ++c)
+            for (int j = lane; j < Z; j += 32) sr[c * G + s0 + j] = su[c * T + u0 + j];
+    }
+    for (int k = warp; k < nx + ny; k += nw) {
+        const int gy = k < nx ? 0 : 1 + (k - nx), gx = k < nx ? 1 + k : 0;
+        if (!inside(gy, gx)) continue;
+        const size_t g0 = gidx(gy, gx);
+        const int s0 = sidx(gy, gx);
+        for (int c = 0; c < 3; ++c)
+            copy_column(&sr[c * G + s0], &a.u[(size_t)c * L + g0], Z, lane, a.vec);
+    }
+    cp_async_wait();
+    __syncthreads();
+    const float fb = a.mode == 1 ? (float)a.scal[1] : 0.f;
+    for (int cidx = warp; cidx < ny * nx; cidx += nw) {
+        const int gy = 1 + cidx / nx, gx = 1 + cidx % nx;
+        const int y = y0 + gy - 1, x = x0 + gx - 1;
+        const bool ylo = y > 0, yhi = y + 1 < v.Y, xlo = x > 0, xhi = x + 1 < v.X;
+        const int s0 = sidx(gy, gx);
+        const size_t g0 = gidx(gy, gx);
+        for (int j = lane; j < Z; j += 32) {
+            const float xv = tile_x(sr, sz, s0 + j, G, GXZ, Z, j, ylo, yhi, xlo, xhi);
+            const size_t e = g0 + j;
+            if (a.mode == 0) {
+                a.out[e] = xv;
+            } else {
+                const float cn = fmaxf(xv - a.theta, 0.f);
+                const float dd = cn - a.c[e];
+                a.c[e] = cn;
+                a.xi[e] = fmaf(fb, dd, cn);
+                if (a.delta) a.delta[e] = dd;
+            }
+        }
+    }
+}
+
+// Dynamic shared memory of fgp_tile_kernel for a TY x TX tile.
+size_t tile_smem_bytes(int TY, int TX, int Z)
+{
+    return ((size_t)5 * (TY + 2) * (TX + 2) * Z + (size_t)3 * TY * TX * Z) * sizeof(float);
+}
+
 // Momentum scalars of Algorithm 1 in FP64: scal[0] = t_k -> t_{k+1},
 // scal[1] = beta_k.
 __global__ void fista_scalars_kernel(double* scal, int mode)
@@ -313,29 +756,119 @@ swopt_status prox_l1(swopt_handle* h, float* x, float thresh, int nonneg, cudaSt
     return SWOPT_OK;
 }
 
-swopt_status prox_tv_iters(swopt_handle* h, const float* z, float tau, int iters,
-                           const double* betas, cudaStream_t st)
+// Barrier words and grid size of the cooperative TV prox: every SM, as many
+// blocks as are co-resident, at most 4 per SM (synchronous; not while
+// capturing).
+swopt_status coop_prepare(swopt_handle* h)
 {
-    const Vol v = vol_of(h);
-    float* rin = h->tvr0;
-    float* rout = h->tvr1;
-    for (int it = 0; it < iters; ++it) {
-        fgp_iter_kernel<<<vol_grid(v), kVolBlock, 0, st>>>(z, rin, rout, h->tvu, v, tau,
-                                                      (float)betas[it], it == 0 ? 1 : 0);
-        SW_LAUNCHED(h);
-        float* t = rin;
-        rin = rout;
-        rout = t;
+    if (!h->coop_bar) {
+        SW_CUDA(cudaMalloc((void**)&h->coop_bar, 4 * sizeof(unsigned)));
+        SW_CUDA(cudaMemset(h->coop_bar, 0, 4 * sizeof(unsigned)));
+    }
+    if (h->tile_ty == 0) {
+        // shared-memory tile: the fewest ghosted columns per SM with every tile
+        // co-resident; else (tile_ty = -1) the global-memory kernel
+        h->tile_ty = -1;
+        int sms = 0;
+        SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+        const int dmax = max_dynamic_smem(h, (const void*)fgp_tile_kernel);
+        double best = 1e300;
+        for (int TY = 1; TY <= std::min(h->Y, 32); ++TY)
+            for (int TX = 1; TX <= std::min(h->X, 32); ++TX) {
+                const size_t sm = tile_smem_bytes(TY, TX, h->Z);
+                if (dmax <= 0 || sm > (size_t)dmax) continue;
+                const long tiles = (long)h->P * ((h->Y + TY - 1) / TY) * ((h->X + TX - 1) / TX);
+                if (tiles > (long)sms * 8) continue;
+                SW_CUDA(cudaFuncSetAttribute(fgp_tile_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, dmax));
+                int per_sm = 0;
+                SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fgp_tile_kernel,
+                                                                      kTileThreads, sm));
+                if (per_sm < 1 || tiles > (long)per_sm * sms) continue;
+                const double cost = (double)((tiles + sms - 1) / sms) * (TY + 2) * (TX + 2) +
+                                    1e-3 * (double)tiles;
+                if (cost < best) {
+                    best = cost;
+                    h->tile_ty = TY;
+                    h->tile_tx = TX;
+                }
+            }
+    }
+    if (h->coop_blocks == 0) {
+        int per_sm = 0, sms = 0;
+        SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fgp_coop_kernel,
+                                                              kCoopThreads, 0));
+        SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+        if (per_sm < 1) {
+            set_error("the TV prox kernel cannot be resident");
+            return SWOPT_ERR_UNSUPPORTED;
+        }
+        h->coop_blocks = sms * std::min(per_sm, 4);
     }
     return SWOPT_OK;
 }
 
-swopt_status prox_tv_finish(swopt_handle* h, const float* z, float* x, cudaStream_t st)
+static swopt_status launch_coop(swopt_handle* h, FgpCoop& a, cudaStream_t st)
 {
-    const Vol v = vol_of(h);
-    fgp_finish_kernel<<<vol_grid(v), kVolBlock, 0, st>>>(z, h->tvu, x, v);
+    if (!h->coop_bar || h->coop_blocks == 0 || h->tile_ty == 0) {
+        set_error("internal: the TV prox kernel was not prepared");
+        return SWOPT_ERR_DEVICE_CHECK;
+    }
+    a.bar = h->coop_bar;
+    if (h->tile_ty > 0) {
+        auto al16 = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
+        a.vec = (h->Z % 4) == 0 && al16(a.z) && al16(a.u) && al16(a.r0) && al16(a.r1);
+        a.TY = h->tile_ty;
+        a.TX = h->tile_tx;
+        a.tilesY = (h->Y + a.TY - 1) / a.TY;
+        a.tilesX = (h->X + a.TX - 1) / a.TX;
+        const int tiles = h->P * a.tilesY * a.tilesX;
+        const int dmax = max_dynamic_smem(h, (const void*)fgp_tile_kernel);
+        SW_CUDA(cudaFuncSetAttribute(fgp_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     dmax));
+        void* args[] = {&a};
+        SW_CUDA(cudaLaunchCooperativeKernel((const void*)fgp_tile_kernel, dim3(tiles),
+                                            dim3(kTileThreads), args,
+                                            tile_smem_bytes(a.TY, a.TX, h->Z), st));
+        SW_LAUNCHED(h);
+        return SWOPT_OK;
+    }
+    void* args[] = {&a};
+    SW_CUDA(cudaLaunchCooperativeKernel((const void*)fgp_coop_kernel, dim3(h->coop_blocks),
+                                        dim3(kCoopThreads), args, 0, st));
     SW_LAUNCHED(h);
     return SWOPT_OK;
+}
+
+swopt_status prox_tv_coop(swopt_handle* h, const float* z, float tau, int iters,
+                          int inner_momentum, float* out, cudaStream_t st)
+{
+    FgpCoop a{};
+    a.z = z; a.xb = h->tvx; a.u = h->tvu; a.r0 = h->tvr0; a.r1 = h->tvr1;
+    a.v = vol_of(h); a.tau = tau; a.iters = iters; a.inner_momentum = inner_momentum;
+    a.mode = 0; a.out = out;
+    return launch_coop(h, a, st);
+}
+
+swopt_status fista_prox_finish(swopt_handle* h, const float* z, float tau, int iters,
+                               int inner_momentum, float theta, float* delta, cudaStream_t st)
+{
+    FgpCoop a{};
+    a.z = z; a.xb = h->tvx; a.u = h->tvu; a.r0 = h->tvr0; a.r1 = h->tvr1;
+    a.v = vol_of(h); a.tau = tau; a.iters = iters; a.inner_momentum = inner_momentum;
+    a.mode = 1; a.c = h->c; a.xi = h->xi; a.delta = delta; a.scal = h->scal;
+    a.momentum = h->prm.momentum; a.theta = theta;
+    return launch_coop(h, a, st);
+}
+
+int coop_error_word(swopt_handle* h)
+{
+    if (!h->coop_bar) return 0;
+    unsigned w[4] = {0, 0, 0, 0};
+    if (cudaMemcpy(w, h->coop_bar, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    if (w[2] == 0) return 0;
+    cudaMemset(h->coop_bar, 0, sizeof(w));
+    return 1;
 }
 
 swopt_status fista_finish(swopt_handle* h, const float* z, bool use_tv, float theta,

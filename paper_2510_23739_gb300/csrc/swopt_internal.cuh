@@ -104,6 +104,7 @@ struct swopt_handle {
     std::vector<int> Cm;          // [Q] pulses per state
     int precision = SWOPT_PREC_FP32;
     int device = 0;
+    int smem_optin = 0;           // opt-in shared memory per block (0: not queried)
 
     // FP32 operator data
     float* Kf = nullptr;          // [Z][k][k][Twp] forward kernel, window-padded
@@ -134,11 +135,14 @@ struct swopt_handle {
     float* tvu = nullptr;         // [3][P][Y][X][Z] dual iterate
     float* tvr0 = nullptr;        // [3][..] extrapolated dual (ping)
     float* tvr1 = nullptr;        // [3][..] (pong)
+    float* tvx = nullptr;         // [P][Y][X][Z] x = z - D^T r of the current inner iteration
+    unsigned* coop_bar = nullptr; // grid barrier of the cooperative TV prox: count, generation, error
+    int coop_blocks = 0;          // its grid size (0: not yet sized)
+    int tile_ty = 0, tile_tx = 0; // shared-memory TV prox tile (0: not chosen, -1: none fits)
     float* tmp = nullptr;         // [P][Y][X][Z] scratch (c_{k+1} - c_k in the refined solve)
     float* G = nullptr;           // [P][Y][X][Z] refined solve: gradient at c_k
     float* xprev = nullptr;       // [P][Y][X][Z] previous momentum iterate (eps2 test)
     int64_t iter = 0;             // FISTA iterations since swopt_fista_init
-    std::vector<double> inner_beta; // momentum coefficients of Algorithm 2
 
     // tensor-core path
     swopt::TcOperator* tc = nullptr;      // operator of `precision`
@@ -158,12 +162,37 @@ struct swopt_handle {
     bool profile = false;
     std::vector<swopt::ProfileRec> prof;
     std::vector<cudaEvent_t> event_pool;
-    double prof_ms[2] = {0, 0};
-    int64_t prof_n[2] = {0, 0};
+    double prof_ms[4] = {0, 0, 0, 0};   // A, A^T, and the two at the resync precision
+    int64_t prof_n[4] = {0, 0, 0, 0};
+    bool in_ref = false;                // launching the refined solve's resync
     int64_t launches = 0;
 };
 
 namespace swopt {
+
+// Largest dynamic shared memory a block may opt in to on the handle's device
+// (queried once; <= 0 if the query failed).
+inline int smem_optin_bytes(swopt_handle* h)
+{
+    if (h->smem_optin == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) !=
+            cudaSuccess)
+            v = -1;
+        h->smem_optin = v;
+    }
+    return h->smem_optin;
+}
+
+// Dynamic shared memory that `func` may be given: the opt-in limit less the
+// function's static shared memory (<= 0 if a query failed).
+inline int max_dynamic_smem(swopt_handle* h, const void* func)
+{
+    const int optin = smem_optin_bytes(h);
+    cudaFuncAttributes fa;
+    if (optin <= 0 || cudaFuncGetAttributes(&fa, func) != cudaSuccess) return -1;
+    return optin - (int)fa.sharedSizeBytes;
+}
 
 inline size_t nc_of(const swopt_handle* h) { return (size_t)h->P * h->S * h->Z; }
 inline size_t nb_of(const swopt_handle* h) { return (size_t)h->Q * h->S * h->Z; }
@@ -219,13 +248,20 @@ swopt_status launch_pt_refine(swopt_handle* h, const float* g, const float* xi, 
 
 // Proximal / FISTA / reduction kernels (prox.cu).
 swopt_status prox_l1(swopt_handle* h, float* x, float thresh, int nonneg, cudaStream_t st);
-swopt_status prox_tv_iters(swopt_handle* h, const float* z, float tau, int iters,
-                           const double* betas, cudaStream_t st);
-swopt_status prox_tv_finish(swopt_handle* h, const float* z, float* x, cudaStream_t st);
 // delta (optional): also write c_{k+1} - c_k there
 swopt_status fista_finish(swopt_handle* h, const float* z, bool use_tv, float theta,
                           float* delta, cudaStream_t st);
 swopt_status fista_scalars(swopt_handle* h, int momentum, cudaStream_t st);
+// The TV prox of Algorithm 2 (iters >= 1 inner iterations) in one cooperative
+// launch: out = z - D^T u (prox_tv_coop), or with the FISTA scalars and
+// fista_finish fused after it (fista_prox_finish).  Needs ensure'd TV buffers.
+swopt_status prox_tv_coop(swopt_handle* h, const float* z, float tau, int iters,
+                          int inner_momentum, float* out, cudaStream_t st);
+swopt_status fista_prox_finish(swopt_handle* h, const float* z, float tau, int iters,
+                               int inner_momentum, float theta, float* delta, cudaStream_t st);
+swopt_status coop_prepare(swopt_handle* h);
+// Reads and clears the cooperative kernel's barrier error word (0 = none).
+int coop_error_word(swopt_handle* h);
 swopt_status fista_reset_scalars(swopt_handle* h, cudaStream_t st);
 // FP64 reductions, result written to h->scal[slot]
 swopt_status reduce_sumsq(swopt_handle* h, const float* x, size_t n, int slot, cudaStream_t st);

@@ -143,6 +143,26 @@ def test_prox_tv_matches_oracle(cases, name, momentum):
     assert rel(got, ref) <= 1e-5
 
 
+def test_prox_tv_unaligned_input_and_medium_volume(cases, medium):
+    """The TV prox keeps its state in shared memory when the volume fits there
+    (the medium volume does) and reads its input column by column: an input
+    that starts 4 bytes past a 16-byte boundary gives bitwise the result of
+    an aligned copy, and the medium volume matches the oracle."""
+    g, s, K, op = cases["tiny"]
+    n = int(np.prod(g.c_shape()))
+    base = torch.zeros(n + 1, device="cuda")
+    z = np.random.default_rng(23).standard_normal(g.c_shape())
+    base[1:] = dev(z).reshape(-1)
+    zu = base[1:].view(g.c_shape())
+    assert zu.data_ptr() % 16 == 4
+    assert torch.equal(op.prox_tv(zu, 0.3, 6), op.prox_tv(dev(z), 0.3, 6))
+    gm, _, _, opm = medium
+    zm = synth.gaussian(gm.c_shape(), 24) * 0.05
+    got = host(opm.prox_tv(dev(zm), 0.02, 10))
+    assert rel(got, oracle.prox_tv(zm, 0.02, 10)) <= 1e-5
+    opm.check_device()
+
+
 def test_prox_tv_zero_iterations_and_zero_tau(cases):
     g, s, K, op = cases["tiny"]
     z = dev(np.random.default_rng(17).standard_normal(g.c_shape()))
