@@ -218,6 +218,22 @@ swopt_status swopt_objective(swopt_handle* h, const float* c_dev, const float* y
 swopt_status swopt_param_grad(swopt_handle* h, const float* c_dev, const float* y_dev,
                               double* dkappa_host, double* dmu, void* stream);
 
+/* Vector-Jacobian product of (kappa, mu) -> H(kappa, mu) c at fixed c: for a
+ * cotangent w_dev in the measurement layout [N][Y][X][T],
+ * dkappa_host[p] = <w, dH/dkappa_p c> (length P) and *dmu = <w, dH/dmu c>
+ * (Eq. final-H differentiated).  swopt_param_grad is this product with
+ * w = H c - y.  Uses the handle's precision for A^T; FP64 accumulation.
+ * Synchronises. */
+swopt_status swopt_param_vjp(swopt_handle* h, const float* c_dev, const float* w_dev,
+                             double* dkappa_host, double* dmu, void* stream);
+
+/* Replaces the switching parameters of Eq. (final-H) (kappa, eps_bar, eps_off
+ * per species and mu, validated as in swopt_create); the geometry, kernel and
+ * precision stay.  Captured FISTA iterations keep working (they read the
+ * switching weights from device memory), but a FISTA state that is in
+ * progress continues with the new model.  Synchronises the device. */
+swopt_status swopt_set_switching(swopt_handle* h, const swopt_switching* sw);
+
 /* CUDA graphs (default on): swopt_fista_step captures one iteration into a
  * CUDA graph on first use after swopt_fista_init (on a stream the handle
  * owns) and replays it on the caller's stream; on = 0 launches the kernels

@@ -100,6 +100,10 @@ _SIGS = {
     "swopt_param_grad": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.c_void_p], ctypes.c_int),
+    "swopt_param_vjp": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                         ctypes.c_void_p], ctypes.c_int),
+    "swopt_set_switching": ([ctypes.c_void_p, ctypes.POINTER(_Switching)], ctypes.c_int),
     "swopt_profile_enable": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "swopt_use_graphs": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "swopt_profile_read": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -223,15 +227,7 @@ class Operator:
         K = np.ascontiguousarray(K, dtype=np.float64)
         if K.shape != (geom.Z, geom.k, geom.k, geom.T):
             raise ValueError(f"kernel shape {K.shape} does not match the geometry")
-        self._kap = np.ascontiguousarray(sw.kappa, dtype=np.float64)
-        self._eb = np.ascontiguousarray(sw.eps_bar, dtype=np.float64)
-        self._eo = np.ascontiguousarray(sw.eps_off, dtype=np.float64)
-        for a in (self._kap, self._eb, self._eo):
-            if a.shape != (geom.P,):
-                raise ValueError("switching parameters must have one entry per species")
-        dp = ctypes.POINTER(ctypes.c_double)
-        s = _Switching(self._kap.ctypes.data_as(dp), self._eb.ctypes.data_as(dp),
-                       self._eo.ctypes.data_as(dp), float(sw.mu_per_mm))
+        s = self._switching_struct(sw.kappa, sw.eps_bar, sw.eps_off, sw.mu_per_mm)
         h = ctypes.c_void_p()
         _check(L.swopt_create(ctypes.byref(g), K.ctypes.data_as(ctypes.c_void_p), ctypes.byref(s),
                               ctypes.byref(h)))
@@ -239,6 +235,31 @@ class Operator:
         if precision != "fp32":
             self.set_precision(precision)
         self.precision = precision
+
+    def _switching_struct(self, kappa, eps_bar, eps_off, mu):
+        self._kap = np.ascontiguousarray(kappa, dtype=np.float64).reshape(-1)
+        self._eb = np.ascontiguousarray(eps_bar, dtype=np.float64).reshape(-1)
+        self._eo = np.ascontiguousarray(eps_off, dtype=np.float64).reshape(-1)
+        for a in (self._kap, self._eb, self._eo):
+            if a.shape != (self.geom.P,):
+                raise ValueError("switching parameters must have one entry per species")
+        self._mu = float(mu)
+        dp = ctypes.POINTER(ctypes.c_double)
+        return _Switching(self._kap.ctypes.data_as(dp), self._eb.ctypes.data_as(dp),
+                          self._eo.ctypes.data_as(dp), self._mu)
+
+    def set_switching(self, kappa=None, mu=None, eps_bar=None, eps_off=None):
+        """Replace (some of) the switching parameters of Eq. (final-H)."""
+        s = self._switching_struct(self._kap if kappa is None else kappa,
+                                   self._eb if eps_bar is None else eps_bar,
+                                   self._eo if eps_off is None else eps_off,
+                                   self._mu if mu is None else mu)
+        _check(lib().swopt_set_switching(self._h, ctypes.byref(s)))
+
+    @property
+    def switching(self):
+        """(kappa, mu, eps_bar, eps_off) in use (FP64 copies)."""
+        return self._kap.copy(), self._mu, self._eb.copy(), self._eo.copy()
 
     # -- lifecycle --------------------------------------------------------
     def close(self):
@@ -358,6 +379,16 @@ class Operator:
                                       ctypes.byref(dmu), _stream(stream)))
         return dk, dmu.value
 
+    def param_vjp(self, c, w, stream=None):
+        """(dkappa [P], dmu) = <w, d(H c)/d(kappa, mu)> for a cotangent w [N][Y][X][T]."""
+        dk = np.zeros(self.geom.P)
+        dmu = ctypes.c_double()
+        _check(lib().swopt_param_vjp(self._h, _ptr(c, self.c_shape, "c"),
+                                     _ptr(w, self.y_shape, "w"),
+                                     dk.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     ctypes.byref(dmu), _stream(stream)))
+        return dk, dmu.value
+
     # -- instrumentation --------------------------------------------------
     def use_graphs(self, on=True):
         _check(lib().swopt_use_graphs(self._h, 1 if on else 0))
@@ -395,25 +426,59 @@ class Operator:
         return n.value
 
 
+_HFUNCTION = None
+
+
 def _make_hfunction():
     import torch
 
     class HFunction(torch.autograd.Function):
-        """y = H c with backward c_grad = H^T y_grad (hand-written adjoint)."""
+        """y = H(kappa, mu) c on the GPU, differentiable in c, kappa and mu.
+
+        ``HFunction.apply(c, kappa, mu, op)``: c [P][Y][X][Z] float32 on the
+        GPU; kappa a tensor of P switching rates and mu a scalar tensor (any
+        device and dtype; used in FP64); eps_bar / eps_off stay those of
+        ``op``.  Forward sets the operator's switching parameters and applies
+        H.  Backward: the hand-written adjoint H^T for c, and
+        ``swopt_param_vjp`` (the cotangent contracted with dH/dkappa c and
+        dH/dmu c) for kappa and mu.
+        """
 
         @staticmethod
-        def forward(ctx, c, op):
-            ctx.op = op
+        def forward(ctx, c, kappa, mu, op):
+            k = kappa.detach().double().cpu().numpy().reshape(-1)
+            m = float(mu.detach().double().cpu())
+            op.set_switching(kappa=k, mu=m)
+            ctx.op, ctx.k, ctx.m = op, k, m
+            ctx.kdev, ctx.kdtype = kappa.device, kappa.dtype
+            ctx.mdev, ctx.mdtype = mu.device, mu.dtype
+            ctx.save_for_backward(c)
             return op.forward(c.contiguous())
 
         @staticmethod
         def backward(ctx, gy):
-            return ctx.op.adjoint(gy.contiguous()), None
+            (c,) = ctx.saved_tensors
+            op = ctx.op
+            k0, m0 = op.switching[0], op.switching[1]
+            if not (np.array_equal(k0, ctx.k) and m0 == ctx.m):
+                op.set_switching(kappa=ctx.k, mu=ctx.m)
+            gy = gy.contiguous()
+            gc = op.adjoint(gy) if ctx.needs_input_grad[0] else None
+            gk = gm = None
+            if ctx.needs_input_grad[1] or ctx.needs_input_grad[2]:
+                dk, dmu = op.param_vjp(c.contiguous(), gy)
+                gk = torch.tensor(dk, dtype=ctx.kdtype, device=ctx.kdev)
+                gm = torch.tensor(dmu, dtype=ctx.mdtype, device=ctx.mdev)
+            return gc, gk, gm, None
 
     return HFunction
 
 
 def __getattr__(name):
+    # torch is imported only when the autograd function is first used
+    global _HFUNCTION
     if name == "HFunction":
-        return _make_hfunction()
+        if _HFUNCTION is None:
+            _HFUNCTION = _make_hfunction()
+        return _HFUNCTION
     raise AttributeError(name)

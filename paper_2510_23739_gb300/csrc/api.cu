@@ -329,6 +329,78 @@ swopt_status lipschitz_impl(swopt_handle* h, const float* v0, int iters, double*
     return SWOPT_OK;
 }
 
+// Switching weights of the Q states (Eq. final-H): Phi_j = exp(-mu j dz) and
+// S[m][p][j] = Phi_j (eps_bar_p exp(-kappa_p Phi_j m) + eps_off_p).
+void switching_states(swopt_handle* h)
+{
+    h->phi.resize(h->Z);
+    for (int j = 0; j < h->Z; ++j) h->phi[j] = std::exp(-h->mu * j * h->dz_mm);
+    h->Sm64.resize((size_t)h->Q * h->P * h->Z);
+    for (int m = 0; m < h->Q; ++m)
+        for (int p = 0; p < h->P; ++p)
+            for (int j = 0; j < h->Z; ++j) {
+                const double ph = h->phi[j];
+                h->Sm64[((size_t)m * h->P + p) * h->Z + j] =
+                    ph * (h->eps_bar[p] * std::exp(-h->kappa[p] * ph * m) + h->eps_off[p]);
+            }
+}
+
+swopt_status check_switching(const swopt_switching* sw, int P)
+{
+    if (!sw || !sw->kappa_host || !sw->eps_bar_host || !sw->eps_off_host) {
+        set_error("null switching pointer");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    if (!is_fin(sw->mu_per_mm)) {
+        set_error("invalid mu_per_mm");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    for (int p = 0; p < P; ++p)
+        if (!is_fin(sw->kappa_host[p]) || !is_fin(sw->eps_bar_host[p]) ||
+            !is_fin(sw->eps_off_host[p])) {
+            set_error("non-finite switching parameter for species %d", p);
+            return SWOPT_ERR_INVALID_ARG;
+        }
+    return SWOPT_OK;
+}
+
+// Chain rule through Eq. (final-H): W[m][p][j] = <(A^T w)_m, c_p> per depth
+// (FP64, from param_weights) -> d/dkappa_p and d/dmu of <w, H c>.
+void switching_chain_rule(const swopt_handle* h, const std::vector<double>& W, double* dkappa,
+                          double* dmu)
+{
+    double dm = 0.0;
+    for (int p = 0; p < h->P; ++p) dkappa[p] = 0.0;
+    for (int m = 0; m < h->Q; ++m)
+        for (int p = 0; p < h->P; ++p)
+            for (int j = 0; j < h->Z; ++j) {
+                const double ph = h->phi[j];
+                const double e = std::exp(-h->kappa[p] * ph * m);
+                const double w = W[((size_t)m * h->P + p) * h->Z + j];
+                const double dS_dk = ph * h->eps_bar[p] * e * (-ph * m);
+                const double dS_dphi =
+                    h->eps_bar[p] * e + h->eps_off[p] + ph * h->eps_bar[p] * e * (-h->kappa[p] * m);
+                const double dphi_dmu = -(double)j * h->dz_mm * ph;
+                dkappa[p] += w * dS_dk;
+                dm += w * dS_dphi * dphi_dmu;
+            }
+    *dmu = dm;
+}
+
+// W from the A^T output in h->g and c, then the chain rule (synchronises).
+swopt_status switching_gradient(swopt_handle* h, const float* c, double* dkappa, double* dmu,
+                                cudaStream_t st)
+{
+    SW_TRY(param_weights(h, h->g, c, 0, st));
+    const size_t nw = (size_t)h->Q * h->P * h->Z;
+    std::vector<double> W(nw);
+    SW_CUDA(cudaMemcpyAsync(W.data(), h->red, nw * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SW_CUDA(cudaStreamSynchronize(st));
+    SW_TRY(device_errors(h));
+    switching_chain_rule(h, W, dkappa, dmu);
+    return SWOPT_OK;
+}
+
 swopt_status validate_params(const swopt_solve_params* p)
 {
     if (!p) {
@@ -563,8 +635,8 @@ swopt_status swopt_create(const swopt_geometry* geom, const double* K_host,
         return SWOPT_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    if (!geom || !K_host || !sw || !sw->kappa_host || !sw->eps_bar_host || !sw->eps_off_host) {
-        set_error("null geometry, kernel or switching pointer");
+    if (!geom || !K_host) {
+        set_error("null geometry or kernel pointer");
         return SWOPT_ERR_INVALID_ARG;
     }
     const swopt_geometry& g = *geom;
@@ -575,16 +647,11 @@ swopt_status swopt_create(const swopt_geometry* geom, const double* K_host,
                   g.Z, g.T, g.N, g.P, g.k, g.pulses_per_cycle);
         return SWOPT_ERR_SHAPE;
     }
-    if (!is_fin(g.dz_mm) || g.dz_mm <= 0 || !is_fin(sw->mu_per_mm)) {
-        set_error("invalid dz_mm or mu_per_mm");
+    if (!is_fin(g.dz_mm) || g.dz_mm <= 0) {
+        set_error("invalid dz_mm");
         return SWOPT_ERR_INVALID_ARG;
     }
-    for (int p = 0; p < g.P; ++p)
-        if (!is_fin(sw->kappa_host[p]) || !is_fin(sw->eps_bar_host[p]) ||
-            !is_fin(sw->eps_off_host[p])) {
-            set_error("non-finite switching parameter for species %d", p);
-            return SWOPT_ERR_INVALID_ARG;
-        }
+    SW_TRY(check_switching(sw, g.P));
     const size_t kn = (size_t)g.Z * g.k * g.k * g.T;
     int tmin = g.T, tmax = -1;
     int64_t nnz = 0;
@@ -624,19 +691,9 @@ swopt_status swopt_create(const swopt_geometry* geom, const double* K_host,
     h->K64.assign(K_host, K_host + kn);
     cudaGetDevice(&h->device);
 
-    // switching states: S[m][p][j] for m < Q (Eq. final-H)
-    h->phi.resize(g.Z);
-    for (int j = 0; j < g.Z; ++j) h->phi[j] = std::exp(-h->mu * j * h->dz_mm);
-    h->Sm64.resize((size_t)h->Q * g.P * g.Z);
+    switching_states(h);
     h->Cm.assign(h->Q, 0);
     for (int n = 0; n < g.N; ++n) h->Cm[n % h->ncyc]++;
-    for (int m = 0; m < h->Q; ++m)
-        for (int p = 0; p < g.P; ++p)
-            for (int j = 0; j < g.Z; ++j) {
-                const double ph = h->phi[j];
-                h->Sm64[((size_t)m * g.P + p) * g.Z + j] =
-                    ph * (h->eps_bar[p] * std::exp(-h->kappa[p] * ph * m) + h->eps_off[p]);
-            }
 
     // FP32 kernel copies and band masks
     const int kk = g.k * g.k;
@@ -984,38 +1041,41 @@ swopt_status swopt_param_grad(swopt_handle* h, const float* c_dev, const float* 
     swopt_status s = launch_fold(h, y_dev, yt, st);
     if (s == SWOPT_OK) s = apply_A(h, c_dev, A_OUT_R, yt, nullptr, 1, st);
     if (s == SWOPT_OK) s = apply_AT(h, false, st);
-    if (s == SWOPT_OK) s = param_weights(h, h->g, c_dev, 0, st);
-    const size_t nw = (size_t)h->Q * h->P * h->Z;
-    std::vector<double> W(nw);
-    if (s == SWOPT_OK) {
-        cudaError_t e = cudaMemcpyAsync(W.data(), h->red, nw * sizeof(double),
-                                        cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            set_error("param_grad copy failed: %s", cudaGetErrorString(e));
-            s = SWOPT_ERR_CUDA;
-        }
-    }
+    if (s == SWOPT_OK) s = switching_gradient(h, c_dev, dkappa_host, dmu, st);
     cudaFree(yt);
-    SW_TRY(s);
-    // d/dtheta of S[m][p][j] = Phi_j (eps_bar_p e^{-kappa_p Phi_j m} + eps_off_p),
-    // Phi_j = exp(-mu j dz)
-    double dm = 0.0;
-    for (int p = 0; p < h->P; ++p) dkappa_host[p] = 0.0;
-    for (int m = 0; m < h->Q; ++m)
-        for (int p = 0; p < h->P; ++p)
-            for (int j = 0; j < h->Z; ++j) {
-                const double ph = h->phi[j];
-                const double e = std::exp(-h->kappa[p] * ph * m);
-                const double w = W[((size_t)m * h->P + p) * h->Z + j];
-                const double dS_dk = ph * h->eps_bar[p] * e * (-ph * m);
-                const double dS_dphi =
-                    h->eps_bar[p] * e + h->eps_off[p] + ph * h->eps_bar[p] * e * (-h->kappa[p] * m);
-                const double dphi_dmu = -(double)j * h->dz_mm * ph;
-                dkappa_host[p] += w * dS_dk;
-                dm += w * dS_dphi * dphi_dmu;
-            }
-    *dmu = dm;
+    return s;
+}
+
+swopt_status swopt_param_vjp(swopt_handle* h, const float* c_dev, const float* w_dev,
+                             double* dkappa_host, double* dmu, void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!c_dev || !w_dev || !dkappa_host || !dmu) {
+        set_error("null argument");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // <w, dH/dtheta c> = sum_m <A^T w~_m, dS_m/dtheta c>, w~ the cotangent
+    // folded over pulses of equal state (H c vanishes outside the window)
+    SW_TRY(launch_fold(h, w_dev, h->u, st));
+    SW_TRY(apply_AT(h, true, st));
+    return switching_gradient(h, c_dev, dkappa_host, dmu, st);
+}
+
+swopt_status swopt_set_switching(swopt_handle* h, const swopt_switching* sw)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    SW_TRY(check_switching(sw, h->P));
+    SW_CUDA(cudaDeviceSynchronize());
+    h->mu = sw->mu_per_mm;
+    h->kappa.assign(sw->kappa_host, sw->kappa_host + h->P);
+    h->eps_bar.assign(sw->eps_bar_host, sw->eps_bar_host + h->P);
+    h->eps_off.assign(sw->eps_off_host, sw->eps_off_host + h->P);
+    switching_states(h);
+    std::vector<float> Smf(h->Sm64.begin(), h->Sm64.end());
+    SW_CUDA(cudaMemcpy(h->Sm, Smf.data(), Smf.size() * sizeof(float), cudaMemcpyHostToDevice));
     return SWOPT_OK;
 }
 

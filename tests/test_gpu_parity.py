@@ -588,3 +588,83 @@ def test_tensor_core_accumulators_option(tc_cases):
     op = sw.Operator(g, K, s, precision="bf16x3")
     assert op.tc_config(0)["accumulators"] == 2 and op.tc_config(1)["accumulators"] == 2
     op.close()
+
+
+# ---------------------------------------------------------------------------
+# Differentiation (tiny workload's shapes, FP32 on the GPU against FP64 on the
+# CPU): the autograd function around H gives the gradient of
+# 1/2 ||H(kappa, mu) c - y||^2 with respect to c, kappa and mu.  References:
+# the oracle's adjoint and parameter gradient, and central differences of the
+# oracle's data fit (h = 1e-4, FP64).
+# ---------------------------------------------------------------------------
+def test_hfunction_gradients_match_oracle_and_central_differences():
+    g, s = TINY.geom, TINY.sw
+    K = synth.transducer_kernel(g, seed=0)
+    op = sw.Operator(g, K, s)
+    rng = np.random.default_rng(50)
+    c = synth.tube_phantom(g, TINY.tubes, seed=3, per_species=True) + 0.05
+    y = oracle.forward(g, s, K, c * 1.05) + 0.02 * rng.standard_normal(g.y_shape())
+    kappa = torch.tensor(s.kappa, dtype=torch.float64, requires_grad=True)
+    mu = torch.tensor(s.mu_per_mm, dtype=torch.float64, requires_grad=True)
+    ct = dev(c).requires_grad_(True)
+    yt = dev(y)
+    H = sw.HFunction
+    assert H is sw.HFunction  # one class, created once
+    loss = 0.5 * (H.apply(ct, kappa, mu, op).double() - yt.double()).pow(2).sum()
+    loss.backward()
+    # c: H^T (H c - y)
+    gc_ref = oracle.adjoint(g, s, K, oracle.forward(g, s, K, c) - y)
+    assert rel(host(ct.grad), gc_ref) <= 1e-5
+    # kappa, mu: the oracle's gradient and central differences
+    dk_ref, dmu_ref = oracle.param_grad(g, s, K, c, y)
+
+    def fit(kap, m):
+        s2 = synth.Switching(tuple(kap), s.eps_bar, s.eps_off, m)
+        return 0.5 * np.sum((oracle.forward(g, s2, K, c) - y) ** 2)
+
+    h = 1e-4
+    kp = list(s.kappa)
+    for p in range(g.P):
+        a, b = list(kp), list(kp)
+        a[p] += h
+        b[p] -= h
+        fd = (fit(a, s.mu_per_mm) - fit(b, s.mu_per_mm)) / (2 * h)
+        if abs(dk_ref[p]) > 0:
+            assert dk_ref[p] == pytest.approx(fd, rel=1e-5)  # O(h^2) truncation
+            assert kappa.grad[p].item() == pytest.approx(dk_ref[p], rel=1e-4)
+        else:
+            assert abs(kappa.grad[p].item()) <= 1e-6 * max(abs(fd), 1.0)
+    fd = (fit(kp, s.mu_per_mm + h) - fit(kp, s.mu_per_mm - h)) / (2 * h)
+    assert dmu_ref == pytest.approx(fd, rel=1e-5)
+    assert mu.grad.item() == pytest.approx(dmu_ref, rel=1e-4)
+    # c along random directions: the data fit's central difference
+    for seed in range(3):
+        v = np.random.default_rng(60 + seed).standard_normal(g.c_shape())
+        fdc = (0.5 * np.sum((oracle.forward(g, s, K, c + h * v) - y) ** 2) -
+               0.5 * np.sum((oracle.forward(g, s, K, c - h * v) - y) ** 2)) / (2 * h)
+        assert float(np.sum(host(ct.grad) * v)) == pytest.approx(fdc, rel=1e-4)
+    op.close()
+
+
+def test_param_vjp_and_set_switching(cases):
+    """<w, dH/dtheta c> for an arbitrary cotangent equals param_grad with
+    y = H c - w; a changed kappa / mu changes the operator like a new handle."""
+    g, s, K, op = cases["ragged"]
+    rng = np.random.default_rng(51)
+    c = np.abs(rng.standard_normal(g.c_shape()))
+    w = rng.standard_normal(g.y_shape())
+    dk, dmu = op.param_vjp(dev(c), dev(w))
+    dk2, dmu2 = op.param_grad(dev(c), dev(oracle.forward(g, s, K, c) - w))
+    np.testing.assert_allclose(dk, dk2, rtol=1e-4, atol=1e-9 * np.abs(dk2).max())
+    assert dmu == pytest.approx(dmu2, rel=1e-4)
+    s2 = synth.Switching(tuple(k * 1.7 for k in s.kappa), s.eps_bar, s.eps_off, s.mu_per_mm * 0.6)
+    fresh = sw.Operator(g, K, s2)
+    ref = host(fresh.forward(dev(c)))
+    fresh.close()
+    try:
+        op.set_switching(kappa=s2.kappa, mu=s2.mu_per_mm)
+        assert np.array_equal(host(op.forward(dev(c))), ref)
+        assert rel(ref, oracle.forward(g, s2, K, c)) <= 1e-5
+    finally:
+        op.set_switching(kappa=s.kappa, mu=s.mu_per_mm)
+    assert rel(host(op.forward(dev(c))), oracle.forward(g, s, K, c)) <= 1e-5
