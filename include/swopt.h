@@ -324,6 +324,21 @@ swopt_status swopt_info(swopt_handle* h, int* t0, int* tw, int* states, int64_t*
 swopt_status swopt_prox_tv_static(int P, int Y, int X, int Z, const float* z_dev, float* x_dev,
                                   float tau, int inner_iters, int momentum, void* stream);
 
+/* Batched problems (independent solves of uneven size).  swopt_batch_create
+ * takes handles whose FISTA state is set up (swopt_fista_init, the same
+ * refine_every and iteration count on all); swopt_batch_step then runs `iters`
+ * FISTA iterations of every problem, each iteration one CUDA-graph launch in
+ * which every problem's kernels run on a stream of their own, so that the
+ * problems overlap on the GPU.  The iterates are those of swopt_fista_step on
+ * each handle.  Stepping a handle on its own or re-initialising it makes the
+ * batch refuse to step (INVALID_ARG); discarding a handle's graphs (precision
+ * or tiling changes) makes it recapture.  The handles must outlive the batch.
+ * swopt_launch_count of the first handle counts the batch's kernels. */
+typedef struct swopt_batch swopt_batch;
+swopt_status swopt_batch_create(swopt_handle* const* handles, int count, swopt_batch** out);
+swopt_status swopt_batch_step(swopt_batch* b, int iters, void* stream);
+swopt_status swopt_batch_destroy(swopt_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

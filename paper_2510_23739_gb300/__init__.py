@@ -23,7 +23,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["lib", "Operator", "SolveParams", "SwoptError", "PRECISION", "MOMENTUM",
-           "HFunction"]
+           "HFunction", "Batch"]
 
 PRECISION = {"fp32": 0, "bf16": 1, "bf16x3": 2}
 MOMENTUM = {"beck_teboulle": 0, "paper_printed": 1, "none": 2}
@@ -104,6 +104,10 @@ _SIGS = {
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                          ctypes.c_void_p], ctypes.c_int),
     "swopt_set_switching": ([ctypes.c_void_p, ctypes.POINTER(_Switching)], ctypes.c_int),
+    "swopt_batch_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                            ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "swopt_batch_step": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "swopt_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "swopt_profile_enable": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "swopt_use_graphs": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "swopt_profile_read": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -424,6 +428,33 @@ class Operator:
         n = ctypes.c_int64()
         _check(lib().swopt_launch_count(self._h, ctypes.byref(n)))
         return n.value
+
+
+class Batch:
+    """Independent problems stepped together (``swopt_batch_*``): every
+    iteration of all of them is one CUDA graph with a stream per problem.
+    Each operator must have been ``fista_init``-ed (same refine_every)."""
+
+    def __init__(self, ops):
+        self.ops = list(ops)
+        arr = (ctypes.c_void_p * len(self.ops))(*[o._h.value for o in self.ops])
+        b = ctypes.c_void_p()
+        _check(lib().swopt_batch_create(arr, len(self.ops), ctypes.byref(b)))
+        self._b = b
+
+    def step(self, iters=1, stream=None):
+        _check(lib().swopt_batch_step(self._b, int(iters), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().swopt_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 _HFUNCTION = None

@@ -140,6 +140,7 @@ void release_graph(swopt_handle* h)
     }
     for (auto& e : h->cap_events) cudaEventDestroy(e.first);
     h->cap_events.clear();
+    ++h->graph_gen;
 }
 
 // Within its scope the handle computes at the refined solve's resync
@@ -1220,6 +1221,199 @@ swopt_status swopt_info(swopt_handle* h, int* t0, int* tw, int* states, int64_t*
     if (tw) *tw = h->tw;
     if (states) *states = h->Q;
     if (kernel_nnz) *kernel_nnz = h->nnz;
+    return SWOPT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched problems: one CUDA graph per iteration kind holds one FISTA
+// iteration of every handle, each on its own forked stream, so that problems
+// of uneven size run concurrently.
+// ---------------------------------------------------------------------------
+struct swopt_batch {
+    std::vector<swopt_handle*> hs;
+    std::vector<cudaStream_t> streams;  // one per problem (capture only)
+    std::vector<cudaEvent_t> events;    // fork / join
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    std::vector<uint64_t> gen;          // handle graph generations at capture
+    int64_t kernels[2] = {0, 0};
+    int64_t iter = 0;
+};
+
+namespace {
+
+void batch_release_graphs(swopt_batch* b)
+{
+    for (auto& g : b->gexec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
+swopt_status batch_capture(swopt_batch* b, int kind)
+{
+    const int n = (int)b->hs.size();
+    std::vector<int64_t> l0(n);
+    std::vector<bool> prof(n);
+    for (int i = 0; i < n; ++i) {
+        l0[i] = b->hs[i]->launches;
+        prof[i] = b->hs[i]->profile;
+        b->hs[i]->profile = false;  // no timing events inside the batch graph
+    }
+    swopt_status s = SWOPT_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int i = 0; i < n && s == SWOPT_OK; ++i) {
+            // fork: problem i's stream waits for the capture origin
+            if (cudaEventRecord(b->events[2 * i], b->cap) != cudaSuccess ||
+                cudaStreamWaitEvent(b->streams[i], b->events[2 * i], 0) != cudaSuccess) {
+                set_error("batch capture: fork failed");
+                s = SWOPT_ERR_CUDA;
+                break;
+            }
+            s = fista_iteration(b->hs[i], kind, b->streams[i]);
+            if (s == SWOPT_OK && (cudaEventRecord(b->events[2 * i + 1], b->streams[i]) !=
+                                      cudaSuccess ||
+                                  cudaStreamWaitEvent(b->cap, b->events[2 * i + 1], 0) !=
+                                      cudaSuccess)) {
+                set_error("batch capture: join failed");
+                s = SWOPT_ERR_CUDA;
+            }
+        }
+        e = cudaStreamEndCapture(b->cap, &g);
+    }
+    int64_t kernels = 0;
+    for (int i = 0; i < n; ++i) {
+        kernels += b->hs[i]->launches - l0[i];
+        b->hs[i]->launches = l0[i];
+        b->hs[i]->profile = prof[i];
+    }
+    if (s != SWOPT_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (s == SWOPT_OK) {
+            set_error("batch capture failed: %s", cudaGetErrorString(e));
+            s = SWOPT_ERR_CUDA;
+        }
+        return s;
+    }
+    e = cudaGraphInstantiate(&b->gexec[kind], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->gexec[kind] = nullptr;
+        set_error("batch graph instantiation failed: %s", cudaGetErrorString(e));
+        return SWOPT_ERR_CUDA;
+    }
+    b->kernels[kind] = kernels;
+    return SWOPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+swopt_status swopt_batch_create(swopt_handle* const* hs, int count, swopt_batch** out)
+{
+    clear_error();
+    if (!out || !hs || count < 1 || count > 4096) {
+        set_error("invalid batch arguments");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    for (int i = 0; i < count; ++i) {
+        swopt_handle* h = hs[i];
+        if (!h || !h->fista_ready) {
+            set_error("batch handle %d is null or has no FISTA state (swopt_fista_init)", i);
+            return SWOPT_ERR_INVALID_ARG;
+        }
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == h) {
+                set_error("batch handle %d repeats handle %d", i, j);
+                return SWOPT_ERR_INVALID_ARG;
+            }
+        if (h->device != hs[0]->device || h->iter != hs[0]->iter ||
+            h->prm.refine_every != hs[0]->prm.refine_every) {
+            set_error("batch handle %d differs from handle 0 in device, iteration count or "
+                      "refine_every", i);
+            return SWOPT_ERR_INVALID_ARG;
+        }
+    }
+    swopt_batch* b = new swopt_batch();
+    b->hs.assign(hs, hs + count);
+    b->iter = hs[0]->iter;
+    swopt_status s = SWOPT_OK;
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) s = SWOPT_ERR_CUDA;
+    for (int i = 0; i < count && s == SWOPT_OK; ++i) {
+        cudaStream_t st;
+        cudaEvent_t e0, e1;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            s = SWOPT_ERR_CUDA;
+            break;
+        }
+        b->streams.push_back(st);
+        if (cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) {
+            s = SWOPT_ERR_CUDA;
+            break;
+        }
+        b->events.push_back(e0);
+        b->events.push_back(e1);
+    }
+    if (s != SWOPT_OK) {
+        set_error("batch: stream or event creation failed");
+        swopt_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return SWOPT_OK;
+}
+
+swopt_status swopt_batch_step(swopt_batch* b, int iters, void* stream)
+{
+    clear_error();
+    if (!b || iters < 0) {
+        set_error("invalid batch arguments");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)b->hs.size();
+    for (int i = 0; i < n; ++i)
+        if (!b->hs[i]->fista_ready || b->hs[i]->iter != b->iter) {
+            set_error("batch handle %d was re-initialised or stepped on its own; create a new "
+                      "batch", i);
+            return SWOPT_ERR_INVALID_ARG;
+        }
+    // captured work is stale if any handle's own graphs were discarded
+    bool stale = b->gen.size() != (size_t)n;
+    for (int i = 0; i < n && !stale; ++i) stale = b->gen[i] != b->hs[i]->graph_gen;
+    if (stale) {
+        batch_release_graphs(b);
+        b->gen.resize(n);
+        for (int i = 0; i < n; ++i) b->gen[i] = b->hs[i]->graph_gen;
+    }
+    for (int it = 0; it < iters; ++it) {
+        for (int i = 0; i < n; ++i) SW_TRY(ensure_ref(b->hs[i]));
+        const int kind = iteration_kind(b->hs[0]);
+        if (!b->gexec[kind]) SW_TRY(batch_capture(b, kind));
+        SW_CUDA(cudaGraphLaunch(b->gexec[kind], st));
+        for (int i = 0; i < n; ++i) ++b->hs[i]->iter;
+        b->hs[0]->launches += b->kernels[kind];  // counted once, on the first handle
+        ++b->iter;
+    }
+    return SWOPT_OK;
+}
+
+swopt_status swopt_batch_destroy(swopt_batch* b)
+{
+    clear_error();
+    if (!b) return SWOPT_OK;
+    batch_release_graphs(b);
+    for (auto st : b->streams) cudaStreamDestroy(st);
+    for (auto e : b->events) cudaEventDestroy(e);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
     return SWOPT_OK;
 }
 

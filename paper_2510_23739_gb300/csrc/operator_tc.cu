@@ -774,8 +774,10 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
         const int NG = (npe + gpairs - 1) / gpairs;
         const size_t tapb = (size_t)gpairs * pair_b;
         const size_t a_bytes = mult * (size_t)GA * D.npos * 16;
-        // group headers plus one entry per run of at most kMaxTapsPerStage taps
-        const size_t tab = ((size_t)NG + (size_t)NG * kk) * 16;
+        // group headers plus one entry per run of taps: at least this with
+        // kMaxTapsPerStage taps per run, and 3 stages of at least one tap
+        const size_t tab = ((size_t)NG + (size_t)NG * ((kk + kMaxTapsPerStage - 1) /
+                                                        kMaxTapsPerStage)) * 16;
         if (a_bytes + tab + 3 * tapb * mult > budget) continue;
         // largest stage (in whole taps, up to kMaxTapsPerStage) with at least 3 stages
         for (int tps = kMaxTapsPerStage; tps >= 1 && !found; --tps) {

@@ -156,6 +156,7 @@ struct swopt_handle {
     bool capturing = false;
     cudaStream_t cap_stream = nullptr;
     swopt::IterGraph graphs[2];
+    uint64_t graph_gen = 0;       // bumped whenever captured work may have gone stale
     std::vector<std::pair<cudaEvent_t, int>> cap_events;
 
     // instrumentation

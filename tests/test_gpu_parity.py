@@ -47,6 +47,8 @@ CASES = {
                       Switching((0.3, 0.0), (1.0, 0.0), (0.0, 1.0), 1.0), 4),
     "support_wider_than_grid": (Geometry(X=4, Y=3, Z=8, T=48, N=5, P=2, k=11, pulses_per_cycle=5),
                                 Switching((0.1, 0.0), (1.0, 0.0), (0.0, 1.0), 2.0), 5),
+    "support_31": (Geometry(X=12, Y=10, Z=24, T=80, N=3, P=2, k=31, pulses_per_cycle=3),
+                   Switching((0.05, 0.0), (1.0, 0.0), (0.0, 1.0), 2.0), 6),
 }
 
 
@@ -365,7 +367,7 @@ TC_TOL = {"bf16x3": 4e-5, "bf16": 5e-3}
 def tc_cases():
     out = {}
     for name in ("tiny", "ragged", "k1_one_pulse", "pulses_below_cycle", "single_column",
-                 "support_wider_than_grid"):
+                 "support_wider_than_grid", "support_31"):
         g, s, seed = CASES[name]
         K = _kernel(g, seed)
         out[name] = (g, s, K)
@@ -374,7 +376,7 @@ def tc_cases():
 
 @pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
 @pytest.mark.parametrize("name", ["tiny", "ragged", "k1_one_pulse", "pulses_below_cycle",
-                                  "single_column", "support_wider_than_grid"])
+                                  "single_column", "support_wider_than_grid", "support_31"])
 def test_tensor_core_operator_matches_oracle(tc_cases, name, prec):
     g, s, K = tc_cases[name]
     op = sw.Operator(g, K, s, precision=prec)
@@ -668,3 +670,55 @@ def test_param_vjp_and_set_switching(cases):
     finally:
         op.set_switching(kappa=s.kappa, mu=s.mu_per_mm)
     assert rel(host(op.forward(dev(c))), oracle.forward(g, s, K, c)) <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Batched uneven problems: one graph per iteration holds every problem's
+# kernels on streams of their own; the iterates are those of each handle
+# stepped alone (bitwise: the same kernels on the same data in the same
+# order per problem).
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec,refine", [("fp32", 0), ("bf16", 3)])
+def test_batch_equals_separate_solves(prec, refine):
+    names = ["tiny", "ragged", "pulses_below_cycle", "support_wider_than_grid"]
+
+    def make():
+        ops, ys = [], []
+        for i, name in enumerate(names):
+            g, s, seed = CASES[name]
+            K = _kernel(g, seed)
+            op = sw.Operator(g, K, s)
+            # a pinned tile configuration: the autotuner's timing-based choice
+            # may differ between the two sets of handles, and the tiling sets
+            # the FP32 summation order on the tensor cores
+            op.tc_configure(0, 1, 1)
+            op.tc_configure(1, 1, 1)
+            op.set_precision(prec)
+            y = dev(np.random.default_rng(70 + i).standard_normal(g.y_shape()))
+            L = op.lipschitz(20)
+            op.fista_init(y, sw.SolveParams(step=0.9 / L, max_iters=9, lambda_l1=0.01,
+                                            lambda_tv=0.01, inner_iters=4,
+                                            refine_every=refine, refine_precision="bf16x3"))
+            ops.append(op)
+            ys.append(y)
+        return ops, ys
+
+    ops, ys = make()
+    b = sw.Batch(ops)
+    b.step(4)
+    b.step(5)
+    got = [op.fista_get().clone() for op in ops]
+    for op in ops:
+        op.check_device()
+    # stepping one handle alone desynchronises the batch
+    ops[0].fista_step(1)
+    with pytest.raises(sw.SwoptError):
+        b.step(1)
+    b.close()
+    ref_ops, _ = make()
+    for op, c in zip(ref_ops, got):
+        op.fista_step(9)
+        assert torch.equal(op.fista_get(), c)
+        op.close()
+    for op in ops:
+        op.close()
