@@ -25,12 +25,15 @@
 // Consecutive taps are grouped into runs of one stage of shared memory (several
 // taps per stage), each arriving with one bulk asynchronous copy.
 //
-// Roles (192 threads): warp 0 stages operands with bulk asynchronous copies
-// (the TMA engine) on mbarriers, one lane of warp 1 issues tcgen05.mma and
-// commits, warps 2-5 zero the accumulator, then read it back with
-// tcgen05.ld and write the epilogue.  Every wait is bounded: on a timeout the
-// CTA records an error in a device word, drains its own copies, frees its
-// TMEM and exits.
+// Roles (224 threads): warp 0 stages operands with bulk asynchronous copies
+// (the TMA engine) on mbarriers; warps 1 and 6 issue tcgen05.mma and commits
+// (an elected lane of each): both walk every stage and take alternate
+// (pair, tap) products into accumulators of their own, because one issuing
+// thread spends about 60 cycles of descriptor and loop work per MMA on top of
+// the tensor core's ~56 and cannot keep it busy alone; warps 2-5 zero the
+// accumulators, then read them back with tcgen05.ld, sum them and write the
+// epilogue.  Every wait is bounded: on a timeout the CTA records an error in
+// a device word, drains its own copies, frees its TMEM and exits.
 //
 // Precisions: BF16 operands with FP32 accumulation (1 term), or a split of
 // both operands into 2 BF16 terms (v = v0 + v1, v1 the BF16 rounding of
@@ -58,7 +61,8 @@ struct TcDir {
     int GA = 0, NG = 0, KS = 0;   // A slices per group, groups, padded slices
     int NB = 0;                   // accumulator columns per tile
     int MT = 1;                   // tiles per CTA
-    int RA = 1;                   // accumulators per tile: 1, or 2 (corrections apart)
+    int RA = 1;                   // accumulators per tile and issuer: 1, or 2 (corrections apart)
+    int NI = 1;                   // MMA-issuing warps (1 or 2), each with its own accumulators
     int NS = 4;                   // stages of the B ring
     uint32_t stage_bytes = 0;     // bytes of one stage (hi part; lo is as large)
     int HX = 0, npos = 0;         // halo width and positions
@@ -83,7 +87,8 @@ struct TcOperator {
 
 namespace {
 
-constexpr int kTcThreads = 192;
+constexpr int kTcThreads = 224;
+constexpr int kIssuer2Warp = 6;  // the second MMA-issuing warp
 constexpr int kMaxStages = 8;
 constexpr int kMaxTapsPerStage = 8;  // taps per stage of the B ring (host-side cap)
 constexpr uint32_t kWaitPolls = 1u << 22;  // x 256 ns back-off: about one second
@@ -259,7 +264,7 @@ struct TcArgs {
     const float* Cmf;           // [Q]
     double* partials;           // per block, or null
     int* err;
-    int Y, X, Yp, Xp, Z, k, r, HY, HX, groupsX, MT, RA;
+    int Y, X, Yp, Xp, Z, k, r, HY, HX, groupsX, MT, RA, NI;
     int KS, GA, NG, NS, NB;
     uint32_t stage_bytes;
     int Twp, KSo;
@@ -269,7 +274,7 @@ struct TcArgs {
 
 // ---------------------------------------------------------------------------
 // The contraction kernel (forward or adjoint, see the file comment).
-// grid = (CTAs over the scan plane, Q); block = 192 threads.
+// grid = (CTAs over the scan plane, Q); block = 224 threads.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
 {
@@ -299,13 +304,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
     for (int i = threadIdx.x; i < a.tab_n; i += kTcThreads)
         reinterpret_cast<uint4*>(smem + tab_region)[i] = a.tab[i];
     if (threadIdx.x == 0) {
+        // every issuer commits to the empty, A-empty and accumulator barriers
         for (int s = 0; s < a.NS; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
-            mbar_init(smem_u32(&bar_empty[s]), 1);
+            mbar_init(smem_u32(&bar_empty[s]), (uint32_t)a.NI);
         }
         mbar_init(smem_u32(&bar_afull), 1);
-        mbar_init(smem_u32(&bar_aempty), 1);
-        mbar_init(smem_u32(&bar_acc), 1);
+        mbar_init(smem_u32(&bar_aempty), (uint32_t)a.NI);
+        mbar_init(smem_u32(&bar_acc), (uint32_t)a.NI);
         s_abort = 0;
         s_red[0] = s_red[1] = s_red[2] = s_red[3] = 0.0;
         fence_mbar_init();
@@ -323,10 +329,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
     // warp-uniform by construction (MMA operands must be uniform values)
     const uint32_t tmem = __shfl_sync(0xffffffffu, s_tmem, 0);
 
-    // zero the accumulator columns of all tiles
-    if (warp >= 2) {
+    // zero the accumulator columns of all tiles and issuers
+    if (warp >= 2 && warp <= 5) {
         const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-        for (int cb = 0; cb < a.MT * a.RA * a.NB / 16; ++cb)
+        for (int cb = 0; cb < a.MT * a.RA * a.NI * a.NB / 16; ++cb)
             tmem_zero16(tmem + lanes + (uint32_t)cb * 16u);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
@@ -400,99 +406,107 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                 !mbar_wait(smem_u32(&bar_afull), (uint32_t)(a_fills - 1) & 1u, &never))
                 atomicExch(a.err, 2);
         }
-    } else if (warp == 1) {
-        // ------------------------------ MMA issuer ----------------------------
-        // The whole warp walks groups, runs, pairs and taps in step, so all
-        // descriptors are warp-uniform arithmetic; one elected lane issues
-        // the MMAs and the commits.
-        const bool leader = elect_one();
-        const uint64_t lbo_a16 = (uint64_t)(a_slice >> 4), sbo_a16 = (uint64_t)(a.HX);
-        // descriptor constant parts: LBO, SBO and the fixed bits 46-48
-        const uint64_t adesc_c = (lbo_a16 << 16) | (sbo_a16 << 32) | ((uint64_t)1 << 46);
-        const uint64_t bdesc_c = ((uint64_t)(128u >> 4) << 32) | ((uint64_t)1 << 46);  // SBO 128 B
-        const uint64_t alo16 = (uint64_t)(a_part >> 4), blo16 = (uint64_t)(a.stage_bytes >> 4);
-        int stage = 0;
-        uint32_t phase = 0;
-        bool ok = true;
-        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                               (((uint32_t)a.NB >> 3) << 17) | ((128u >> 4) << 24);
-        const uint64_t bdesc = bdesc_c | ((uint64_t)a.NB << 16);  // LBO = N x 16 B
-        const uint32_t pair_b = 2u * (uint32_t)a.NB * 16u;         // B bytes of one pair
-        const int MT = a.MT, NBc = a.NB;
-        const int terms = a.terms;
-        int run = 0;
-        for (int g = 0; g < a.NG && ok; ++g) {
-            const uint4 hd = s_tab[g];
-            const int tpr = __shfl_sync(0xffffffffu, (int)hd.z, 0);
-            const uint32_t tapb = __shfl_sync(0xffffffffu, hd.y, 0);
-            const int np = __shfl_sync(0xffffffffu, (int)hd.w, 0);
-            if (g > 0 && leader) tc_commit(smem_u32(&bar_aempty));
-            __syncwarp();
-            if (!mbar_wait_warp(smem_u32(&bar_afull), (uint32_t)g & 1u, &s_abort)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            for (int d0 = 0; d0 < kk; d0 += tpr) {
-                const int nt = min(tpr, kk - d0);
-                if (!mbar_wait_warp(smem_u32(&bar_full[stage]), phase, &s_abort)) {
+    } else if (warp == 1 || warp == kIssuer2Warp) {
+        // ------------------------------ MMA issuers ---------------------------
+        // Issuer j (warp 1, and warp 6 when NI = 2) walks the groups, runs,
+        // pairs and taps as a converged warp (waits and table reads are
+        // warp-wide, descriptors warp-uniform); its elected lane issues every
+        // NI-th (pair, tap) product, counted in the same order by both
+        // issuers, into the issuer's accumulator sets j RA (main) and
+        // j RA + RA - 1 (corrections).  A lone lane running the whole loop by
+        // itself was measured an order of magnitude slower per MMA.
+        const int j = warp == 1 ? 0 : 1;
+        if (j < a.NI) {
+            const bool leader = elect_one();
+            const uint64_t lbo_a16 = (uint64_t)(a_slice >> 4), sbo_a16 = (uint64_t)(a.HX);
+            // descriptor constant parts: LBO, SBO and the fixed bits 46-48
+            const uint64_t adesc_c = (lbo_a16 << 16) | (sbo_a16 << 32) | ((uint64_t)1 << 46);
+            const uint64_t bdesc_c = ((uint64_t)(128u >> 4) << 32) | ((uint64_t)1 << 46);
+            const uint64_t alo16 = (uint64_t)(a_part >> 4), blo16 = (uint64_t)(a.stage_bytes >> 4);
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                   (((uint32_t)a.NB >> 3) << 17) | ((128u >> 4) << 24);
+            const uint64_t bdesc = bdesc_c | ((uint64_t)a.NB << 16);  // LBO = N x 16 B
+            const uint32_t pair_b = 2u * (uint32_t)a.NB * 16u;         // B bytes of one pair
+            const int MT = a.MT, NBc = a.NB, terms = a.terms;
+            const uint32_t turn_mask = (uint32_t)a.NI - 1u;
+            const int set_main = j * a.RA, set_corr = j * a.RA + a.RA - 1;
+            int stage = 0, run = 0;
+            uint32_t phase = 0, turn = 0;
+            bool ok = true;
+            for (int g = 0; g < a.NG && ok; ++g) {
+                const uint4 hd = s_tab[g];
+                const int tpr = __shfl_sync(0xffffffffu, (int)hd.z, 0);
+                const uint32_t tapb = __shfl_sync(0xffffffffu, hd.y, 0);
+                const int np = __shfl_sync(0xffffffffu, (int)hd.w, 0);
+                const uint64_t tapb16 = (uint64_t)(tapb >> 4);
+                if (g > 0 && leader) tc_commit(smem_u32(&bar_aempty));
+                __syncwarp();
+                if (!mbar_wait_warp(smem_u32(&bar_afull), (uint32_t)g & 1u, &s_abort)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t bst = sB + (uint32_t)stage * stage_total;
-                // A offsets of this stage's taps (16-B units), from the run table
-                const uint4 ro = s_tab[a.NG + run];
-                const uint32_t ow[4] = {__shfl_sync(0xffffffffu, ro.x, 0),
-                                        __shfl_sync(0xffffffffu, ro.y, 0),
-                                        __shfl_sync(0xffffffffu, ro.z, 0),
-                                        __shfl_sync(0xffffffffu, ro.w, 0)};
-                ++run;
-                const uint64_t tapb16 = tapb >> 4;
-                for (int i = 0; i < MT; ++i) {
-                    const uint32_t dt = tmem + (uint32_t)(i * NBc);
-                    // correction products: own accumulator when RA == 2
-                    const uint32_t dc = tmem + (uint32_t)((a.RA > 1 ? MT + i : i) * NBc);
-                    for (int p = 0; p < np; ++p) {
-                        const uint64_t adp = adesc_c | (uint64_t)((sA + 2u * (uint32_t)p * a_slice +
-                                                                   (uint32_t)i * 128u) >> 4);
-                        const uint64_t bdp = bdesc | (uint64_t)((bst + (uint32_t)p * pair_b) >> 4);
-                        if (leader) {
+                for (int d0 = 0; d0 < kk; d0 += tpr) {
+                    const int nt = min(tpr, kk - d0);
+                    if (!mbar_wait_warp(smem_u32(&bar_full[stage]), phase, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t bst = sB + (uint32_t)stage * stage_total;
+                    // A offsets of this stage's taps (16-B units), from the run table
+                    const uint4 ro = s_tab[a.NG + run];
+                    const uint32_t ow[4] = {__shfl_sync(0xffffffffu, ro.x, 0),
+                                            __shfl_sync(0xffffffffu, ro.y, 0),
+                                            __shfl_sync(0xffffffffu, ro.z, 0),
+                                            __shfl_sync(0xffffffffu, ro.w, 0)};
+                    ++run;
+                    for (int i = 0; i < MT; ++i) {
+                        const uint32_t dt = tmem + (uint32_t)((set_main * MT + i) * NBc);
+                        const uint32_t dc = tmem + (uint32_t)((set_corr * MT + i) * NBc);
+                        for (int p = 0; p < np; ++p) {
+                            const uint64_t adp =
+                                adesc_c |
+                                (uint64_t)((sA + 2u * (uint32_t)p * a_slice + (uint32_t)i * 128u) >> 4);
+                            const uint64_t bdp = bdesc | (uint64_t)((bst + (uint32_t)p * pair_b) >> 4);
+                            if (leader) {
 #pragma unroll
-                            for (int t = 0; t < kMaxTapsPerStage; ++t) {
-                                if (t < nt) {
-                                    const uint64_t ad =
-                                        adp + (uint64_t)((ow[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
-                                    const uint64_t bd = bdp + (uint64_t)t * tapb16;
-                                    tc_mma(dt, ad, bd, idesc, 1u);
-                                    if (terms > 1) {
-                                        tc_mma(dc, ad, bd + blo16, idesc, 1u);
-                                        tc_mma(dc, ad + alo16, bd, idesc, 1u);
+                                for (int t = 0; t < kMaxTapsPerStage; ++t) {
+                                    if (t < nt && ((turn + (uint32_t)t) & turn_mask) == (uint32_t)j) {
+                                        const uint64_t ad =
+                                            adp + (uint64_t)((ow[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
+                                        const uint64_t bd = bdp + (uint64_t)t * tapb16;
+                                        tc_mma(dt, ad, bd, idesc, 1u);
+                                        if (terms > 1) {
+                                            tc_mma(dc, ad, bd + blo16, idesc, 1u);
+                                            tc_mma(dc, ad + alo16, bd, idesc, 1u);
+                                        }
                                     }
                                 }
                             }
+                            turn += (uint32_t)nt;
                         }
                     }
-                }
-                __syncwarp();
-                if (leader) tc_commit(smem_u32(&bar_empty[stage]));
-                __syncwarp();
-                if (++stage == a.NS) {
-                    stage = 0;
-                    phase ^= 1u;
+                    __syncwarp();
+                    if (leader) tc_commit(smem_u32(&bar_empty[stage]));
+                    __syncwarp();
+                    if (++stage == a.NS) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
                 }
             }
-        }
-        // signals the epilogue; also covers every MMA issued above
-        if (leader) tc_commit(smem_u32(&bar_acc));
-        __syncwarp();
-        if (!ok) {
-            if (leader) {
-                s_abort = 1;
-                atomicExch(a.err, 1);
+            // signals the epilogue; also covers every MMA issued above
+            if (leader) tc_commit(smem_u32(&bar_acc));
+            __syncwarp();
+            if (!ok) {
+                if (leader) {
+                    s_abort = 1;
+                    atomicExch(a.err, 1);
+                }
+                volatile int never = 0;
+                if (!mbar_wait(smem_u32(&bar_acc), 0u, &never) && leader) atomicExch(a.err, 2);
             }
-            volatile int never = 0;
-            if (!mbar_wait(smem_u32(&bar_acc), 0u, &never) && leader) atomicExch(a.err, 2);
         }
     } else {
         // ------------------------------ epilogue ------------------------------
@@ -514,7 +528,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                 for (int cb = 0; cb < a.NB / 16; ++cb) {
                     float v[16];
                     tmem_ld16(tmem + lanes + (uint32_t)(ti * a.NB + cb * 16), v);
-                    for (int rp = 1; rp < a.RA; ++rp) {
+                    for (int rp = 1; rp < a.RA * a.NI; ++rp) {
                         float w[16];
                         tmem_ld16(tmem + lanes + (uint32_t)((rp * a.MT + ti) * a.NB + cb * 16), w);
 #pragma unroll
@@ -725,7 +739,7 @@ struct DirHost {
 
 // Builds the banded kernel of one direction for MT tiles per CTA within a
 // shared-memory budget.  Returns false if it does not fit.
-bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int RA,
+bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int RA, int NI,
               size_t budget, DirHost* out)
 {
     const int kk = h->k * h->k;
@@ -733,12 +747,13 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
     TcDir D;
     D.MT = MT;
     D.RA = RA;
+    D.NI = NI;
     D.NB = adj ? t->Zp16 : h->Twp;
     const int ks_min = adj ? h->Twp / 8 : t->Zp16 / 8;  // both even
     const int npairs = ks_min / 2;
     D.HX = 8 * MT + 2 * h->r;
     D.npos = t->HY * D.HX;
-    D.cols = (int)pow2_cols(MT * RA * D.NB);
+    D.cols = (int)pow2_cols(MT * RA * NI * D.NB);
     if (D.cols > 512) return false;
     D.groupsX = (t->tilesX + MT - 1) / MT;
 
@@ -881,6 +896,7 @@ TcArgs dir_args(const swopt_handle* h, const TcOperator* t, const TcDir& D, bool
     a.err = t->err;
     a.Y = h->Y; a.X = h->X; a.Yp = t->Yp; a.Xp = t->Xp; a.Z = h->Z; a.k = h->k; a.r = h->r;
     a.HY = t->HY; a.HX = D.HX; a.groupsX = D.groupsX; a.MT = D.MT; a.RA = D.RA;
+    a.NI = D.NI;
     a.KS = D.KS; a.GA = D.GA; a.NG = D.NG; a.NS = D.NS; a.NB = D.NB;
     a.stage_bytes = D.stage_bytes;
     a.Twp = h->Twp;
@@ -958,7 +974,10 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
             if (force_mt > 0 && c.MT != force_mt) continue;
             if (force_ctas > 0 && (force_ctas == 2) != (c.budget < 200 * 1024)) continue;
             DirHost H;
-            if (plan_dir(h, t, adj, c.MT, ra, c.budget, &H)) plans.push_back(std::move(H));
+            // two MMA-issuing warps where TMEM holds their accumulators
+            if (plan_dir(h, t, adj, c.MT, ra, 2, c.budget, &H) ||
+                plan_dir(h, t, adj, c.MT, ra, 1, c.budget, &H))
+                plans.push_back(std::move(H));
         }
     }
     if (plans.empty()) {
