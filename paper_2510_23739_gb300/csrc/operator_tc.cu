@@ -740,7 +740,7 @@ struct DirHost {
 // Builds the banded kernel of one direction for MT tiles per CTA within a
 // shared-memory budget.  Returns false if it does not fit.
 bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int RA, int NI,
-              size_t budget, DirHost* out)
+              int skip, size_t budget, DirHost* out)
 {
     const int kk = h->k * h->k;
     const int terms = t->terms;
@@ -779,12 +779,16 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
     }
     if (npe == 0) npe = 1;
     const size_t pair_b = 2 * (size_t)D.NB * 16;
-    // smallest number of groups whose A slices and B ring fit the budget;
-    // prefer stages that hold several taps
+    // smallest number of groups whose A slices and B ring fit the budget (the
+    // `skip`-th next one when skip > 0: more groups leave room for stages of
+    // more taps); prefer stages that hold several taps
     const size_t mult = (size_t)terms;
     bool found = false;
+    int last_gpairs = 0;
     for (int ng = 1; ng <= npe && !found; ++ng) {
         const int gpairs = (npe + ng - 1) / ng;
+        if (gpairs == last_gpairs) continue;
+        last_gpairs = gpairs;
         const int GA = 2 * gpairs;
         const int NG = (npe + gpairs - 1) / gpairs;
         const size_t tapb = (size_t)gpairs * pair_b;
@@ -813,6 +817,10 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
                     break;
                 }
             }
+        }
+        if (found && skip > 0) {
+            --skip;
+            found = false;
         }
     }
     if (!found) return false;
@@ -973,11 +981,14 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
         for (const Cand& c : kCands) {
             if (force_mt > 0 && c.MT != force_mt) continue;
             if (force_ctas > 0 && (force_ctas == 2) != (c.budget < 200 * 1024)) continue;
-            DirHost H;
-            // two MMA-issuing warps where TMEM holds their accumulators
-            if (plan_dir(h, t, adj, c.MT, ra, 2, c.budget, &H) ||
-                plan_dir(h, t, adj, c.MT, ra, 1, c.budget, &H))
-                plans.push_back(std::move(H));
+            // two MMA-issuing warps where TMEM holds their accumulators; the
+            // fewest slice groups that fit, and the next split (larger stages)
+            for (int skip = 0; skip < 2; ++skip) {
+                DirHost H;
+                if (plan_dir(h, t, adj, c.MT, ra, 2, skip, c.budget, &H) ||
+                    plan_dir(h, t, adj, c.MT, ra, 1, skip, c.budget, &H))
+                    plans.push_back(std::move(H));
+            }
         }
     }
     if (plans.empty()) {
