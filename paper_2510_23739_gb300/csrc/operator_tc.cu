@@ -63,6 +63,9 @@ struct TcDir {
     int MT = 1;                   // tiles per CTA
     int RA = 1;                   // accumulators per tile and issuer: 1, or 2 (corrections apart)
     int NI = 1;                   // MMA-issuing warps (1 or 2), each with its own accumulators
+    int KSPL = 1;                 // CTAs per tile-state splitting the slice groups (1 or 2)
+    float* part = nullptr;        // KSPL > 1: [KSPL][units][MT][NB/16][128][16] partial sums
+    int* ticket = nullptr;        // KSPL > 1: [units] arrival counters (return to 0)
     int NS = 4;                   // stages of the B ring
     uint32_t stage_bytes = 0;     // bytes of one stage (hi part; lo is as large)
     int HX = 0, npos = 0;         // halo width and positions
@@ -264,7 +267,9 @@ struct TcArgs {
     const float* Cmf;           // [Q]
     double* partials;           // per block, or null
     int* err;
-    int Y, X, Yp, Xp, Z, k, r, HY, HX, groupsX, MT, RA, NI;
+    int Y, X, Yp, Xp, Z, k, r, HY, HX, groupsX, MT, RA, NI, KSPL;
+    float* part;                // KSPL > 1: partial sums of the split contraction
+    int* ticket;                // KSPL > 1: per tile-state arrival counters
     int KS, GA, NG, NS, NB;
     uint32_t stage_bytes;
     int Twp, KSo;
@@ -274,7 +279,12 @@ struct TcArgs {
 
 // ---------------------------------------------------------------------------
 // The contraction kernel (forward or adjoint, see the file comment).
-// grid = (CTAs over the scan plane, Q); block = 224 threads.
+// grid = (CTAs over the scan plane, Q, KSPL); block = 224 threads.  With
+// KSPL = 2 the two CTAs of a tile-state take the first and second half of the
+// slice groups (two waves of half-size work units quantise better on 152
+// SMs); each writes its summed accumulators to `part`, takes a ticket, and the
+// second to arrive adds the other's partial sums (a + b: the same bits
+// whichever arrives last) and runs the epilogue.  No CTA waits for another.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
 {
@@ -285,11 +295,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     __shared__ double s_red[4];
+    __shared__ int s_last;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m = blockIdx.y;
     const int x0 = (blockIdx.x % a.groupsX) * 8 * a.MT, y0 = (blockIdx.x / a.groupsX) * 16;
     const int kk = a.k * a.k;
+    // slice groups of this CTA's part of the contraction
+    const int sp = (int)blockIdx.z;
+    const int gper = (a.NG + a.KSPL - 1) / a.KSPL;
+    const int g_lo = sp * gper, g_hi = min(a.NG, g_lo + gper);
     const uint32_t npos = (uint32_t)(a.HY * a.HX);
     const uint32_t a_slice = npos * 16u;                       // bytes of one A slice
     const uint32_t a_part = (uint32_t)a.GA * a_slice;          // hi (or lo) A bytes
@@ -348,9 +363,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         for (int s = 0; s < kMaxStages; ++s) fills[s] = 0;
         int a_fills = 0;
         bool ok = true;
-        for (int g = 0; g < a.NG && ok; ++g) {
+        for (int g = g_lo; g < g_hi && ok; ++g) {
             const uint4 hd = s_tab[g];  // {base16, tap bytes, taps per run, pairs}
-            if (g > 0 &&
+            if (g > g_lo &&
                 !mbar_wait_warp(smem_u32(&bar_aempty), (uint32_t)(a_fills - 1) & 1u, &s_abort)) {
                 ok = false;
                 break;
@@ -433,15 +448,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
             int stage = 0, run = 0;
             uint32_t phase = 0, turn = 0;
             bool ok = true;
-            for (int g = 0; g < a.NG && ok; ++g) {
+            for (int g = 0; g < g_lo; ++g) {  // runs of the groups before this CTA's
+                const int tg = (int)s_tab[g].z;
+                run += (kk + tg - 1) / tg;
+            }
+            for (int g = g_lo; g < g_hi && ok; ++g) {
                 const uint4 hd = s_tab[g];
                 const int tpr = __shfl_sync(0xffffffffu, (int)hd.z, 0);
                 const uint32_t tapb = __shfl_sync(0xffffffffu, hd.y, 0);
                 const int np = __shfl_sync(0xffffffffu, (int)hd.w, 0);
                 const uint64_t tapb16 = (uint64_t)(tapb >> 4);
-                if (g > 0 && leader) tc_commit(smem_u32(&bar_aempty));
+                if (g > g_lo && leader) tc_commit(smem_u32(&bar_aempty));
                 __syncwarp();
-                if (!mbar_wait_warp(smem_u32(&bar_afull), (uint32_t)g & 1u, &s_abort)) {
+                if (!mbar_wait_warp(smem_u32(&bar_afull), (uint32_t)(g - g_lo) & 1u, &s_abort)) {
                     ok = false;
                     break;
                 }
@@ -513,11 +532,52 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         const int q = warp & 3;
         const int li = q * 32 + lane;
         const int yl = li >> 3, xl = li & 7;
-        const bool ok = mbar_wait_warp(smem_u32(&bar_acc), 0u, &s_abort);
+        bool ok = mbar_wait_warp(smem_u32(&bar_acc), 0u, &s_abort);
         tc_fence_after();
         double part = 0.0;
+        const uint32_t lanes = (uint32_t)(q * 32) << 16;
+        // the summed accumulator sets of tile ti, columns 16 cb .. 16 cb + 15
+        auto acc16 = [&](int ti, int cb, float (&v)[16]) {
+            tmem_ld16(tmem + lanes + (uint32_t)(ti * a.NB + cb * 16), v);
+            for (int rp = 1; rp < a.RA * a.NI; ++rp) {
+                float w[16];
+                tmem_ld16(tmem + lanes + (uint32_t)((rp * a.MT + ti) * a.NB + cb * 16), w);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) v[e] += w[e];
+            }
+        };
+        const size_t unit = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        const size_t units = (size_t)gridDim.y * gridDim.x;
+        const size_t unit_floats = (size_t)a.MT * a.NB * 128;
+        auto part_at = [&](int split, int ti, int cb) -> float* {
+            return a.part + ((size_t)split * units + unit) * unit_floats +
+                   (((size_t)ti * (a.NB / 16) + cb) * 128 + li) * 16;
+        };
+        if (a.KSPL > 1) {
+            // publish this CTA's partial sums, then the ticket decides who ends
+            if (ok)
+                for (int ti = 0; ti < a.MT; ++ti)
+                    for (int cb = 0; cb < a.NB / 16; ++cb) {
+                        float v[16];
+                        acc16(ti, cb, v);
+                        float4* dst = reinterpret_cast<float4*>(part_at(sp, ti, cb));
+#pragma unroll
+                        for (int e4 = 0; e4 < 4; ++e4)
+                            dst[e4] = make_float4(v[4 * e4], v[4 * e4 + 1], v[4 * e4 + 2],
+                                                  v[4 * e4 + 3]);
+                    }
+            __threadfence();
+            asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps
+            if (warp == 2 && lane == 0) {
+                const int prev = atomicAdd(a.ticket + unit, 1);
+                s_last = prev == a.KSPL - 1;
+                if (s_last) a.ticket[unit] = 0;  // ready for the next launch
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            ok = ok && s_last;
+            __threadfence();
+        }
         if (ok) {
-            const uint32_t lanes = (uint32_t)(q * 32) << 16;
             const size_t S = (size_t)a.Y * a.X;
             const float cm = a.scale ? a.Cmf[m] : 1.f;
             const int y = y0 + yl;
@@ -527,12 +587,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                 const size_t pos = (size_t)y * a.X + x;
                 for (int cb = 0; cb < a.NB / 16; ++cb) {
                     float v[16];
-                    tmem_ld16(tmem + lanes + (uint32_t)(ti * a.NB + cb * 16), v);
-                    for (int rp = 1; rp < a.RA * a.NI; ++rp) {
-                        float w[16];
-                        tmem_ld16(tmem + lanes + (uint32_t)((rp * a.MT + ti) * a.NB + cb * 16), w);
+                    acc16(ti, cb, v);
+                    if (a.KSPL > 1) {  // + the other CTA's partial sums
+                        const float4* o4 = reinterpret_cast<const float4*>(part_at(1 - sp, ti, cb));
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) v[e] += w[e];
+                        for (int e4 = 0; e4 < 4; ++e4) {
+                            const float4 w = __ldcg(o4 + e4);  // written by another SM
+                            v[4 * e4] += w.x;
+                            v[4 * e4 + 1] += w.y;
+                            v[4 * e4 + 2] += w.z;
+                            v[4 * e4 + 3] += w.w;
+                        }
                     }
                     if (!valid) continue;
                     if (a.adj) {
@@ -599,7 +664,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
     tc_fence_before();
     __syncthreads();
     if (a.partials && threadIdx.x == 0)
-        a.partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] =
+        a.partials[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] =
             s_red[0] + s_red[1] + s_red[2] + s_red[3];
     if (warp == 1) {
         tc_fence_after();
@@ -728,6 +793,10 @@ void free_dir(TcDir& D)
     }
     cudaFree(D.tab);
     D.tab = nullptr;
+    cudaFree(D.part);
+    D.part = nullptr;
+    cudaFree(D.ticket);
+    D.ticket = nullptr;
 }
 
 // Host image of one direction's packed operator.
@@ -740,7 +809,7 @@ struct DirHost {
 // Builds the banded kernel of one direction for MT tiles per CTA within a
 // shared-memory budget.  Returns false if it does not fit.
 bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int RA, int NI,
-              int skip, size_t budget, DirHost* out)
+              int skip, int kspl, size_t budget, DirHost* out)
 {
     const int kk = h->k * h->k;
     const int terms = t->terms;
@@ -748,6 +817,7 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
     D.MT = MT;
     D.RA = RA;
     D.NI = NI;
+    D.KSPL = kspl;
     D.NB = adj ? t->Zp16 : h->Twp;
     const int ks_min = adj ? h->Twp / 8 : t->Zp16 / 8;  // both even
     const int npairs = ks_min / 2;
@@ -824,6 +894,7 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
         }
     }
     if (!found) return false;
+    if (D.KSPL > 1 && D.NG < 2) return false;  // nothing to split
     // At most 512 / cols CTAs may share an SM's 512 TMEM columns: request
     // enough shared memory that no more can be resident (233472 B per SM,
     // so more than 233472 / (512 / cols + 1) bytes per CTA).
@@ -879,11 +950,13 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
     return true;
 }
 
-swopt_status upload_dir(const DirHost& H, int terms, TcDir* D)
+swopt_status upload_dir(const DirHost& H, int terms, size_t units, TcDir* D)
 {
     *D = H.cfg;
-    D->Bt[0] = D->Bt[1] = D->Bt[2] = nullptr;
+    for (int tt = 0; tt < kMaxTerms; ++tt) D->Bt[tt] = nullptr;
     D->tab = nullptr;
+    D->part = nullptr;
+    D->ticket = nullptr;
     auto up16 = [&](__nv_bfloat16** dst, const std::vector<uint16_t>& v) -> swopt_status {
         SW_TRY(tc_alloc(dst, v.size()));
         SW_CUDA(cudaMemcpy(*dst, v.data(), v.size() * 2, cudaMemcpyHostToDevice));
@@ -892,6 +965,14 @@ swopt_status upload_dir(const DirHost& H, int terms, TcDir* D)
     swopt_status s = SWOPT_OK;
     for (int tt = 0; tt < terms && s == SWOPT_OK; ++tt) s = up16(&D->Bt[tt], H.t[tt]);
     if (s == SWOPT_OK) s = tc_upload(&D->tab, H.tab);
+    if (s == SWOPT_OK && D->KSPL > 1) {
+        s = tc_alloc(&D->part, (size_t)D->KSPL * units * D->MT * D->NB * 128);
+        if (s == SWOPT_OK) s = tc_alloc(&D->ticket, units);
+        if (s == SWOPT_OK && cudaMemset(D->ticket, 0, units * sizeof(int)) != cudaSuccess) {
+            set_error("cudaMemset failed");
+            s = SWOPT_ERR_CUDA;
+        }
+    }
     if (s != SWOPT_OK) free_dir(*D);
     return s;
 }
@@ -905,6 +986,9 @@ TcArgs dir_args(const swopt_handle* h, const TcOperator* t, const TcDir& D, bool
     a.Y = h->Y; a.X = h->X; a.Yp = t->Yp; a.Xp = t->Xp; a.Z = h->Z; a.k = h->k; a.r = h->r;
     a.HY = t->HY; a.HX = D.HX; a.groupsX = D.groupsX; a.MT = D.MT; a.RA = D.RA;
     a.NI = D.NI;
+    a.KSPL = D.KSPL;
+    a.part = D.part;
+    a.ticket = D.ticket;
     a.KS = D.KS; a.GA = D.GA; a.NG = D.NG; a.NS = D.NS; a.NB = D.NB;
     a.stage_bytes = D.stage_bytes;
     a.Twp = h->Twp;
@@ -932,7 +1016,7 @@ swopt_status launch_conv(swopt_handle* h, const TcDir& D, const TcArgs& a, cudaS
     }
     SW_CUDA(cudaFuncSetAttribute(tc_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  dmax));
-    dim3 grid(D.groupsX * h->tc->tilesY, h->Q);
+    dim3 grid(D.groupsX * h->tc->tilesY, h->Q, D.KSPL);
     tc_conv_kernel<<<grid, kTcThreads, D.smem, st>>>(a);
     SW_LAUNCHED(h);
     return SWOPT_OK;
@@ -983,12 +1067,14 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
             if (force_ctas > 0 && (force_ctas == 2) != (c.budget < 200 * 1024)) continue;
             // two MMA-issuing warps where TMEM holds their accumulators; the
             // fewest slice groups that fit, and the next split (larger stages)
-            for (int skip = 0; skip < 2; ++skip) {
-                DirHost H;
-                if (plan_dir(h, t, adj, c.MT, ra, 2, skip, c.budget, &H) ||
-                    plan_dir(h, t, adj, c.MT, ra, 1, skip, c.budget, &H))
-                    plans.push_back(std::move(H));
-            }
+            // (and, with two or more groups, the groups split over 2 CTAs)
+            for (int skip = 0; skip < 2; ++skip)
+                for (int kspl = 1; kspl <= 2; ++kspl) {
+                    DirHost H;
+                    if (plan_dir(h, t, adj, c.MT, ra, 2, skip, kspl, c.budget, &H) ||
+                        plan_dir(h, t, adj, c.MT, ra, 1, skip, kspl, c.budget, &H))
+                        plans.push_back(std::move(H));
+                }
         }
     }
     if (plans.empty()) {
@@ -1004,7 +1090,8 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
         float best_ms = 1e30f;
         for (size_t i = 0; i < plans.size(); ++i) {
             TcDir D;
-            SW_TRY(upload_dir(plans[i], t->terms, &D));
+            SW_TRY(upload_dir(plans[i], t->terms,
+                              (size_t)plans[i].cfg.groupsX * t->tilesY * h->Q, &D));
             TcArgs a = dir_args(h, t, D, adj);
             a.out_f = adj ? h->g : h->u;
             a.mode = 0;
@@ -1035,7 +1122,8 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
             return SWOPT_ERR_TIMEOUT;
         }
     }
-    return upload_dir(plans[best_i], t->terms, best);
+    return upload_dir(plans[best_i], t->terms,
+                      (size_t)plans[best_i].cfg.groupsX * t->tilesY * h->Q, best);
 }
 
 swopt_status tc_prepare(swopt_handle* h)
@@ -1110,7 +1198,8 @@ swopt_status tc_prepare(swopt_handle* h)
 
 int tc_forward_blocks(const swopt_handle* h)
 {
-    return ((h->X + 7) / 8) * ((h->Y + 15) / 16) * h->Q;
+    // upper bound: up to 2 CTAs per tile-state
+    return 2 * ((h->X + 7) / 8) * ((h->Y + 15) / 16) * h->Q;
 }
 
 swopt_status tc_states(swopt_handle* h, const float* c, cudaStream_t st)

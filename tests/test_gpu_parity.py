@@ -681,29 +681,18 @@ def test_param_vjp_and_set_switching(cases):
 @pytest.mark.parametrize("prec,refine", [("fp32", 0), ("bf16", 3)])
 def test_batch_equals_separate_solves(prec, refine):
     names = ["tiny", "ragged", "pulses_below_cycle", "support_wider_than_grid"]
-
-    def make():
-        ops, ys = [], []
-        for i, name in enumerate(names):
-            g, s, seed = CASES[name]
-            K = _kernel(g, seed)
-            op = sw.Operator(g, K, s)
-            # a pinned tile configuration: the autotuner's timing-based choice
-            # may differ between the two sets of handles, and the tiling sets
-            # the FP32 summation order on the tensor cores
-            op.tc_configure(0, 1, 1)
-            op.tc_configure(1, 1, 1)
-            op.set_precision(prec)
-            y = dev(np.random.default_rng(70 + i).standard_normal(g.y_shape()))
-            L = op.lipschitz(20)
-            op.fista_init(y, sw.SolveParams(step=0.9 / L, max_iters=9, lambda_l1=0.01,
-                                            lambda_tv=0.01, inner_iters=4,
-                                            refine_every=refine, refine_precision="bf16x3"))
-            ops.append(op)
-            ys.append(y)
-        return ops, ys
-
-    ops, ys = make()
+    ops, ys, prms = [], [], []
+    for i, name in enumerate(names):
+        g, s, seed = CASES[name]
+        op = sw.Operator(g, _kernel(g, seed), s, precision=prec)
+        y = dev(np.random.default_rng(70 + i).standard_normal(g.y_shape()))
+        prm = sw.SolveParams(step=0.9 / op.lipschitz(20), max_iters=9, lambda_l1=0.01,
+                             lambda_tv=0.01, inner_iters=4, refine_every=refine,
+                             refine_precision="bf16x3")
+        op.fista_init(y, prm)
+        ops.append(op)
+        ys.append(y)
+        prms.append(prm)
     b = sw.Batch(ops)
     b.step(4)
     b.step(5)
@@ -715,10 +704,10 @@ def test_batch_equals_separate_solves(prec, refine):
     with pytest.raises(sw.SwoptError):
         b.step(1)
     b.close()
-    ref_ops, _ = make()
-    for op, c in zip(ref_ops, got):
+    # the same handles (same tuned tile configurations, hence the same FP32
+    # summation order on the tensor cores) stepped one by one
+    for op, y, prm, c in zip(ops, ys, prms, got):
+        op.fista_init(y, prm)
         op.fista_step(9)
         assert torch.equal(op.fista_get(), c)
-        op.close()
-    for op in ops:
         op.close()
