@@ -27,10 +27,10 @@
 //
 // Roles (224 threads): warp 0 stages operands with bulk asynchronous copies
 // (the TMA engine) on mbarriers; warps 1 and 6 issue tcgen05.mma and commits
-// (an elected lane of each): both walk every stage and take alternate
-// (pair, tap) products into accumulators of their own, because one issuing
-// thread spends about 60 cycles of descriptor and loop work per MMA on top of
-// the tensor core's ~56 and cannot keep it busy alone; warps 2-5 zero the
+// (an elected lane of each): they take alternate stages (runs of taps) into
+// accumulators of their own, because one issuing thread spends about 60
+// cycles of descriptor, loop and barrier work per MMA on top of the tensor
+// core's ~56 and cannot keep it busy alone; warps 2-5 zero the
 // accumulators, then read them back with tcgen05.ld, sum them and write the
 // epilogue.  Every wait is bounded: on a timeout the CTA records an error in
 // a device word, drains its own copies, frees its TMEM and exits.
@@ -319,10 +319,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
     for (int i = threadIdx.x; i < a.tab_n; i += kTcThreads)
         reinterpret_cast<uint4*>(smem + tab_region)[i] = a.tab[i];
     if (threadIdx.x == 0) {
-        // every issuer commits to the empty, A-empty and accumulator barriers
+        // a stage is consumed by one issuer; every issuer commits to the
+        // A-empty and accumulator barriers
         for (int s = 0; s < a.NS; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
-            mbar_init(smem_u32(&bar_empty[s]), (uint32_t)a.NI);
+            mbar_init(smem_u32(&bar_empty[s]), 1);
         }
         mbar_init(smem_u32(&bar_afull), 1);
         mbar_init(smem_u32(&bar_aempty), (uint32_t)a.NI);
@@ -423,13 +424,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         }
     } else if (warp == 1 || warp == kIssuer2Warp) {
         // ------------------------------ MMA issuers ---------------------------
-        // Issuer j (warp 1, and warp 6 when NI = 2) walks the groups, runs,
-        // pairs and taps as a converged warp (waits and table reads are
-        // warp-wide, descriptors warp-uniform); its elected lane issues every
-        // NI-th (pair, tap) product, counted in the same order by both
-        // issuers, into the issuer's accumulator sets j RA (main) and
-        // j RA + RA - 1 (corrections).  A lone lane running the whole loop by
-        // itself was measured an order of magnitude slower per MMA.
+        // Issuer j (warp 1, and warp 6 when NI = 2) walks the groups and runs
+        // as a converged warp (waits and table reads are warp-wide,
+        // descriptors warp-uniform) and takes every NI-th run of taps (one
+        // stage of the ring) of this CTA; its elected lane issues all (pair,
+        // tap) products of those stages into the issuer's accumulator sets
+        // j RA (main) and j RA + RA - 1 (corrections).  A lone lane running
+        // the whole loop by itself was measured an order of magnitude slower
+        // per MMA.
         const int j = warp == 1 ? 0 : 1;
         if (j < a.NI) {
             const bool leader = elect_one();
@@ -445,8 +447,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
             const int MT = a.MT, NBc = a.NB, terms = a.terms;
             const uint32_t turn_mask = (uint32_t)a.NI - 1u;
             const int set_main = j * a.RA, set_corr = j * a.RA + a.RA - 1;
-            int stage = 0, run = 0;
-            uint32_t phase = 0, turn = 0;
+            int run = 0, local = 0;  // run: table index; local: this CTA's runs so far
             bool ok = true;
             for (int g = 0; g < g_lo; ++g) {  // runs of the groups before this CTA's
                 const int tg = (int)s_tab[g].z;
@@ -465,8 +466,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                     break;
                 }
                 tc_fence_after();
-                for (int d0 = 0; d0 < kk; d0 += tpr) {
+                for (int d0 = 0; d0 < kk; d0 += tpr, ++run, ++local) {
+                    if (((uint32_t)local & turn_mask) != (uint32_t)j) continue;  // the other issuer's
                     const int nt = min(tpr, kk - d0);
+                    const int stage = local % a.NS;
+                    const uint32_t phase = (uint32_t)(local / a.NS) & 1u;
                     if (!mbar_wait_warp(smem_u32(&bar_full[stage]), phase, &s_abort)) {
                         ok = false;
                         break;
@@ -479,7 +483,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                                             __shfl_sync(0xffffffffu, ro.y, 0),
                                             __shfl_sync(0xffffffffu, ro.z, 0),
                                             __shfl_sync(0xffffffffu, ro.w, 0)};
-                    ++run;
                     for (int i = 0; i < MT; ++i) {
                         const uint32_t dt = tmem + (uint32_t)((set_main * MT + i) * NBc);
                         const uint32_t dc = tmem + (uint32_t)((set_corr * MT + i) * NBc);
@@ -491,7 +494,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                             if (leader) {
 #pragma unroll
                                 for (int t = 0; t < kMaxTapsPerStage; ++t) {
-                                    if (t < nt && ((turn + (uint32_t)t) & turn_mask) == (uint32_t)j) {
+                                    if (t < nt) {
                                         const uint64_t ad =
                                             adp + (uint64_t)((ow[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
                                         const uint64_t bd = bdp + (uint64_t)t * tapb16;
@@ -503,16 +506,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                                     }
                                 }
                             }
-                            turn += (uint32_t)nt;
                         }
                     }
                     __syncwarp();
                     if (leader) tc_commit(smem_u32(&bar_empty[stage]));
                     __syncwarp();
-                    if (++stage == a.NS) {
-                        stage = 0;
-                        phase ^= 1u;
-                    }
                 }
             }
             // signals the epilogue; also covers every MMA issued above
