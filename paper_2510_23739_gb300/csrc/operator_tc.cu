@@ -54,7 +54,8 @@
 
 namespace swopt {
 
-constexpr int kMaxTerms = 2;  // BF16 terms per operand of the split precision
+constexpr int kMaxTerms = 2;    // BF16 terms per operand of the split precision
+constexpr int kMaxSpecies = 8;  // the geometry's limit on P
 
 // Operator data of one direction (forward or adjoint).
 struct TcDir {
@@ -680,30 +681,52 @@ struct TermPtrs {
 
 __global__ void tc_states_kernel(const float* __restrict__ c, const float* __restrict__ Sm,
                                  TermPtrs out, int terms, int Q, int P, int Y, int X, int Z,
-                                 int slices, int KS, int Yp, int Xp, int r)
+                                 int slices, int KS, int Yp, int Xp, int r, int vec)
 {
-    const size_t n = (size_t)Q * slices * Y * X;
+    // one thread per (slice, y, x): the P x 8 values of c are read once and
+    // every switching state m is written from them
+    const unsigned n = (unsigned)slices * Y * X;
     const size_t SZ = (size_t)Y * X * Z;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % X);
-        const int y = (int)((i / X) % Y);
-        const int s8 = (int)((i / ((size_t)X * Y)) % slices);
-        const int m = (int)(i / ((size_t)X * Y * slices));
-        float v[8];
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int x = (int)(i % (unsigned)X);
+        const int y = (int)((i / (unsigned)X) % (unsigned)Y);
+        const int s8 = (int)(i / ((unsigned)X * Y));
+        const int j0 = 8 * s8;
+        float cv[kMaxSpecies][8];  // static indices only: kept in registers
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int j = 8 * s8 + e;
-            float acc = 0.f;
-            if (j < Z)
-                for (int p = 0; p < P; ++p)
-                    acc = fmaf(Sm[(m * P + p) * Z + j], c[p * SZ + ((size_t)y * X + x) * Z + j], acc);
-            v[e] = acc;
+        for (int p = 0; p < kMaxSpecies; ++p) {
+            if (p >= P) break;
+            const float* src = c + p * SZ + ((size_t)y * X + x) * Z + j0;
+            if (vec && j0 + 8 <= Z) {
+                const float4 a = reinterpret_cast<const float4*>(src)[0];
+                const float4 b = reinterpret_cast<const float4*>(src)[1];
+                cv[p][0] = a.x; cv[p][1] = a.y; cv[p][2] = a.z; cv[p][3] = a.w;
+                cv[p][4] = b.x; cv[p][5] = b.y; cv[p][6] = b.z; cv[p][7] = b.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) cv[p][e] = j0 + e < Z ? src[e] : 0.f;
+            }
         }
-        uint4 parts[kMaxTerms];
-        split_terms(v, parts, terms);
-        const size_t o = ((((size_t)m * KS + s8) * Yp + (y + r)) * Xp + (x + r)) * 8;
-        for (int tt = 0; tt < terms; ++tt) *reinterpret_cast<uint4*>(out.p[tt] + o) = parts[tt];
+        for (int m = 0; m < Q; ++m) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int j = j0 + e;
+                float acc = 0.f;
+                if (j < Z) {
+#pragma unroll
+                    for (int p = 0; p < kMaxSpecies; ++p) {
+                        if (p >= P) break;
+                        acc = fmaf(Sm[(m * P + p) * Z + j], cv[p][e], acc);
+                    }
+                }
+                v[e] = acc;
+            }
+            uint4 parts[kMaxTerms];
+            split_terms(v, parts, terms);
+            const size_t o = ((((size_t)m * KS + s8) * Yp + (y + r)) * Xp + (x + r)) * 8;
+            for (int tt = 0; tt < terms; ++tt) *reinterpret_cast<uint4*>(out.p[tt] + o) = parts[tt];
+        }
     }
 }
 
@@ -1204,12 +1227,18 @@ swopt_status tc_states(swopt_handle* h, const float* c, cudaStream_t st)
 {
     TcOperator* t = h->tc;
     const int slices = (h->Z + 7) / 8;
-    const size_t n = (size_t)h->Q * slices * h->Y * h->X;
+    const size_t n = (size_t)slices * h->Y * h->X;
+    if (h->P > kMaxSpecies || n > 0x7FFFFFFFull) {
+        set_error("internal: state images beyond the kernel's limits");
+        return SWOPT_ERR_UNSUPPORTED;
+    }
     int grid = grid_for(n, 256);
     if (grid > 152 * 16) grid = 152 * 16;
     TermPtrs out{{t->bpad[0], t->bpad[1]}};
+    // 16-byte loads when every run of 8 depths starts on a 16-byte boundary
+    const int vec = (h->Z % 4) == 0 && ((uintptr_t)c & 15u) == 0;
     tc_states_kernel<<<grid, 256, 0, st>>>(c, h->Sm, out, t->terms, h->Q, h->P, h->Y, h->X, h->Z,
-                                           slices, t->F.KS, t->Yp, t->Xp, h->r);
+                                           slices, t->F.KS, t->Yp, t->Xp, h->r, vec);
     SW_LAUNCHED(h);
     return SWOPT_OK;
 }
