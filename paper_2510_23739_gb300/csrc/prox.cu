@@ -35,16 +35,28 @@ __device__ __forceinline__ double block_sum(double v, double* sh)
     return s;
 }
 
-__global__ void prox_l1_kernel(float* __restrict__ x, size_t n, float th, int nonneg)
+__device__ __forceinline__ float soft(float v, float th, int nonneg)
 {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const float v = x[i];
-        float o;
-        if (nonneg) o = fmaxf(v - th, 0.f);
-        else o = v > th ? v - th : (v < -th ? v + th : 0.f);
-        x[i] = o;
+    if (nonneg) return fmaxf(v - th, 0.f);
+    return v > th ? v - th : (v < -th ? v + th : 0.f);
+}
+
+// In place; 16-byte accesses over the first n4 = n / 4 groups when x is
+// 16-byte aligned (n4 = 0 otherwise), then the remaining entries.
+__global__ void prox_l1_kernel(float* __restrict__ x, size_t n, size_t n4, float th, int nonneg)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t first = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    float4* x4 = reinterpret_cast<float4*>(x);
+    for (size_t i = first; i < n4; i += stride) {
+        float4 v = x4[i];
+        v.x = soft(v.x, th, nonneg);
+        v.y = soft(v.y, th, nonneg);
+        v.z = soft(v.z, th, nonneg);
+        v.w = soft(v.w, th, nonneg);
+        x4[i] = v;
     }
+    for (size_t i = 4 * n4 + first; i < n; i += stride) x[i] = soft(x[i], th, nonneg);
 }
 
 struct Vol {
@@ -751,7 +763,8 @@ int ew_grid(size_t n)
 swopt_status prox_l1(swopt_handle* h, float* x, float thresh, int nonneg, cudaStream_t st)
 {
     const size_t n = nc_of(h);
-    prox_l1_kernel<<<ew_grid(n), 256, 0, st>>>(x, n, thresh, nonneg);
+    const size_t n4 = ((uintptr_t)x & 15u) == 0 ? n / 4 : 0;
+    prox_l1_kernel<<<ew_grid(n4 ? n4 : n), 256, 0, st>>>(x, n, n4, thresh, nonneg);
     SW_LAUNCHED(h);
     return SWOPT_OK;
 }
