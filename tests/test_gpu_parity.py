@@ -711,3 +711,27 @@ def test_batch_equals_separate_solves(prec, refine):
         op.fista_step(9)
         assert torch.equal(op.fista_get(), c)
         op.close()
+
+
+def test_prox_and_fista_on_a_volume_beyond_shared_memory():
+    """2 x 48 x 48 x 256: the TV prox state (about 37.7 MB) exceeds the
+    shared memory of all SMs together, so the prox runs as the cooperative
+    kernel on global memory instead of the shared-memory one; prox and a
+    short FISTA solve match the oracle."""
+    g = Geometry(X=48, Y=48, Z=256, T=32, N=2, P=2, k=3, pulses_per_cycle=2)
+    s = Switching((0.2, 0.0), (1.0, 0.0), (0.0, 1.0), 1.0)
+    K = np.random.default_rng(80).standard_normal(g.k_shape())
+    K[..., :8] = 0.0
+    op = sw.Operator(g, K, s)
+    z = np.random.default_rng(81).standard_normal(g.c_shape())
+    got = host(op.prox_tv(dev(z), 0.15, 10))
+    assert rel(got, oracle.prox_tv(z, 0.15, 10)) <= 1e-5
+    y = np.random.default_rng(82).standard_normal(g.y_shape())
+    alpha = 0.5 / oracle.power(g, s, K, synth.gaussian(g.c_shape(), 83), 30)
+    params = sw.SolveParams(step=alpha, lambda_l1=0.01, lambda_tv=0.05, inner_iters=6,
+                            max_iters=4)
+    c, _ = op.solve(dev(y), params)
+    op.check_device()
+    ref = oracle.fista(g, s, K, y, alpha, 4, 0.01, 0.05, 6)
+    assert rel(host(c), ref) <= 1e-4
+    op.close()
