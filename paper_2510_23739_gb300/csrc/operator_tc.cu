@@ -1291,7 +1291,15 @@ int tc_error_word(swopt_handle* h)
     if (!h->tc || !h->tc->err) return 0;
     int v = 0;
     if (cudaMemcpy(&v, h->tc->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
-    if (v) cudaMemset(h->tc->err, 0, sizeof(int));
+    if (v) {
+        cudaMemset(h->tc->err, 0, sizeof(int));
+        // a launch that gave up may have left split tickets counted: clear
+        // them so that later launches pair their partial sums correctly
+        for (TcDir* D : {&h->tc->F, &h->tc->A})
+            if (D->ticket)
+                cudaMemset(D->ticket, 0,
+                           sizeof(int) * (size_t)D->groupsX * h->tc->tilesY * h->Q);
+    }
     return v;
 }
 
