@@ -229,20 +229,19 @@ swopt_status ensure_ytil(swopt_handle* h)
 // Device-side failures recorded by the kernels (a bounded wait that gave up).
 swopt_status device_errors(swopt_handle* h)
 {
+    // every error word is read (and so cleared, with the state it guards) on
+    // every check, so that one failure is reported once and leaves no residue
     int w = tc_error_word(h);
-    if (w == 0) {
-        std::swap(h->tc, h->tc_ref);
-        w = tc_error_word(h);
-        std::swap(h->tc, h->tc_ref);
+    std::swap(h->tc, h->tc_ref);
+    const int w_ref = tc_error_word(h);
+    std::swap(h->tc, h->tc_ref);
+    const int c = coop_error_word(h);
+    if (w == 0) w = w_ref;
+    if (w == 0 && c > 0) {
+        set_error("the TV prox kernel gave up a bounded grid barrier");
+        return SWOPT_ERR_TIMEOUT;
     }
-    if (w == 0) {
-        const int c = coop_error_word(h);
-        if (c > 0) {
-            set_error("the TV prox kernel gave up a bounded grid barrier");
-            return SWOPT_ERR_TIMEOUT;
-        }
-        if (c < 0) w = -1;
-    }
+    if (w == 0 && c < 0) w = -1;
     if (w > 0) {
         set_error("a tensor-core kernel gave up a bounded wait (code %d)", w);
         return SWOPT_ERR_TIMEOUT;
