@@ -64,7 +64,9 @@ struct TcDir {
     int MT = 1;                   // tiles per CTA
     int RA = 1;                   // accumulators per tile and issuer: 1, or 2 (corrections apart)
     int NI = 1;                   // MMA-issuing warps (1 or 2), each with its own accumulators
-    int KSPL = 1;                 // CTAs per tile-state splitting the slice groups (1 or 2)
+    int KSPL = 1;                 // work units per tile-state splitting the slice groups (1 or 2)
+    int NBUF = 1;                 // accumulator buffers in TMEM (2: epilogue overlaps the next unit)
+    int grid = 0;                 // persistent CTAs launched
     float* part = nullptr;        // KSPL > 1: [KSPL][units][MT][NB/16][128][16] partial sums
     int* ticket = nullptr;        // KSPL > 1: [units] arrival counters (return to 0)
     int NS = 4;                   // stages of the B ring
@@ -119,6 +121,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
@@ -276,36 +283,68 @@ struct TcArgs {
     int Twp, KSo;
     int adj, terms, scale, mode;
     uint32_t tcols;
+    int NBUF;                   // accumulator buffers in TMEM (1, or 2: epilogue overlapped)
+    int ntiles;                 // tiles of the scan plane
+    int units_ts;               // tile-states: ntiles x Q
+    int units;                  // work units: units_ts x KSPL
 };
 
 // ---------------------------------------------------------------------------
 // The contraction kernel (forward or adjoint, see the file comment).
-// grid = (CTAs over the scan plane, Q, KSPL); block = 224 threads.  With
-// KSPL = 2 the two CTAs of a tile-state take the first and second half of the
-// slice groups (two waves of half-size work units quantise better on 152
-// SMs); each writes its summed accumulators to `part`, takes a ticket, and the
-// second to arrive adds the other's partial sums (a + b: the same bits
-// whichever arrives last) and runs the epilogue.  No CTA waits for another.
+// Persistent: grid = min(work units, resident CTAs), block = 224 threads.  A
+// work unit is one tile-state, or with KSPL = 2 one half of its slice groups;
+// CTA b takes units b, b + grid, b + 2 grid, ...  Every role walks the same
+// unit sequence.  With NBUF = 2 the accumulators are double-buffered in TMEM,
+// so that the epilogue of one unit overlaps the MMAs of the next.  With
+// KSPL = 2 the two halves of a tile-state each write their summed
+// accumulators to `part` and take a ticket; the second to arrive adds the
+// other's partial sums (a + b: the same bits whichever arrives last) and runs
+// the epilogue.  No CTA waits for another.
 // ---------------------------------------------------------------------------
+struct TcUnit {
+    int ts, sp;  // tile-state (m * tiles + tile) and half of the slice groups
+    int m, x0, y0, g_lo, g_hi;
+};
+
+// Unit k of this CTA; false past the end.  Halves are ordered so that one CTA
+// alternates between first and second halves (they may differ in work).
+__device__ __forceinline__ bool tc_unit(const TcArgs& a, int k, TcUnit& u)
+{
+    const int G = (int)gridDim.x;
+    const int p = (int)blockIdx.x + k * G;
+    if (p >= a.units) return false;
+    if (a.KSPL == 1) {
+        u.ts = p;
+        u.sp = 0;
+    } else {
+        u.ts = p >> 1;
+        u.sp = (G & 1) ? (p & 1) : ((p + p / G) & 1);
+    }
+    u.m = u.ts / a.ntiles;
+    const int tile = u.ts - u.m * a.ntiles;
+    u.x0 = (tile % a.groupsX) * 8 * a.MT;
+    u.y0 = (tile / a.groupsX) * 16;
+    const int gper = (a.NG + a.KSPL - 1) / a.KSPL;
+    u.g_lo = u.sp * gper;
+    u.g_hi = min(a.NG, u.g_lo + gper);
+    return true;
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t bar_full[kMaxStages];
     __shared__ __align__(8) uint64_t bar_empty[kMaxStages];
-    __shared__ __align__(8) uint64_t bar_afull, bar_aempty, bar_acc;
+    __shared__ __align__(8) uint64_t bar_afull, bar_aempty;
+    __shared__ __align__(8) uint64_t bar_accfull[2], bar_accfree[2], bar_drain[2];
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     __shared__ double s_red[4];
     __shared__ int s_last;
+    __shared__ int s_eok[4];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m = blockIdx.y;
-    const int x0 = (blockIdx.x % a.groupsX) * 8 * a.MT, y0 = (blockIdx.x / a.groupsX) * 16;
     const int kk = a.k * a.k;
-    // slice groups of this CTA's part of the contraction
-    const int sp = (int)blockIdx.z;
-    const int gper = (a.NG + a.KSPL - 1) / a.KSPL;
-    const int g_lo = sp * gper, g_hi = min(a.NG, g_lo + gper);
     const uint32_t npos = (uint32_t)(a.HY * a.HX);
     const uint32_t a_slice = npos * 16u;                       // bytes of one A slice
     const uint32_t a_part = (uint32_t)a.GA * a_slice;          // hi (or lo) A bytes
@@ -315,20 +354,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
     const uint32_t stage_total = a.stage_bytes * (uint32_t)a.terms;
     const uint32_t tab_region = b_region + (uint32_t)a.NS * stage_total;
     const uint4* s_tab = reinterpret_cast<const uint4*>(smem + tab_region);
+    // TMEM columns of one accumulator buffer (all tiles, issuers and sets)
+    const uint32_t buf_cols = (uint32_t)(a.MT * a.RA * a.NI * a.NB);
 
     // the group / pair table is small: stage it once
     for (int i = threadIdx.x; i < a.tab_n; i += kTcThreads)
         reinterpret_cast<uint4*>(smem + tab_region)[i] = a.tab[i];
     if (threadIdx.x == 0) {
         // a stage is consumed by one issuer; every issuer commits to the
-        // A-empty and accumulator barriers
+        // A-empty and accumulator-full barriers; every epilogue thread
+        // arrives on accumulator-free
         for (int s = 0; s < a.NS; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
             mbar_init(smem_u32(&bar_empty[s]), 1);
         }
         mbar_init(smem_u32(&bar_afull), 1);
         mbar_init(smem_u32(&bar_aempty), (uint32_t)a.NI);
-        mbar_init(smem_u32(&bar_acc), (uint32_t)a.NI);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&bar_accfull[b]), (uint32_t)a.NI);
+            mbar_init(smem_u32(&bar_accfree[b]), 128u);
+            mbar_init(smem_u32(&bar_drain[b]), 1u);
+        }
         s_abort = 0;
         s_red[0] = s_red[1] = s_red[2] = s_red[3] = 0.0;
         fence_mbar_init();
@@ -346,11 +392,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
     // warp-uniform by construction (MMA operands must be uniform values)
     const uint32_t tmem = __shfl_sync(0xffffffffu, s_tmem, 0);
 
-    // zero the accumulator columns of all tiles and issuers
+    // zero the accumulator columns of every buffer
     if (warp >= 2 && warp <= 5) {
         const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-        for (int cb = 0; cb < a.MT * a.RA * a.NI * a.NB / 16; ++cb)
-            tmem_zero16(tmem + lanes + (uint32_t)cb * 16u);
+        for (uint32_t cb = 0; cb < (uint32_t)a.NBUF * buf_cols / 16u; ++cb)
+            tmem_zero16(tmem + lanes + cb * 16u);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
@@ -365,46 +411,52 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         for (int s = 0; s < kMaxStages; ++s) fills[s] = 0;
         int a_fills = 0;
         bool ok = true;
-        for (int g = g_lo; g < g_hi && ok; ++g) {
-            const uint4 hd = s_tab[g];  // {base16, tap bytes, taps per run, pairs}
-            if (g > g_lo &&
-                !mbar_wait_warp(smem_u32(&bar_aempty), (uint32_t)(a_fills - 1) & 1u, &s_abort)) {
-                ok = false;
-                break;
-            }
-            if (lane == 0) mbar_expect_tx(smem_u32(&bar_afull), a_part * (uint32_t)a.terms);
-            ++a_fills;
-            __syncwarp();
-            const size_t img = (size_t)m * a.KS + (size_t)g * a.GA;
-            for (int idx = lane; idx < a.GA * a.HY; idx += 32) {
-                const int sl = idx / a.HY, hy = idx - sl * a.HY;
-                const size_t goff = (((img + sl) * a.Yp + (size_t)(y0 + hy)) * a.Xp + x0) * 8;
-                const uint32_t soff = (uint32_t)sl * a_slice + (uint32_t)(hy * a.HX) * 16u;
-                for (int tt = 0; tt < a.terms; ++tt)
-                    bulk_g2s(sA + (uint32_t)tt * a_part + soff, a.a_t[tt] + goff,
-                             (uint32_t)a.HX * 16u, smem_u32(&bar_afull));
-            }
-            for (int d0 = 0; d0 < kk && ok; d0 += (int)hd.z) {
-                const int nt = min((int)hd.z, kk - d0);
-                if (!mbar_wait_warp(smem_u32(&bar_empty[stage]), phase ^ 1u, &s_abort)) {
+        TcUnit u;
+        for (int k = 0; ok && tc_unit(a, k, u); ++k) {
+            for (int g = u.g_lo; g < u.g_hi && ok; ++g) {
+                const uint4 hd = s_tab[g];  // {base16, tap bytes, taps per run, pairs}
+                if (a_fills > 0 &&
+                    !mbar_wait_warp(smem_u32(&bar_aempty), (uint32_t)(a_fills - 1) & 1u,
+                                    &s_abort)) {
                     ok = false;
                     break;
                 }
-                if (lane == 0) {
-                    const uint32_t bar = smem_u32(&bar_full[stage]);
-                    const uint32_t dst = sB + (uint32_t)stage * stage_total;
-                    const uint32_t bytes = (uint32_t)nt * hd.y;
-                    const size_t src = ((size_t)hd.x * 16 + (size_t)d0 * hd.y) / 2;  // elements
-                    mbar_expect_tx(bar, bytes * (uint32_t)a.terms);
-                    if (bytes)
-                        for (int tt = 0; tt < a.terms; ++tt)
-                            bulk_g2s(dst + (uint32_t)tt * a.stage_bytes, a.b_t[tt] + src, bytes, bar);
-                }
-                fills[stage]++;
+                if (lane == 0) mbar_expect_tx(smem_u32(&bar_afull), a_part * (uint32_t)a.terms);
+                ++a_fills;
                 __syncwarp();
-                if (++stage == a.NS) {
-                    stage = 0;
-                    phase ^= 1u;
+                const size_t img = (size_t)u.m * a.KS + (size_t)g * a.GA;
+                for (int idx = lane; idx < a.GA * a.HY; idx += 32) {
+                    const int sl = idx / a.HY, hy = idx - sl * a.HY;
+                    const size_t goff =
+                        (((img + sl) * a.Yp + (size_t)(u.y0 + hy)) * a.Xp + u.x0) * 8;
+                    const uint32_t soff = (uint32_t)sl * a_slice + (uint32_t)(hy * a.HX) * 16u;
+                    for (int tt = 0; tt < a.terms; ++tt)
+                        bulk_g2s(sA + (uint32_t)tt * a_part + soff, a.a_t[tt] + goff,
+                                 (uint32_t)a.HX * 16u, smem_u32(&bar_afull));
+                }
+                for (int d0 = 0; d0 < kk && ok; d0 += (int)hd.z) {
+                    const int nt = min((int)hd.z, kk - d0);
+                    if (!mbar_wait_warp(smem_u32(&bar_empty[stage]), phase ^ 1u, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    if (lane == 0) {
+                        const uint32_t bar = smem_u32(&bar_full[stage]);
+                        const uint32_t dst = sB + (uint32_t)stage * stage_total;
+                        const uint32_t bytes = (uint32_t)nt * hd.y;
+                        const size_t src = ((size_t)hd.x * 16 + (size_t)d0 * hd.y) / 2;  // elements
+                        mbar_expect_tx(bar, bytes * (uint32_t)a.terms);
+                        if (bytes)
+                            for (int tt = 0; tt < a.terms; ++tt)
+                                bulk_g2s(dst + (uint32_t)tt * a.stage_bytes, a.b_t[tt] + src,
+                                         bytes, bar);
+                    }
+                    fills[stage]++;
+                    __syncwarp();
+                    if (++stage == a.NS) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
                 }
             }
         }
@@ -425,14 +477,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         }
     } else if (warp == 1 || warp == kIssuer2Warp) {
         // ------------------------------ MMA issuers ---------------------------
-        // Issuer j (warp 1, and warp 6 when NI = 2) walks the groups and runs
-        // as a converged warp (waits and table reads are warp-wide,
-        // descriptors warp-uniform) and takes every NI-th run of taps (one
-        // stage of the ring) of this CTA; its elected lane issues all (pair,
-        // tap) products of those stages into the issuer's accumulator sets
-        // j RA (main) and j RA + RA - 1 (corrections).  A lone lane running
-        // the whole loop by itself was measured an order of magnitude slower
-        // per MMA.
+        // Issuer j (warp 1, and warp 6 when NI = 2) walks every unit and
+        // group and runs as a converged warp (waits and table reads are
+        // warp-wide, descriptors warp-uniform); it takes every NI-th run of
+        // taps (one stage of the ring) of this CTA, and its elected lane issues
+        // all (pair, tap) products of those stages into the issuer's
+        // accumulator sets of the unit's buffer: j RA (main) and j RA + RA - 1
+        // (corrections).  A lone lane running the whole loop by itself was
+        // measured an order of magnitude slower per MMA.
         const int j = warp == 1 ? 0 : 1;
         if (j < a.NI) {
             const bool leader = elect_one();
@@ -448,210 +500,248 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
             const int MT = a.MT, NBc = a.NB, terms = a.terms;
             const uint32_t turn_mask = (uint32_t)a.NI - 1u;
             const int set_main = j * a.RA, set_corr = j * a.RA + a.RA - 1;
-            int run = 0, local = 0;  // run: table index; local: this CTA's runs so far
+            int local = 0;  // this CTA's runs so far (ring position and turn)
+            int ag = 0;     // A fills consumed
             bool ok = true;
-            for (int g = 0; g < g_lo; ++g) {  // runs of the groups before this CTA's
-                const int tg = (int)s_tab[g].z;
-                run += (kk + tg - 1) / tg;
-            }
-            for (int g = g_lo; g < g_hi && ok; ++g) {
-                const uint4 hd = s_tab[g];
-                const int tpr = __shfl_sync(0xffffffffu, (int)hd.z, 0);
-                const uint32_t tapb = __shfl_sync(0xffffffffu, hd.y, 0);
-                const int np = __shfl_sync(0xffffffffu, (int)hd.w, 0);
-                const uint64_t tapb16 = (uint64_t)(tapb >> 4);
-                if (g > g_lo && leader) tc_commit(smem_u32(&bar_aempty));
-                __syncwarp();
-                if (!mbar_wait_warp(smem_u32(&bar_afull), (uint32_t)(g - g_lo) & 1u, &s_abort)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                for (int d0 = 0; d0 < kk; d0 += tpr, ++run, ++local) {
-                    if (((uint32_t)local & turn_mask) != (uint32_t)j) continue;  // the other issuer's
-                    const int nt = min(tpr, kk - d0);
-                    const int stage = local % a.NS;
-                    const uint32_t phase = (uint32_t)(local / a.NS) & 1u;
-                    if (!mbar_wait_warp(smem_u32(&bar_full[stage]), phase, &s_abort)) {
+            TcUnit u;
+            for (int k = 0; ok && tc_unit(a, k, u); ++k) {
+                const int buf = a.NBUF == 2 ? (k & 1) : 0;
+                if (k >= a.NBUF) {  // the epilogue has drained this buffer
+                    if (!mbar_wait_warp(smem_u32(&bar_accfree[buf]),
+                                        (uint32_t)(k / a.NBUF - 1) & 1u, &s_abort)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t bst = sB + (uint32_t)stage * stage_total;
-                    // A offsets of this stage's taps (16-B units), from the run table
-                    const uint4 ro = s_tab[a.NG + run];
-                    const uint32_t ow[4] = {__shfl_sync(0xffffffffu, ro.x, 0),
-                                            __shfl_sync(0xffffffffu, ro.y, 0),
-                                            __shfl_sync(0xffffffffu, ro.z, 0),
-                                            __shfl_sync(0xffffffffu, ro.w, 0)};
-                    for (int i = 0; i < MT; ++i) {
-                        const uint32_t dt = tmem + (uint32_t)((set_main * MT + i) * NBc);
-                        const uint32_t dc = tmem + (uint32_t)((set_corr * MT + i) * NBc);
-                        for (int p = 0; p < np; ++p) {
-                            const uint64_t adp =
-                                adesc_c |
-                                (uint64_t)((sA + 2u * (uint32_t)p * a_slice + (uint32_t)i * 128u) >> 4);
-                            const uint64_t bdp = bdesc | (uint64_t)((bst + (uint32_t)p * pair_b) >> 4);
-                            if (leader) {
+                }
+                const uint32_t tbuf = tmem + (uint32_t)buf * buf_cols;
+                int run = 0;  // run table index
+                for (int g = 0; g < u.g_lo; ++g) {  // runs of the groups before this unit's
+                    const int tg = (int)s_tab[g].z;
+                    run += (kk + tg - 1) / tg;
+                }
+                for (int g = u.g_lo; g < u.g_hi && ok; ++g) {
+                    const uint4 hd = s_tab[g];
+                    const int tpr = __shfl_sync(0xffffffffu, (int)hd.z, 0);
+                    const uint32_t tapb = __shfl_sync(0xffffffffu, hd.y, 0);
+                    const int np = __shfl_sync(0xffffffffu, (int)hd.w, 0);
+                    const uint64_t tapb16 = (uint64_t)(tapb >> 4);
+                    if (ag > 0 && leader) tc_commit(smem_u32(&bar_aempty));
+                    __syncwarp();
+                    if (!mbar_wait_warp(smem_u32(&bar_afull), (uint32_t)ag & 1u, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    ++ag;
+                    tc_fence_after();
+                    for (int d0 = 0; d0 < kk; d0 += tpr, ++run, ++local) {
+                        if (((uint32_t)local & turn_mask) != (uint32_t)j) continue;  // the other issuer's
+                        const int nt = min(tpr, kk - d0);
+                        const int stage = local % a.NS;
+                        const uint32_t phase = (uint32_t)(local / a.NS) & 1u;
+                        if (!mbar_wait_warp(smem_u32(&bar_full[stage]), phase, &s_abort)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t bst = sB + (uint32_t)stage * stage_total;
+                        // A offsets of this stage's taps (16-B units), from the run table
+                        const uint4 ro = s_tab[a.NG + run];
+                        const uint32_t ow[4] = {__shfl_sync(0xffffffffu, ro.x, 0),
+                                                __shfl_sync(0xffffffffu, ro.y, 0),
+                                                __shfl_sync(0xffffffffu, ro.z, 0),
+                                                __shfl_sync(0xffffffffu, ro.w, 0)};
+                        for (int i = 0; i < MT; ++i) {
+                            const uint32_t dt = tbuf + (uint32_t)((set_main * MT + i) * NBc);
+                            const uint32_t dc = tbuf + (uint32_t)((set_corr * MT + i) * NBc);
+                            for (int p = 0; p < np; ++p) {
+                                const uint64_t adp =
+                                    adesc_c |
+                                    (uint64_t)((sA + 2u * (uint32_t)p * a_slice + (uint32_t)i * 128u) >> 4);
+                                const uint64_t bdp = bdesc | (uint64_t)((bst + (uint32_t)p * pair_b) >> 4);
+                                if (leader) {
 #pragma unroll
-                                for (int t = 0; t < kMaxTapsPerStage; ++t) {
-                                    if (t < nt) {
-                                        const uint64_t ad =
-                                            adp + (uint64_t)((ow[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
-                                        const uint64_t bd = bdp + (uint64_t)t * tapb16;
-                                        tc_mma(dt, ad, bd, idesc, 1u);
-                                        if (terms > 1) {
-                                            tc_mma(dc, ad, bd + blo16, idesc, 1u);
-                                            tc_mma(dc, ad + alo16, bd, idesc, 1u);
+                                    for (int t = 0; t < kMaxTapsPerStage; ++t) {
+                                        if (t < nt) {
+                                            const uint64_t ad =
+                                                adp + (uint64_t)((ow[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
+                                            const uint64_t bd = bdp + (uint64_t)t * tapb16;
+                                            tc_mma(dt, ad, bd, idesc, 1u);
+                                            if (terms > 1) {
+                                                tc_mma(dc, ad, bd + blo16, idesc, 1u);
+                                                tc_mma(dc, ad + alo16, bd, idesc, 1u);
+                                            }
                                         }
                                     }
                                 }
                             }
                         }
+                        __syncwarp();
+                        if (leader) tc_commit(smem_u32(&bar_empty[stage]));
+                        __syncwarp();
                     }
-                    __syncwarp();
-                    if (leader) tc_commit(smem_u32(&bar_empty[stage]));
-                    __syncwarp();
                 }
+                if (!ok) break;
+                // the unit's accumulators are complete once every MMA issued so far is
+                if (leader) tc_commit(smem_u32(&bar_accfull[buf]));
+                __syncwarp();
             }
-            // signals the epilogue; also covers every MMA issued above
-            if (leader) tc_commit(smem_u32(&bar_acc));
+            if (!ok && leader) {
+                s_abort = 1;
+                atomicExch(a.err, 1);
+            }
+            // every MMA of this issuer has completed before TMEM is freed
+            if (leader) tc_commit(smem_u32(&bar_drain[j]));
             __syncwarp();
-            if (!ok) {
-                if (leader) {
-                    s_abort = 1;
-                    atomicExch(a.err, 1);
-                }
-                volatile int never = 0;
-                if (!mbar_wait(smem_u32(&bar_acc), 0u, &never) && leader) atomicExch(a.err, 2);
-            }
+            volatile int never = 0;
+            if (!mbar_wait_warp(smem_u32(&bar_drain[j]), 0u, &never) && leader) atomicExch(a.err, 2);
         }
     } else {
         // ------------------------------ epilogue ------------------------------
         const int q = warp & 3;
         const int li = q * 32 + lane;
         const int yl = li >> 3, xl = li & 7;
-        bool ok = mbar_wait_warp(smem_u32(&bar_acc), 0u, &s_abort);
-        tc_fence_after();
         double part = 0.0;
         const uint32_t lanes = (uint32_t)(q * 32) << 16;
-        // the summed accumulator sets of tile ti, columns 16 cb .. 16 cb + 15
-        auto acc16 = [&](int ti, int cb, float (&v)[16]) {
-            tmem_ld16(tmem + lanes + (uint32_t)(ti * a.NB + cb * 16), v);
-            for (int rp = 1; rp < a.RA * a.NI; ++rp) {
-                float w[16];
-                tmem_ld16(tmem + lanes + (uint32_t)((rp * a.MT + ti) * a.NB + cb * 16), w);
-#pragma unroll
-                for (int e = 0; e < 16; ++e) v[e] += w[e];
-            }
-        };
-        const size_t unit = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-        const size_t units = (size_t)gridDim.y * gridDim.x;
         const size_t unit_floats = (size_t)a.MT * a.NB * 128;
-        auto part_at = [&](int split, int ti, int cb) -> float* {
-            return a.part + ((size_t)split * units + unit) * unit_floats +
-                   (((size_t)ti * (a.NB / 16) + cb) * 128 + li) * 16;
-        };
-        if (a.KSPL > 1) {
-            // publish this CTA's partial sums, then the ticket decides who ends
-            if (ok)
+        const size_t S = (size_t)a.Y * a.X;
+        TcUnit u;
+        for (int k = 0; tc_unit(a, k, u); ++k) {
+            const int buf = a.NBUF == 2 ? (k & 1) : 0;
+            const uint32_t tbuf = tmem + lanes + (uint32_t)buf * buf_cols;
+            const bool w_ok =
+                mbar_wait_warp(smem_u32(&bar_accfull[buf]), (uint32_t)(k / a.NBUF) & 1u, &s_abort);
+            tc_fence_after();
+            if (lane == 0) s_eok[q] = w_ok ? 1 : 0;
+            asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps
+            if (!(s_eok[0] && s_eok[1] && s_eok[2] && s_eok[3])) {
+                if (lane == 0) {
+                    s_abort = 1;
+                    atomicExch(a.err, 1);
+                }
+                break;  // the same decision in all four warps
+            }
+            // the summed accumulator sets of tile ti, columns 16 cb .. 16 cb + 15
+            auto acc16 = [&](int ti, int cb, float (&v)[16]) {
+                tmem_ld16(tbuf + (uint32_t)(ti * a.NB + cb * 16), v);
+                for (int rp = 1; rp < a.RA * a.NI; ++rp) {
+                    float w[16];
+                    tmem_ld16(tbuf + (uint32_t)((rp * a.MT + ti) * a.NB + cb * 16), w);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) v[e] += w[e];
+                }
+            };
+            auto part_at = [&](int split, int ti, int cb) -> float* {
+                return a.part + ((size_t)split * a.units_ts + u.ts) * unit_floats +
+                       (((size_t)ti * (a.NB / 16) + cb) * 128 + li) * 16;
+            };
+            bool last = true;
+            if (a.KSPL > 1) {
+                // publish this unit's partial sums, then the ticket decides who ends
                 for (int ti = 0; ti < a.MT; ++ti)
                     for (int cb = 0; cb < a.NB / 16; ++cb) {
                         float v[16];
                         acc16(ti, cb, v);
-                        float4* dst = reinterpret_cast<float4*>(part_at(sp, ti, cb));
+                        float4* dst = reinterpret_cast<float4*>(part_at(u.sp, ti, cb));
 #pragma unroll
                         for (int e4 = 0; e4 < 4; ++e4)
                             dst[e4] = make_float4(v[4 * e4], v[4 * e4 + 1], v[4 * e4 + 2],
                                                   v[4 * e4 + 3]);
                     }
-            __threadfence();
-            asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps
-            if (warp == 2 && lane == 0) {
-                const int prev = atomicAdd(a.ticket + unit, 1);
-                s_last = prev == a.KSPL - 1;
-                if (s_last) a.ticket[unit] = 0;  // ready for the next launch
+                __threadfence();
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (warp == 2 && lane == 0) {
+                    const int prev = atomicAdd(a.ticket + u.ts, 1);
+                    s_last = prev == a.KSPL - 1;
+                    if (s_last) a.ticket[u.ts] = 0;  // ready for the next launch
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                last = s_last != 0;
+                __threadfence();
             }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            ok = ok && s_last;
-            __threadfence();
-        }
-        if (ok) {
-            const size_t S = (size_t)a.Y * a.X;
-            const float cm = a.scale ? a.Cmf[m] : 1.f;
-            const int y = y0 + yl;
-            for (int ti = 0; ti < a.MT; ++ti) {
-                const int x = x0 + 8 * ti + xl;
-                const bool valid = (y < a.Y) && (x < a.X);
-                const size_t pos = (size_t)y * a.X + x;
-                for (int cb = 0; cb < a.NB / 16; ++cb) {
-                    float v[16];
-                    acc16(ti, cb, v);
-                    if (a.KSPL > 1) {  // + the other CTA's partial sums
-                        const float4* o4 = reinterpret_cast<const float4*>(part_at(1 - sp, ti, cb));
+            if (last) {
+                const float cm = a.scale ? a.Cmf[u.m] : 1.f;
+                const int y = u.y0 + yl;
+                for (int ti = 0; ti < a.MT; ++ti) {
+                    const int x = u.x0 + 8 * ti + xl;
+                    const bool valid = (y < a.Y) && (x < a.X);
+                    const size_t pos = (size_t)y * a.X + x;
+                    for (int cb = 0; cb < a.NB / 16; ++cb) {
+                        float v[16];
+                        acc16(ti, cb, v);
+                        if (a.KSPL > 1) {  // + the other half's partial sums
+                            const float4* o4 =
+                                reinterpret_cast<const float4*>(part_at(1 - u.sp, ti, cb));
 #pragma unroll
-                        for (int e4 = 0; e4 < 4; ++e4) {
-                            const float4 w = __ldcg(o4 + e4);  // written by another SM
-                            v[4 * e4] += w.x;
-                            v[4 * e4 + 1] += w.y;
-                            v[4 * e4 + 2] += w.z;
-                            v[4 * e4 + 3] += w.w;
-                        }
-                    }
-                    if (!valid) continue;
-                    if (a.adj) {
-                        float* out = a.out_f + ((size_t)m * S + pos) * a.Z + cb * 16;
-                        const int nz = min(16, a.Z - cb * 16);
-                        if (nz == 16 && (a.Z & 3) == 0) {
-#pragma unroll
-                            for (int e = 0; e < 16; e += 4)
-                                *reinterpret_cast<float4*>(out + e) =
-                                    make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
-                        } else {
-                            for (int e = 0; e < nz; ++e) out[e] = v[e];
-                        }
-                        continue;
-                    }
-                    const size_t ub = ((size_t)m * S + pos) * a.Twp + cb * 16;
-                    float o[16];
-                    if (a.ytil) {
-                        const float4* yt = reinterpret_cast<const float4*>(a.ytil + ub);
-#pragma unroll
-                        for (int e4 = 0; e4 < 4; ++e4) {
-                            const float4 w = yt[e4];
-                            const float wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) {
-                                const float acc = v[4 * e4 + c];
-                                o[4 * e4 + c] = cm * acc - wv[c];
-                                if (a.partials)
-                                    part += (double)cm * (double)acc * acc -
-                                            2.0 * (double)acc * wv[c];
+                            for (int e4 = 0; e4 < 4; ++e4) {
+                                const float4 w = __ldcg(o4 + e4);  // written by another SM
+                                v[4 * e4] += w.x;
+                                v[4 * e4 + 1] += w.y;
+                                v[4 * e4 + 2] += w.z;
+                                v[4 * e4 + 3] += w.w;
                             }
                         }
-                    } else {
+                        if (!valid) continue;
+                        if (a.adj) {
+                            float* out = a.out_f + ((size_t)u.m * S + pos) * a.Z + cb * 16;
+                            const int nz = min(16, a.Z - cb * 16);
+                            if (nz == 16 && (a.Z & 3) == 0) {
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) o[e] = cm * v[e];
-                    }
-                    if (a.mode == 0) {
-                        float4* out = reinterpret_cast<float4*>(a.out_f + ub);
+                                for (int e = 0; e < 16; e += 4)
+                                    *reinterpret_cast<float4*>(out + e) =
+                                        make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                            } else {
+                                for (int e = 0; e < nz; ++e) out[e] = v[e];
+                            }
+                            continue;
+                        }
+                        const size_t ub = ((size_t)u.m * S + pos) * a.Twp + cb * 16;
+                        float o[16];
+                        if (a.ytil) {
+                            const float4* yt = reinterpret_cast<const float4*>(a.ytil + ub);
 #pragma unroll
-                        for (int e4 = 0; e4 < 4; ++e4)
-                            out[e4] = make_float4(o[4 * e4], o[4 * e4 + 1], o[4 * e4 + 2],
-                                                  o[4 * e4 + 3]);
-                    } else {
+                            for (int e4 = 0; e4 < 4; ++e4) {
+                                const float4 w = yt[e4];
+                                const float wv[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const size_t ro = ((((size_t)m * a.KSo + 2 * cb + h) * a.Yp +
-                                                (y + a.r)) * a.Xp + (x + a.r)) * 8;
-                            uint4 parts[kMaxTerms];
-                            split_terms(o + 8 * h, parts, a.terms);
-                            for (int tt = 0; tt < a.terms; ++tt)
-                                *reinterpret_cast<uint4*>(a.out_t[tt] + ro) = parts[tt];
+                                for (int c = 0; c < 4; ++c) {
+                                    const float acc = v[4 * e4 + c];
+                                    o[4 * e4 + c] = cm * acc - wv[c];
+                                    if (a.partials)
+                                        part += (double)cm * (double)acc * acc -
+                                                2.0 * (double)acc * wv[c];
+                                }
+                            }
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) o[e] = cm * v[e];
+                        }
+                        if (a.mode == 0) {
+                            float4* out = reinterpret_cast<float4*>(a.out_f + ub);
+#pragma unroll
+                            for (int e4 = 0; e4 < 4; ++e4)
+                                out[e4] = make_float4(o[4 * e4], o[4 * e4 + 1], o[4 * e4 + 2],
+                                                      o[4 * e4 + 3]);
+                        } else {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const size_t ro = ((((size_t)u.m * a.KSo + 2 * cb + h) * a.Yp +
+                                                    (y + a.r)) * a.Xp + (x + a.r)) * 8;
+                                uint4 parts[kMaxTerms];
+                                split_terms(o + 8 * h, parts, a.terms);
+                                for (int tt = 0; tt < a.terms; ++tt)
+                                    *reinterpret_cast<uint4*>(a.out_t[tt] + ro) = parts[tt];
+                            }
                         }
                     }
                 }
             }
+            // hand the buffer back zeroed for the unit after next
+            for (uint32_t cb = 0; cb < buf_cols / 16u; ++cb) tmem_zero16(tbuf + cb * 16u);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            mbar_arrive(smem_u32(&bar_accfree[buf]));
+            asm volatile("bar.sync 1, 128;" ::: "memory");  // s_eok and s_last are reused
         }
         if (a.partials) {
 #pragma unroll
@@ -663,8 +753,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
     tc_fence_before();
     __syncthreads();
     if (a.partials && threadIdx.x == 0)
-        a.partials[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] =
-            s_red[0] + s_red[1] + s_red[2] + s_red[3];
+        a.partials[blockIdx.x] = s_red[0] + s_red[1] + s_red[2] + s_red[3];
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -830,7 +919,7 @@ struct DirHost {
 // Builds the banded kernel of one direction for MT tiles per CTA within a
 // shared-memory budget.  Returns false if it does not fit.
 bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int RA, int NI,
-              int skip, int kspl, size_t budget, DirHost* out)
+              int NBUF, int skip, int kspl, size_t budget, DirHost* out)
 {
     const int kk = h->k * h->k;
     const int terms = t->terms;
@@ -839,12 +928,13 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
     D.RA = RA;
     D.NI = NI;
     D.KSPL = kspl;
+    D.NBUF = NBUF;
     D.NB = adj ? t->Zp16 : h->Twp;
     const int ks_min = adj ? h->Twp / 8 : t->Zp16 / 8;  // both even
     const int npairs = ks_min / 2;
     D.HX = 8 * MT + 2 * h->r;
     D.npos = t->HY * D.HX;
-    D.cols = (int)pow2_cols(MT * RA * NI * D.NB);
+    D.cols = (int)pow2_cols(NBUF * MT * RA * NI * D.NB);
     if (D.cols > 512) return false;
     D.groupsX = (t->tilesX + MT - 1) / MT;
 
@@ -1020,6 +1110,10 @@ TcArgs dir_args(const swopt_handle* h, const TcOperator* t, const TcDir& D, bool
     a.tab = reinterpret_cast<const uint4*>(D.tab);
     a.tab_n = D.tab_words / 4;
     a.tcols = (uint32_t)D.cols;
+    a.NBUF = D.NBUF;
+    a.ntiles = D.groupsX * t->tilesY;
+    a.units_ts = a.ntiles * h->Q;
+    a.units = a.units_ts * D.KSPL;
     for (int tt = 0; tt < kMaxTerms; ++tt) a.a_t[tt] = adj ? t->rpad[tt] : t->bpad[tt];
     return a;
 }
@@ -1037,9 +1131,34 @@ swopt_status launch_conv(swopt_handle* h, const TcDir& D, const TcArgs& a, cudaS
     }
     SW_CUDA(cudaFuncSetAttribute(tc_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  dmax));
-    dim3 grid(D.groupsX * h->tc->tilesY, h->Q, D.KSPL);
-    tc_conv_kernel<<<grid, kTcThreads, D.smem, st>>>(a);
+    if (D.grid <= 0) {
+        set_error("internal: tensor-core configuration without a grid");
+        return SWOPT_ERR_UNSUPPORTED;
+    }
+    tc_conv_kernel<<<D.grid, kTcThreads, D.smem, st>>>(a);
     SW_LAUNCHED(h);
+    return SWOPT_OK;
+}
+
+// Persistent grid of a configuration: every work unit, or as many CTAs as can
+// be resident at once (by shared memory and by TMEM columns), if fewer.
+swopt_status set_grid(swopt_handle* h, TcDir* D)
+{
+    const int dmax = max_dynamic_smem(h, (const void*)tc_conv_kernel);
+    if (dmax <= 0 || D->smem > (size_t)dmax) {
+        set_error("tensor-core kernel needs %zu bytes of shared memory (device limit %d)", D->smem,
+                  dmax);
+        return SWOPT_ERR_UNSUPPORTED;
+    }
+    SW_CUDA(cudaFuncSetAttribute(tc_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 dmax));
+    int nsm = 0, occ = 0;
+    SW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tc_conv_kernel, kTcThreads,
+                                                          D->smem));
+    occ = std::max(1, std::min(occ, 512 / D->cols));
+    const long long units = (long long)D->groupsX * h->tc->tilesY * h->Q * D->KSPL;
+    D->grid = (int)std::min<long long>(units, (long long)std::max(nsm, 1) * occ);
     return SWOPT_OK;
 }
 
@@ -1091,10 +1210,14 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
             // (and, with two or more groups, the groups split over 2 CTAs)
             for (int skip = 0; skip < 2; ++skip)
                 for (int kspl = 1; kspl <= 2; ++kspl) {
-                    DirHost H;
-                    if (plan_dir(h, t, adj, c.MT, ra, 2, skip, kspl, c.budget, &H) ||
-                        plan_dir(h, t, adj, c.MT, ra, 1, skip, kspl, c.budget, &H))
-                        plans.push_back(std::move(H));
+                    // double-buffered accumulators (the epilogue overlaps the
+                    // next unit's MMAs) where TMEM holds them, and single ones
+                    for (int nbuf = 2; nbuf >= 1; --nbuf) {
+                        DirHost H;
+                        if (plan_dir(h, t, adj, c.MT, ra, 2, nbuf, skip, kspl, c.budget, &H) ||
+                            plan_dir(h, t, adj, c.MT, ra, 1, nbuf, skip, kspl, c.budget, &H))
+                            plans.push_back(std::move(H));
+                    }
                 }
         }
     }
@@ -1113,6 +1236,12 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
             TcDir D;
             SW_TRY(upload_dir(plans[i], t->terms,
                               (size_t)plans[i].cfg.groupsX * t->tilesY * h->Q, &D));
+            if (swopt_status sg = set_grid(h, &D); sg != SWOPT_OK) {
+                free_dir(D);
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return sg;
+            }
             TcArgs a = dir_args(h, t, D, adj);
             a.out_f = adj ? h->g : h->u;
             a.mode = 0;
@@ -1143,8 +1272,13 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
             return SWOPT_ERR_TIMEOUT;
         }
     }
-    return upload_dir(plans[best_i], t->terms,
-                      (size_t)plans[best_i].cfg.groupsX * t->tilesY * h->Q, best);
+    SW_TRY(upload_dir(plans[best_i], t->terms,
+                      (size_t)plans[best_i].cfg.groupsX * t->tilesY * h->Q, best));
+    if (swopt_status sg = set_grid(h, best); sg != SWOPT_OK) {
+        free_dir(*best);
+        return sg;
+    }
+    return SWOPT_OK;
 }
 
 swopt_status tc_prepare(swopt_handle* h)
