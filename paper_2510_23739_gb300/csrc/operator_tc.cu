@@ -13,27 +13,29 @@
 // tap d and tile i is the same buffer at a byte offset (rows of 8
 // consecutive x are 16 B apart; 8-row groups are one halo row apart).
 //
-// Measured on GB300, an M = 128, K = 16 MMA costs max(96, N/2) cycles, and
-// switching the accumulator between consecutive MMAs adds about 150 cycles.
-// So every MMA covers the whole output range (N = the time window for A, the
-// padded depth count for A^T) at TMEM column 0 of its tile, and the issue
-// order keeps one accumulator for as long as possible (tiles outermost within
-// a stage).  Trailing pairs of slices whose kernel is zero for every tap are
-// dropped.  The kernel is pre-packed per tap as [pair][slice][N rows][8]
-// (leading offset N x 16 B), so every descriptor of the MMA loop is uniform
-// arithmetic on loop counters and one elected lane issues MMAs back to back.
-// Consecutive taps are grouped into runs of one stage of shared memory (several
-// taps per stage), each arriving with one bulk asynchronous copy.
+// Measured on GB300: one warp (its elected lane) issues a tcgen05.mma about
+// every 150 cycles whatever the shape or the accumulator, while the tensor
+// core takes about 56 cycles for M = 128, N = 96, K = 16; two issuing warps
+// reach about 76 cycles per MMA between them.  So every MMA covers the whole
+// output range (N = the time window for A, the padded depth count for A^T)
+// at TMEM column 0 of its tile, and two warps issue.  Trailing pairs of
+// slices whose kernel is zero for every tap are dropped.  The kernel is
+// pre-packed per tap as [pair][slice][N rows][8] (leading offset N x 16 B),
+// so every descriptor of the MMA loop is uniform arithmetic on loop
+// counters.  Consecutive taps are grouped into runs of one stage of shared
+// memory (several taps per stage), each arriving with one bulk asynchronous
+// copy.
 //
-// Roles (224 threads): warp 0 stages operands with bulk asynchronous copies
-// (the TMA engine) on mbarriers; warps 1 and 6 issue tcgen05.mma and commits
-// (an elected lane of each): they take alternate stages (runs of taps) into
-// accumulators of their own, because one issuing thread spends about 60
-// cycles of descriptor, loop and barrier work per MMA on top of the tensor
-// core's ~56 and cannot keep it busy alone; warps 2-5 zero the
-// accumulators, then read them back with tcgen05.ld, sum them and write the
-// epilogue.  Every wait is bounded: on a timeout the CTA records an error in
-// a device word, drains its own copies, frees its TMEM and exits.
+// Roles (224 threads) of a persistent CTA: warp 0 stages operands with bulk
+// asynchronous copies (the TMA engine) on mbarriers; warps 1 and 6 issue
+// tcgen05.mma and commits (an elected lane of each, in a converged warp):
+// they take alternate stages (runs of taps) into accumulators of their own;
+// warps 2-5 read the accumulators back with tcgen05.ld, sum them, write the
+// epilogue and hand the accumulators back zeroed.  The CTAs share the runs
+// of all tile-states equally (the stream-K split), so a tile-state may be
+// contracted in pieces by neighbouring CTAs and finished by the last of them
+// to arrive.  Every wait is bounded: on a timeout the CTA records an error in
+// a device word, drains its own copies and MMAs, frees its TMEM and exits.
 //
 // Precisions: BF16 operands with FP32 accumulation (1 term), or a split of
 // both operands into 2 BF16 terms (v = v0 + v1, v1 the BF16 rounding of
@@ -64,11 +66,15 @@ struct TcDir {
     int MT = 1;                   // tiles per CTA
     int RA = 1;                   // accumulators per tile and issuer: 1, or 2 (corrections apart)
     int NI = 1;                   // MMA-issuing warps (1 or 2), each with its own accumulators
-    int KSPL = 1;                 // work units per tile-state splitting the slice groups (1 or 2)
+    int whole = 1;                // 1: CTAs take whole tile-states; 0: balanced runs (stream-K)
+    int runs = 0;                 // runs of taps per tile-state (all groups)
     int NBUF = 1;                 // accumulator buffers in TMEM (2: epilogue overlaps the next unit)
     int grid = 0;                 // persistent CTAs launched
-    float* part = nullptr;        // KSPL > 1: [KSPL][units][MT][NB/16][128][16] partial sums
-    int* ticket = nullptr;        // KSPL > 1: [units] arrival counters (return to 0)
+    int quantum = 1;              // runs per indivisible piece of work
+    long long wq = 0;             // pieces of work in all: tile-states x runs / quantum
+    int max_pieces = 1;           // most CTAs sharing one tile-state
+    float* part = nullptr;        // max_pieces > 1: [tile-states][max_pieces][MT][NB/16][128][16]
+    int* ticket = nullptr;        // max_pieces > 1: [tile-states] arrival counters (return to 0)
     int NS = 4;                   // stages of the B ring
     uint32_t stage_bytes = 0;     // bytes of one stage (hi part; lo is as large)
     int HX = 0, npos = 0;         // halo width and positions
@@ -275,9 +281,9 @@ struct TcArgs {
     const float* Cmf;           // [Q]
     double* partials;           // per block, or null
     int* err;
-    int Y, X, Yp, Xp, Z, k, r, HY, HX, groupsX, MT, RA, NI, KSPL;
-    float* part;                // KSPL > 1: partial sums of the split contraction
-    int* ticket;                // KSPL > 1: per tile-state arrival counters
+    int Y, X, Yp, Xp, Z, k, r, HY, HX, groupsX, MT, RA, NI;
+    float* part;                // partial sums of tile-states shared by several CTAs
+    int* ticket;                // per tile-state arrival counters
     int KS, GA, NG, NS, NB;
     uint32_t stage_bytes;
     int Twp, KSo;
@@ -285,48 +291,58 @@ struct TcArgs {
     uint32_t tcols;
     int NBUF;                   // accumulator buffers in TMEM (1, or 2: epilogue overlapped)
     int ntiles;                 // tiles of the scan plane
-    int units_ts;               // tile-states: ntiles x Q
-    int units;                  // work units: units_ts x KSPL
+    int runs;                   // runs of taps per tile-state
+    int quantum;                // runs per indivisible piece of work
+    long long wq;               // pieces of work in all: tile-states x runs / quantum
+    int max_pieces;             // partial-sum slots per tile-state
 };
 
 // ---------------------------------------------------------------------------
 // The contraction kernel (forward or adjoint, see the file comment).
-// Persistent: grid = min(work units, resident CTAs), block = 224 threads.  A
-// work unit is one tile-state, or with KSPL = 2 one half of its slice groups;
-// CTA b takes units b, b + grid, b + 2 grid, ...  Every role walks the same
-// unit sequence.  With NBUF = 2 the accumulators are double-buffered in TMEM,
-// so that the epilogue of one unit overlaps the MMAs of the next.  With
-// KSPL = 2 the two halves of a tile-state each write their summed
-// accumulators to `part` and take a ticket; the second to arrive adds the
-// other's partial sums (a + b: the same bits whichever arrives last) and runs
-// the epilogue.  No CTA waits for another.
+// Persistent: grid = min(pieces of work, resident CTAs), block = 224 threads.
+// The work is the runs of taps of every tile-state, in order (tile-state
+// major); CTA b takes the b-th of gridDim.x equal shares of it, rounded to
+// whole pieces of `quantum` runs (one run: the stream-K split, which leaves
+// no wave tail; all runs of a tile-state: whole tile-states).  A CTA's share
+// cut by tile-state boundaries gives its work units; every role walks the
+// same unit sequence.  With NBUF = 2 the accumulators are double-buffered in
+// TMEM, so that the epilogue of one unit overlaps the MMAs of the next.  A
+// tile-state shared by several CTAs is finished by the last to arrive: each
+// writes its summed accumulators to `part` and takes a ticket; the last adds
+// the partial sums (two: a + b, the same bits whichever arrives last; more:
+// in piece order) and runs the epilogue.  No CTA waits for another.
 // ---------------------------------------------------------------------------
 struct TcUnit {
-    int ts, sp;  // tile-state (m * tiles + tile) and half of the slice groups
-    int m, x0, y0, g_lo, g_hi;
+    int ts, r0, r1;      // tile-state (m * tiles + tile) and its runs [r0, r1)
+    int m, x0, y0;
+    int piece, pieces;   // this CTA's piece of the tile-state, of how many
 };
 
-// Unit k of this CTA; false past the end.  Halves are ordered so that one CTA
-// alternates between first and second halves (they may differ in work).
+// The CTA whose share holds run x of the whole work.
+__device__ __forceinline__ int tc_owner(const TcArgs& a, long long x)
+{
+    const long long xq = x / a.quantum;
+    return (int)(((xq + 1) * (long long)gridDim.x - 1) / a.wq);
+}
+
+// Unit k of this CTA; false past the end.
 __device__ __forceinline__ bool tc_unit(const TcArgs& a, int k, TcUnit& u)
 {
-    const int G = (int)gridDim.x;
-    const int p = (int)blockIdx.x + k * G;
-    if (p >= a.units) return false;
-    if (a.KSPL == 1) {
-        u.ts = p;
-        u.sp = 0;
-    } else {
-        u.ts = p >> 1;
-        u.sp = (G & 1) ? (p & 1) : ((p + p / G) & 1);
-    }
+    const long long G = gridDim.x, R = a.runs;
+    const long long b0 = (long long)a.quantum * ((long long)blockIdx.x * a.wq / G);
+    const long long b1 = (long long)a.quantum * (((long long)blockIdx.x + 1) * a.wq / G);
+    const long long ts = b0 / R + k;
+    if (ts * R >= b1) return false;
+    u.ts = (int)ts;
+    u.r0 = (int)(b0 > ts * R ? b0 - ts * R : 0);
+    u.r1 = (int)(b1 - ts * R < R ? b1 - ts * R : R);
+    const int first = tc_owner(a, ts * R), last = tc_owner(a, ts * R + R - 1);
+    u.pieces = last - first + 1;
+    u.piece = (int)blockIdx.x - first;
     u.m = u.ts / a.ntiles;
     const int tile = u.ts - u.m * a.ntiles;
     u.x0 = (tile % a.groupsX) * 8 * a.MT;
     u.y0 = (tile / a.groupsX) * 16;
-    const int gper = (a.NG + a.KSPL - 1) / a.KSPL;
-    u.g_lo = u.sp * gper;
-    u.g_hi = min(a.NG, u.g_lo + gper);
     return true;
 }
 
@@ -413,8 +429,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         bool ok = true;
         TcUnit u;
         for (int k = 0; ok && tc_unit(a, k, u); ++k) {
-            for (int g = u.g_lo; g < u.g_hi && ok; ++g) {
+            int rb = 0;  // first run of group g
+            for (int g = 0; g < a.NG && ok; ++g) {
                 const uint4 hd = s_tab[g];  // {base16, tap bytes, taps per run, pairs}
+                const int nr = (kk + (int)hd.z - 1) / (int)hd.z;
+                const int lo = max(u.r0, rb), hi = min(u.r1, rb + nr);
+                rb += nr;
+                if (lo >= hi) continue;  // no run of this group in the unit
                 if (a_fills > 0 &&
                     !mbar_wait_warp(smem_u32(&bar_aempty), (uint32_t)(a_fills - 1) & 1u,
                                     &s_abort)) {
@@ -434,7 +455,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                         bulk_g2s(sA + (uint32_t)tt * a_part + soff, a.a_t[tt] + goff,
                                  (uint32_t)a.HX * 16u, smem_u32(&bar_afull));
                 }
-                for (int d0 = 0; d0 < kk && ok; d0 += (int)hd.z) {
+                for (int run = lo; run < hi && ok; ++run) {
+                    const int d0 = (run - (rb - nr)) * (int)hd.z;
                     const int nt = min((int)hd.z, kk - d0);
                     if (!mbar_wait_warp(smem_u32(&bar_empty[stage]), phase ^ 1u, &s_abort)) {
                         ok = false;
@@ -515,17 +537,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                     tc_fence_after();
                 }
                 const uint32_t tbuf = tmem + (uint32_t)buf * buf_cols;
-                int run = 0;  // run table index
-                for (int g = 0; g < u.g_lo; ++g) {  // runs of the groups before this unit's
-                    const int tg = (int)s_tab[g].z;
-                    run += (kk + tg - 1) / tg;
-                }
-                for (int g = u.g_lo; g < u.g_hi && ok; ++g) {
+                int rb = 0;  // first run of group g
+                for (int g = 0; g < a.NG && ok; ++g) {
                     const uint4 hd = s_tab[g];
                     const int tpr = __shfl_sync(0xffffffffu, (int)hd.z, 0);
                     const uint32_t tapb = __shfl_sync(0xffffffffu, hd.y, 0);
                     const int np = __shfl_sync(0xffffffffu, (int)hd.w, 0);
                     const uint64_t tapb16 = (uint64_t)(tapb >> 4);
+                    const int nr = (kk + tpr - 1) / tpr;
+                    const int lo = max(u.r0, rb), hi = min(u.r1, rb + nr);
+                    const int gb = rb;
+                    rb += nr;
+                    if (lo >= hi) continue;  // no run of this group in the unit
                     if (ag > 0 && leader) tc_commit(smem_u32(&bar_aempty));
                     __syncwarp();
                     if (!mbar_wait_warp(smem_u32(&bar_afull), (uint32_t)ag & 1u, &s_abort)) {
@@ -534,8 +557,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                     }
                     ++ag;
                     tc_fence_after();
-                    for (int d0 = 0; d0 < kk; d0 += tpr, ++run, ++local) {
+                    for (int run = lo; run < hi; ++run, ++local) {
                         if (((uint32_t)local & turn_mask) != (uint32_t)j) continue;  // the other issuer's
+                        const int d0 = (run - gb) * tpr;
                         const int nt = min(tpr, kk - d0);
                         const int stage = local % a.NS;
                         const uint32_t phase = (uint32_t)(local / a.NS) & 1u;
@@ -631,18 +655,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                     for (int e = 0; e < 16; ++e) v[e] += w[e];
                 }
             };
-            auto part_at = [&](int split, int ti, int cb) -> float* {
-                return a.part + ((size_t)split * a.units_ts + u.ts) * unit_floats +
+            auto part_at = [&](int piece, int ti, int cb) -> float* {
+                return a.part + ((size_t)u.ts * a.max_pieces + piece) * unit_floats +
                        (((size_t)ti * (a.NB / 16) + cb) * 128 + li) * 16;
             };
             bool last = true;
-            if (a.KSPL > 1) {
+            if (u.pieces > 1) {
                 // publish this unit's partial sums, then the ticket decides who ends
                 for (int ti = 0; ti < a.MT; ++ti)
                     for (int cb = 0; cb < a.NB / 16; ++cb) {
                         float v[16];
                         acc16(ti, cb, v);
-                        float4* dst = reinterpret_cast<float4*>(part_at(u.sp, ti, cb));
+                        float4* dst = reinterpret_cast<float4*>(part_at(u.piece, ti, cb));
 #pragma unroll
                         for (int e4 = 0; e4 < 4; ++e4)
                             dst[e4] = make_float4(v[4 * e4], v[4 * e4 + 1], v[4 * e4 + 2],
@@ -652,7 +676,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 if (warp == 2 && lane == 0) {
                     const int prev = atomicAdd(a.ticket + u.ts, 1);
-                    s_last = prev == a.KSPL - 1;
+                    s_last = prev == u.pieces - 1;
                     if (s_last) a.ticket[u.ts] = 0;  // ready for the next launch
                 }
                 asm volatile("bar.sync 1, 128;" ::: "memory");
@@ -668,17 +692,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                     const size_t pos = (size_t)y * a.X + x;
                     for (int cb = 0; cb < a.NB / 16; ++cb) {
                         float v[16];
-                        acc16(ti, cb, v);
-                        if (a.KSPL > 1) {  // + the other half's partial sums
-                            const float4* o4 =
-                                reinterpret_cast<const float4*>(part_at(1 - u.sp, ti, cb));
+                        if (u.pieces <= 2) {
+                            acc16(ti, cb, v);
+                            if (u.pieces == 2) {  // + the other piece's partial sums
+                                const float4* o4 =
+                                    reinterpret_cast<const float4*>(part_at(1 - u.piece, ti, cb));
 #pragma unroll
-                            for (int e4 = 0; e4 < 4; ++e4) {
-                                const float4 w = __ldcg(o4 + e4);  // written by another SM
-                                v[4 * e4] += w.x;
-                                v[4 * e4 + 1] += w.y;
-                                v[4 * e4 + 2] += w.z;
-                                v[4 * e4 + 3] += w.w;
+                                for (int e4 = 0; e4 < 4; ++e4) {
+                                    const float4 w = __ldcg(o4 + e4);  // written by another SM
+                                    v[4 * e4] += w.x;
+                                    v[4 * e4 + 1] += w.y;
+                                    v[4 * e4 + 2] += w.z;
+                                    v[4 * e4 + 3] += w.w;
+                                }
+                            }
+                        } else {  // every piece's partial sums, in piece order
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) v[e] = 0.f;
+                            for (int pc = 0; pc < u.pieces; ++pc) {
+                                const float4* o4 = reinterpret_cast<const float4*>(part_at(pc, ti, cb));
+#pragma unroll
+                                for (int e4 = 0; e4 < 4; ++e4) {
+                                    const float4 w = __ldcg(o4 + e4);
+                                    v[4 * e4] += w.x;
+                                    v[4 * e4 + 1] += w.y;
+                                    v[4 * e4 + 2] += w.z;
+                                    v[4 * e4 + 3] += w.w;
+                                }
                             }
                         }
                         if (!valid) continue;
@@ -919,7 +959,7 @@ struct DirHost {
 // Builds the banded kernel of one direction for MT tiles per CTA within a
 // shared-memory budget.  Returns false if it does not fit.
 bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int RA, int NI,
-              int NBUF, int skip, int kspl, size_t budget, DirHost* out)
+              int NBUF, int skip, int whole, size_t budget, DirHost* out)
 {
     const int kk = h->k * h->k;
     const int terms = t->terms;
@@ -927,7 +967,7 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
     D.MT = MT;
     D.RA = RA;
     D.NI = NI;
-    D.KSPL = kspl;
+    D.whole = whole;
     D.NBUF = NBUF;
     D.NB = adj ? t->Zp16 : h->Twp;
     const int ks_min = adj ? h->Twp / 8 : t->Zp16 / 8;  // both even
@@ -1005,7 +1045,6 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
         }
     }
     if (!found) return false;
-    if (D.KSPL > 1 && D.NG < 2) return false;  // nothing to split
     // At most 512 / cols CTAs may share an SM's 512 TMEM columns: request
     // enough shared memory that no more can be resident (233472 B per SM,
     // so more than 233472 / (512 / cols + 1) bytes per CTA).
@@ -1025,6 +1064,7 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
         const uint32_t tpr = std::min<uint32_t>(
             kMaxTapsPerStage, std::max<uint32_t>(1, D.stage_bytes / tapb));
         out->tab.insert(out->tab.end(), {base16, tapb, tpr, (uint32_t)np});
+        D.runs += (kk + (int)tpr - 1) / (int)tpr;
         // runs of tpr taps: A offsets (16-B units) of each tap of the run
         for (int d0 = 0; d0 < kk; d0 += (int)tpr) {
             uint32_t w[4] = {0, 0, 0, 0};
@@ -1076,15 +1116,8 @@ swopt_status upload_dir(const DirHost& H, int terms, size_t units, TcDir* D)
     swopt_status s = SWOPT_OK;
     for (int tt = 0; tt < terms && s == SWOPT_OK; ++tt) s = up16(&D->Bt[tt], H.t[tt]);
     if (s == SWOPT_OK) s = tc_upload(&D->tab, H.tab);
-    if (s == SWOPT_OK && D->KSPL > 1) {
-        s = tc_alloc(&D->part, (size_t)D->KSPL * units * D->MT * D->NB * 128);
-        if (s == SWOPT_OK) s = tc_alloc(&D->ticket, units);
-        if (s == SWOPT_OK && cudaMemset(D->ticket, 0, units * sizeof(int)) != cudaSuccess) {
-            set_error("cudaMemset failed");
-            s = SWOPT_ERR_CUDA;
-        }
-    }
     if (s != SWOPT_OK) free_dir(*D);
+    (void)units;
     return s;
 }
 
@@ -1097,7 +1130,6 @@ TcArgs dir_args(const swopt_handle* h, const TcOperator* t, const TcDir& D, bool
     a.Y = h->Y; a.X = h->X; a.Yp = t->Yp; a.Xp = t->Xp; a.Z = h->Z; a.k = h->k; a.r = h->r;
     a.HY = t->HY; a.HX = D.HX; a.groupsX = D.groupsX; a.MT = D.MT; a.RA = D.RA;
     a.NI = D.NI;
-    a.KSPL = D.KSPL;
     a.part = D.part;
     a.ticket = D.ticket;
     a.KS = D.KS; a.GA = D.GA; a.NG = D.NG; a.NS = D.NS; a.NB = D.NB;
@@ -1112,8 +1144,10 @@ TcArgs dir_args(const swopt_handle* h, const TcOperator* t, const TcDir& D, bool
     a.tcols = (uint32_t)D.cols;
     a.NBUF = D.NBUF;
     a.ntiles = D.groupsX * t->tilesY;
-    a.units_ts = a.ntiles * h->Q;
-    a.units = a.units_ts * D.KSPL;
+    a.runs = D.runs;
+    a.quantum = D.quantum;
+    a.wq = D.wq;
+    a.max_pieces = D.max_pieces;
     for (int tt = 0; tt < kMaxTerms; ++tt) a.a_t[tt] = adj ? t->rpad[tt] : t->bpad[tt];
     return a;
 }
@@ -1140,8 +1174,9 @@ swopt_status launch_conv(swopt_handle* h, const TcDir& D, const TcArgs& a, cudaS
     return SWOPT_OK;
 }
 
-// Persistent grid of a configuration: every work unit, or as many CTAs as can
-// be resident at once (by shared memory and by TMEM columns), if fewer.
+// Persistent grid of a configuration: as many CTAs as can be resident at once
+// (by shared memory, registers and TMEM columns), or one per piece of work if
+// fewer; then the partial-sum slots and tickets of shared tile-states.
 swopt_status set_grid(swopt_handle* h, TcDir* D)
 {
     const int dmax = max_dynamic_smem(h, (const void*)tc_conv_kernel);
@@ -1157,8 +1192,25 @@ swopt_status set_grid(swopt_handle* h, TcDir* D)
     SW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tc_conv_kernel, kTcThreads,
                                                           D->smem));
     occ = std::max(1, std::min(occ, 512 / D->cols));
-    const long long units = (long long)D->groupsX * h->tc->tilesY * h->Q * D->KSPL;
-    D->grid = (int)std::min<long long>(units, (long long)std::max(nsm, 1) * occ);
+    const long long units_ts = (long long)D->groupsX * h->tc->tilesY * h->Q;
+    const long long R = std::max(D->runs, 1);
+    D->quantum = D->whole ? (int)R : 1;
+    D->wq = units_ts * R / D->quantum;
+    const long long G = std::min<long long>(D->wq, (long long)std::max(nsm, 1) * occ);
+    D->grid = (int)G;
+    // CTAs sharing a tile-state: the owners of its first and last runs and
+    // every CTA between (each share holds at least one piece of work)
+    auto owner = [&](long long x) { return ((x / D->quantum + 1) * G - 1) / D->wq; };
+    long long most = 1;
+    for (long long ts = 0; ts < units_ts; ++ts)
+        most = std::max(most, owner(ts * R + R - 1) - owner(ts * R) + 1);
+    D->max_pieces = (int)most;
+    if (most > 1) {
+        const size_t unit_floats = (size_t)D->MT * D->NB * 128;
+        SW_TRY(tc_alloc(&D->part, (size_t)units_ts * most * unit_floats));
+        SW_TRY(tc_alloc(&D->ticket, (size_t)units_ts));
+        SW_CUDA(cudaMemset(D->ticket, 0, (size_t)units_ts * sizeof(int)));
+    }
     return SWOPT_OK;
 }
 
@@ -1206,16 +1258,16 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
             if (force_mt > 0 && c.MT != force_mt) continue;
             if (force_ctas > 0 && (force_ctas == 2) != (c.budget < 200 * 1024)) continue;
             // two MMA-issuing warps where TMEM holds their accumulators; the
-            // fewest slice groups that fit, and the next split (larger stages)
-            // (and, with two or more groups, the groups split over 2 CTAs)
+            // fewest slice groups that fit, and the next split (larger stages);
+            // CTAs taking whole tile-states, or equal shares of all runs
             for (int skip = 0; skip < 2; ++skip)
-                for (int kspl = 1; kspl <= 2; ++kspl) {
+                for (int whole = 1; whole >= 0; --whole) {
                     // double-buffered accumulators (the epilogue overlaps the
                     // next unit's MMAs) where TMEM holds them, and single ones
                     for (int nbuf = 2; nbuf >= 1; --nbuf) {
                         DirHost H;
-                        if (plan_dir(h, t, adj, c.MT, ra, 2, nbuf, skip, kspl, c.budget, &H) ||
-                            plan_dir(h, t, adj, c.MT, ra, 1, nbuf, skip, kspl, c.budget, &H))
+                        if (plan_dir(h, t, adj, c.MT, ra, 2, nbuf, skip, whole, c.budget, &H) ||
+                            plan_dir(h, t, adj, c.MT, ra, 1, nbuf, skip, whole, c.budget, &H))
                             plans.push_back(std::move(H));
                     }
                 }
@@ -1353,8 +1405,10 @@ swopt_status tc_prepare(swopt_handle* h)
 
 int tc_forward_blocks(const swopt_handle* h)
 {
-    // upper bound: up to 2 CTAs per tile-state
-    return 2 * ((h->X + 7) / 8) * ((h->Y + 15) / 16) * h->Q;
+    // upper bound on the persistent grid: at most the resident CTAs (two per
+    // SM at most, on up to 1024 SMs)
+    (void)h;
+    return 2048;
 }
 
 swopt_status tc_states(swopt_handle* h, const float* c, cudaStream_t st)
