@@ -288,6 +288,24 @@ swopt_status swopt_tc_configure(swopt_handle* h, int kernel_id, int tiles_per_ct
 swopt_status swopt_tc_config(swopt_handle* h, int kernel_id, int* tiles_per_cta, int* ctas_per_sm,
                              int* stages, int* groups, int* accumulators);
 
+/* Work schedule of the tensor-core contraction (kernel_id 0: A, 1: A^T).
+ * The kernel is persistent (at most one CTA per resident slot).  split
+ * selects how the runs of taps of all (switching state, tile) pairs are
+ * shared out: 1 = whole pairs per CTA, 2 = equal shares of all runs (a pair
+ * cut between neighbouring CTAs is summed by the last to finish, in a fixed
+ * order: the results do not depend on which finishes last).  buffers = 2
+ * double-buffers the TMEM accumulators (the epilogue overlaps the next
+ * unit's MMAs), 1 does not.  0 leaves a field to the timed choice.
+ * swopt_tc_schedule pins them and rebuilds the operator if one is active
+ * (synchronises); INVALID_ARG for values out of range, UNSUPPORTED at the
+ * rebuild if no configuration satisfies the pins.  swopt_tc_schedule_info
+ * reports the schedule in use: split (1 or 2), buffers, the CTAs launched
+ * and the most CTAs that share one pair (INVALID_ARG if no BF16 precision is
+ * selected). */
+swopt_status swopt_tc_schedule(swopt_handle* h, int kernel_id, int split, int buffers);
+swopt_status swopt_tc_schedule_info(swopt_handle* h, int kernel_id, int* split, int* buffers,
+                                    int* grid, int* max_pieces);
+
 /* Operator facts: the time window [t0, t0 + tw) that holds every nonzero
  * kernel sample, the number of distinct switching states Q = min(N,
  * pulses_per_cycle) and the number of nonzero kernel entries. */

@@ -123,6 +123,9 @@ _SIGS = {
                             ctypes.c_int], ctypes.c_int),
     "swopt_tc_config": ([ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 5,
                         ctypes.c_int),
+    "swopt_tc_schedule": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "swopt_tc_schedule_info": ([ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4,
+                               ctypes.c_int),
     "swopt_prox_tv_static": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int,
                               ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
@@ -423,6 +426,19 @@ class Operator:
         _check(lib().swopt_tc_config(self._h, int(kernel_id), *[ctypes.byref(x) for x in v]))
         return {"tiles_per_cta": v[0].value, "ctas_per_sm": v[1].value, "stages": v[2].value,
                 "groups": v[3].value, "accumulators": v[4].value}
+
+    def tc_schedule(self, kernel_id, split=0, buffers=0):
+        """Pin the work split (1 whole pairs, 2 equal shares of all runs) and
+        the accumulator buffers (1 or 2) of a contraction; 0 leaves the timed
+        choice."""
+        _check(lib().swopt_tc_schedule(self._h, int(kernel_id), int(split), int(buffers)))
+
+    def tc_schedule_info(self, kernel_id):
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(lib().swopt_tc_schedule_info(self._h, int(kernel_id),
+                                            *[ctypes.byref(x) for x in v]))
+        return {"split": v[0].value, "buffers": v[1].value, "grid": v[2].value,
+                "max_pieces": v[3].value}
 
     def launch_count(self):
         n = ctypes.c_int64()

@@ -1200,6 +1200,42 @@ swopt_status swopt_tc_config(swopt_handle* h, int kernel_id, int* tiles_per_cta,
     return SWOPT_OK;
 }
 
+swopt_status swopt_tc_schedule(swopt_handle* h, int kernel_id, int split, int buffers)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (kernel_id < 0 || kernel_id > 1 || split < 0 || split > 2 || buffers < 0 || buffers > 2) {
+        set_error("invalid tensor-core schedule");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    release_graph(h);
+    h->tc_force_split[kernel_id] = split;
+    h->tc_force_nbuf[kernel_id] = buffers;
+    release_ref(h);
+    if (h->tc) {
+        tc_release(h);
+        if (use_tc(h)) return tc_prepare(h);
+    }
+    return SWOPT_OK;
+}
+
+swopt_status swopt_tc_schedule_info(swopt_handle* h, int kernel_id, int* split, int* buffers,
+                                    int* grid, int* max_pieces)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (kernel_id < 0 || kernel_id > 1 || !split || !buffers || !grid || !max_pieces) {
+        set_error("invalid arguments");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    if (!h->tc) {
+        set_error("no tensor-core precision selected");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    tc_schedule_info(h, kernel_id, split, buffers, grid, max_pieces);
+    return SWOPT_OK;
+}
+
 swopt_status swopt_launch_count(swopt_handle* h, int64_t* count)
 {
     clear_error();

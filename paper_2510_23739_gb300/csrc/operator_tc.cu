@@ -1241,10 +1241,13 @@ void tc_release(swopt_handle* h)
 }
 
 // Chooses, for one direction, the fastest candidate configuration (timed
-// with CUDA events on zeroed operands) unless `force_mt` > 0 pins the tiles
-// per CTA.  The padded images must already be sized for max_ks slices.
+// with CUDA events on zeroed operands) among those the pins allow: `force_mt`
+// tiles per CTA, `force_ctas` CTAs per SM, `force_ra` accumulators per tile,
+// `force_split` (1: whole tile-states, 2: stream-K) and `force_nbuf`
+// accumulator buffers, each 0 for free.  The padded images must already be
+// sized for max_ks slices.
 static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_ctas,
-                             int force_ra, TcDir* best)
+                             int force_ra, int force_split, int force_nbuf, TcDir* best)
 {
     TcOperator* t = h->tc;
     std::vector<DirHost> plans;
@@ -1262,9 +1265,11 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
             // CTAs taking whole tile-states, or equal shares of all runs
             for (int skip = 0; skip < 2; ++skip)
                 for (int whole = 1; whole >= 0; --whole) {
+                    if (force_split > 0 && whole != (force_split == 1 ? 1 : 0)) continue;
                     // double-buffered accumulators (the epilogue overlaps the
                     // next unit's MMAs) where TMEM holds them, and single ones
                     for (int nbuf = 2; nbuf >= 1; --nbuf) {
+                        if (force_nbuf > 0 && nbuf != force_nbuf) continue;
                         DirHost H;
                         if (plan_dir(h, t, adj, c.MT, ra, 2, nbuf, skip, whole, c.budget, &H) ||
                             plan_dir(h, t, adj, c.MT, ra, 1, nbuf, skip, whole, c.budget, &H))
@@ -1381,9 +1386,11 @@ swopt_status tc_prepare(swopt_handle* h)
     zero(t->err, sizeof(int));
     // the adjoint's slice count fixes the layout the forward epilogue writes
     if (s == SWOPT_OK)
-        s = tune_dir(h, true, h->tc_force_mt[1], h->tc_force_ctas[1], h->tc_force_ra[1], &t->A);
+        s = tune_dir(h, true, h->tc_force_mt[1], h->tc_force_ctas[1], h->tc_force_ra[1],
+                     h->tc_force_split[1], h->tc_force_nbuf[1], &t->A);
     if (s == SWOPT_OK)
-        s = tune_dir(h, false, h->tc_force_mt[0], h->tc_force_ctas[0], h->tc_force_ra[0], &t->F);
+        s = tune_dir(h, false, h->tc_force_mt[0], h->tc_force_ctas[0], h->tc_force_ra[0],
+                     h->tc_force_split[0], h->tc_force_nbuf[0], &t->F);
     if (s == SWOPT_OK && (t->F.KS > ksf_max || t->A.KS > ksa_max)) {
         set_error("internal: padded slice count exceeds the allocation");
         s = SWOPT_ERR_DEVICE_CHECK;
@@ -1507,6 +1514,16 @@ void tc_config(const swopt_handle* h, int kernel, int* mt, int* ctas_per_sm, int
     if (*ctas_per_sm > 512 / D.cols) *ctas_per_sm = 512 / D.cols;
     *stages = D.NS;
     *groups = D.NG;
+}
+
+void tc_schedule_info(const swopt_handle* h, int kernel, int* split, int* buffers, int* grid,
+                      int* max_pieces)
+{
+    const TcDir& D = kernel == 0 ? h->tc->F : h->tc->A;
+    *split = D.whole ? 1 : 2;
+    *buffers = D.NBUF;
+    *grid = D.grid;
+    *max_pieces = D.max_pieces;
 }
 
 }  // namespace swopt

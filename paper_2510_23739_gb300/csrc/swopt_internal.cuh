@@ -150,6 +150,8 @@ struct swopt_handle {
     int tc_force_mt[2] = {0, 0};     // tiles per CTA of A / A^T (0: tuned)
     int tc_force_ctas[2] = {0, 0};   // CTAs per SM of A / A^T (0: tuned)
     int tc_force_ra[2] = {0, 0};     // accumulators per tile of A / A^T (0: default)
+    int tc_force_split[2] = {0, 0};  // work split of A / A^T (1 whole, 2 stream-K; 0: tuned)
+    int tc_force_nbuf[2] = {0, 0};   // accumulator buffers of A / A^T (0: tuned)
 
     // CUDA graph of one FISTA iteration (rebuilt when the settings change)
     bool use_graph = true;
@@ -234,6 +236,8 @@ double tc_issued_macs(const swopt_handle* h, int kernel);
 // configuration chosen for the forward (0) / adjoint (1)
 void tc_config(const swopt_handle* h, int kernel, int* mt, int* ctas_per_sm, int* stages,
                int* groups, int* accumulators);
+void tc_schedule_info(const swopt_handle* h, int kernel, int* split, int* buffers, int* grid,
+                      int* max_pieces);
 
 // Elementwise / layout kernels (operator_simt.cu).
 swopt_status launch_states(swopt_handle* h, const float* c, float* b, cudaStream_t st);

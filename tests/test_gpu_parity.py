@@ -573,6 +573,73 @@ def test_refined_medium_tracks_fp32_objective(medium):
         ev.close()
 
 
+@pytest.mark.parametrize("split,buffers", [(1, 1), (1, 2), (2, 1), (2, 2)])
+@pytest.mark.parametrize("name", ["tiny", "ragged", "support_31"])
+def test_tensor_core_schedules_match_oracle(tc_cases, name, split, buffers):
+    """Every work split (whole (state, tile) pairs per CTA, or equal shares of
+    all runs, where a pair cut between CTAs is summed by the last to finish)
+    and either accumulator buffering gives the oracle's A and A^T, and the
+    split-precision results of one handle are bitwise repeatable."""
+    g, s, K = tc_cases[name]
+    c = np.random.default_rng(41).standard_normal(g.c_shape())
+    yv = np.random.default_rng(42).standard_normal(g.y_shape())
+    op = sw.Operator(g, K, s)
+    try:
+        for kid in (0, 1):
+            op.tc_schedule(kid, split=split, buffers=buffers)
+        op.set_precision("bf16x3")
+        for kid in (0, 1):
+            info = op.tc_schedule_info(kid)
+            assert info["split"] == split and info["buffers"] == buffers
+            assert info["grid"] >= 1
+            if split == 1:
+                assert info["max_pieces"] == 1
+        f = host(op.forward(dev(c)))
+        a = host(op.adjoint(dev(yv)))
+        assert np.array_equal(f, host(op.forward(dev(c))))
+        assert np.array_equal(a, host(op.adjoint(dev(yv))))
+        op.check_device()
+        assert rel(f, oracle.forward(g, s, K, c)) <= TC_TOL["bf16x3"]
+        assert rel(a, oracle.adjoint(g, s, K, yv)) <= TC_TOL["bf16x3"]
+    finally:
+        op.close()
+
+
+def test_tensor_core_stream_k_sums_many_pieces(tc_cases):
+    """On the tiny workload the equal-share split cuts every (state, tile)
+    pair among many CTAs (more than two pieces: summed in piece order)."""
+    g, s, K = tc_cases["tiny"]
+    op = sw.Operator(g, K, s)
+    try:
+        op.tc_schedule(0, split=2)
+        op.tc_schedule(1, split=2)
+        op.set_precision("bf16")
+        assert op.tc_schedule_info(0)["max_pieces"] > 2
+        assert op.tc_schedule_info(1)["max_pieces"] > 2
+        c = np.random.default_rng(43).standard_normal(g.c_shape())
+        yv = np.random.default_rng(44).standard_normal(g.y_shape())
+        f = host(op.forward(dev(c)))
+        a = host(op.adjoint(dev(yv)))
+        op.check_device()
+        assert rel(f, oracle.forward(g, s, K, c)) <= TC_TOL["bf16"]
+        assert rel(a, oracle.adjoint(g, s, K, yv)) <= TC_TOL["bf16"]
+    finally:
+        op.close()
+
+
+def test_tensor_core_schedule_rejects_bad_values(tc_cases):
+    g, s, K = tc_cases["tiny"]
+    op = sw.Operator(g, K, s)
+    try:
+        for bad in ((0, 3, 0), (0, 0, 3), (2, 1, 1), (0, -1, 0)):
+            with pytest.raises(Exception):
+                op.tc_schedule(*bad)
+        with pytest.raises(Exception):
+            op.tc_schedule_info(0)  # no tensor-core precision selected
+    finally:
+        op.close()
+
+
 def test_tensor_core_accumulators_option(tc_cases):
     """One accumulator per tile (corrections summed with the main products)
     stays within the split tolerance; two is the default of the split mode."""
