@@ -156,13 +156,33 @@ def _profiled_traffic(kernel_name: str, workload: str):
     return float(m_bytes.group(1))
 
 
-def make_problem(prob, seed: int, device):
+def workload_problem(name: str, kernel: str = "aperture"):
+    """The named workload; the paper-literal kernel runs on the matched time
+    grid (c dt = dz) that its construction assumes."""
+    prob = synth.workload(name)
+    if kernel == "semicircle":
+        prob = synth.small_variant(prob, dt_us=synth.matched_time_grid(prob.geom).dt_us)
+    return prob
+
+
+def semicircle_args(g):
+    """Arguments of the paper-literal kernel for geometry g: 3D half-sphere
+    masks, lateral pitch in depth pitches, the focus at the middle depth and
+    at the middle time sample, the synthetic SPR image and impulse response."""
+    return (g.Z, g.k, g.T, 3, g.dx_mm / g.dz_mm, (g.Z - 1) / 2.0, g.T // 2,
+            synth.spr_image(g, seed=0), synth.eir_taps(g))
+
+
+def make_problem(prob, seed: int, device, kernel: str = "aperture"):
     """Seeded synthetic inputs on the device: kernel, phantom, measurements."""
     import torch
     import paper_2510_23739_gb300 as sw
 
     g = prob.geom
-    K = synth.transducer_kernel(g, seed=0)
+    if kernel == "semicircle":
+        K = sw.semicircle_kernel(*semicircle_args(g))
+    else:
+        K = synth.transducer_kernel(g, seed=0)
     op = sw.Operator(g, K, prob.sw)
     c_true = torch.tensor(synth.tube_phantom(g, prob.tubes, seed=seed,
                                              per_species=prob.tubes_per_species),
@@ -181,9 +201,9 @@ def run_swopt(args, rank, world, device):
     import torch
     import paper_2510_23739_gb300 as sw
 
-    prob = synth.workload(args.workload)
+    prob = workload_problem(args.workload, args.kernel)
     g = prob.geom
-    op, K, c_true, y = make_problem(prob, seed=rank, device=device)
+    op, K, c_true, y = make_problem(prob, seed=rank, device=device, kernel=args.kernel)
     if args.precision != "fp32":
         op.set_precision(args.precision)
     L = op.lipschitz(100)
@@ -392,7 +412,7 @@ def combine_ranks(total_ms: float, e2e_ms: float, steps: int, world: int, device
     return (total_ms, e2e_ms, world * steps / (total_ms / 1e3), world * steps / (e2e_ms / 1e3))
 
 
-def cpu_oracle_iteration_ms(prob, sample_pulses: int):
+def cpu_oracle_iteration_ms(prob, sample_pulses: int, kernel: str = "aperture"):
     """Time the FP64 oracle on a bounded sample of one FISTA iteration and
     extrapolate to the full workload: forward + adjoint on `sample_pulses`
     pulses (the per-pulse work is identical), the TV/l1 prox on the full
@@ -401,7 +421,10 @@ def cpu_oracle_iteration_ms(prob, sample_pulses: int):
     from dataclasses import replace
 
     g = prob.geom
-    K = synth.transducer_kernel(g, seed=0)
+    if kernel == "semicircle":
+        K = oracle.semicircle_kernel(*semicircle_args(g))
+    else:
+        K = synth.transducer_kernel(g, seed=0)
     gs = replace(g, N=sample_pulses)
     c = synth.tube_phantom(g, prob.tubes, seed=0)
     y = synth.gaussian(gs.y_shape(), 7) * 0.01
@@ -422,12 +445,12 @@ def cpu_oracle_iteration_ms(prob, sample_pulses: int):
 def run_reference(args):
     """The reference arm: the FP64 CPU oracle, each step a bounded sample of
     one FISTA iteration extrapolated to the full workload."""
-    prob = synth.workload(args.workload)
+    prob = workload_problem(args.workload, args.kernel)
     times = []
     sample = ""
     cores = 1
     for i in range(args.warmup + args.steps):
-        ms, sample, cores = cpu_oracle_iteration_ms(prob, args.ref_sample_pulses)
+        ms, sample, cores = cpu_oracle_iteration_ms(prob, args.ref_sample_pulses, args.kernel)
         if i >= args.warmup:
             times.append(ms)
     ms = sum(times) / len(times)
@@ -436,7 +459,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "impl": "FP64 CPU oracle (plain C, OpenMP)",
+            "config": {"workload": args.workload, "kernel": args.kernel,
+                       "impl": "FP64 CPU oracle (plain C, OpenMP)",
                        "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "it/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
@@ -453,6 +477,9 @@ def main():
     ap.add_argument("--impl", default="swopt", choices=["swopt", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--kernel", default="aperture", choices=["aperture", "semicircle"],
+                    help="per-depth kernel: the aperture-point transducer model, or the "
+                         "paper-literal SPR on discrete half spheres (matched time grid)")
     ap.add_argument("--refine", type=int, default=None,
                     help="refined solve: exact gradient every R iterations (0: off; "
                          "default 25 for bf16, else 0)")
@@ -515,11 +542,11 @@ def main():
             peak = peaks["bf16_tflops_sustained"] / nprod
             bound, peak_note = "tensor", f"bf16 dense sustained / {nprod} products ({peak_src})"
         kname = ["A_forward", "AT_adjoint"][dom]
-        traffic = _profiled_traffic(kname, args.workload)
+        traffic = _profiled_traffic(kname, args.workload) if args.kernel == "aperture" else None
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            ms_cpu, sample, cores = cpu_oracle_iteration_ms(synth.workload(args.workload),
-                                                            args.cpu_sample_pulses)
+            ms_cpu, sample, cores = cpu_oracle_iteration_ms(
+                workload_problem(args.workload, args.kernel), args.cpu_sample_pulses, args.kernel)
             cpu = {"value": 1000.0 / ms_cpu, "unit": "it/s", "cores": cores, "kind": "oracle",
                    "sample": sample}
         line = {
@@ -530,7 +557,8 @@ def main():
                 args.precision] + (f" + refinement (exact {args.refine_precision} gradient every "
                                    f"{args.refine} iterations)" if args.refine > 0 else ""),
             "data": "synthetic (seeded tube phantom, transducer kernel, 20 dB noise)",
-            "config": {"workload": args.workload, "precision": args.precision,
+            "config": {"workload": args.workload, "kernel": args.kernel,
+                       "precision": args.precision,
                        "refine_every": args.refine,
                        "refine_precision": args.refine_precision if args.refine > 0 else None,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

@@ -306,6 +306,33 @@ swopt_status swopt_tc_schedule(swopt_handle* h, int kernel_id, int split, int bu
 swopt_status swopt_tc_schedule_info(swopt_handle* h, int kernel_id, int* split, int* buffers,
                                     int* grid, int* max_pieces);
 
+/* The paper-literal acoustic kernel (Sec. 2.3.1 "Acoustic Model", Eqs.
+ * q-above-final / q-below-final with the discrete semicircles of Eqs.
+ * discrete-upper-circle / discrete-lower-circle), as the per-depth kernel
+ * that swopt_create takes.  Host only: no GPU is used.
+ *   K_out[j][dy][dx][t] = sum_s M[j][dy][dx][t - s] eir[s + J],
+ *   M[j][dy][dx][t] = eta[j][dy][dx] if voxel (j, dy, dx) meets the upper
+ *   (t < focal_sample) or lower (t > focal_sample) half sphere of radius
+ *   |t - focal_sample| about the focus, else 0,
+ * in depth pitches (the time grid matches the depth grid, c0 dt = dz; one
+ * lateral pitch is lateral_ratio depth pitches; the focus is at depth index
+ * focal_depth, which may be fractional).  A voxel meets a half sphere when
+ * its closed box, clipped to the half space (z <= 0 above the focus, z >= 0
+ * below), has its nearest point at most and its farthest point at least the
+ * radius from the focus; at t = focal_sample the voxels whose box holds the
+ * focus count.  dims = 3 uses the voxel box; dims = 2 the pixel box in the
+ * (x, z) plane, with dy = 0 only (a 2D scan is Y = 1).
+ * eta: host [Z][k][k] FP64 (the spatial response of the transducer about
+ * its focus, caller-owned); eir: host [eir_len] FP64, eir_len odd, centred
+ * (s = -J .. J); K_out: host [Z][k][k][T] FP64, written.
+ * Errors: SHAPE for Z, k (odd), T out of the limits of swopt_geometry;
+ * INVALID_ARG for null pointers, dims not 2 or 3, a non-positive or
+ * non-finite lateral_ratio, a non-finite focal_depth, focal_sample outside
+ * [0, T) or an even eir_len. */
+swopt_status swopt_semicircle_kernel(int Z, int k, int T, int dims, double lateral_ratio,
+                                     double focal_depth, int focal_sample, const double* eta,
+                                     const double* eir, int eir_len, double* K_out);
+
 /* Operator facts: the time window [t0, t0 + tw) that holds every nonzero
  * kernel sample, the number of distinct switching states Q = min(N,
  * pulses_per_cycle) and the number of nonzero kernel entries. */

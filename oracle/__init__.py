@@ -5,7 +5,8 @@ optoacoustic hot path (arXiv 2510.23739): the switching matrix of
 Eq. (final-H)/(Sij-detailed), the forward H = W_tot S of Sec. 2.3 and
 Eq. (full-forward), its exact adjoint, the l1 and TV proximal maps of
 Eq. (prox)/(prox-dual) and Algorithm 2, FISTA (Algorithm 1), the power
-iteration for the step size, and the kappa/mu gradient of the data fit.
+iteration for the step size, the kappa/mu gradient of the data fit, and the
+paper-literal semicircle kernel of Eqs. (q-above-final)/(q-below-final).
 
 Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's
 CPU-baseline leg may import this package.  It shares no code with the CUDA
@@ -224,6 +225,20 @@ def power(geom, sw, K, v0, iters):
     S = switch_matrix(geom, sw)
     return float(lib().oracle_power(*_dims(geom), _p(S), _p(_f64(K)), _p(_f64(v0)),
                                     ctypes.c_int(iters)))
+
+
+def semicircle_kernel(Z, k, T, dims, rho, focal_depth, focal_sample, eta, eir):
+    """K[Z][k][k][T]: the paper-literal kernel of Eqs. (q-above-final) /
+    (q-below-final), the spatial response on the discrete half spheres of
+    each time sample, convolved along t with the centred impulse response."""
+    eta = _f64(eta).reshape(Z, k, k)
+    eir = _f64(eir).ravel()
+    K = np.empty((Z, k, k, T))
+    lib().oracle_semicircle_kernel(ctypes.c_int(Z), ctypes.c_int(k), ctypes.c_int(T),
+                                   ctypes.c_int(dims), ctypes.c_double(rho),
+                                   ctypes.c_double(focal_depth), ctypes.c_int(focal_sample),
+                                   _p(eta), _p(eir), ctypes.c_int(eir.size), _p(K))
+    return K
 
 
 def param_grad(geom, sw, K, c, y):

@@ -522,6 +522,73 @@ void oracle_param_grad(int N, int P, int Y, int X, int Z, int T, int k,
     free(phi); free(S); free(res); free(g);
 }
 
+/* The paper-literal per-depth kernel (Sec. 2.3.1 "Acoustic Model", Eqs.
+ * q-above-final and q-below-final, discrete semicircles of Eqs.
+ * discrete-upper-circle / discrete-lower-circle): the weight of depth j,
+ * lateral offset (dy, dx) and time sample t is eta[j][dy][dx] if the voxel
+ * meets the half sphere of radius |t - tf| about the focus (depth kf), on
+ * the side of the focus that sample t sees (upper for t < tf, lower for
+ * t > tf), else 0; then every column is convolved with the centred impulse
+ * response eir.  Units: depth pitches (time grid matched to the depth grid;
+ * one lateral pitch is rho depth pitches).  "Meets" is read as: the closed
+ * voxel box, clipped to the half space, holds a point at distance exactly
+ * the radius; as |p| is continuous on the (connected) box, that is: the
+ * nearest point of the box is within the radius and some corner is not
+ * inside it.  2D (dims 2): the (x, z) plane, dy = 0 only. */
+void oracle_semicircle_kernel(int Z, int k, int T, int dims, double rho, double kf, int tf,
+                              const double* eta, const double* eir, int eir_len, double* K)
+{
+    const int r = k / 2, J = eir_len / 2;
+    double* col = (double*)malloc(sizeof(double) * (size_t)T);
+    for (int j = 0; j < Z; ++j)
+        for (int iy = 0; iy < k; ++iy)
+            for (int ix = 0; ix < k; ++ix) {
+                const int dy = iy - r, dx = ix - r;
+                const double w = eta[((size_t)j * k + iy) * k + ix];
+                for (int t = 0; t < T; ++t) {
+                    col[t] = 0.0;
+                    if (dims == 2 && dy != 0) continue;
+                    double lo[3], hi[3];
+                    lo[0] = (dx - 0.5) * rho; hi[0] = (dx + 0.5) * rho;
+                    lo[1] = (dy - 0.5) * rho; hi[1] = (dy + 0.5) * rho;
+                    if (dims == 2) lo[1] = hi[1] = 0.0;
+                    lo[2] = (double)j - kf - 0.5; hi[2] = (double)j - kf + 0.5;
+                    if (t < tf && hi[2] > 0.0) hi[2] = 0.0;
+                    if (t > tf && lo[2] < 0.0) lo[2] = 0.0;
+                    if (lo[2] > hi[2]) continue;
+                    const double n2 = (double)(t - tf) * (double)(t - tf);
+                    /* nearest point of the box: the focus clamped into it */
+                    double near2 = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        double c = 0.0;
+                        if (c < lo[a]) c = lo[a];
+                        if (c > hi[a]) c = hi[a];
+                        near2 += c * c;
+                    }
+                    /* farthest point: one of the eight corners */
+                    double far2 = 0.0;
+                    for (int corner = 0; corner < 8; ++corner) {
+                        double d2 = 0.0;
+                        for (int a = 0; a < 3; ++a) {
+                            const double c = (corner >> a) & 1 ? hi[a] : lo[a];
+                            d2 += c * c;
+                        }
+                        if (d2 > far2) far2 = d2;
+                    }
+                    if (near2 <= n2 && far2 >= n2) col[t] = w;
+                }
+                /* each source sample u spreads over t = u + s, s in [-J, J] */
+                double* out = K + (((size_t)j * k + iy) * k + ix) * (size_t)T;
+                for (int t = 0; t < T; ++t) out[t] = 0.0;
+                for (int u = 0; u < T; ++u) {
+                    if (col[u] == 0.0) continue;
+                    for (int s = -J; s <= J; ++s)
+                        if (u + s >= 0 && u + s < T) out[u + s] += col[u] * eir[s + J];
+                }
+            }
+    free(col);
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP

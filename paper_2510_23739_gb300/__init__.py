@@ -123,6 +123,9 @@ _SIGS = {
                             ctypes.c_int], ctypes.c_int),
     "swopt_tc_config": ([ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 5,
                         ctypes.c_int),
+    "swopt_semicircle_kernel": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "swopt_tc_schedule": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "swopt_tc_schedule_info": ([ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4,
                                ctypes.c_int),
@@ -149,6 +152,25 @@ def lib():
 
 def library_path() -> str:
     return _build.LIB
+
+
+def semicircle_kernel(Z, k, T, dims, lateral_ratio, focal_depth, focal_sample, eta, eir):
+    """The paper-literal per-depth kernel K[Z][k][k][T] (FP64 numpy array):
+    the spatial response eta [Z][k][k] on the discrete half spheres of each
+    time sample (Eqs. q-above-final / q-below-final), convolved along t with
+    the centred impulse response eir.  Host only (no GPU); see
+    swopt_semicircle_kernel in include/swopt.h."""
+    import numpy as np
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    eir = np.ascontiguousarray(eir, dtype=np.float64)
+    if eta.shape != (Z, k, k) or eir.ndim != 1:
+        raise ValueError("eta must be [Z][k][k] and eir one-dimensional")
+    out = np.empty((Z, k, k, T), dtype=np.float64)
+    _check(lib().swopt_semicircle_kernel(int(Z), int(k), int(T), int(dims), float(lateral_ratio),
+                                         float(focal_depth), int(focal_sample),
+                                         eta.ctypes.data, eir.ctypes.data, int(eir.size),
+                                         out.ctypes.data))
+    return out
 
 
 def _check(status: int):

@@ -26,6 +26,8 @@ __all__ = [
     "workload",
     "transducer_kernel",
     "eir_taps",
+    "spr_image",
+    "matched_time_grid",
     "tube_phantom",
     "gaussian",
     "noise_sigma",
@@ -220,6 +222,36 @@ def transducer_kernel(geom: Geometry, seed: int = 0) -> np.ndarray:
         else:
             K[..., : geom.T + s] += q[..., -s:] * v[si]
     return K
+
+
+def matched_time_grid(geom: Geometry) -> Geometry:
+    """The same geometry with the time pitch set so that one sample of
+    travel distance equals one depth pitch (c dt = dz), the matched
+    measurement and image grids of the paper's discretised acoustic model."""
+    return replace(geom, dt_us=geom.dz_mm / geom.c_mm_per_us)
+
+
+def spr_image(geom: Geometry, seed: int = 0) -> np.ndarray:
+    """Synthetic spatial response eta[z][dy][dx] (FP64) of a focused
+    transducer about its focus, standing in for the measured SPR image that
+    the paper uses and does not publish: a Gaussian beam whose width grows
+    away from the focal plane (w(z) = w0 sqrt(1 + (z / zR)^2), w0 from the
+    aperture's numerical aperture), with a seeded multiplicative ripple of
+    a few per cent.  Depth z is measured from the focal plane (depths
+    centred on it, as in ``transducer_kernel``)."""
+    rng = np.random.default_rng(seed)
+    r = geom.r
+    na = geom.aperture_mm / geom.focal_mm
+    lam = geom.c_mm_per_us / geom.eir_mhz          # wavelength at the centre frequency
+    w0 = max(0.5 * lam / na, 0.5 * geom.dx_mm)
+    zr = math.pi * w0 * w0 / lam
+    z = (np.arange(geom.Z) - (geom.Z - 1) / 2.0) * geom.dz_mm
+    w = w0 * np.sqrt(1.0 + (z / zr) ** 2)
+    lat = np.arange(-r, r + 1) * geom.dx_mm
+    rho2 = lat[None, :, None] ** 2 + lat[None, None, :] ** 2
+    eta = np.exp(-rho2 / (2.0 * w[:, None, None] ** 2)) * (w0 / w)[:, None, None]
+    eta *= 1.0 + 0.03 * rng.standard_normal(eta.shape)
+    return eta
 
 
 def _segment_distance(p, a, b):

@@ -94,3 +94,36 @@ def test_null_handle_calls_fail_cleanly():
     assert L.swopt_fista_step(None, 1, None) == 1
     assert b"null handle" in L.swopt_last_error()
     assert L.swopt_version().decode().count(".") == 2
+
+
+@pytest.mark.parametrize("dims,rho,kf", [(2, 2.0, 3.5), (3, 2.0, 3.5), (3, 1.0, 4.0)])
+def test_semicircle_kernel_builder_matches_oracle(dims, rho, kf):
+    """The library's host builder of the paper-literal kernel against the
+    oracle's: the masks bit-exact (their decisions are exact in FP64 here),
+    the weighted and convolved kernel to FP64 rounding."""
+    import oracle
+    Z, k, T, tf = 10, 9, 30, 15
+    ones = np.ones((Z, k, k))
+    a = sw.semicircle_kernel(Z, k, T, dims, rho, kf, tf, ones, np.array([1.0]))
+    b = oracle.semicircle_kernel(Z, k, T, dims, rho, kf, tf, ones, np.array([1.0]))
+    assert np.array_equal(a, b) and a.any()
+    rng = np.random.default_rng(3)
+    eta = rng.random((Z, k, k))
+    eir = rng.standard_normal(7)
+    a = sw.semicircle_kernel(Z, k, T, dims, rho, kf, tf, eta, eir)
+    b = oracle.semicircle_kernel(Z, k, T, dims, rho, kf, tf, eta, eir)
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
+
+
+def test_semicircle_kernel_builder_rejects_bad_arguments():
+    ones = np.ones((4, 3, 3))
+    good = dict(Z=4, k=3, T=8, dims=3, lateral_ratio=1.0, focal_depth=1.5, focal_sample=4,
+                eta=ones, eir=np.array([1.0]))
+    sw.semicircle_kernel(**good)
+    for bad in (dict(dims=1), dict(lateral_ratio=0.0), dict(lateral_ratio=float("nan")),
+                dict(focal_sample=8), dict(focal_sample=-1), dict(eir=np.array([1.0, 2.0])),
+                dict(focal_depth=float("inf"))):
+        with pytest.raises(sw.SwoptError):
+            sw.semicircle_kernel(**{**good, **bad})
+    with pytest.raises(sw.SwoptError):
+        sw.semicircle_kernel(**{**good, "k": 4, "eta": np.ones((4, 4, 4))})

@@ -640,6 +640,39 @@ def test_tensor_core_schedule_rejects_bad_values(tc_cases):
         op.close()
 
 
+def _semicircle_problem(Y, dims):
+    """A small scan with the paper-literal kernel (SPR on discrete half
+    spheres, matched time grid).  The library's host builder makes the
+    kernel the GPU uses; the oracle builds its own for the expected values."""
+    g = synth.matched_time_grid(Geometry(X=13, Y=Y, Z=18, T=48, N=5, P=2, k=9,
+                                         pulses_per_cycle=4))
+    s = Switching((0.08, 0.0), (1.0, 0.0), (0.05, 1.0), 2.0)
+    args = (g.Z, g.k, g.T, dims, g.dx_mm / g.dz_mm, (g.Z - 1) / 2.0, g.T // 2,
+            synth.spr_image(g, seed=9), synth.eir_taps(g))
+    return g, s, sw.semicircle_kernel(*args), oracle.semicircle_kernel(*args)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+@pytest.mark.parametrize("Y,dims", [(11, 3), (1, 2)])
+def test_semicircle_kernel_operator_matches_oracle(Y, dims, prec):
+    """H and H^T with the paper-literal kernel (a thin shell per depth, the
+    very sparse kernel of Eqs. q-above-final / q-below-final), in 3D and on
+    a 2D scan (Y = 1), against the oracle."""
+    g, s, K, K_or = _semicircle_problem(Y, dims)
+    tol = {"fp32": 1e-5, **TC_TOL}[prec]
+    op = sw.Operator(g, K, s, precision=prec)
+    try:
+        c = np.random.default_rng(50).standard_normal(g.c_shape())
+        yv = np.random.default_rng(51).standard_normal(g.y_shape())
+        f = host(op.forward(dev(c)))
+        a = host(op.adjoint(dev(yv)))
+        op.check_device()
+        assert rel(f, oracle.forward(g, s, K_or, c)) <= tol
+        assert rel(a, oracle.adjoint(g, s, K_or, yv)) <= tol
+    finally:
+        op.close()
+
+
 def test_tensor_core_accumulators_option(tc_cases):
     """One accumulator per tile (corrections summed with the main products)
     stays within the split tolerance; two is the default of the split mode."""

@@ -490,3 +490,127 @@ def test_incremental_gradient_fista_equals_algorithm_1():
             c, G = cn, Gn
         ref = oracle.fista(g, sw, K, y, alpha, iters, lam1, lamtv, inner)
         assert np.linalg.norm(c - ref) <= 1e-12 * np.linalg.norm(ref), R
+
+
+# --------------------------------------------------------------------------
+# Paper-literal acoustic kernel (Sec. 2.3.1 "Acoustic Model", Eqs.
+# q-above-final / q-below-final, discrete semicircles)
+# --------------------------------------------------------------------------
+
+def _shell_mask(Z, k, T, dims, rho, kf, tf):
+    """The oracle's mask: eta = 1 and a unit impulse response."""
+    return oracle.semicircle_kernel(Z, k, T, dims, rho, kf, tf, np.ones((Z, k, k)),
+                                    np.array([1.0])) != 0.0
+
+
+def _brute_meets(lo, hi, n):
+    """Does the closed box [lo, hi] hold a point at distance exactly n from 0?
+    |p|^2 - n^2 evaluated on a grid of each box: every corner, a 9-point
+    subdivision of each edge, and 0 on every axis the box spans (where the
+    minimum of |p| lies); continuity on the connected box does the rest."""
+    axes = []
+    for a in range(3):
+        pts = set(np.linspace(lo[a], hi[a], 9).tolist())
+        if lo[a] <= 0.0 <= hi[a]:
+            pts.add(0.0)
+        axes.append(np.array(sorted(pts)))
+    f = (axes[0][:, None, None] ** 2 + axes[1][None, :, None] ** 2
+         + axes[2][None, None, :] ** 2 - n * n)
+    return f.min() <= 0.0 <= f.max()
+
+
+@pytest.mark.parametrize("dims,rho,kf", [(2, 1.0, 4.0), (2, 2.0, 3.5), (3, 1.0, 3.5),
+                                          (3, 2.0, 4.0)])
+def test_semicircle_mask_matches_brute_force(dims, rho, kf):
+    """Voxel by voxel and sample by sample against the definition, evaluated
+    by brute force on each (clipped) box."""
+    Z, k, T, tf = 9, 7, 20, 10
+    M = _shell_mask(Z, k, T, dims, rho, kf, tf)
+    r = k // 2
+    for j in range(Z):
+        for iy in range(k):
+            for ix in range(k):
+                dy, dx = iy - r, ix - r
+                for t in range(T):
+                    want = False
+                    if dims == 3 or dy == 0:
+                        lo = [(dx - 0.5) * rho, (dy - 0.5) * rho if dims == 3 else 0.0,
+                              j - kf - 0.5]
+                        hi = [(dx + 0.5) * rho, (dy + 0.5) * rho if dims == 3 else 0.0,
+                              j - kf + 0.5]
+                        if t < tf:
+                            hi[2] = min(hi[2], 0.0)
+                        if t > tf:
+                            lo[2] = max(lo[2], 0.0)
+                        want = lo[2] <= hi[2] and _brute_meets(lo, hi, float(abs(t - tf)))
+                    assert M[j, iy, ix, t] == want, (j, dy, dx, t)
+
+
+def test_semicircle_points_on_the_sphere_lie_in_the_mask():
+    """Random points exactly on the half sphere of sample t (away from voxel
+    faces) fall in voxels of the mask, on the side of the focus that the
+    sample sees: above the focus before the focal sample, below after."""
+    Z, k, T, tf, kf, rho = 13, 11, 26, 13, 6.0, 1.0
+    M = _shell_mask(Z, k, T, 3, rho, kf, tf)
+    r = k // 2
+    rng = np.random.default_rng(5)
+    hits = 0
+    for t in range(T):
+        n = abs(t - tf)
+        if n == 0 or n > 5:
+            continue
+        u = rng.standard_normal((400, 3))
+        u /= np.linalg.norm(u, axis=1)[:, None]
+        p = n * u
+        p[:, 2] = -np.abs(p[:, 2]) if t < tf else np.abs(p[:, 2])
+        cell = p / np.array([rho, rho, 1.0])
+        idx = np.rint(cell)
+        away = np.all(np.abs(np.abs(cell - idx) - 0.5) > 1e-6, axis=1)
+        for (x, y, z), ok in zip(idx.astype(int), away):
+            if not ok:
+                continue
+            j = z + int(kf)
+            assert M[j, y + r, x + r, t], (t, x, y, z)
+            hits += 1
+    assert hits > 1000
+
+
+def test_semicircle_sources_above_focus_arrive_before_it():
+    """One source voxel at depth offset -d (above the focus) on the axis is
+    heard only at sample t_F - d, one at +d only at t_F + d (Eqs.
+    q-above-2d / q-below-2d: the upper semicircle before the focal time,
+    the lower after); the focal voxel only at t_F."""
+    Z, k, T, tf, kf = 11, 5, 24, 12, 5.0
+    M = _shell_mask(Z, k, T, 2, 1.0, kf, tf)
+    r = k // 2
+    for d in range(0, 5):
+        up = np.nonzero(M[int(kf) - d, r, r])[0].tolist()
+        down = np.nonzero(M[int(kf) + d, r, r])[0].tolist()
+        assert up == [tf - d] and down == [tf + d], (d, up, down)
+    # a half-integer focus: the two voxels around it both hold it
+    Mh = _shell_mask(6, 3, 10, 3, 1.0, 2.5, 5)
+    assert sorted(zip(*np.nonzero(Mh[..., 5]))) == [(2, 1, 1), (3, 1, 1)]
+
+
+def test_semicircle_kernel_weights_and_impulse_response():
+    """K = eta on the mask, convolved along t with the centred impulse
+    response: a response with a single tap at s = +1 delays every column by
+    one sample; a symmetric three-tap response is the sum of shifts; in 2D
+    only dy = 0 carries weight, and the mask is even in dx."""
+    Z, k, T, tf, kf = 7, 5, 16, 8, 3.0
+    rng = np.random.default_rng(7)
+    eta = rng.random((Z, k, k)) + 0.5
+    M = _shell_mask(Z, k, T, 3, 2.0, kf, tf)
+    K0 = oracle.semicircle_kernel(Z, k, T, 3, 2.0, kf, tf, eta, np.array([1.0]))
+    assert np.array_equal(K0, np.where(M, eta[..., None], 0.0))
+    K1 = oracle.semicircle_kernel(Z, k, T, 3, 2.0, kf, tf, eta, np.array([0.0, 0.0, 1.0]))
+    assert np.array_equal(K1[..., 1:], K0[..., :-1]) and not K1[..., 0].any()
+    v = np.array([0.25, 0.5, -0.75])
+    K3 = oracle.semicircle_kernel(Z, k, T, 3, 2.0, kf, tf, eta, v)
+    want = 0.5 * K0
+    want[..., 1:] += -0.75 * K0[..., :-1]
+    want[..., :-1] += 0.25 * K0[..., 1:]
+    assert np.allclose(K3, want, rtol=0, atol=1e-15)
+    M2 = _shell_mask(Z, k, T, 2, 2.0, kf, tf)
+    assert not M2[:, [0, 1, 3, 4]].any() and M2[:, 2].any()
+    assert np.array_equal(M2, M2[:, :, ::-1]) and np.array_equal(M, M[:, ::-1, ::-1])
