@@ -306,6 +306,73 @@ def run_swopt(args, rank, world, device):
     return result
 
 
+def run_two_step(args, device):
+    """The two-step approach (per-pulse acoustic inversion with TV, then
+    unmixing with l1 + TV; swopt_two_step) against the one-step solve on the
+    same data, both FP32 with `steps` FISTA iterations per solve and steps
+    from the power iteration computed before the timed region."""
+    import torch
+    from dataclasses import replace
+    import paper_2510_23739_gb300 as sw
+
+    prob = workload_problem(args.workload, args.kernel)
+    g = prob.geom
+    op, K, c_true, y = make_problem(prob, seed=0, device=device, kernel=args.kernel)
+    g1 = replace(g, N=1, P=1, pulses_per_cycle=1)
+    s1 = synth.Switching((0.0,), (0.0,), (1.0,), 0.0)
+    op1 = sw.Operator(g1, K, s1)
+    eye = np.zeros((g.Z, 1, 1, g.Z))
+    for j in range(g.Z):
+        eye[j, 0, 0, j] = 1.0
+    op2 = sw.Operator(replace(g, T=g.Z, k=1), eye, prob.sw)
+    a0, a1, a2 = (1.0 / o.lipschitz(100) for o in (op, op1, op2))
+    op1.close()
+    op2.close()
+    iters = args.steps
+    acoustic = sw.SolveParams(step=a1, lambda_l1=0.0, lambda_tv=prob.lam_tv,
+                              inner_iters=prob.inner, max_iters=iters)
+    unmixing = sw.SolveParams(step=a2, lambda_l1=prob.lam_l1, lambda_tv=prob.lam_tv,
+                              inner_iters=prob.inner, max_iters=iters)
+    one = sw.SolveParams(step=a0, lambda_l1=prob.lam_l1, lambda_tv=prob.lam_tv,
+                         inner_iters=prob.inner, max_iters=iters)
+    stream = torch.cuda.current_stream()
+    sw.two_step(g, K, prob.sw, y, replace_iters(acoustic, 2), replace_iters(unmixing, 2))
+    op.solve(y, replace_iters(one, 2))
+    times = {}
+    for name, fn in (("two_step", lambda: sw.two_step(g, K, prob.sw, y, acoustic, unmixing)),
+                     ("one_step", lambda: op.solve(y, one))):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1)
+        if name == "two_step":
+            c2 = out[0]
+        else:
+            c1 = out[0]
+    ct = c_true.double()
+    err = {k: float((v.double() - ct).norm() / ct.norm()) for k, v in (("two_step", c2),
+                                                                       ("one_step", c1))}
+    print(json.dumps({
+        "metric": "two-step reconstruction time", "value": times["two_step"], "unit": "ms",
+        "higher_is_better": False, "n_gpus": 1, "steps": iters, "dtype": "f32",
+        "data": "synthetic (seeded tube phantom, transducer kernel, 20 dB noise)",
+        "config": {"workload": args.workload, "kernel": args.kernel,
+                   "iterations_per_solve": iters, "pulses": g.N},
+        "one_step_ms_same_iterations": times["one_step"],
+        "relative_error_vs_phantom": err}), flush=True)
+
+
+def replace_iters(params, iters):
+    import copy
+    p = copy.copy(params)
+    p.max_iters = iters
+    return p
+
+
 def run_batch(args, device):
     """Sixteen independent problems of uneven size (scan 32^2..128^2, depths
     48-128, T 128-512, 20-80 pulses, 2-3 species, supports 11-31; seeded):
@@ -477,6 +544,8 @@ def main():
     ap.add_argument("--impl", default="swopt", choices=["swopt", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--method", default="one-step", choices=["one-step", "two-step"],
+                    help="two-step: time swopt_two_step against the one-step solve (FP32)")
     ap.add_argument("--kernel", default="aperture", choices=["aperture", "semicircle"],
                     help="per-depth kernel: the aperture-point transducer model, or the "
                          "paper-literal SPR on discrete half spheres (matched time grid)")
@@ -510,6 +579,12 @@ def main():
 
     import paper_2510_23739_gb300 as sw
     sw.lib()
+    if args.method == "two-step":
+        if rank == 0:
+            run_two_step(args, device)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     if args.workload == "batch16":
         if rank == 0:
             run_batch(args, device)

@@ -205,6 +205,26 @@ swopt_status swopt_fista_get(swopt_handle* h, float* c_dev, void* stream);
 swopt_status swopt_solve(swopt_handle* h, const float* y_dev, float* c_dev,
                          const swopt_solve_params* prm, swopt_solve_stats* stats, void* stream);
 
+/* The two-step approach (the paper's "Two-Step Approach", the comparison
+ * method of the one-step reconstruction): first the acoustic problem of
+ * Eq. (acoustic-inverse) with R1 = lambda_tv TV (+ lambda_l1 l1 if nonzero),
+ * pulse by pulse (W_tot is block diagonal over pulses), for b[N][Y][X][Z];
+ * then the unmixing problem of Eq. (unmixing), min 1/2||S c - b||^2 +
+ * lambda_l1 ||c||_1 + lambda_tv TV(c) + delta_{>=0}(c), for c[P][Y][X][Z].
+ * Both are solved with Algorithm 1 (swopt_solve semantics: a step <= 0 is
+ * taken from power iteration) on internal handles created and released by
+ * the call: the first with the caller's kernel and an identity switching
+ * model, the second with the caller's switching model and an identity
+ * acoustic kernel.  geom, K_host and sw as for swopt_create; y_dev: device
+ * [N][Y][X][T] (the data p); b_dev: device [N][Y][X][Z], caller-owned,
+ * receives the acoustic reconstruction; c_dev: device [P][Y][X][Z] receives
+ * the unmixed concentrations.  Precision FP32.  Errors as for swopt_create
+ * and swopt_solve (the message of the failing step is kept).  Synchronises. */
+swopt_status swopt_two_step(const swopt_geometry* geom, const double* K_host,
+                            const swopt_switching* sw, const float* y_dev, float* b_dev,
+                            float* c_dev, const swopt_solve_params* acoustic,
+                            const swopt_solve_params* unmixing, void* stream);
+
 /* Objective of Eq. (one-step), in FP64: *F = 1/2||H c - y||^2 + lambda_tv sum_p TV(c_p)
  * + lambda_l1 ||c||_1, *fit = the data-fit term (either may be NULL).  c is not
  * checked for nonnegativity.  Synchronises. */

@@ -6,7 +6,8 @@ Eq. (final-H)/(Sij-detailed), the forward H = W_tot S of Sec. 2.3 and
 Eq. (full-forward), its exact adjoint, the l1 and TV proximal maps of
 Eq. (prox)/(prox-dual) and Algorithm 2, FISTA (Algorithm 1), the power
 iteration for the step size, the kappa/mu gradient of the data fit, and the
-paper-literal semicircle kernel of Eqs. (q-above-final)/(q-below-final).
+paper-literal semicircle kernel of Eqs. (q-above-final)/(q-below-final), and
+the two-step approach (Eqs. (acoustic-inverse), (unmixing)).
 
 Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's
 CPU-baseline leg may import this package.  It shares no code with the CUDA
@@ -225,6 +226,23 @@ def power(geom, sw, K, v0, iters):
     S = switch_matrix(geom, sw)
     return float(lib().oracle_power(*_dims(geom), _p(S), _p(_f64(K)), _p(_f64(v0)),
                                     ctypes.c_int(iters)))
+
+
+def two_step(geom, sw, K, y, alpha1, iters1, lam_l1_1, lam_tv_1, inner1,
+             alpha2, iters2, lam_l1_2, lam_tv_2, inner2):
+    """The two-step approach: per-pulse acoustic inversion (Eq.
+    (acoustic-inverse)) into b[N][Y][X][Z], then unmixing (Eq. (unmixing))
+    into c[P][Y][X][Z]; returns (c, b)."""
+    S = switch_matrix(geom, sw)
+    b = np.empty((geom.N, geom.Y, geom.X, geom.Z))
+    c = np.empty(geom.c_shape())
+    lib().oracle_two_step(*_dims(geom), _p(S), _p(_f64(K)), _p(_f64(y)),
+                          ctypes.c_double(alpha1), ctypes.c_int(iters1),
+                          ctypes.c_double(lam_l1_1), ctypes.c_double(lam_tv_1), ctypes.c_int(inner1),
+                          ctypes.c_double(alpha2), ctypes.c_int(iters2),
+                          ctypes.c_double(lam_l1_2), ctypes.c_double(lam_tv_2), ctypes.c_int(inner2),
+                          _p(b), _p(c))
+    return c, b
 
 
 def semicircle_kernel(Z, k, T, dims, rho, focal_depth, focal_sample, eta, eir):

@@ -589,6 +589,34 @@ void oracle_semicircle_kernel(int Z, int k, int T, int dims, double rho, double 
     free(col);
 }
 
+/* The two-step approach (the paper's "Two-Step Approach"): the acoustic
+ * problem of Eq. (acoustic-inverse) and then the unmixing problem of Eq.
+ * (unmixing), each by Algorithm 1 (oracle_fista, Beck-Teboulle momentum).
+ * W_tot is block diagonal over the pulses, so the acoustic problem is solved
+ * pulse by pulse with the switching matrix 1 (one species, weight 1 at
+ * every depth); the unmixing operator is S alone, which is H with the
+ * depth-to-time identity as its acoustic kernel (k = 1, T = Z).
+ * S: [N][P][Z]; yv: [N][Y][X][T]; b_out: [N][Y][X][Z]; c_out: [P][Y][X][Z]. */
+void oracle_two_step(int N, int P, int Y, int X, int Z, int T, int k,
+                     const double* S, const double* K, const double* yv,
+                     double alpha1, int iters1, double lam_l1_1, double lam_tv_1, int inner1,
+                     double alpha2, int iters2, double lam_l1_2, double lam_tv_2, int inner2,
+                     double* b_out, double* c_out)
+{
+    const size_t yxt = (size_t)Y * X * T, yxz = (size_t)Y * X * Z;
+    double* S1 = (double*)malloc(sizeof(double) * (size_t)Z);
+    for (int j = 0; j < Z; ++j) S1[j] = 1.0;
+    for (int n = 0; n < N; ++n)
+        oracle_fista(1, 1, Y, X, Z, T, k, S1, K, yv + (size_t)n * yxt, alpha1, iters1, lam_l1_1,
+                     lam_tv_1, inner1, 0, 0, b_out + (size_t)n * yxz, NULL);
+    double* eye = (double*)calloc((size_t)Z * Z, sizeof(double));
+    for (int j = 0; j < Z; ++j) eye[(size_t)j * Z + j] = 1.0;
+    oracle_fista(N, P, Y, X, Z, Z, 1, S, eye, b_out, alpha2, iters2, lam_l1_2, lam_tv_2, inner2,
+                 0, 0, c_out, NULL);
+    free(S1);
+    free(eye);
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP

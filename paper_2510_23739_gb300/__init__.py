@@ -123,6 +123,9 @@ _SIGS = {
                             ctypes.c_int], ctypes.c_int),
     "swopt_tc_config": ([ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 5,
                         ctypes.c_int),
+    "swopt_two_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                        ctypes.c_void_p], ctypes.c_int),
     "swopt_semicircle_kernel": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
@@ -466,6 +469,37 @@ class Operator:
         n = ctypes.c_int64()
         _check(lib().swopt_launch_count(self._h, ctypes.byref(n)))
         return n.value
+
+
+def two_step(geom, K, sw, y, acoustic: "SolveParams", unmixing: "SolveParams", b_out=None,
+             c_out=None, stream=None):
+    """The two-step approach: per-pulse acoustic inversion (TV) into b
+    [N][Y][X][Z], then unmixing (l1 + TV) of b into c [P][Y][X][Z]; see
+    swopt_two_step.  Returns (c, b)."""
+    import torch
+    g = _Geometry(int(geom.X), int(geom.Y), int(geom.Z), int(geom.T), int(geom.N),
+                  int(geom.P), int(geom.k), int(geom.pulses_per_cycle), float(geom.dz_mm))
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    if K.shape != (geom.Z, geom.k, geom.k, geom.T):
+        raise ValueError(f"kernel shape {K.shape} does not match the geometry")
+    arrs = [np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+            for v in (sw.kappa, sw.eps_bar, sw.eps_off)]
+    if any(a.shape != (geom.P,) for a in arrs):
+        raise ValueError("switching parameters must have one entry per species")
+    dp = ctypes.POINTER(ctypes.c_double)
+    s = _Switching(*(a.ctypes.data_as(dp) for a in arrs), float(sw.mu_per_mm))
+    b_shape = (geom.N, geom.Y, geom.X, geom.Z)
+    c_shape = (geom.P, geom.Y, geom.X, geom.Z)
+    if b_out is None:
+        b_out = torch.empty(b_shape, device=y.device, dtype=torch.float32)
+    if c_out is None:
+        c_out = torch.empty(c_shape, device=y.device, dtype=torch.float32)
+    pa, pu = acoustic._c(None), unmixing._c(None)
+    _check(lib().swopt_two_step(ctypes.byref(g), K.ctypes.data, ctypes.byref(s),
+                                _ptr(y, (geom.N, geom.Y, geom.X, geom.T), "y"),
+                                _ptr(b_out, b_shape, "b"), _ptr(c_out, c_shape, "c"),
+                                ctypes.byref(pa), ctypes.byref(pu), _stream(stream)))
+    return c_out, b_out
 
 
 class Batch:

@@ -5,6 +5,8 @@
 #include <cstdarg>
 #include <cstring>
 #include <algorithm>
+#include <cstdio>
+#include <vector>
 
 #include "swopt_internal.cuh"
 
@@ -1010,6 +1012,59 @@ swopt_status swopt_solve(swopt_handle* h, const float* y_dev, float* c_dev,
         SW_CUDA(cudaStreamSynchronize(st));
     }
     return SWOPT_OK;
+}
+
+// The two-step approach (the paper's "Two-Step Approach"): first the acoustic
+// problem of Eq. (acoustic-inverse), which separates over the pulses because
+// W_tot is block diagonal, solved pulse by pulse on one handle whose
+// switching model is the identity (one species, no switching, no fluence
+// decay), then the unmixing problem of Eq. (unmixing) on a handle whose
+// acoustic kernel is the identity (k = 1, T = Z, K[j][0][0][t] = [t = j]), so
+// that its forward operator is S itself.  Both solves run Algorithm 1 with
+// the caller's parameters (R1 = lambda_tv TV, R2 = lambda_l1 l1 + lambda_tv TV).
+swopt_status swopt_two_step(const swopt_geometry* geom, const double* K_host,
+                            const swopt_switching* sw, const float* y_dev, float* b_dev,
+                            float* c_dev, const swopt_solve_params* acoustic,
+                            const swopt_solve_params* unmixing, void* stream)
+{
+    clear_error();
+    if (!geom || !K_host || !sw || !y_dev || !b_dev || !c_dev || !acoustic || !unmixing) {
+        set_error("null argument");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    auto keep_error = [](swopt_status s, swopt_handle* h) {
+        char msg[sizeof(g_err)];
+        std::snprintf(msg, sizeof(msg), "%s", g_err);
+        swopt_destroy(h);
+        if (s != SWOPT_OK) set_error("%s", msg);
+        return s;
+    };
+    // step 1: per pulse, H = W (one species with weight 1 at every depth)
+    swopt_geometry g1 = *geom;
+    g1.N = 1;
+    g1.P = 1;
+    g1.pulses_per_cycle = 1;
+    const double zero = 0.0, one = 1.0;
+    const swopt_switching s1 = {&zero, &zero, &one, 0.0};
+    swopt_handle* h1 = nullptr;
+    SW_TRY(swopt_create(&g1, K_host, &s1, &h1));
+    const size_t yxt = (size_t)geom->Y * geom->X * geom->T;
+    const size_t yxz = (size_t)geom->Y * geom->X * geom->Z;
+    swopt_status s = SWOPT_OK;
+    for (int n = 0; n < geom->N && s == SWOPT_OK; ++n)
+        s = swopt_solve(h1, y_dev + (size_t)n * yxt, b_dev + (size_t)n * yxz, acoustic, nullptr,
+                        stream);
+    SW_TRY(keep_error(s, h1));
+    // step 2: H = S (identity acoustic kernel; b is read as the data [N][Y][X][T = Z])
+    swopt_geometry g2 = *geom;
+    g2.T = geom->Z;
+    g2.k = 1;
+    std::vector<double> eye((size_t)geom->Z * geom->Z, 0.0);
+    for (int j = 0; j < geom->Z; ++j) eye[(size_t)j * geom->Z + j] = 1.0;
+    swopt_handle* h2 = nullptr;
+    SW_TRY(swopt_create(&g2, eye.data(), sw, &h2));
+    s = swopt_solve(h2, b_dev, c_dev, unmixing, nullptr, stream);
+    return keep_error(s, h2);
 }
 
 swopt_status swopt_objective(swopt_handle* h, const float* c_dev, const float* y_dev,

@@ -673,6 +673,33 @@ def test_semicircle_kernel_operator_matches_oracle(Y, dims, prec):
         op.close()
 
 
+def test_two_step_matches_oracle():
+    """The two-step approach (per-pulse acoustic inversion with TV, then
+    unmixing with l1 + TV) against the oracle's, with the same steps: the
+    acoustic images b and the concentrations c within the FISTA tolerance."""
+    from dataclasses import replace
+    g, s = TINY.geom, TINY.sw
+    K = synth.transducer_kernel(g, seed=0)
+    c_true = synth.tube_phantom(g, 4, seed=3)
+    y = oracle.forward(g, s, K, c_true)
+    y = y + 0.02 * np.abs(y).max() * synth.gaussian(g.y_shape(), 11)
+    g1 = replace(g, N=1, P=1, pulses_per_cycle=1)
+    s1 = Switching((0.0,), (0.0,), (1.0,), 0.0)
+    L1 = oracle.power(g1, s1, K, synth.gaussian(g1.c_shape(), 12), 60)
+    S = oracle.switch_matrix(g, s)
+    L2 = max(np.linalg.norm(S[:, :, j], 2) ** 2 for j in range(g.Z))
+    a1, a2 = 0.9 / L1, 0.9 / L2
+    acoustic = sw.SolveParams(step=a1, lambda_l1=0.0, lambda_tv=2e-3, inner_iters=10,
+                              max_iters=20)
+    unmixing = sw.SolveParams(step=a2, lambda_l1=1e-3, lambda_tv=1e-3, inner_iters=10,
+                              max_iters=20)
+    c, b = sw.two_step(g, K, s, dev(y), acoustic, unmixing)
+    torch.cuda.synchronize()
+    c_or, b_or = oracle.two_step(g, s, K, y, a1, 20, 0.0, 2e-3, 10, a2, 20, 1e-3, 1e-3, 10)
+    assert rel(host(b), b_or) <= 1e-4
+    assert rel(host(c), c_or) <= 1e-4
+
+
 def test_tensor_core_accumulators_option(tc_cases):
     """One accumulator per tile (corrections summed with the main products)
     stays within the split tolerance; two is the default of the split mode."""

@@ -614,3 +614,68 @@ def test_semicircle_kernel_weights_and_impulse_response():
     M2 = _shell_mask(Z, k, T, 2, 2.0, kf, tf)
     assert not M2[:, [0, 1, 3, 4]].any() and M2[:, 2].any()
     assert np.array_equal(M2, M2[:, :, ::-1]) and np.array_equal(M, M[:, ::-1, ::-1])
+
+
+# --------------------------------------------------------------------------
+# Two-step approach (Eqs. acoustic-inverse and unmixing)
+# --------------------------------------------------------------------------
+
+def test_two_step_acoustic_part_equals_the_joint_block_diagonal_solve():
+    """The acoustic problem over all pulses at once (W_tot block diagonal:
+    the pulses as N 'species' with the identity switching matrix, TV summed
+    over them) gives, with the same step, the per-pulse solves' iterates:
+    the separation the two-step oracle relies on."""
+    g, sw, K, y = _small_problem()
+    alpha, iters, lam_tv, inner = 0.02, 15, 0.03, 8
+    _, b = oracle.two_step(g, sw, K, y, alpha, iters, 0.0, lam_tv, inner,
+                           0.01, 1, 0.0, 0.0, 0)
+    S_id = np.zeros((g.N, g.N, g.Z))
+    for n in range(g.N):
+        S_id[n, n, :] = 1.0
+    joint = np.empty((g.N, g.Y, g.X, g.Z))
+    oracle.lib().oracle_fista(*[ctypes_int(v) for v in (g.N, g.N, g.Y, g.X, g.Z, g.T, g.k)],
+                              oracle._p(S_id), oracle._p(np.ascontiguousarray(K)),
+                              oracle._p(np.ascontiguousarray(y)), ctypes_double(alpha),
+                              ctypes_int(iters), ctypes_double(0.0), ctypes_double(lam_tv),
+                              ctypes_int(inner), ctypes_int(0), ctypes_int(0), oracle._p(joint),
+                              ctypes_void(0))
+    assert np.abs(b - joint).max() <= 1e-12 * np.abs(joint).max()
+
+
+def test_two_step_unmixing_recovers_exact_concentrations():
+    """Unmixing exact data b = S c_true (no regularisation, a well-posed S:
+    N = 4 pulses over 2 species) converges to c_true, the per-voxel least
+    squares solution of numpy's lstsq; the acoustic step with an identity
+    acoustic kernel and exact data returns that data."""
+    g = _geom(X=3, Y=2, Z=3, T=3, N=4, P=2, k=1, pulses_per_cycle=4)
+    sw = Switching(kappa=(1.2, 0.0), eps_bar=(1.0, 0.0), eps_off=(0.1, 1.0), mu_per_mm=2.0)
+    rng = np.random.default_rng(4)
+    c_true = rng.random(g.c_shape()) + 0.2
+    S = oracle.switch_matrix(g, sw)
+    b_true = np.einsum("npj,pyxj->nyxj", S, c_true)
+    eye = np.zeros(g.k_shape())
+    for j in range(g.Z):
+        eye[j, 0, 0, j] = 1.0
+    lip = max(np.linalg.norm(S[:, :, j], 2) ** 2 for j in range(g.Z))
+    c, b = oracle.two_step(g, sw, eye, b_true, 1.0, 60, 0.0, 0.0, 0,
+                           1.0 / lip, 6000, 0.0, 0.0, 0)
+    assert np.abs(b - b_true).max() <= 1e-10
+    for j in range(g.Z):
+        sol = np.linalg.lstsq(S[:, :, j], b_true[:, :, :, j].reshape(g.N, -1), rcond=None)[0]
+        assert np.abs(sol.reshape(g.P, g.Y, g.X) - c_true[..., j]).max() <= 1e-10
+    assert np.abs(c - c_true).max() <= 1e-6 * np.abs(c_true).max()
+
+
+def ctypes_int(v):
+    import ctypes
+    return ctypes.c_int(int(v))
+
+
+def ctypes_double(v):
+    import ctypes
+    return ctypes.c_double(float(v))
+
+
+def ctypes_void(v):
+    import ctypes
+    return ctypes.c_void_p(v)
