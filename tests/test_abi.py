@@ -93,6 +93,11 @@ def test_null_handle_calls_fail_cleanly():
     assert L.swopt_set_precision(None, 0) == 1
     assert L.swopt_fista_step(None, 1, None) == 1
     assert b"null handle" in L.swopt_last_error()
+    assert L.swopt_tc_schedule(None, 0, 1, 1) == 1
+    i = ctypes.c_int()
+    assert L.swopt_tc_schedule_info(None, 0, *[ctypes.byref(i)] * 4) == 1
+    assert L.swopt_two_step(None, None, None, None, None, None, None, None, None) == 1
+    assert b"null" in L.swopt_last_error()
     assert L.swopt_version().decode().count(".") == 2
 
 
