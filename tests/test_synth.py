@@ -71,3 +71,19 @@ def test_batch_shapes_are_in_range():
         assert 128 <= g.T <= 512 and g.T % 16 == 0
         assert 20 <= g.N <= 80 and g.N % 10 == 0 and g.P in (2, 3)
         assert g.k % 2 == 1 and 11 <= g.k <= 31
+
+
+def test_spr_image_is_a_seeded_beam_narrowest_at_the_focus():
+    g = synth.matched_time_grid(synth.workload("medium_64x64x64_T256_k15_N40_P2").geom)
+    assert abs(g.c_mm_per_us * g.dt_us - g.dz_mm) < 1e-15
+    a, b = synth.spr_image(g, seed=2), synth.spr_image(g, seed=2)
+    assert np.array_equal(a, b) and not np.array_equal(a, synth.spr_image(g, seed=3))
+    r = g.r
+    # on-axis amplitude peaks at the focal plane; off-axis energy spreads away from it
+    axis = a[:, r, r]
+    mid = (g.Z - 1) / 2.0
+    centre = axis[int(mid) - 2:int(mid) + 3].mean()
+    assert centre > 2.0 * axis[0] and centre > 2.0 * axis[-1]
+    width = (a * (np.arange(-r, r + 1)[None, None, :] ** 2)).sum(axis=(1, 2)) / a.sum(axis=(1, 2))
+    assert width[0] > width[int(mid)] and width[-1] > width[int(mid)]
+    assert np.all(a > 0)
