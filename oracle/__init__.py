@@ -7,7 +7,9 @@ Eq. (full-forward), its exact adjoint, the l1 and TV proximal maps of
 Eq. (prox)/(prox-dual) and Algorithm 2, FISTA (Algorithm 1), the power
 iteration for the step size, the kappa/mu gradient of the data fit, and the
 paper-literal semicircle kernel of Eqs. (q-above-final)/(q-below-final), and
-the two-step approach (Eqs. (acoustic-inverse), (unmixing)).
+the two-step approach (Eqs. (acoustic-inverse), (unmixing)), and the
+proximal map of the full R3 with its lambda_3 term (Algorithm 2 on the
+stacked L).
 
 Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's
 CPU-baseline leg may import this package.  It shares no code with the CUDA
@@ -195,6 +197,25 @@ def prox(z, alpha, lam_l1, lam_tv, inner, momentum="beck_teboulle"):
                       ctypes.c_double(lam_tv), ctypes.c_int(inner),
                       ctypes.c_int(MOMENTUM[momentum]))
     return x
+
+
+def prox_joint(geom, sw, z, alpha, lam_tv, lam_l1, lam_b, iters, step2,
+               momentum="beck_teboulle", return_dual=False):
+    """prox of alpha (R3 + delta_{>=0}) with the lambda_3 term (Eq.
+    (reg-tv-l1-one)) by Algorithm 2 on the stacked L; returns x (and the
+    dual u = [uc (P x 3L), ul (P L), ub (N x 3L)] if asked)."""
+    S = switch_matrix(geom, sw)
+    z = _f64(z).reshape(geom.c_shape())
+    x = np.empty(geom.c_shape())
+    L = geom.Y * geom.X * geom.Z
+    u = np.empty(geom.P * 4 * L + geom.N * 3 * L) if return_dual else None
+    lib().oracle_prox_joint(ctypes.c_int(geom.N), ctypes.c_int(geom.P), ctypes.c_int(geom.Y),
+                            ctypes.c_int(geom.X), ctypes.c_int(geom.Z), _p(S), _p(z), _p(x),
+                            ctypes.c_double(alpha), ctypes.c_double(lam_tv),
+                            ctypes.c_double(lam_l1), ctypes.c_double(lam_b), ctypes.c_int(iters),
+                            ctypes.c_double(step2), ctypes.c_int(MOMENTUM[momentum]),
+                            _p(u) if return_dual else ctypes.c_void_p(0))
+    return (x, u) if return_dual else x
 
 
 def objective(geom, sw, K, c, y, lam_l1, lam_tv):

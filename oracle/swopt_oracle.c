@@ -358,6 +358,107 @@ void oracle_prox(int P, int Y, int X, int Z, const double* z, double* x,
     oracle_prox_l1(n, x, alpha * lam_l1, 1);
 }
 
+/* ---------------------------------------------------------------------------
+ * The proximal map of alpha (R3 + delta_{>=0}) with all three terms of Eq.
+ * (reg-tv-l1-one), by Algorithm 2 on the stacked operator
+ *   L v = [ lam_tv D v_p  (p = 0..P-1) ;  lam_l1 v ;  lam_b D (S v)^n  (n = 0..N-1) ],
+ * (S v)^n[j] = sum_p S[n][p][j] v_p[j] at every voxel, D the 3D forward
+ * differences (one TV per species and one per pulse image, as R3 sums them).
+ * Dual u = [uc (P x 3L) ; ul (P L) ; ub (N x 3L)] in the box |u| <= alpha
+ * (Eq. prox-dual; the lambdas live in L), dual step `step2` (at most
+ * 1/eig_max(L L^T)), u and its momentum iterate start at zero:
+ *   for i = 1..iters:
+ *     w   = z - L^T r
+ *     u_i = clamp(r + step2 L w, -alpha, alpha)
+ *     t_{i+1} = (1 + sqrt(1 + 4 t_i^2)) / 2
+ *     r   = u_i + beta_i (u_i - u_{i-1})
+ *   x = max(z - L^T u_iters, 0)
+ * u_out (optional) receives u_iters.  Sizes: S [N][P][Z], z and x [P][Y][X][Z].
+ * ------------------------------------------------------------------------- */
+static void joint_LT(int N, int P, int Y, int X, int Z, const double* S, double lam_tv,
+                     double lam_l1, double lam_b, const double* u, double* out, double* tmp)
+{
+    const size_t L = (size_t)Y * X * Z;
+    const double* uc = u;
+    const double* ul = u + (size_t)P * 3 * L;
+    const double* ub = ul + (size_t)P * L;
+    for (int p = 0; p < P; ++p) {
+        grad3T(Y, X, Z, uc + (size_t)p * 3 * L, out + (size_t)p * L);
+        for (size_t i = 0; i < L; ++i)
+            out[(size_t)p * L + i] = lam_tv * out[(size_t)p * L + i] + lam_l1 * ul[(size_t)p * L + i];
+    }
+    for (int n = 0; n < N; ++n) {
+        grad3T(Y, X, Z, ub + (size_t)n * 3 * L, tmp);  /* D^T ub_n, a pulse image */
+        for (int p = 0; p < P; ++p)
+            for (size_t i = 0; i < L; ++i) {
+                const int j = (int)(i % (size_t)Z);
+                out[(size_t)p * L + i] += lam_b * S[((size_t)n * P + p) * Z + j] * tmp[i];
+            }
+    }
+}
+
+static void joint_L(int N, int P, int Y, int X, int Z, const double* S, double lam_tv,
+                    double lam_l1, double lam_b, const double* v, double* out, double* tmp)
+{
+    const size_t L = (size_t)Y * X * Z;
+    double* oc = out;
+    double* ol = out + (size_t)P * 3 * L;
+    double* ob = ol + (size_t)P * L;
+    for (int p = 0; p < P; ++p) {
+        grad3(Y, X, Z, v + (size_t)p * L, oc + (size_t)p * 3 * L);
+        for (size_t i = 0; i < 3 * L; ++i) oc[(size_t)p * 3 * L + i] *= lam_tv;
+        for (size_t i = 0; i < L; ++i) ol[(size_t)p * L + i] = lam_l1 * v[(size_t)p * L + i];
+    }
+    for (int n = 0; n < N; ++n) {
+        for (size_t i = 0; i < L; ++i) {
+            const int j = (int)(i % (size_t)Z);
+            double b = 0.0;
+            for (int p = 0; p < P; ++p) b += S[((size_t)n * P + p) * Z + j] * v[(size_t)p * L + i];
+            tmp[i] = b;
+        }
+        grad3(Y, X, Z, tmp, ob + (size_t)n * 3 * L);
+        for (size_t i = 0; i < 3 * L; ++i) ob[(size_t)n * 3 * L + i] *= lam_b;
+    }
+}
+
+void oracle_prox_joint(int N, int P, int Y, int X, int Z, const double* S, const double* z,
+                       double* x, double alpha, double lam_tv, double lam_l1, double lam_b,
+                       int iters, double step2, int momentum, double* u_out)
+{
+    const size_t L = (size_t)Y * X * Z, nc = (size_t)P * L;
+    const size_t nu = (size_t)P * 3 * L + (size_t)P * L + (size_t)N * 3 * L;
+    double* u = (double*)calloc(nu, sizeof(double));
+    double* u_prev = (double*)calloc(nu, sizeof(double));
+    double* rr = (double*)calloc(nu, sizeof(double));
+    double* g = (double*)malloc(sizeof(double) * nu);
+    double* w = (double*)malloc(sizeof(double) * nc);
+    double* tmp = (double*)malloc(sizeof(double) * 3 * L);
+    double t = 1.0;
+    for (int it = 0; it < iters; ++it) {
+        joint_LT(N, P, Y, X, Z, S, lam_tv, lam_l1, lam_b, rr, w, tmp);
+        for (size_t i = 0; i < nc; ++i) w[i] = z[i] - w[i];
+        joint_L(N, P, Y, X, Z, S, lam_tv, lam_l1, lam_b, w, g, tmp);
+        for (size_t i = 0; i < nu; ++i) {
+            const double v = rr[i] + step2 * g[i];
+            u[i] = v > alpha ? alpha : (v < -alpha ? -alpha : v);
+        }
+        const double t1 = next_t(t);
+        const double beta = momentum_coef(momentum, t, t1);
+        for (size_t i = 0; i < nu; ++i) {
+            rr[i] = u[i] + beta * (u[i] - u_prev[i]);
+            u_prev[i] = u[i];
+        }
+        t = t1;
+    }
+    joint_LT(N, P, Y, X, Z, S, lam_tv, lam_l1, lam_b, u, w, tmp);
+    for (size_t i = 0; i < nc; ++i) {
+        const double v = z[i] - w[i];
+        x[i] = v > 0.0 ? v : 0.0;
+    }
+    if (u_out) memcpy(u_out, u, sizeof(double) * nu);
+    free(u); free(u_prev); free(rr); free(g); free(w); free(tmp);
+}
+
 /* F(c) = 1/2 ||Hc - y||^2 + lambda_TV sum_p TV(c_p) + lambda_l1 ||c||_1 for c >= 0
  * (Eq. one-step with Eq. reg-tv-l1-one, lambda_3 = 0).  Returns also the
  * data-fit term in *fit. */

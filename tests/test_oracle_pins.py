@@ -679,3 +679,106 @@ def ctypes_double(v):
 def ctypes_void(v):
     import ctypes
     return ctypes.c_void_p(v)
+
+
+# --------------------------------------------------------------------------
+# Full R3 with its lambda_3 term (Eq. reg-tv-l1-one): Algorithm 2 on the
+# stacked L
+# --------------------------------------------------------------------------
+
+def _diff_matrix(Y, X, Z):
+    """3D forward differences as a dense (3L x L) matrix, one row per
+    (axis, voxel); rows of the last voxel along an axis are zero."""
+    L = Y * X * Z
+    idx = np.arange(L).reshape(Y, X, Z)
+    D = np.zeros((3 * L, L))
+    for axis in range(3):
+        a = np.moveaxis(idx, axis, 0)
+        for lo, hi in zip(a[:-1].ravel(), a[1:].ravel()):
+            D[axis * L + lo, hi] = 1.0
+            D[axis * L + lo, lo] = -1.0
+    return D
+
+
+def _stacked_L(g, sw, lam_tv, lam_l1, lam_b):
+    """R3 = ||L c||_1: TV of each species, l1, TV of each pulse image (S c)^n."""
+    L = g.Y * g.X * g.Z
+    D = _diff_matrix(g.Y, g.X, g.Z)
+    S = oracle.switch_matrix(g, sw)                      # [N][P][Z], pinned elsewhere
+    depth = np.tile(np.arange(g.Z), g.Y * g.X)           # depth of each voxel
+    blocks = []
+    for p in range(g.P):
+        row = np.zeros((3 * L, g.P * L))
+        row[:, p * L:(p + 1) * L] = lam_tv * D
+        blocks.append(row)
+    blocks.append(lam_l1 * np.eye(g.P * L))
+    for n in range(g.N):
+        Sn = np.concatenate([np.diag(S[n, p, depth]) for p in range(g.P)], axis=1)
+        blocks.append(lam_b * D @ Sn)
+    return np.concatenate(blocks, axis=0)
+
+
+def _box_dual_prox(Lmat, z, alpha):
+    """argmin_x 1/2||x - z||^2 + alpha ||L x||_1 through its dual, min over
+    |u| <= alpha of 1/2 ||z - L^T u||^2, by scipy's L-BFGS-B."""
+    def fun(u):
+        w = z - Lmat.T @ u
+        return 0.5 * w @ w, -(Lmat @ w)
+    res = scipy.optimize.minimize(fun, np.zeros(Lmat.shape[0]), jac=True, method="L-BFGS-B",
+                                  bounds=[(-alpha, alpha)] * Lmat.shape[0],
+                                  options={"maxiter": 20000, "ftol": 1e-15, "gtol": 1e-12})
+    return z - Lmat.T @ res.x
+
+
+def _joint_case(N=3, P=2):
+    g = _geom(X=3, Y=2, Z=3, T=3, N=N, P=P, k=1, pulses_per_cycle=3)
+    sw = _sw(P, mu=3.0)
+    return g, sw
+
+
+@pytest.mark.parametrize("lams", [(0.3, 0.1, 0.2), (0.0, 0.0, 0.4), (0.25, 0.15, 0.0)])
+def test_joint_prox_matches_the_dual_solution(lams):
+    """Algorithm 2 on the stacked L of R3 (all three terms) converges to the
+    prox computed from its dual by an independent solver; the inputs keep the
+    result positive, so Algorithm 2's final clip is inactive."""
+    g, sw = _joint_case()
+    lam_tv, lam_l1, lam_b = lams
+    rng = np.random.default_rng(31)
+    z = rng.standard_normal(g.c_shape()) + 4.0
+    alpha = 0.7
+    Lmat = _stacked_L(g, sw, lam_tv, lam_l1, lam_b)
+    want = _box_dual_prox(Lmat, z.ravel(), alpha)
+    assert want.min() > 0
+    step2 = 1.0 / np.linalg.norm(Lmat, 2) ** 2
+    got = oracle.prox_joint(g, sw, z, alpha, lam_tv, lam_l1, lam_b, 20000, step2)
+    # both sides iterate to a tolerance: ~4e-6 is where L-BFGS-B stops
+    np.testing.assert_allclose(got.ravel(), want, atol=1e-5)
+
+
+def test_joint_prox_without_lambda3_is_the_composite_prox():
+    """With lambda_3 = 0 the joint dual gives max(prox_TV(z) - alpha lambda_l1, 0),
+    the composition the solver uses (reading O8)."""
+    g, sw = _joint_case()
+    rng = np.random.default_rng(32)
+    z = rng.standard_normal(g.c_shape()) + 1.0
+    alpha, lam_tv, lam_l1 = 0.8, 0.3, 0.1
+    Lmat = _stacked_L(g, sw, lam_tv, lam_l1, 0.0)
+    step2 = 1.0 / np.linalg.norm(Lmat, 2) ** 2
+    got = oracle.prox_joint(g, sw, z, alpha, lam_tv, lam_l1, 0.0, 8000, step2)
+    comp = oracle.prox(z, alpha, lam_l1, lam_tv, 8000)
+    np.testing.assert_allclose(got, comp, atol=2e-6)
+
+
+def test_joint_prox_lambda3_on_identical_pulse_images_is_a_tv_prox():
+    """One species with weight 1 at every depth (no switching, no fluence
+    decay): every pulse image is c itself, so lambda_3 sum_n TV((S c)^n) =
+    N lambda_3 TV(c) and the prox is the TV prox with threshold alpha N lambda_3."""
+    g = _geom(X=3, Y=2, Z=4, T=4, N=3, P=1, k=1, pulses_per_cycle=3)
+    sw = Switching(kappa=(0.0,), eps_bar=(0.0,), eps_off=(1.0,), mu_per_mm=0.0)
+    rng = np.random.default_rng(33)
+    z = rng.standard_normal(g.c_shape()) + 3.0
+    alpha, lam_b = 0.5, 0.2
+    step2 = 1.0 / (12.0 * (g.N * lam_b) ** 2)
+    got = oracle.prox_joint(g, sw, z, alpha, 0.0, 0.0, lam_b, 8000, step2)
+    want = oracle.prox_tv(z, alpha * g.N * lam_b, 8000)
+    np.testing.assert_allclose(got, want, atol=2e-6)
