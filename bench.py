@@ -366,6 +366,49 @@ def run_two_step(args, device):
         "relative_error_vs_phantom": err}), flush=True)
 
 
+def run_prox_joint(args, device):
+    """The prox of the full R3 with its lambda_3 term (swopt_prox_joint) on
+    the workload's volume and pulses: time per call of `inner` dual
+    iterations, CUDA events over `steps` calls after `warmup`, inputs larger
+    than L2."""
+    import torch
+    import paper_2510_23739_gb300 as sw
+
+    prob = workload_problem(args.workload, args.kernel)
+    g = prob.geom
+    K = synth.transducer_kernel(g, seed=0)
+    op = sw.Operator(g, K, prob.sw)
+    z = torch.tensor(synth.gaussian(g.c_shape(), 5), dtype=torch.float32, device=device) + 0.5
+    lam_tv, lam_l1, lam_b, alpha, inner = prob.lam_tv, prob.lam_l1, prob.lam_tv, 0.5, prob.inner
+    # a dual step below 1/||L||^2 (|S| <= 2 here); the time does not depend on it
+    step2 = 1.0 / (12 * lam_tv ** 2 + lam_l1 ** 2 + 12 * lam_b ** 2 * g.N * 4.0)
+    out = torch.empty_like(z)
+    for _ in range(args.warmup):
+        op.prox_joint(z, alpha, lam_tv, lam_l1, lam_b, inner, step2, out=out)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        op.prox_joint(z, alpha, lam_tv, lam_l1, lam_b, inner, step2, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    L = g.Y * g.X * g.Z
+    nu = (4 * g.P + 3 * g.N) * L
+    # per dual iteration: L^T reads the momentum duals and z, writes w; the
+    # update reads w (and neighbours), reads and writes u and r
+    bytes_iter = 4 * (nu + 2 * g.P * L) + 4 * (g.P * L + 4 * nu)
+    print(json.dumps({
+        "metric": "joint prox time (full R3, lambda_3 term)", "value": ms, "unit": "ms",
+        "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "dtype": "f32", "data": "synthetic (seeded Gaussian input)",
+        "config": {"workload": args.workload, "inner_iters": inner, "pulses": g.N,
+                   "species": g.P, "dual_values": nu},
+        "algorithmic_gb_per_s": bytes_iter * inner / (ms * 1e-3) / 1e9}), flush=True)
+
+
 def replace_iters(params, iters):
     import copy
     p = copy.copy(params)
@@ -544,8 +587,9 @@ def main():
     ap.add_argument("--impl", default="swopt", choices=["swopt", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "bf16x3"])
-    ap.add_argument("--method", default="one-step", choices=["one-step", "two-step"],
-                    help="two-step: time swopt_two_step against the one-step solve (FP32)")
+    ap.add_argument("--method", default="one-step", choices=["one-step", "two-step", "prox-joint"],
+                    help="two-step: time swopt_two_step against the one-step solve (FP32); "
+                         "prox-joint: time the prox of the full R3 (lambda_3 term)")
     ap.add_argument("--kernel", default="aperture", choices=["aperture", "semicircle"],
                     help="per-depth kernel: the aperture-point transducer model, or the "
                          "paper-literal SPR on discrete half spheres (matched time grid)")
@@ -579,6 +623,12 @@ def main():
 
     import paper_2510_23739_gb300 as sw
     sw.lib()
+    if args.method == "prox-joint":
+        if rank == 0:
+            run_prox_joint(args, device)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     if args.method == "two-step":
         if rank == 0:
             run_two_step(args, device)

@@ -205,6 +205,22 @@ swopt_status swopt_fista_get(swopt_handle* h, float* c_dev, void* stream);
 swopt_status swopt_solve(swopt_handle* h, const float* y_dev, float* c_dev,
                          const swopt_solve_params* prm, swopt_solve_stats* stats, void* stream);
 
+/* Proximal map of alpha (R3 + delta_{>=0}) with all three terms of Eq.
+ * (reg-tv-l1-one), including lambda_3 sum_n TV((S c)^n) (lambda_b here):
+ * Algorithm 2 on the stacked L = [lambda_tv D per species; lambda_l1 I;
+ * lambda_b D S per pulse] with dual step step2 (at most 1/eig_max(L L^T);
+ * 12 lambda_tv^2 + lambda_l1^2 + 12 lambda_b^2 N max_j ||S_j||^2 bounds it),
+ * `iters` dual iterations (Beck-Teboulle momentum) from a zero dual, output
+ * max(z - L^T u, 0).  S is the handle's switching model (pulse n takes state
+ * n mod pulses_per_cycle).  z_dev, x_dev: device [P][Y][X][Z] (x may equal z).
+ * Scratch of (4P + 3N) * 2 + P volumes is taken from the stream-ordered
+ * allocator for the call.  Errors: INVALID_ARG (null pointers, negative or
+ * non-finite weights, iters < 0, step2 <= 0 with iters > 0), UNSUPPORTED
+ * for P > 8, OOM, CUDA.  Asynchronous on the stream. */
+swopt_status swopt_prox_joint(swopt_handle* h, const float* z_dev, float* x_dev, double alpha,
+                              double lambda_tv, double lambda_l1, double lambda_b, int iters,
+                              double step2, void* stream);
+
 /* The two-step approach (the paper's "Two-Step Approach", the comparison
  * method of the one-step reconstruction): first the acoustic problem of
  * Eq. (acoustic-inverse) with R1 = lambda_tv TV (+ lambda_l1 l1 if nonzero),

@@ -123,6 +123,9 @@ _SIGS = {
                             ctypes.c_int], ctypes.c_int),
     "swopt_tc_config": ([ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 5,
                         ctypes.c_int),
+    "swopt_prox_joint": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                          ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                          ctypes.c_double, ctypes.c_void_p], ctypes.c_int),
     "swopt_two_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                         ctypes.c_void_p], ctypes.c_int),
@@ -393,6 +396,19 @@ class Operator:
         if history:
             stats["history"] = hist[: st.iters]
         return out, stats
+
+    def prox_joint(self, z, alpha, lambda_tv, lambda_l1, lambda_b, iters, step2, out=None,
+                   stream=None):
+        """prox of alpha (R3 + delta_{>=0}) with the lambda_3 term (lambda_b),
+        Algorithm 2 on the stacked L (see swopt_prox_joint)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.c_shape, device=z.device, dtype=torch.float32)
+        _check(lib().swopt_prox_joint(self._h, _ptr(z, self.c_shape, "z"),
+                                      _ptr(out, self.c_shape, "x"), float(alpha),
+                                      float(lambda_tv), float(lambda_l1), float(lambda_b),
+                                      int(iters), float(step2), _stream(stream)))
+        return out
 
     def objective(self, c, y, lambda_l1, lambda_tv, stream=None):
         F, fit = ctypes.c_double(), ctypes.c_double()

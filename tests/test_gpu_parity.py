@@ -700,6 +700,32 @@ def test_two_step_matches_oracle():
     assert rel(host(c), c_or) <= 1e-4
 
 
+@pytest.mark.parametrize("lams", [(0.3, 0.1, 0.2), (0.0, 0.0, 0.4), (0.25, 0.15, 0.0)])
+def test_prox_joint_matches_oracle(lams):
+    """The prox of the full R3 with its lambda_3 term (TV of every pulse
+    image), Algorithm 2 on the stacked L with a fixed iteration count, against
+    the oracle's iterates (pulses fold onto 3 switching states; some outputs
+    clip at zero)."""
+    g = Geometry(X=7, Y=5, Z=6, T=8, N=5, P=2, k=3, pulses_per_cycle=3)
+    s = Switching((0.2, 0.0), (1.0, 0.0), (0.05, 1.0), 3.0)
+    K = np.random.default_rng(60).standard_normal(g.k_shape())
+    lam_tv, lam_l1, lam_b = lams
+    S = oracle.switch_matrix(g, s)
+    bound = 12 * lam_tv ** 2 + lam_l1 ** 2 + 12 * lam_b ** 2 * g.N * max(
+        np.linalg.norm(S[:, :, j], 2) ** 2 for j in range(g.Z))
+    step2 = 1.0 / bound
+    z = np.random.default_rng(61).standard_normal(g.c_shape()) + 0.5
+    op = sw.Operator(g, K, s)
+    try:
+        got = host(op.prox_joint(dev(z), 0.6, lam_tv, lam_l1, lam_b, 40, step2))
+        op.check_device()
+    finally:
+        op.close()
+    want = oracle.prox_joint(g, s, z, 0.6, lam_tv, lam_l1, lam_b, 40, step2)
+    assert (want == 0).any() and (want > 0).any()
+    assert rel(got, want) <= 1e-5
+
+
 def test_tensor_core_accumulators_option(tc_cases):
     """One accumulator per tile (corrections summed with the main products)
     stays within the split tolerance; two is the default of the split mode."""
