@@ -9,7 +9,8 @@ iteration for the step size, the kappa/mu gradient of the data fit, and the
 paper-literal semicircle kernel of Eqs. (q-above-final)/(q-below-final), and
 the two-step approach (Eqs. (acoustic-inverse), (unmixing)), and the
 proximal map of the full R3 with its lambda_3 term (Algorithm 2 on the
-stacked L).
+stacked L), and the derivative of the unrolled solve with respect to the
+switching parameters (forward mode).
 
 Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's
 CPU-baseline leg may import this package.  It shares no code with the CUDA
@@ -278,6 +279,34 @@ def semicircle_kernel(Z, k, T, dims, rho, focal_depth, focal_sample, eta, eir):
                                    ctypes.c_double(focal_depth), ctypes.c_int(focal_sample),
                                    _p(eta), _p(eir), ctypes.c_int(eir.size), _p(K))
     return K
+
+
+def switch_matrix_derivative(geom, sw, which):
+    """dS/dkappa_p (which = p < P) or dS/dmu (which = P) of Eq. (final-H)."""
+    dS = np.empty((geom.N, geom.P, geom.Z))
+    lib().oracle_switch_matrix_derivative(
+        ctypes.c_int(geom.N), ctypes.c_int(geom.P), ctypes.c_int(geom.Z),
+        ctypes.c_int(geom.pulses_per_cycle), ctypes.c_double(sw.mu_per_mm),
+        ctypes.c_double(geom.dz_mm), _p(_f64(sw.kappa)), _p(_f64(sw.eps_bar)),
+        _p(_f64(sw.eps_off)), ctypes.c_int(which), _p(dS))
+    return dS
+
+
+def fista_tangent(geom, sw, K, y, alpha, iters, lam_l1, lam_tv, inner, which,
+                  momentum="beck_teboulle", inner_momentum="beck_teboulle"):
+    """Algorithm 1's output c_K and its derivative dc_K/dtheta through the
+    unrolled solve (forward mode), theta = kappa_p (which = p) or mu (which = P),
+    with the step, weights and counts held fixed."""
+    S = switch_matrix(geom, sw)
+    dS = switch_matrix_derivative(geom, sw, which)
+    c = np.empty(geom.c_shape())
+    dc = np.empty(geom.c_shape())
+    lib().oracle_fista_tangent(*_dims(geom), _p(S), _p(dS), _p(_f64(K)), _p(_f64(y)),
+                               ctypes.c_double(alpha), ctypes.c_int(iters),
+                               ctypes.c_double(lam_l1), ctypes.c_double(lam_tv),
+                               ctypes.c_int(inner), ctypes.c_int(MOMENTUM[momentum]),
+                               ctypes.c_int(MOMENTUM[inner_momentum]), _p(c), _p(dc))
+    return c, dc
 
 
 def param_grad(geom, sw, K, c, y):

@@ -718,6 +718,169 @@ void oracle_two_step(int N, int P, int Y, int X, int Z, int T, int k,
     free(eye);
 }
 
+/* ---------------------------------------------------------------------------
+ * Derivative of the switching matrix of Eq. (final-H) with respect to one
+ * parameter: which = p (0 <= p < P) for kappa_p, which = P for mu.
+ *   S = Phi (eps_bar e^{-kappa Phi m} + eps_off),  Phi = e^{-mu j dz}
+ *   dS/dkappa_p = -Phi^2 m eps_bar_p e^{-kappa_p Phi m}   (species p only)
+ *   dS/dmu      = dS/dPhi * dPhi/dmu,  dPhi/dmu = -j dz Phi,
+ *   dS/dPhi     = eps_bar e^{-kappa Phi m} + eps_off - Phi eps_bar kappa m e^{-kappa Phi m}
+ * ------------------------------------------------------------------------- */
+void oracle_switch_matrix_derivative(int N, int P, int Z, int pulses_per_cycle, double mu_per_mm,
+                                     double dz_mm, const double* kappa, const double* eps_bar,
+                                     const double* eps_off, int which, double* dS)
+{
+    for (int n = 0; n < N; ++n) {
+        const double m = (double)(n % pulses_per_cycle);
+        for (int p = 0; p < P; ++p)
+            for (int j = 0; j < Z; ++j) {
+                const double ph = exp(-mu_per_mm * (double)j * dz_mm);
+                const double e = exp(-kappa[p] * ph * m);
+                double d = 0.0;
+                if (which == P) {
+                    const double dS_dphi = eps_bar[p] * e + eps_off[p] - ph * eps_bar[p] * kappa[p] * m * e;
+                    d = dS_dphi * (-(double)j * dz_mm * ph);
+                } else if (which == p) {
+                    d = -ph * ph * m * eps_bar[p] * e;
+                }
+                dS[IDX4(0, n, p, j, N, P, Z)] = d;
+            }
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Differentiating through the unrolled solve (forward mode): Algorithm 1
+ * exactly as oracle_fista (step alpha, weights and counts held fixed), with
+ * the tangent of every quantity carried along for a change of S by dS (the
+ * derivative of S with respect to one switching parameter):
+ *   r  = H xi - y,                     dr  = A(dS xi) + A(S dxi)
+ *   g  = H^T r,                        dg  = dS^T A^T r + S^T A^T dr
+ *   z  = xi - alpha g,                 dz  = dxi - alpha dg
+ *   Algorithm 2 (per species): w = z - D^T q, v = q + D w / 12,
+ *     u = clamp(v, -tau, tau),         du  = [|v| < tau] (dq + D dw / 12)
+ *     q = u + beta (u - u_prev),       dq  = du + beta (du - du_prev)
+ *   x = z - D^T u,  c = max(x - alpha lambda_l1, 0),
+ *                                      dc  = [x - alpha lambda_l1 > 0] dx
+ *   xi = c + beta (c - c_prev),        dxi = dc + beta (dc - dc_prev)
+ * The map is piecewise linear in the data; the tangent is the derivative
+ * wherever no clamp or clip sits exactly on its threshold.
+ * c_out, dc_out: [P][Y][X][Z].
+ * ------------------------------------------------------------------------- */
+static void prox_tv_tangent(int Y, int X, int Z, const double* z, const double* dz, double* x,
+                            double* dx, double tau, int iters, int momentum)
+{
+    const size_t L = (size_t)Y * X * Z;
+    double* u = (double*)calloc(3 * L, sizeof(double));
+    double* up = (double*)calloc(3 * L, sizeof(double));
+    double* q = (double*)calloc(3 * L, sizeof(double));
+    double* du = (double*)calloc(3 * L, sizeof(double));
+    double* dup = (double*)calloc(3 * L, sizeof(double));
+    double* dq = (double*)calloc(3 * L, sizeof(double));
+    double* g = (double*)malloc(sizeof(double) * 3 * L);
+    double* dg = (double*)malloc(sizeof(double) * 3 * L);
+    double* w = (double*)malloc(sizeof(double) * L);
+    double* dw = (double*)malloc(sizeof(double) * L);
+    double t = 1.0;
+    for (int it = 0; it < iters; ++it) {
+        grad3T(Y, X, Z, q, w);
+        grad3T(Y, X, Z, dq, dw);
+        for (size_t i = 0; i < L; ++i) {
+            w[i] = z[i] - w[i];
+            dw[i] = dz[i] - dw[i];
+        }
+        grad3(Y, X, Z, w, g);
+        grad3(Y, X, Z, dw, dg);
+        for (size_t i = 0; i < 3 * L; ++i) {
+            const double v = q[i] + g[i] / 12.0;
+            if (v > tau) {
+                u[i] = tau;
+                du[i] = 0.0;
+            } else if (v < -tau) {
+                u[i] = -tau;
+                du[i] = 0.0;
+            } else {
+                u[i] = v;
+                du[i] = dq[i] + dg[i] / 12.0;
+            }
+        }
+        const double t1 = next_t(t);
+        const double beta = momentum_coef(momentum, t, t1);
+        for (size_t i = 0; i < 3 * L; ++i) {
+            q[i] = u[i] + beta * (u[i] - up[i]);
+            dq[i] = du[i] + beta * (du[i] - dup[i]);
+            up[i] = u[i];
+            dup[i] = du[i];
+        }
+        t = t1;
+    }
+    grad3T(Y, X, Z, u, w);
+    grad3T(Y, X, Z, du, dw);
+    for (size_t i = 0; i < L; ++i) {
+        x[i] = z[i] - w[i];
+        dx[i] = dz[i] - dw[i];
+    }
+    free(u); free(up); free(q); free(du); free(dup); free(dq); free(g); free(dg); free(w); free(dw);
+}
+
+void oracle_fista_tangent(int N, int P, int Y, int X, int Z, int T, int k, const double* S,
+                          const double* dS, const double* K, const double* yv, double alpha,
+                          int iters, double lam_l1, double lam_tv, int inner, int momentum,
+                          int inner_momentum, double* c_out, double* dc_out)
+{
+    const size_t ny = (size_t)N * Y * X * T, nc = (size_t)P * Y * X * Z, L = (size_t)Y * X * Z;
+    double* c = (double*)calloc(nc, sizeof(double));
+    double* dc = (double*)calloc(nc, sizeof(double));
+    double* xi = (double*)calloc(nc, sizeof(double));
+    double* dxi = (double*)calloc(nc, sizeof(double));
+    double* zin = (double*)malloc(sizeof(double) * nc);
+    double* dzin = (double*)malloc(sizeof(double) * nc);
+    double* xv = (double*)malloc(sizeof(double) * nc);
+    double* dxv = (double*)malloc(sizeof(double) * nc);
+    double* g = (double*)malloc(sizeof(double) * nc);
+    double* tmpc = (double*)malloc(sizeof(double) * nc);
+    double* res = (double*)malloc(sizeof(double) * ny);
+    double* dres = (double*)malloc(sizeof(double) * ny);
+    double* tmpy = (double*)malloc(sizeof(double) * ny);
+    double t = 1.0;
+    for (int it = 0; it < iters; ++it) {
+        oracle_forward(N, P, Y, X, Z, T, k, S, K, xi, res);
+        for (size_t i = 0; i < ny; ++i) res[i] -= yv[i];
+        oracle_forward(N, P, Y, X, Z, T, k, dS, K, xi, dres);
+        oracle_forward(N, P, Y, X, Z, T, k, S, K, dxi, tmpy);
+        for (size_t i = 0; i < ny; ++i) dres[i] += tmpy[i];
+        oracle_adjoint(N, P, Y, X, Z, T, k, S, K, res, g);
+        for (size_t i = 0; i < nc; ++i) zin[i] = xi[i] - alpha * g[i];
+        oracle_adjoint(N, P, Y, X, Z, T, k, dS, K, res, g);
+        oracle_adjoint(N, P, Y, X, Z, T, k, S, K, dres, tmpc);
+        for (size_t i = 0; i < nc; ++i) dzin[i] = dxi[i] - alpha * (g[i] + tmpc[i]);
+        if (lam_tv > 0.0 && inner > 0) {
+            for (int p = 0; p < P; ++p)
+                prox_tv_tangent(Y, X, Z, zin + p * L, dzin + p * L, xv + p * L, dxv + p * L,
+                                alpha * lam_tv, inner, inner_momentum);
+        } else {
+            memcpy(xv, zin, sizeof(double) * nc);
+            memcpy(dxv, dzin, sizeof(double) * nc);
+        }
+        const double t1 = next_t(t);
+        const double beta = momentum_coef(momentum, t, t1);
+        const double th = alpha * lam_l1;
+        for (size_t i = 0; i < nc; ++i) {
+            const double v = xv[i] - th;
+            const double cn = v > 0.0 ? v : 0.0;
+            const double dcn = v > 0.0 ? dxv[i] : 0.0;
+            xi[i] = cn + beta * (cn - c[i]);
+            dxi[i] = dcn + beta * (dcn - dc[i]);
+            c[i] = cn;
+            dc[i] = dcn;
+        }
+        t = t1;
+    }
+    memcpy(c_out, c, sizeof(double) * nc);
+    memcpy(dc_out, dc, sizeof(double) * nc);
+    free(c); free(dc); free(xi); free(dxi); free(zin); free(dzin); free(xv); free(dxv);
+    free(g); free(tmpc); free(res); free(dres); free(tmpy);
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP

@@ -782,3 +782,53 @@ def test_joint_prox_lambda3_on_identical_pulse_images_is_a_tv_prox():
     got = oracle.prox_joint(g, sw, z, alpha, 0.0, 0.0, lam_b, 8000, step2)
     want = oracle.prox_tv(z, alpha * g.N * lam_b, 8000)
     np.testing.assert_allclose(got, want, atol=2e-6)
+
+
+# --------------------------------------------------------------------------
+# Differentiating through the unrolled solve (forward mode)
+# --------------------------------------------------------------------------
+
+def test_switch_matrix_derivative_matches_central_differences():
+    g = _geom(Z=6, N=7, P=3, pulses_per_cycle=4)
+    sw = _sw(3, kappa=[0.8, 1.7, 0.0], mu=2.5)
+    h = 1e-6
+    for which in range(g.P + 1):
+        dS = oracle.switch_matrix_derivative(g, sw, which)
+        if which < g.P:
+            kp, km = list(sw.kappa), list(sw.kappa)
+            kp[which] += h
+            km[which] -= h
+            sp, sm = (Switching(tuple(kp), sw.eps_bar, sw.eps_off, sw.mu_per_mm),
+                      Switching(tuple(km), sw.eps_bar, sw.eps_off, sw.mu_per_mm))
+        else:
+            sp = Switching(sw.kappa, sw.eps_bar, sw.eps_off, sw.mu_per_mm + h)
+            sm = Switching(sw.kappa, sw.eps_bar, sw.eps_off, sw.mu_per_mm - h)
+        fd = (oracle.switch_matrix(g, sp) - oracle.switch_matrix(g, sm)) / (2 * h)
+        assert np.abs(dS - fd).max() <= 1e-8 * max(1.0, np.abs(fd).max()), which
+
+
+@pytest.mark.parametrize("which", [0, 2])
+def test_unrolled_solve_tangent_matches_central_differences(which):
+    """dc_K/dtheta carried through every step of Algorithm 1 (and the
+    Algorithm 2 iterations inside its prox) equals the central difference of
+    the oracle's own solve at theta +- h (kappa_0, or mu), FP64."""
+    g, sw, K, y = _small_problem()
+    lip = oracle.power(g, sw, K, np.random.default_rng(0).standard_normal(g.c_shape()), 200)
+    alpha, iters, lam1, lamtv, inner = 0.9 / lip, 16, 0.05, 0.02, 10
+    c, dc = oracle.fista_tangent(g, sw, K, y, alpha, iters, lam1, lamtv, inner, which)
+    ref = oracle.fista(g, sw, K, y, alpha, iters, lam1, lamtv, inner)
+    assert np.array_equal(c, ref)
+    h = 1e-6
+
+    def at(delta):
+        if which < g.P:
+            kap = list(sw.kappa)
+            kap[which] += delta
+            s2 = Switching(tuple(kap), sw.eps_bar, sw.eps_off, sw.mu_per_mm)
+        else:
+            s2 = Switching(sw.kappa, sw.eps_bar, sw.eps_off, sw.mu_per_mm + delta)
+        return oracle.fista(g, s2, K, y, alpha, iters, lam1, lamtv, inner)
+
+    fd = (at(h) - at(-h)) / (2 * h)
+    assert 0 < (c > 0).mean() < 1 and np.abs(dc).max() > 1e-2   # some outputs clipped, some not
+    assert np.linalg.norm(dc - fd) <= 1e-5 * np.linalg.norm(fd)
