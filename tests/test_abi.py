@@ -97,6 +97,7 @@ def test_null_handle_calls_fail_cleanly():
     i = ctypes.c_int()
     assert L.swopt_tc_schedule_info(None, 0, *[ctypes.byref(i)] * 4) == 1
     assert L.swopt_two_step(None, None, None, None, None, None, None, None, None) == 1
+    assert L.swopt_prox_joint(None, None, None, 1.0, 0.1, 0.1, 0.1, 1, 0.1, None) == 1
     assert b"null" in L.swopt_last_error()
     assert L.swopt_version().decode().count(".") == 2
 
