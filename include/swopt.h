@@ -123,6 +123,18 @@ typedef struct {
     int refine_every;
     int refine_precision; /* swopt_precision of the initial and periodic exact gradients */
     double* history_host; /* optional [max_iters]: F(c_{k+1}) per iteration */
+    /* Device-side resync test of the refined solve (refine_every >= 1):
+     * > 0 also recomputes the gradient exactly at the end of iteration k when
+     * the sum of rho_i = ||c_{i+1} - c_i|| / ||c_{i+1}|| (FP64) over the
+     * iterations since the last exact gradient, this one included, exceeds
+     * refine_budget.  The low-precision increments since a resync then add a
+     * gradient error of about eps * refine_budget relative to the gradient
+     * (eps the rounding of the increment's arithmetic), whatever the phase of
+     * the solve: early iterations, whose steps are large, resync every time;
+     * late ones rarely.  The decision is made on the GPU (no host
+     * synchronisation): both branches are launched, and the one not taken
+     * returns at once.  0: off (resync every refine_every iterations only). */
+    double refine_budget;
 } swopt_solve_params;
 
 typedef struct {
@@ -198,6 +210,41 @@ swopt_status swopt_fista_init(swopt_handle* h, const float* y_dev, const swopt_s
                               void* stream);
 swopt_status swopt_fista_step(swopt_handle* h, int iters, void* stream);
 swopt_status swopt_fista_get(swopt_handle* h, float* c_dev, void* stream);
+
+/* Progress of the refined solve since swopt_fista_init: *iterations run and
+ * *resyncs, the exact gradients computed (the initial one included; with
+ * refine_every = 0 both count iterations and resyncs is 0).  Synchronises
+ * the stream when the schedule is decided on the device. */
+swopt_status swopt_refine_stats(swopt_handle* h, int64_t* iterations, int64_t* resyncs,
+                                void* stream);
+
+/* Checkpoint of the FISTA state (Algorithm 1 between two iterations): the
+ * iterates c_k and xi_k, the next prox input and the refined solve's
+ * gradient, the momentum scalars t_k, beta_k (FP64), the refined schedule's
+ * state and the iteration counters.  swopt_fista_state_bytes gives the size
+ * of the host buffer; swopt_fista_save copies the state into host_buf
+ * (synchronises); swopt_fista_restore loads it into a handle with the same
+ * geometry whose swopt_fista_init bound the same measurements and settings
+ * (the measurements are not part of the state), after which the iterations
+ * continue exactly as they would have from the saved point: 10 iterations,
+ * save, restore, 10 iterations equal 20 iterations bit for bit.  Errors:
+ * INVALID_ARG (no FISTA state, a buffer too small, or a state of another
+ * geometry or settings). */
+swopt_status swopt_fista_state_bytes(swopt_handle* h, size_t* bytes);
+swopt_status swopt_fista_save(swopt_handle* h, void* host_buf, size_t bytes, void* stream);
+swopt_status swopt_fista_restore(swopt_handle* h, const void* host_buf, size_t bytes,
+                                 void* stream);
+
+/* Failure-detection test hook for the cooperative TV prox's software grid
+ * barrier (not needed in normal use).  phantom_arrivals > 0 makes every
+ * barrier wait for that many blocks more than the launch has, so that no
+ * barrier completes; poll_limit > 0 replaces the barrier's default poll
+ * limit (about a second).  A barrier that reaches the limit records an
+ * error, every later barrier of the launch returns at once, and the next
+ * synchronising call (swopt_check_device) reports SWOPT_ERR_TIMEOUT and
+ * clears the error, after which the handle works normally.  0, 0 restores
+ * the defaults.  Synchronises. */
+swopt_status swopt_debug_barrier(swopt_handle* h, int phantom_arrivals, unsigned poll_limit);
 
 /* Complete solve (Algorithm 1): init, up to max_iters iterations with the
  * eps1/eps2 stopping tests and the optional history, then c_dev <- c_K and
@@ -382,19 +429,25 @@ swopt_status swopt_info(swopt_handle* h, int* t0, int* tw, int* states, int64_t*
  * a real-time loop that cannot afford cudaMalloc's implicit device-wide
  * synchronisation after start-up.  It needs no handle.
  *
- * It computes the same map as swopt_prox_tv (same kernels, same arguments
- * apart from the volume shape P x Y x X x Z given directly): z_dev and x_dev
- * are caller-owned device arrays [P][Y][X][Z] that may not alias.  Its
- * scratch (the three FGP dual arrays, 9 floats per volume element) is a
- * file-scope static device array sized for SWOPT_PROX_TV_STATIC_MAX_ELEMS
- * elements (18 MiB); every GPU that loads the library holds that array until
- * the process exits.  Volumes with P*Y*X*Z above the limit are rejected with
- * SWOPT_ERR_SHAPE and a message; the call never allocates (no cudaMalloc,
- * cudaFree or allocating library routine).
+ * It computes the same map as swopt_prox_tv with the same arithmetic (one
+ * launch of the per-iteration FGP kernel per inner iteration, then the
+ * primal recovery), and takes the same arguments apart from the volume shape
+ * P x Y x X x Z given directly: z_dev and x_dev are caller-owned device
+ * arrays [P][Y][X][Z] that may not alias.  Its scratch (the three FGP dual
+ * arrays, 9 floats per volume element) is a file-scope static device array
+ * sized for SWOPT_PROX_TV_STATIC_MAX_ELEMS elements (18 MiB).  The array is
+ * placed on a device when the library's module is first loaded there (with
+ * lazy module loading, the CUDA default, that may be this call's first use
+ * of the device, and placing it is the only memory the call ever causes to
+ * be reserved); it stays until the process exits or the context is reset.
+ * Volumes with P*Y*X*Z above the limit are rejected with SWOPT_ERR_SHAPE and
+ * a message; the call never allocates (no cudaMalloc, cudaFree or
+ * allocating library routine).
  *
- * The first call on a device looks up the device address of the array
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls in the process share the one array:
+ * Every call looks up the device address of the array (cudaGetSymbolAddress)
+ * in the current device's context; make the first call on each device before
+ * any stream capture, so that the module load does not happen inside one.
+ * All calls in the process share the one array:
  * calls whose GPU work overlaps in time (different streams, or host threads
  * using the same device) race on it, so serialise them.  The array keeps
  * the last call's contents, but nothing in it needs clearing: each call

@@ -88,6 +88,11 @@ def num_threads() -> int:
     return int(lib().oracle_num_threads())
 
 
+def set_threads(n: int) -> None:
+    """OpenMP threads of later oracle calls (timing only)."""
+    lib().oracle_set_threads(ctypes.c_int(int(n)))
+
+
 def fluence(geom, sw):
     """Phi_j = exp(-mu j dz)."""
     out = np.empty(geom.Z)

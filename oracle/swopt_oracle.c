@@ -890,3 +890,14 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of later parallel regions (timing only; no effect on results). */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}

@@ -23,10 +23,17 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["lib", "Operator", "SolveParams", "SwoptError", "PRECISION", "MOMENTUM",
-           "HFunction", "Batch"]
+           "HFunction", "Batch", "REFINED_DEFAULTS"]
 
 PRECISION = {"fp32": 0, "bf16": 1, "bf16x3": 2}
 MOMENTUM = {"beck_teboulle": 0, "paper_printed": 1, "none": 2}
+# The refined solve's recommended schedule for BF16 contractions: an exact
+# (two-term BF16) gradient every 25 iterations, and sooner whenever the
+# relative steps ||c_{k+1} - c_k|| / ||c_{k+1}|| taken on BF16 increments since
+# the last exact gradient add up to more than 0.1 (see refine_budget in
+# swopt_solve_params).
+REFINED_DEFAULTS = {"refine_every": 25, "refine_precision": "bf16x3", "refine_budget": 0.1}
+
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "SHAPE", 3: "CUDA", 4: "OOM", 5: "TIMEOUT",
            6: "DEVICE_CHECK", 7: "UNSUPPORTED"}
 
@@ -58,7 +65,8 @@ class _SolveParams(ctypes.Structure):
                 ("eps2", ctypes.c_double), ("momentum", ctypes.c_int),
                 ("inner_momentum", ctypes.c_int), ("power_iters", ctypes.c_int),
                 ("refine_every", ctypes.c_int), ("refine_precision", ctypes.c_int),
-                ("history_host", ctypes.POINTER(ctypes.c_double))]
+                ("history_host", ctypes.POINTER(ctypes.c_double)),
+                ("refine_budget", ctypes.c_double)]
 
 
 class _SolveStats(ctypes.Structure):
@@ -138,6 +146,14 @@ _SIGS = {
     "swopt_prox_tv_static": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int,
                               ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "swopt_refine_stats": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                            ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p], ctypes.c_int),
+    "swopt_fista_state_bytes": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "swopt_fista_save": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p],
+                         ctypes.c_int),
+    "swopt_fista_restore": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p],
+                            ctypes.c_int),
+    "swopt_debug_barrier": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_uint], ctypes.c_int),
 }
 
 
@@ -208,7 +224,7 @@ class SolveParams:
 
     def __init__(self, step=0.0, lambda_l1=1e-3, lambda_tv=1e-3, inner_iters=10, max_iters=100,
                  eps1=0.0, eps2=0.0, momentum="beck_teboulle", inner_momentum="beck_teboulle",
-                 power_iters=100, refine_every=0, refine_precision="bf16x3"):
+                 power_iters=100, refine_every=0, refine_precision="bf16x3", refine_budget=0.0):
         self.step = step
         self.lambda_l1 = lambda_l1
         self.lambda_tv = lambda_tv
@@ -221,6 +237,7 @@ class SolveParams:
         self.power_iters = power_iters
         self.refine_every = refine_every
         self.refine_precision = refine_precision
+        self.refine_budget = refine_budget
 
     def _c(self, history=None):
         p = _SolveParams()
@@ -241,6 +258,7 @@ class SolveParams:
                               else int(self.refine_precision))
         p.history_host = (history.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
                           if history is not None else ctypes.POINTER(ctypes.c_double)())
+        p.refine_budget = float(self.refine_budget)
         return p
 
 
@@ -381,6 +399,31 @@ class Operator:
             out = torch.empty(self.c_shape, device="cuda", dtype=torch.float32)
         _check(lib().swopt_fista_get(self._h, _ptr(out, self.c_shape, "c"), _stream(stream)))
         return out
+
+    def refine_stats(self, stream=None):
+        """(iterations, exact gradients) of the refined solve since fista_init."""
+        it, rs = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().swopt_refine_stats(self._h, ctypes.byref(it), ctypes.byref(rs),
+                                        _stream(stream)))
+        return it.value, rs.value
+
+    def fista_save(self, stream=None) -> bytes:
+        """Checkpoint of the FISTA state (host bytes)."""
+        n = ctypes.c_size_t()
+        _check(lib().swopt_fista_state_bytes(self._h, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().swopt_fista_save(self._h, buf, n, _stream(stream)))
+        return buf.raw
+
+    def fista_restore(self, state: bytes, stream=None):
+        """Load a checkpoint into this handle (after fista_init with the same
+        measurements and settings)."""
+        buf = ctypes.create_string_buffer(state, len(state))
+        _check(lib().swopt_fista_restore(self._h, buf, len(state), _stream(stream)))
+
+    def debug_barrier(self, phantom_arrivals=0, poll_limit=0):
+        """Failure-detection test hook of the TV prox's grid barrier."""
+        _check(lib().swopt_debug_barrier(self._h, int(phantom_arrivals), int(poll_limit)))
 
     def solve(self, y, params: SolveParams, history=False, out=None, stream=None):
         import torch

@@ -33,6 +33,7 @@ enum {
     SC_C = 4,
     SC_D = 5,
     SC_YSQ = 6,    // ||y||^2 of the measurements bound by fista_init
+    SC_BUDGET = 7, // refined solve: accumulated rho since the last exact gradient
     SC_COUNT = 16
 };
 
@@ -55,6 +56,7 @@ bool take_events(swopt_handle* h, cudaEvent_t* a, cudaEvent_t* b)
 void prof_begin(swopt_handle* h, int kernel, cudaStream_t st, ProfileRec* rec)
 {
     rec->kernel = -1;
+    rec->iter = h->gate ? h->iter : -1;
     if (h->in_ref) kernel += 2;  // launches at the refined solve's resync precision
     if (h->capturing) {
         // an event-record node in the graph; its event is swapped per replay
@@ -64,7 +66,8 @@ void prof_begin(swopt_handle* h, int kernel, cudaStream_t st, ProfileRec* rec)
             cudaEventDestroy(a);
             return;
         }
-        h->cap_events.push_back({a, kernel});
+        // a gated launch is marked by an offset of 16 in the captured kind
+        h->cap_events.push_back({a, kernel + (h->gate ? 16 : 0)});
         rec->a = a;
         rec->kernel = kernel;
         return;
@@ -88,7 +91,7 @@ void prof_end(swopt_handle* h, ProfileRec* rec, cudaStream_t st)
             cudaEventDestroy(b);
             return;
         }
-        h->cap_events.push_back({b, -1 - rec->kernel});  // end marker
+        h->cap_events.push_back({b, -1 - (rec->kernel + (h->gate ? 16 : 0))});  // end marker
         return;
     }
     cudaEventRecord(rec->b, st);
@@ -189,7 +192,7 @@ void release_all(swopt_handle* h)
     dfree(h->b); dfree(h->u); dfree(h->g); dfree(h->ytil); dfree(h->red); dfree(h->scal);
     dfree(h->c); dfree(h->xi); dfree(h->zin); dfree(h->tvu); dfree(h->tvr0); dfree(h->tvr1);
     dfree(h->tvx); dfree(h->coop_bar);
-    dfree(h->tmp); dfree(h->G); dfree(h->xprev);
+    dfree(h->tmp); dfree(h->G); dfree(h->xprev); dfree(h->sched); dfree(h->rlog);
     if (h->scal_host) cudaFreeHost(h->scal_host);
     h->scal_host = nullptr;
     for (auto& r : h->prof) {
@@ -414,6 +417,7 @@ swopt_status validate_params(const swopt_solve_params* p)
         p->inner_iters > 100000 || p->max_iters < 0 || p->momentum < 0 || p->momentum > 2 ||
         p->inner_momentum < 0 || p->inner_momentum > 2 || p->refine_every < 0 ||
         p->refine_precision < SWOPT_PREC_FP32 || p->refine_precision > SWOPT_PREC_BF16X3 ||
+        !is_fin(p->refine_budget) || p->refine_budget < 0 ||
         (p->step <= 0 && (p->power_iters < 1 || p->power_iters > 100000))) {
         set_error("invalid solve parameters");
         return SWOPT_ERR_INVALID_ARG;
@@ -447,8 +451,21 @@ swopt_status ensure_ref(swopt_handle* h)
 int iteration_kind(const swopt_handle* h)
 {
     const int R = h->prm.refine_every;
+    if (R > 0 && h->prm.refine_budget > 0) return 2;  // decided on the device
     return (R > 0 && (h->iter + 1) % R == 0) ? 1 : 0;
 }
+
+// Within its scope, launches run behind the refined solve's gate and only
+// when the device decision equals `want`.
+struct GateScope {
+    swopt_handle* h;
+    GateScope(swopt_handle* hh, int want) : h(hh)
+    {
+        h->gate = h->sched;
+        h->gate_want = want;
+    }
+    ~GateScope() { h->gate = nullptr; }
+};
 
 // One FISTA iteration on the bound measurements (all on `st`, no host sync).
 //
@@ -483,6 +500,20 @@ swopt_status fista_iteration(swopt_handle* h, int kind, cudaStream_t st)
     }
     if (!refined) return SWOPT_OK;
     if (kind == 1) return exact_gradient(h, st);
+    if (kind == 2) {
+        // the device decides between the increment and the exact gradient;
+        // both branches are launched behind the gate
+        SW_TRY(refine_decide(h, h->tmp, h->c, SC_BUDGET, h->prm.refine_every,
+                             h->prm.refine_budget, st));
+        {
+            GateScope g0(h, 0);
+            SW_TRY(apply_A(h, h->tmp, A_OUT_R, nullptr, nullptr, 1, st));
+            SW_TRY(apply_AT(h, false, st));
+            SW_TRY(launch_pt_refine(h, h->g, h->xi, alpha, h->G, h->zin, 1, st));
+        }
+        GateScope g1(h, 1);
+        return exact_gradient(h, st);
+    }
     SW_TRY(apply_A(h, h->tmp, A_OUT_R, nullptr, nullptr, 1, st));        // C A P delta
     SW_TRY(apply_AT(h, false, st));
     return launch_pt_refine(h, h->g, h->xi, alpha, h->G, h->zin, 1, st);
@@ -543,7 +574,8 @@ swopt_status build_graph(swopt_handle* h, int kind)
             pr.end = node_of(en.first);
             pr.ev_begin = b.first;
             pr.ev_end = en.first;
-            pr.kernel = b.second;
+            pr.gated = b.second >= 16;
+            pr.kernel = b.second & 15;
             if (pr.begin && pr.end) G.probes.push_back(pr);
             ++i;
         }
@@ -561,6 +593,7 @@ swopt_status launch_graph(swopt_handle* h, int kind, cudaStream_t st)
             ProfileRec rec;
             if (!take_events(h, &rec.a, &rec.b)) continue;
             rec.kernel = pr.kernel;
+            rec.iter = pr.gated ? h->iter : -1;
             SW_CUDA(cudaGraphExecEventRecordNodeSetEvent(G.gexec, pr.begin, rec.a));
             SW_CUDA(cudaGraphExecEventRecordNodeSetEvent(G.gexec, pr.end, rec.b));
             h->prof.push_back(rec);
@@ -582,6 +615,7 @@ swopt_status run_iteration(swopt_handle* h, cudaStream_t st)
     } else {
         SW_TRY(fista_iteration(h, kind, st));
     }
+    if (kind == 1) ++h->resyncs;
     ++h->iter;
     return SWOPT_OK;
 }
@@ -922,6 +956,14 @@ swopt_status swopt_fista_init(swopt_handle* h, const float* y_dev, const swopt_s
     SW_CUDA(cudaMemsetAsync(h->xi, 0, nc_of(h) * sizeof(float), st));
     SW_TRY(fista_reset_scalars(h, st));
     h->iter = 0;
+    h->resyncs = prm->refine_every > 0 ? 1 : 0;
+    if (prm->refine_every > 0 && prm->refine_budget > 0) {
+        if (!h->sched) SW_TRY(dalloc(&h->sched, 4));
+        if (!h->rlog) SW_TRY(dalloc(&h->rlog, (size_t)kRefineLog));
+        SW_CUDA(cudaMemsetAsync(h->sched, 0, 4 * sizeof(int), st));
+        SW_CUDA(cudaMemsetAsync(h->rlog, 0xff, (size_t)kRefineLog * sizeof(int), st));
+        SW_CUDA(cudaMemsetAsync(h->scal + SC_BUDGET, 0, sizeof(double), st));
+    }
     if (prm->refine_every > 0) {
         // gradient at c_0 = 0 and the first prox input, at the resync precision
         if (!h->G) SW_TRY(dalloc(&h->G, nc_of(h)));
@@ -960,6 +1002,161 @@ swopt_status swopt_fista_get(swopt_handle* h, float* c_dev, void* stream)
     }
     SW_CUDA(cudaMemcpyAsync(c_dev, h->c, nc_of(h) * sizeof(float), cudaMemcpyDeviceToDevice,
                             (cudaStream_t)stream));
+    return SWOPT_OK;
+}
+
+swopt_status swopt_refine_stats(swopt_handle* h, int64_t* iterations, int64_t* resyncs,
+                                void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!iterations || !resyncs || !h->fista_ready) {
+        set_error("null output or no FISTA state");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    *iterations = h->iter;
+    *resyncs = h->resyncs;
+    if (iteration_kind(h) == 2) {
+        int sc[4] = {0, 0, 0, 0};
+        cudaStream_t st = (cudaStream_t)stream;
+        SW_CUDA(cudaMemcpyAsync(sc, h->sched, sizeof(sc), cudaMemcpyDeviceToHost, st));
+        SW_CUDA(cudaStreamSynchronize(st));
+        *resyncs = 1 + (int64_t)sc[2];  // the initial exact gradient and the device's
+    }
+    return SWOPT_OK;
+}
+
+namespace {
+
+// Host image of the FISTA state (swopt_fista_save / swopt_fista_restore).
+struct FistaStateHeader {
+    uint64_t magic;
+    int32_t version, P, Y, X, Z, N, refine_every, refined, gated;
+    int32_t inner_iters, momentum, inner_momentum, refine_precision;
+    double step, lambda_l1, lambda_tv, refine_budget;
+    int64_t iter, resyncs;
+};
+constexpr uint64_t kStateMagic = 0x5357'4F50'5446'5354ull;  // "SWOPTFST"
+
+size_t fista_state_size(const swopt_handle* h)
+{
+    const size_t n = nc_of(h);
+    const bool refined = h->prm.refine_every > 0;
+    return sizeof(FistaStateHeader) + (refined ? 4 : 3) * n * sizeof(float) +
+           SC_COUNT * sizeof(double) + 4 * sizeof(int);
+}
+
+}  // namespace
+
+swopt_status swopt_fista_state_bytes(swopt_handle* h, size_t* bytes)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!bytes || !h->fista_ready) {
+        set_error("null output or no FISTA state");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    *bytes = fista_state_size(h);
+    return SWOPT_OK;
+}
+
+swopt_status swopt_fista_save(swopt_handle* h, void* host_buf, size_t bytes, void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!host_buf || !h->fista_ready || bytes < fista_state_size(h)) {
+        set_error("null buffer, no FISTA state, or a buffer below swopt_fista_state_bytes");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = nc_of(h);
+    FistaStateHeader hd{};
+    hd.magic = kStateMagic;
+    hd.version = 1;
+    hd.P = h->P; hd.Y = h->Y; hd.X = h->X; hd.Z = h->Z; hd.N = h->N;
+    hd.refine_every = h->prm.refine_every;
+    hd.refined = h->prm.refine_every > 0;
+    hd.gated = iteration_kind(h) == 2;
+    hd.inner_iters = h->prm.inner_iters;
+    hd.momentum = h->prm.momentum;
+    hd.inner_momentum = h->prm.inner_momentum;
+    hd.refine_precision = h->prm.refine_precision;
+    hd.step = h->step;
+    hd.lambda_l1 = h->prm.lambda_l1;
+    hd.lambda_tv = h->prm.lambda_tv;
+    hd.refine_budget = h->prm.refine_budget;
+    hd.iter = h->iter;
+    hd.resyncs = h->resyncs;
+    uint8_t* p = static_cast<uint8_t*>(host_buf);
+    std::memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    const float* vecs[4] = {h->c, h->xi, h->zin, h->G};
+    for (int v = 0; v < (hd.refined ? 4 : 3); ++v) {
+        SW_CUDA(cudaMemcpyAsync(p, vecs[v], n * sizeof(float), cudaMemcpyDeviceToHost, st));
+        p += n * sizeof(float);
+    }
+    SW_CUDA(cudaMemcpyAsync(p, h->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
+    p += SC_COUNT * sizeof(double);
+    if (hd.gated) SW_CUDA(cudaMemcpyAsync(p, h->sched, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    else std::memset(p, 0, 4 * sizeof(int));
+    SW_CUDA(cudaStreamSynchronize(st));
+    return device_errors(h);
+}
+
+swopt_status swopt_fista_restore(swopt_handle* h, const void* host_buf, size_t bytes,
+                                 void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!host_buf || !h->fista_ready || bytes < fista_state_size(h)) {
+        set_error("null buffer, no FISTA state (call swopt_fista_init first), or a buffer "
+                  "below swopt_fista_state_bytes");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    FistaStateHeader hd;
+    std::memcpy(&hd, host_buf, sizeof(hd));
+    if (hd.magic != kStateMagic || hd.version != 1 || hd.P != h->P || hd.Y != h->Y ||
+        hd.X != h->X || hd.Z != h->Z || hd.N != h->N ||
+        hd.refine_every != h->prm.refine_every || hd.gated != (iteration_kind(h) == 2) ||
+        hd.inner_iters != h->prm.inner_iters || hd.momentum != h->prm.momentum ||
+        hd.inner_momentum != h->prm.inner_momentum ||
+        hd.refine_precision != h->prm.refine_precision || hd.lambda_l1 != h->prm.lambda_l1 ||
+        hd.lambda_tv != h->prm.lambda_tv || hd.refine_budget != h->prm.refine_budget ||
+        !(hd.step > 0) || hd.iter < 0) {
+        set_error("the saved FISTA state belongs to another geometry or other settings");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = nc_of(h);
+    if (hd.refined && !h->G) SW_TRY(dalloc(&h->G, n));
+    const uint8_t* p = static_cast<const uint8_t*>(host_buf) + sizeof(hd);
+    float* vecs[4] = {h->c, h->xi, h->zin, h->G};
+    for (int v = 0; v < (hd.refined ? 4 : 3); ++v) {
+        SW_CUDA(cudaMemcpyAsync(vecs[v], p, n * sizeof(float), cudaMemcpyHostToDevice, st));
+        p += n * sizeof(float);
+    }
+    SW_CUDA(cudaMemcpyAsync(h->scal, p, SC_COUNT * sizeof(double), cudaMemcpyHostToDevice, st));
+    p += SC_COUNT * sizeof(double);
+    if (hd.gated) SW_CUDA(cudaMemcpyAsync(h->sched, p, 4 * sizeof(int), cudaMemcpyHostToDevice, st));
+    SW_CUDA(cudaStreamSynchronize(st));
+    // the step is baked into captured iterations: capture again
+    release_graph(h);
+    h->step = hd.step;
+    h->iter = hd.iter;
+    h->resyncs = hd.resyncs;
+    return SWOPT_OK;
+}
+
+swopt_status swopt_debug_barrier(swopt_handle* h, int phantom_arrivals, unsigned poll_limit)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (phantom_arrivals < 0 || phantom_arrivals > 1024) {
+        set_error("phantom_arrivals must be in [0, 1024]");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    SW_TRY(coop_debug(h, (unsigned)phantom_arrivals, poll_limit));
+    SW_CUDA(cudaDeviceSynchronize());
     return SWOPT_OK;
 }
 
@@ -1160,16 +1357,36 @@ swopt_status swopt_profile_read(swopt_handle* h, int kernel_id, double* total_ms
         set_error("kernel_id must be 0 (A), 1 (A^T), 2 or 3 (A, A^T at the resync precision)");
         return SWOPT_ERR_INVALID_ARG;
     }
+    // launches behind the refined solve's gate count only where the device
+    // decided for their branch (ids 0/1: the increment, 2/3: the exact
+    // gradient), read from the decision log
+    std::vector<int> dlog;
     for (auto& r : h->prof) {
         cudaError_t e = cudaEventSynchronize(r.b);
         if (e != cudaSuccess) {
             set_error("cudaEventSynchronize failed: %s", cudaGetErrorString(e));
             return SWOPT_ERR_CUDA;
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, r.a, r.b);
-        h->prof_ms[r.kernel] += ms;
-        h->prof_n[r.kernel] += 1;
+        bool ran = true;
+        if (r.iter >= 0) {
+            if (dlog.empty()) {
+                if (!h->rlog) {
+                    set_error("internal: gated launch without a decision log");
+                    return SWOPT_ERR_DEVICE_CHECK;
+                }
+                dlog.resize(kRefineLog);
+                SW_CUDA(cudaMemcpy(dlog.data(), h->rlog, kRefineLog * sizeof(int),
+                                   cudaMemcpyDeviceToHost));
+            }
+            const int d = dlog[(size_t)(r.iter & (kRefineLog - 1))];
+            ran = d == (r.kernel >= 2 ? 1 : 0);
+        }
+        if (ran) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, r.a, r.b);
+            h->prof_ms[r.kernel] += ms;
+            h->prof_n[r.kernel] += 1;
+        }
         h->event_pool.push_back(r.a);
         h->event_pool.push_back(r.b);
     }
@@ -1326,9 +1543,9 @@ struct swopt_batch {
     std::vector<cudaStream_t> streams;  // one per problem (capture only)
     std::vector<cudaEvent_t> events;    // fork / join
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
     std::vector<uint64_t> gen;          // handle graph generations at capture
-    int64_t kernels[2] = {0, 0};
+    int64_t kernels[3] = {0, 0, 0};
     int64_t iter = 0;
 };
 
@@ -1424,9 +1641,10 @@ swopt_status swopt_batch_create(swopt_handle* const* hs, int count, swopt_batch*
                 return SWOPT_ERR_INVALID_ARG;
             }
         if (h->device != hs[0]->device || h->iter != hs[0]->iter ||
-            h->prm.refine_every != hs[0]->prm.refine_every) {
-            set_error("batch handle %d differs from handle 0 in device, iteration count or "
-                      "refine_every", i);
+            h->prm.refine_every != hs[0]->prm.refine_every ||
+            (h->prm.refine_budget > 0) != (hs[0]->prm.refine_budget > 0)) {
+            set_error("batch handle %d differs from handle 0 in device, iteration count, "
+                      "refine_every or the use of refine_budget", i);
             return SWOPT_ERR_INVALID_ARG;
         }
     }
@@ -1488,7 +1706,10 @@ swopt_status swopt_batch_step(swopt_batch* b, int iters, void* stream)
         const int kind = iteration_kind(b->hs[0]);
         if (!b->gexec[kind]) SW_TRY(batch_capture(b, kind));
         SW_CUDA(cudaGraphLaunch(b->gexec[kind], st));
-        for (int i = 0; i < n; ++i) ++b->hs[i]->iter;
+        for (int i = 0; i < n; ++i) {
+            if (kind == 1) ++b->hs[i]->resyncs;
+            ++b->hs[i]->iter;
+        }
         b->hs[0]->launches += b->kernels[kind];  // counted once, on the first handle
         ++b->iter;
     }

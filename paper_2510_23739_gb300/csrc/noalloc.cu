@@ -4,50 +4,32 @@
 // of memory from cudaMalloc; see the declaration in swopt.h for the limits
 // and the sharing rules.
 #include <cmath>
-#include <mutex>
 
 #include "swopt_internal.cuh"
 
 namespace {
 
 constexpr size_t kMaxElems = SWOPT_PROX_TV_STATIC_MAX_ELEMS;
-constexpr int kMaxDevices = 64;
-
 // u, r (ping) and r (pong), three components each, for up to kMaxElems
 // volume elements.  Every GPU that loads the library holds this array until
 // the process exits.
 __device__ __align__(256) float g_tv_scratch[9 * kMaxElems];
 
-std::mutex g_setup_mu;
-float* g_scratch_dev[kMaxDevices] = {};
-
-// Device address of g_tv_scratch on the current device (set up once per
-// device).  In host code the symbol is only a host-side stand-in: the kernels
-// must receive this address.
+// Device address of g_tv_scratch in the current device's context.  In host
+// code the symbol is only a host-side stand-in: the kernels must receive this
+// address.  It is looked up on every call rather than cached: the lookup
+// allocates nothing once the module is loaded, and a context that was torn
+// down and created again (cudaDeviceReset) may place the module elsewhere.
 swopt_status scratch_address(float** out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        swopt::set_error("cudaGetDevice failed: %s", cudaGetErrorString(e));
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_tv_scratch);
+    if (e != cudaSuccess || !p) {
+        swopt::set_error("cudaGetSymbolAddress of the static scratch failed: %s",
+                         cudaGetErrorString(e));
         return SWOPT_ERR_CUDA;
     }
-    if (dev < 0 || dev >= kMaxDevices) {
-        swopt::set_error("device ordinal %d beyond the %d supported", dev, kMaxDevices);
-        return SWOPT_ERR_UNSUPPORTED;
-    }
-    std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_dev[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_tv_scratch);
-        if (e != cudaSuccess || !p) {
-            swopt::set_error("cudaGetSymbolAddress of the static scratch failed: %s",
-                             cudaGetErrorString(e));
-            return SWOPT_ERR_CUDA;
-        }
-        g_scratch_dev[dev] = static_cast<float*>(p);
-    }
-    *out = g_scratch_dev[dev];
+    *out = static_cast<float*>(p);
     return SWOPT_OK;
 }
 

@@ -35,10 +35,11 @@ fwd_simt_kernel(const float* __restrict__ b, const float* __restrict__ Kf,
                 const uint8_t* __restrict__ fmask, const float* __restrict__ Cmf,
                 const float* __restrict__ ytil, float* __restrict__ u,
                 double* __restrict__ partials, int Y, int X, int Z, int k, int Twp,
-                int nTc, int jc, int scale)
+                int nTc, int jc, int scale, const int* gate, int want)
 {
     extern __shared__ float sm[];
     __shared__ double red[kThreads / 32];
+    if (gated_off(gate, want)) return;
     const int r = k >> 1;
     const int HX = TILE + 2 * r, HY = TILE + 2 * r;
     const int tilesX = (X + TILE - 1) / TILE;
@@ -163,9 +164,10 @@ fwd_simt_kernel(const float* __restrict__ b, const float* __restrict__ Kf,
 __global__ void __launch_bounds__(kThreads)
 adj_simt_kernel(const float* __restrict__ u, const float* __restrict__ Ka,
                 const uint8_t* __restrict__ amask, float* __restrict__ g, int Y, int X,
-                int Z, int k, int Twp, int Zp, int nJc, int tcs)
+                int Z, int k, int Twp, int Zp, int nJc, int tcs, const int* gate, int want)
 {
     extern __shared__ float sm[];
+    if (gated_off(gate, want)) return;
     const int r = k >> 1;
     const int HX = TILE + 2 * r, HY = TILE + 2 * r;
     const int tilesX = (X + TILE - 1) / TILE;
@@ -248,8 +250,10 @@ adj_simt_kernel(const float* __restrict__ u, const float* __restrict__ Ka,
 
 // b[m][s][j] = sum_p Sm[m][p][j] c[p][s][j]
 __global__ void states_kernel(const float* __restrict__ c, const float* __restrict__ Sm,
-                              float* __restrict__ b, int Q, int P, int S, int Z)
+                              float* __restrict__ b, int Q, int P, int S, int Z,
+                              const int* gate, int want)
 {
+    if (gated_off(gate, want)) return;
     const size_t n = (size_t)Q * S * Z;
     const size_t SZ = (size_t)S * Z;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
@@ -328,8 +332,10 @@ __global__ void pt_kernel(const float* __restrict__ g, const float* __restrict__
 __global__ void pt_refine_kernel(const float* __restrict__ g, const float* __restrict__ Sm,
                                  const float* __restrict__ xi, float alpha, float* G,
                                  float* __restrict__ out, const double* __restrict__ scal,
-                                 int Q, int P, int S, int Z, int add)
+                                 int Q, int P, int S, int Z, int add, const int* gate,
+                                 int want)
 {
+    if (gated_off(gate, want)) return;
     const size_t SZ = (size_t)S * Z;
     const size_t n = (size_t)P * SZ;
     const float beta = (float)scal[1];
@@ -388,7 +394,7 @@ swopt_status simt_forward(swopt_handle* h, const float* b, float* u, const float
     prof_begin(h, 0, st, &rec);
     fwd_simt_kernel<<<grid, kThreads, smem, st>>>(b, h->Kf, h->fmask, h->Cmf, ytil, u, partials,
                                                   h->Y, h->X, h->Z, h->k, h->Twp, h->nTc, jc,
-                                                  scale);
+                                                  scale, h->gate, h->gate_want);
     SW_LAUNCHED(h);
     prof_end(h, &rec, st);
     return SWOPT_OK;
@@ -406,7 +412,8 @@ swopt_status simt_adjoint(swopt_handle* h, const float* u, float* g, cudaStream_
     ProfileRec rec;
     prof_begin(h, 1, st, &rec);
     adj_simt_kernel<<<grid, kThreads, smem, st>>>(u, h->Ka, h->amask, g, h->Y, h->X, h->Z, h->k,
-                                                  h->Twp, h->Zp, h->nJc, tcs);
+                                                  h->Twp, h->Zp, h->nJc, tcs, h->gate,
+                                                  h->gate_want);
     SW_LAUNCHED(h);
     prof_end(h, &rec, st);
     return SWOPT_OK;
@@ -415,7 +422,8 @@ swopt_status simt_adjoint(swopt_handle* h, const float* u, float* g, cudaStream_
 swopt_status launch_states(swopt_handle* h, const float* c, float* b, cudaStream_t st)
 {
     const size_t n = nb_of(h);
-    states_kernel<<<grid_for(n, 256), 256, 0, st>>>(c, h->Sm, b, h->Q, h->P, h->S, h->Z);
+    states_kernel<<<grid_for(n, 256), 256, 0, st>>>(c, h->Sm, b, h->Q, h->P, h->S, h->Z, h->gate,
+                                                    h->gate_want);
     SW_LAUNCHED(h);
     return SWOPT_OK;
 }
@@ -455,7 +463,8 @@ swopt_status launch_pt_refine(swopt_handle* h, const float* g, const float* xi, 
 {
     const size_t n = nc_of(h);
     pt_refine_kernel<<<grid_for(n, 256), 256, 0, st>>>(g, h->Sm, xi, alpha, G, out, h->scal,
-                                                        h->Q, h->P, h->S, h->Z, add);
+                                                        h->Q, h->P, h->S, h->Z, add, h->gate,
+                                                        h->gate_want);
     SW_LAUNCHED(h);
     return SWOPT_OK;
 }

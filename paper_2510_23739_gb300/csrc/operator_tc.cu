@@ -295,6 +295,8 @@ struct TcArgs {
     int quantum;                // runs per indivisible piece of work
     long long wq;               // pieces of work in all: tile-states x runs / quantum
     int max_pieces;             // partial-sum slots per tile-state
+    const int* gate;            // launch runs only if *gate == want (null: always)
+    int want;
 };
 
 // ---------------------------------------------------------------------------
@@ -349,6 +351,8 @@ __device__ __forceinline__ bool tc_unit(const TcArgs& a, int k, TcUnit& u)
 __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
+    // a closed gate: return before any barrier, TMEM or copy is set up
+    if (gated_off(a.gate, a.want)) return;
     __shared__ __align__(8) uint64_t bar_full[kMaxStages];
     __shared__ __align__(8) uint64_t bar_empty[kMaxStages];
     __shared__ __align__(8) uint64_t bar_afull, bar_aempty;
@@ -810,8 +814,10 @@ struct TermPtrs {
 
 __global__ void tc_states_kernel(const float* __restrict__ c, const float* __restrict__ Sm,
                                  TermPtrs out, int terms, int Q, int P, int Y, int X, int Z,
-                                 int slices, int KS, int Yp, int Xp, int r, int vec)
+                                 int slices, int KS, int Yp, int Xp, int r, int vec,
+                                 const int* gate, int want)
 {
+    if (gated_off(gate, want)) return;
     // one thread per (slice, y, x): the P x 8 values of c are read once and
     // every switching state m is written from them
     const unsigned n = (unsigned)slices * Y * X;
@@ -1149,6 +1155,8 @@ TcArgs dir_args(const swopt_handle* h, const TcOperator* t, const TcDir& D, bool
     a.wq = D.wq;
     a.max_pieces = D.max_pieces;
     for (int tt = 0; tt < kMaxTerms; ++tt) a.a_t[tt] = adj ? t->rpad[tt] : t->bpad[tt];
+    a.gate = h->gate;
+    a.want = h->gate_want;
     return a;
 }
 
@@ -1300,6 +1308,7 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
                 return sg;
             }
             TcArgs a = dir_args(h, t, D, adj);
+            a.gate = nullptr;  // tuning launches always run
             a.out_f = adj ? h->g : h->u;
             a.mode = 0;
             swopt_status s = launch_conv(h, D, a, 0);  // warm-up
@@ -1433,7 +1442,8 @@ swopt_status tc_states(swopt_handle* h, const float* c, cudaStream_t st)
     // 16-byte loads when every run of 8 depths starts on a 16-byte boundary
     const int vec = (h->Z % 4) == 0 && ((uintptr_t)c & 15u) == 0;
     tc_states_kernel<<<grid, 256, 0, st>>>(c, h->Sm, out, t->terms, h->Q, h->P, h->Y, h->X, h->Z,
-                                           slices, t->F.KS, t->Yp, t->Xp, h->r, vec);
+                                           slices, t->F.KS, t->Yp, t->Xp, h->r, vec, h->gate,
+                                           h->gate_want);
     SW_LAUNCHED(h);
     return SWOPT_OK;
 }

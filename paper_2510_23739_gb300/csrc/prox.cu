@@ -193,7 +193,9 @@ constexpr uint32_t kBarrierPolls = 1u << 25;  // x 32 ns back-off: about a secon
 // arrivals, bar[1] is the generation, bar[2] an error word: a block that polls
 // kBarrierPolls times without seeing the generation advance sets it, and from
 // then on every barrier returns at once (the results are then invalid and the
-// host reports a timeout).
+// host reports a timeout).  bar[4] and bar[5] are a failure-detection test
+// hook (swopt_debug_barrier): blocks the barrier waits for beyond the launch's
+// own, and a poll limit replacing kBarrierPolls (0: the default).
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
 {
     unsigned v;
@@ -211,17 +213,20 @@ __device__ __forceinline__ void grid_sync(unsigned* bar, unsigned nblocks)
     if (threadIdx.x == 0) {
         volatile unsigned* vb = bar;
         if (vb[2] == 0u) {
+            const unsigned expected = nblocks + vb[4];
+            uint32_t limit = kBarrierPolls;
+            if (vb[5] != 0u) limit = vb[5];
             const unsigned gen = ld_acquire(bar + 1);
             unsigned arrived;
             asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;"
                          : "=r"(arrived) : "l"(bar) : "memory");
-            if (arrived == nblocks - 1) {
+            if (arrived == expected - 1) {
                 atomicExch(&bar[0], 0u);
                 asm volatile("red.release.gpu.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
             } else {
                 uint32_t polls = 0;
                 while (ld_acquire(bar + 1) == gen && vb[2] == 0u) {
-                    if (++polls > kBarrierPolls) {
+                    if (++polls > limit) {
                         atomicExch(&bar[2], 1u);
                         break;
                     }
@@ -697,6 +702,58 @@ __global__ void red_final_kernel(const double* parts, int count, double* out)
     if (threadIdx.x == 0) *out = s;
 }
 
+// parts[b] = this block's sum of d^2, parts[gridDim.x + b] = its sum of c^2
+__global__ void red_pair_kernel(const float* __restrict__ d, const float* __restrict__ c,
+                                size_t n, double* parts)
+{
+    __shared__ double sh[kRedThreads / 32];
+    double sd = 0.0, sc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const double a = d[i], b = c[i];
+        sd += a * a;
+        sc += b * b;
+    }
+    sd = block_sum(sd, sh);
+    __syncthreads();  // sh is reused
+    sc = block_sum(sc, sh);
+    if (threadIdx.x == 0) {
+        parts[blockIdx.x] = sd;
+        parts[gridDim.x + blockIdx.x] = sc;
+    }
+}
+
+// The refined solve's device-side resync decision for the iteration just
+// finished (sched[1] of them so far): rho = ||d|| / ||c|| joins the budget
+// accumulator; the gate opens (sched[0] = 1) on every R-th iteration or once
+// the accumulated rho exceeds the budget, and the accumulator restarts.
+__global__ void refine_decide_kernel(const double* parts, int count, double* scal, int slot,
+                                     int* sched, int* rlog, int R, double budget)
+{
+    __shared__ double sh[kRedThreads / 32];
+    double sd = 0.0, sc = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        sd += parts[i];
+        sc += parts[count + i];
+    }
+    sd = block_sum(sd, sh);
+    __syncthreads();
+    sc = block_sum(sc, sh);
+    if (threadIdx.x != 0) return;
+    const int it = sched[1];
+    const double rho = sc > 0.0 ? sqrt(sd / sc) : (sd > 0.0 ? 1e300 : 0.0);
+    double acc = scal[slot] + rho;
+    const int exact = ((R > 0 && (it + 1) % R == 0) || acc > budget) ? 1 : 0;
+    if (exact) {
+        acc = 0.0;
+        sched[2] += 1;
+    }
+    scal[slot] = acc;
+    sched[0] = exact;
+    sched[1] = it + 1;
+    rlog[it & (kRefineLog - 1)] = exact;
+}
+
 __global__ void scale_inv_sqrt_kernel(const float* __restrict__ in, float* __restrict__ out,
                                       size_t n, const double* __restrict__ s)
 {
@@ -775,8 +832,8 @@ swopt_status prox_l1(swopt_handle* h, float* x, float thresh, int nonneg, cudaSt
 swopt_status coop_prepare(swopt_handle* h)
 {
     if (!h->coop_bar) {
-        SW_CUDA(cudaMalloc((void**)&h->coop_bar, 4 * sizeof(unsigned)));
-        SW_CUDA(cudaMemset(h->coop_bar, 0, 4 * sizeof(unsigned)));
+        SW_CUDA(cudaMalloc((void**)&h->coop_bar, 8 * sizeof(unsigned)));
+        SW_CUDA(cudaMemset(h->coop_bar, 0, 8 * sizeof(unsigned)));
     }
     if (h->tile_ty == 0) {
         // shared-memory tile: the fewest ghosted columns per SM with every tile
@@ -874,6 +931,14 @@ swopt_status fista_prox_finish(swopt_handle* h, const float* z, float tau, int i
     return launch_coop(h, a, st);
 }
 
+swopt_status coop_debug(swopt_handle* h, unsigned phantom, unsigned poll_limit)
+{
+    SW_TRY(coop_prepare(h));
+    const unsigned w[2] = {phantom, poll_limit};
+    SW_CUDA(cudaMemcpy(h->coop_bar + 4, w, sizeof(w), cudaMemcpyHostToDevice));
+    return SWOPT_OK;
+}
+
 int coop_error_word(swopt_handle* h)
 {
     if (!h->coop_bar) return 0;
@@ -950,6 +1015,17 @@ swopt_status reduce_partials(swopt_handle* h, const double* parts, int count, in
                              cudaStream_t st)
 {
     red_final_kernel<<<1, kRedThreads, 0, st>>>(parts, count, h->scal + slot);
+    SW_LAUNCHED(h);
+    return SWOPT_OK;
+}
+
+swopt_status refine_decide(swopt_handle* h, const float* d, const float* c, int slot, int R,
+                           double budget, cudaStream_t st)
+{
+    red_pair_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(d, c, nc_of(h), h->red);
+    SW_LAUNCHED(h);
+    refine_decide_kernel<<<1, kRedThreads, 0, st>>>(h->red, kRedBlocks, h->scal, slot, h->sched,
+                                                    h->rlog, R, budget);
     SW_LAUNCHED(h);
     return SWOPT_OK;
 }

@@ -44,6 +44,9 @@ void clear_error();
         if (s_ != SWOPT_OK) return s_;                                             \
     } while (0)
 
+// Entries of the refined solve's decision log (a ring).
+constexpr int kRefineLog = 1 << 16;
+
 // Time samples are processed in chunks of 32 (a warp's worth of outputs in
 // the FP32 kernels, two 16-wide N tiles on the tensor cores).
 constexpr int TCHUNK = 32;
@@ -63,7 +66,17 @@ struct TcOperator;
 struct ProfileRec {
     cudaEvent_t a, b;
     int kernel;
+    int64_t iter = -1;  // FISTA iteration of a gated launch (see swopt_handle::gate), else -1
 };
+
+// A kernel launched behind a gate runs only when the device word *gate
+// equals `want`; otherwise every thread returns at once.  Both branches of a
+// device-side decision are launched (and captured) unconditionally, so that
+// one CUDA graph serves every iteration.
+__device__ __forceinline__ bool gated_off(const int* gate, int want)
+{
+    return gate != nullptr && *(volatile const int*)gate != want;
+}
 
 // An event-record node pair of the captured FISTA iteration that brackets
 // one launch of the A (0) or A^T (1) kernel.
@@ -71,10 +84,13 @@ struct GraphProbe {
     cudaGraphNode_t begin = nullptr, end = nullptr;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // placeholders used at capture
     int kernel = 0;
+    bool gated = false;  // the bracketed launch runs behind the refinement gate
 };
 
 // One captured FISTA iteration (kind 0: plain or incremental-gradient
-// iteration; kind 1: the resync iteration of the refined solve).
+// iteration; kind 1: the resync iteration of the refined solve; kind 2: the
+// refined iteration whose resync is decided on the device, both branches
+// behind the gate).
 struct IterGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -143,6 +159,15 @@ struct swopt_handle {
     float* G = nullptr;           // [P][Y][X][Z] refined solve: gradient at c_k
     float* xprev = nullptr;       // [P][Y][X][Z] previous momentum iterate (eps2 test)
     int64_t iter = 0;             // FISTA iterations since swopt_fista_init
+    int64_t resyncs = 0;          // exact gradients of the refined solve (host-scheduled)
+    // Device-side resync decision of the refined solve (refine_budget > 0):
+    // sched[0] gate (1: this iteration recomputes the gradient exactly),
+    // sched[1] iterations decided, sched[2] resyncs; rlog[i % kRefineLog] the
+    // decision of iteration i (read back for the profile).
+    int* sched = nullptr;
+    int* rlog = nullptr;
+    const int* gate = nullptr;    // while launching one branch: the gate word, else null
+    int gate_want = 0;            // and the value that lets it run
 
     // tensor-core path
     swopt::TcOperator* tc = nullptr;      // operator of `precision`
@@ -157,7 +182,7 @@ struct swopt_handle {
     bool use_graph = true;
     bool capturing = false;
     cudaStream_t cap_stream = nullptr;
-    swopt::IterGraph graphs[2];
+    swopt::IterGraph graphs[3];
     uint64_t graph_gen = 0;       // bumped whenever captured work may have gone stale
     std::vector<std::pair<cudaEvent_t, int>> cap_events;
 
@@ -265,6 +290,8 @@ swopt_status prox_tv_coop(swopt_handle* h, const float* z, float tau, int iters,
 swopt_status fista_prox_finish(swopt_handle* h, const float* z, float tau, int iters,
                                int inner_momentum, float theta, float* delta, cudaStream_t st);
 swopt_status coop_prepare(swopt_handle* h);
+// Failure-detection test hook of the cooperative kernels' grid barrier.
+swopt_status coop_debug(swopt_handle* h, unsigned phantom, unsigned poll_limit);
 // Reads and clears the cooperative kernel's barrier error word (0 = none).
 int coop_error_word(swopt_handle* h);
 swopt_status fista_reset_scalars(swopt_handle* h, cudaStream_t st);
@@ -276,6 +303,12 @@ swopt_status reduce_abs(swopt_handle* h, const float* x, size_t n, int slot, cud
 swopt_status reduce_tv(swopt_handle* h, const float* x, int slot, cudaStream_t st);
 swopt_status reduce_partials(swopt_handle* h, const double* parts, int count, int slot,
                              cudaStream_t st);
+// Refined solve, device-side schedule: rho = ||d|| / ||c|| (FP64) is added
+// to the budget accumulator scal[slot]; the gate h->sched[0] opens the exact
+// resync when the iteration is a multiple of R or the accumulated sum
+// exceeds `budget` (which then restarts from 0).
+swopt_status refine_decide(swopt_handle* h, const float* d, const float* c, int slot, int R,
+                           double budget, cudaStream_t st);
 swopt_status scale_by_inv_sqrt(swopt_handle* h, const float* in, float* out, size_t n, int slot,
                                cudaStream_t st);
 swopt_status fill_counter_random(swopt_handle* h, float* x, size_t n, uint64_t seed,
