@@ -268,19 +268,23 @@ def run_swopt(args, rank, world, device):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     op.fista_init(y, params)
-    # the first iterations of the solve (graph capture on the first one is
-    # outside: it happens at the first step of each iteration kind)
-    op.fista_step(1)
-    n_early = max(0, min(args.presolve, 25) - 1)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    op.fista_step(n_early)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    early = {"iterations": f"2..{n_early + 1}", "ms_per_iteration":
-             e0.elapsed_time(e1) / max(n_early, 1),
-             "exact_gradients": op.refine_stats()[1] if refine else None}
-    op.fista_step(max(0, args.presolve - 1 - n_early))
+    early = None
+    if args.presolve >= 2:
+        # the first iterations of the solve (the graph of an iteration kind is
+        # captured at its first step: iteration 1 stays outside the timing)
+        op.fista_step(1)
+        n_early = min(args.presolve, 25) - 1
+        torch.cuda.synchronize()
+        e0.record(stream)
+        op.fista_step(n_early)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        early = {"iterations": f"2..{n_early + 1}", "ms_per_iteration":
+                 e0.elapsed_time(e1) / n_early,
+                 "exact_gradients": op.refine_stats()[1] if refine else None}
+        op.fista_step(args.presolve - 1 - n_early)
+    else:
+        op.fista_step(args.presolve)
     op.fista_step(args.warmup)
     torch.cuda.synchronize()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)

@@ -1,38 +1,43 @@
 // Tensor-core (tcgen05, sm_103a) kernels for the acoustic correlation A and
 // its transpose A^T (Sec. 2.3.3, Eq. acoustic-full-forward).
 //
-// Both are implicit GEMMs over tiles of 16 x 8 scan positions (M = 128, one
-// TMEM lane per position):
-//   A  : D[pos][t] += sum_j b[pos + d][j] K[j][d][t]     (K-dim: depth j)
-//   A^T: D[pos][j] += sum_t r[pos - d][t] K[j][d][t]     (K-dim: window sample t)
-// for every lateral tap d.  One CTA owns MT tiles side by side (16 x 8 MT
-// positions) for one switching state, so every staged block of the kernel
-// feeds MT MMAs.  Operands live in shared memory in the no-swizzle K-major
-// core-matrix layout: the A operand is a halo of the CTA's tiles stored as
-// [8-element slice][halo row][halo column][8 elements], so the operand of
-// tap d and tile i is the same buffer at a byte offset (rows of 8
-// consecutive x are 16 B apart; 8-row groups are one halo row apart).
+// Both are implicit GEMMs whose M dimension is the output channel and whose
+// N dimension is a tile of 32 x 8 = 256 scan positions:
+//   A  : D[t][pos] += sum_j K[j][d][t] b[pos + d][j]     (channel t, K-dim depth j)
+//   A^T: D[j][pos] += sum_t K[j][d][t] r[pos - d][t]     (channel j, K-dim sample t)
+// for every lateral tap d.  One MMA is M = 128 channels x N = 256 positions
+// x K = 16 (one pair of 8-element slices of the contracted dimension).  The
+// kernel block of a (tap, pair) is the A operand, streamed through a ring of
+// shared-memory stages by bulk asynchronous copies; the image is the B
+// operand: a halo of the CTA's tiles, staged once per group of slice pairs
+// as [8-element slice][halo row][halo column][8 elements], so that the
+// operand of tap d is the same buffer at a byte offset (8 consecutive x of
+// a halo row form one 16 B x 8 core matrix; consecutive rows are one halo
+// row apart).  MT tiles side by side share every staged kernel block.
 //
-// Measured on GB300: one warp (its elected lane) issues a tcgen05.mma about
-// every 150 cycles whatever the shape or the accumulator, while the tensor
-// core takes about 56 cycles for M = 128, N = 96, K = 16; two issuing warps
-// reach about 76 cycles per MMA between them.  So every MMA covers the whole
-// output range (N = the time window for A, the padded depth count for A^T)
-// at TMEM column 0 of its tile, and two warps issue.  Trailing pairs of
-// slices whose kernel is zero for every tap are dropped.  The kernel is
-// pre-packed per tap as [pair][slice][N rows][8] (leading offset N x 16 B),
-// so every descriptor of the MMA loop is uniform arithmetic on loop
-// counters.  Consecutive taps are grouped into runs of one stage of shared
-// memory (several taps per stage), each arriving with one bulk asynchronous
-// copy.
+// Measured on GB300 (one SM, operands in shared memory): an MMA of
+// M = 128 x N x K = 16 takes max(N / 2, (128 + N) / 4) cycles, the larger
+// term being the tensor core's shared-memory operand reads at 128 B per
+// cycle; one issuing warp keeps the tensor core busy.  N = 256 makes the MMA
+// compute-bound (128 cycles against 96 of operand reads), which leaves
+// shared-memory bandwidth for the copies that feed the next MMAs.
 //
-// Roles (224 threads) of a persistent CTA: warp 0 stages operands with bulk
-// asynchronous copies (the TMA engine) on mbarriers; warps 1 and 6 issue
-// tcgen05.mma and commits (an elected lane of each, in a converged warp):
-// they take alternate stages (runs of taps) into accumulators of their own;
-// warps 2-5 read the accumulators back with tcgen05.ld, sum them, write the
-// epilogue and hand the accumulators back zeroed.  The CTAs share the runs
-// of all tile-states equally (the stream-K split), so a tile-state may be
+// Measured too: the issue loop must stay simple.  With the MMAs of a stage
+// issued from nested loops whose trip counts and branches depend on the
+// configuration (pairs per group, channel blocks, tiles, which products),
+// the issuing thread took about 230 cycles per MMA; the same stage issued
+// from one loop over its taps with the products of a tap unrolled at
+// compile time takes about 113 (the tensor core then sets the pace).  So
+// each group holds one slice pair, and the products of a tap come from a
+// loop specialised per (tiles, channel blocks, precision), chosen once per
+// stage.
+//
+// Roles (192 threads) of a persistent CTA: warp 0 stages operands with bulk
+// asynchronous copies (the TMA engine) on mbarriers; warp 1 issues
+// tcgen05.mma and commits (its elected lane, in a converged warp); warps 2-5
+// read the accumulators back with tcgen05.ld (lane = channel), run the
+// epilogue and hand the accumulators back zeroed.  The CTAs share the runs of
+// taps of all tile-states equally (the stream-K split), so a tile-state may be
 // contracted in pieces by neighbouring CTAs and finished by the last of them
 // to arrive.  Every wait is bounded: on a timeout the CTA records an error in
 // a device word, drains its own copies and MMAs, frees its TMEM and exits.
@@ -40,12 +45,9 @@
 // Precisions: BF16 operands with FP32 accumulation (1 term), or a split of
 // both operands into 2 BF16 terms (v = v0 + v1, v1 the BF16 rounding of
 // v - v0) with the 3 products v0 w0, v0 w1, v1 w0 (the dropped v1 w1 is
-// below 2^-16 of |v w|) accumulated in FP32.  The 2 correction products go
-// to an accumulator of their own, so that the tensor core's FP32
-// accumulation rounds them on their own (2^-8 smaller) scale; what remains
-// is the rounding of the main accumulation, a few 1e-6 relative at depth x
-// support sums of 10^4 terms.  A third term (6 products) was measured to
-// give no further gain for that reason and is not offered.
+// below 2^-16 of |v w|) accumulated in FP32; the 2 correction products go to
+// an accumulator of their own where TMEM holds it, so that the tensor core's
+// FP32 accumulation rounds them on their own (2^-8 smaller) scale.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -58,14 +60,18 @@ namespace swopt {
 
 constexpr int kMaxTerms = 2;    // BF16 terms per operand of the split precision
 constexpr int kMaxSpecies = 8;  // the geometry's limit on P
+constexpr int kRows = 128;      // MMA M: output channels per block
+constexpr int kTileY = 32;      // scan rows of a position tile
+constexpr int kTilePos = 256;   // MMA N: positions of a tile (32 rows x 8 columns)
+constexpr int kBlockBytes = 2 * kRows * 16;  // one (tap, pair, channel block) kernel block
 
 // Operator data of one direction (forward or adjoint).
 struct TcDir {
-    int GA = 0, NG = 0, KS = 0;   // A slices per group, groups, padded slices
-    int NB = 0;                   // accumulator columns per tile
-    int MT = 1;                   // tiles per CTA
-    int RA = 1;                   // accumulators per tile and issuer: 1, or 2 (corrections apart)
-    int NI = 1;                   // MMA-issuing warps (1 or 2), each with its own accumulators
+    int GA = 0, NG = 0, KS = 0;   // image slices per group (even), groups, padded slices
+    int MB = 1;                   // channel blocks of 128 rows
+    int rows = 0;                 // valid channels (window samples for A, depths for A^T)
+    int MT = 1;                   // position tiles per CTA, side by side along x
+    int RA = 1;                   // accumulators per (block, tile): 2 keeps corrections apart
     int whole = 1;                // 1: CTAs take whole tile-states; 0: balanced runs (stream-K)
     int runs = 0;                 // runs of taps per tile-state (all groups)
     int NBUF = 1;                 // accumulator buffers in TMEM (2: epilogue overlaps the next unit)
@@ -73,16 +79,17 @@ struct TcDir {
     int quantum = 1;              // runs per indivisible piece of work
     long long wq = 0;             // pieces of work in all: tile-states x runs / quantum
     int max_pieces = 1;           // most CTAs sharing one tile-state
-    float* part = nullptr;        // max_pieces > 1: [tile-states][max_pieces][MT][NB/16][128][16]
+    float* part = nullptr;        // max_pieces > 1: [tile-states][max_pieces][MB][MT][16][128][16]
     int* ticket = nullptr;        // max_pieces > 1: [tile-states] arrival counters (return to 0)
-    int NS = 4;                   // stages of the B ring
+    int NS = 4;                   // stages of the kernel ring
     uint32_t stage_bytes = 0;     // bytes of one stage (hi part; lo is as large)
     int HX = 0, npos = 0;         // halo width and positions
     int cols = 0;                 // TMEM columns allocated
     size_t smem = 0;              // dynamic shared memory requested
     int groupsX = 0;              // CTAs along x
-    __nv_bfloat16* Bt[kMaxTerms] = {nullptr, nullptr};  // kernel per term, [group][tap][pair][2][N][8]
-    uint32_t* tab = nullptr;      // per group: header + pair table (see TcArgs)
+    __nv_bfloat16* Wt[kMaxTerms] = {nullptr, nullptr};  // kernel per term,
+                                  // [group][tap][pair][MB][2][128][8]
+    uint32_t* tab = nullptr;      // per group: header + run table (see TcArgs)
     int tab_words = 0;
     double macs = 0;              // issued MACs per launch
 };
@@ -99,10 +106,9 @@ struct TcOperator {
 
 namespace {
 
-constexpr int kTcThreads = 224;
-constexpr int kIssuer2Warp = 6;  // the second MMA-issuing warp
+constexpr int kTcThreads = 192;
 constexpr int kMaxStages = 8;
-constexpr int kMaxTapsPerStage = 8;  // taps per stage of the B ring (host-side cap)
+constexpr int kMaxTapsPerStage = 8;  // taps per stage of the kernel ring (host-side cap)
 constexpr uint32_t kWaitPolls = 1u << 22;  // x 256 ns back-off: about one second
 
 // ---------------------------------------------------------------------------
@@ -269,11 +275,12 @@ __device__ __forceinline__ void split_terms(const float* v, uint4* out, int term
 }
 
 struct TcArgs {
-    const __nv_bfloat16* a_t[kMaxTerms];  // per term: [Q][KS][Yp][Xp][8]
-    const __nv_bfloat16* b_t[kMaxTerms];  // per term: kernel [group][tap][pair][2][N][8]
+    const __nv_bfloat16* img[kMaxTerms];  // per term: padded images [Q][KS][Yp][Xp][8]
+    const __nv_bfloat16* w[kMaxTerms];    // per term: kernel [group][tap][pair][MB][2][128][8]
     const uint4* tab;           // per group g: {base (16 B units), tap bytes, taps per
-                                // run, pairs}, then per run of taps (groups in order)
-                                // eight 16-bit A offsets of its taps in 16-B units
+                                // run, pairs}, then per run of taps of a group (the
+                                // same for every group) eight 16-bit halo offsets of
+                                // its taps in 16-B units
     int tab_n;                  // uint4 entries in tab
     float* out_f;               // forward mode 0: [Q][S][Twp]; adjoint: [Q][S][Z]
     __nv_bfloat16* out_t[kMaxTerms];    // forward mode 1, per term: [Q][KSo][Yp][Xp][8]
@@ -281,16 +288,16 @@ struct TcArgs {
     const float* Cmf;           // [Q]
     double* partials;           // per block, or null
     int* err;
-    int Y, X, Yp, Xp, Z, k, r, HY, HX, groupsX, MT, RA, NI;
+    int Y, X, Yp, Xp, Z, k, r, HY, HX, groupsX, MT, RA, MB, rows;
     float* part;                // partial sums of tile-states shared by several CTAs
     int* ticket;                // per tile-state arrival counters
-    int KS, GA, NG, NS, NB;
+    int KS, GA, NG, NS;
     uint32_t stage_bytes;
     int Twp, KSo;
     int adj, terms, scale, mode;
     uint32_t tcols;
     int NBUF;                   // accumulator buffers in TMEM (1, or 2: epilogue overlapped)
-    int ntiles;                 // tiles of the scan plane
+    int ntiles;                 // CTA tiles of the scan plane
     int runs;                   // runs of taps per tile-state
     int quantum;                // runs per indivisible piece of work
     long long wq;               // pieces of work in all: tile-states x runs / quantum
@@ -301,7 +308,7 @@ struct TcArgs {
 
 // ---------------------------------------------------------------------------
 // The contraction kernel (forward or adjoint, see the file comment).
-// Persistent: grid = min(pieces of work, resident CTAs), block = 224 threads.
+// Persistent: grid = min(pieces of work, resident CTAs), block = 192 threads.
 // The work is the runs of taps of every tile-state, in order (tile-state
 // major); CTA b takes the b-th of gridDim.x equal shares of it, rounded to
 // whole pieces of `quantum` runs (one run: the stream-K split, which leaves
@@ -344,57 +351,125 @@ __device__ __forceinline__ bool tc_unit(const TcArgs& a, int k, TcUnit& u)
     u.m = u.ts / a.ntiles;
     const int tile = u.ts - u.m * a.ntiles;
     u.x0 = (tile % a.groupsX) * 8 * a.MT;
-    u.y0 = (tile / a.groupsX) * 16;
+    u.y0 = (tile / a.groupsX) * kTileY;
     return true;
+}
+
+// Constants of a launch's MMA products: the bytes between channel blocks of
+// a kernel block, and the offsets (16-B descriptor units) of the second BF16
+// terms of the halo and of the stage.
+struct IssueCfg {
+    uint32_t tap_bytes;     // the MB channel blocks of one tap (kBlockBytes apart)
+    uint32_t halo_lo16;     // halo of the second term
+    uint32_t stage_lo16;    // kernel blocks of the second term
+    uint32_t idesc;
+};
+
+// The products of every tap of a stage, specialised at compile time: MT
+// tiles, MB channel blocks, and MODE 0 (one BF16 term), 1 (two terms, the
+// corrections in accumulator set 1) or 2 (two terms, one accumulator set).
+// Accumulator of (set, block, tile): columns ((set MB + block) MT + tile) 256.
+template <int MT, int MB, int MODE>
+__device__ __forceinline__ void issue_taps(const IssueCfg& c, uint32_t tbuf, uint64_t a0,
+                                           uint64_t b0, const uint32_t (&ow)[4], int nt)
+{
+    const uint64_t tap16 = (uint64_t)(c.tap_bytes >> 4);
+    for (int t = 0; t < nt; ++t) {
+        const uint32_t off = (ow[(t >> 1) & 3] >> (16 * (t & 1))) & 0xFFFFu;
+        const uint64_t at = a0 + (uint64_t)t * tap16;
+        const uint64_t bt = b0 + (uint64_t)off;
+#pragma unroll
+        for (int mb = 0; mb < MB; ++mb) {
+            const uint64_t am = at + (uint64_t)(mb * (kBlockBytes >> 4));
+#pragma unroll
+            for (int i = 0; i < MT; ++i) {
+                const uint64_t bi = bt + (uint64_t)(i * 8);  // the next tile: 8 positions x 16 B
+                const uint32_t dm = tbuf + (uint32_t)((mb * MT + i) * kTilePos);
+                tc_mma(dm, am, bi, c.idesc, 1u);
+                if (MODE != 0) {
+                    const uint32_t dc =
+                        MODE == 1 ? tbuf + (uint32_t)(((MB + mb) * MT + i) * kTilePos) : dm;
+                    tc_mma(dc, am + c.stage_lo16, bi, c.idesc, 1u);
+                    tc_mma(dc, am, bi + c.halo_lo16, c.idesc, 1u);
+                }
+            }
+        }
+    }
+}
+
+__host__ __device__ __forceinline__ int issue_kind(int MT, int MB, int terms, int RA)
+{
+    const int mode = terms == 1 ? 0 : (RA == 2 ? 1 : 2);
+    return ((MT - 1) * 2 + (MB - 1)) * 3 + mode;
+}
+
+__device__ __forceinline__ void issue_stage(int kind, const IssueCfg& c, uint32_t tbuf,
+                                            uint64_t a0, uint64_t b0, const uint32_t (&ow)[4],
+                                            int nt)
+{
+    switch (kind) {
+    case 0: issue_taps<1, 1, 0>(c, tbuf, a0, b0, ow, nt); break;
+    case 1: issue_taps<1, 1, 1>(c, tbuf, a0, b0, ow, nt); break;
+    case 2: issue_taps<1, 1, 2>(c, tbuf, a0, b0, ow, nt); break;
+    case 3: issue_taps<1, 2, 0>(c, tbuf, a0, b0, ow, nt); break;
+    case 4: issue_taps<1, 2, 1>(c, tbuf, a0, b0, ow, nt); break;
+    case 5: issue_taps<1, 2, 2>(c, tbuf, a0, b0, ow, nt); break;
+    case 6: issue_taps<2, 1, 0>(c, tbuf, a0, b0, ow, nt); break;
+    case 7: issue_taps<2, 1, 1>(c, tbuf, a0, b0, ow, nt); break;
+    case 8: issue_taps<2, 1, 2>(c, tbuf, a0, b0, ow, nt); break;
+    case 9: issue_taps<2, 2, 0>(c, tbuf, a0, b0, ow, nt); break;
+    case 10: issue_taps<2, 2, 1>(c, tbuf, a0, b0, ow, nt); break;
+    default: issue_taps<2, 2, 2>(c, tbuf, a0, b0, ow, nt); break;
+    }
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
-    // a closed gate: return before any barrier, TMEM or copy is set up
-    if (gated_off(a.gate, a.want)) return;
     __shared__ __align__(8) uint64_t bar_full[kMaxStages];
     __shared__ __align__(8) uint64_t bar_empty[kMaxStages];
     __shared__ __align__(8) uint64_t bar_afull, bar_aempty;
-    __shared__ __align__(8) uint64_t bar_accfull[2], bar_accfree[2], bar_drain[2];
+    __shared__ __align__(8) uint64_t bar_accfull[2], bar_accfree[2], bar_drain;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     __shared__ double s_red[4];
     __shared__ int s_last;
     __shared__ int s_eok[4];
+    // a closed gate: return before any barrier, TMEM or copy is set up
+    if (gated_off(a.gate, a.want)) return;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kk = a.k * a.k;
     const uint32_t npos = (uint32_t)(a.HY * a.HX);
-    const uint32_t a_slice = npos * 16u;                       // bytes of one A slice
-    const uint32_t a_part = (uint32_t)a.GA * a_slice;          // hi (or lo) A bytes
+    const uint32_t a_slice = npos * 16u;                       // bytes of one image slice
+    const uint32_t a_part = (uint32_t)a.GA * a_slice;          // hi (or lo) halo bytes
     const uint32_t sA = __shfl_sync(0xffffffffu, smem_u32(smem), 0);
-    const uint32_t b_region = a_part * (uint32_t)a.terms;
-    const uint32_t sB = sA + b_region;
+    const uint32_t halo_region = a_part * (uint32_t)a.terms;
+    const uint32_t sW = sA + halo_region;
     const uint32_t stage_total = a.stage_bytes * (uint32_t)a.terms;
-    const uint32_t tab_region = b_region + (uint32_t)a.NS * stage_total;
+    const uint32_t tab_region = halo_region + (uint32_t)a.NS * stage_total;
     const uint4* s_tab = reinterpret_cast<const uint4*>(smem + tab_region);
-    // TMEM columns of one accumulator buffer (all tiles, issuers and sets)
-    const uint32_t buf_cols = (uint32_t)(a.MT * a.RA * a.NI * a.NB);
+    // TMEM columns of one accumulator buffer: [set][block][tile][256 positions]
+    const uint32_t buf_cols = (uint32_t)(a.RA * a.MB * a.MT * kTilePos);
 
-    // the group / pair table is small: stage it once
+    // the group / run table is small: stage it once
     for (int i = threadIdx.x; i < a.tab_n; i += kTcThreads)
         reinterpret_cast<uint4*>(smem + tab_region)[i] = a.tab[i];
     if (threadIdx.x == 0) {
-        // a stage is consumed by one issuer; every issuer commits to the
-        // A-empty and accumulator-full barriers; every epilogue thread
-        // arrives on accumulator-free
+        // the issuer commits to the stage-empty, halo-empty and
+        // accumulator-full barriers; every epilogue thread arrives on
+        // accumulator-free
         for (int s = 0; s < a.NS; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
             mbar_init(smem_u32(&bar_empty[s]), 1);
         }
         mbar_init(smem_u32(&bar_afull), 1);
-        mbar_init(smem_u32(&bar_aempty), (uint32_t)a.NI);
+        mbar_init(smem_u32(&bar_aempty), 1);
         for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&bar_accfull[b]), (uint32_t)a.NI);
+            mbar_init(smem_u32(&bar_accfull[b]), 1);
             mbar_init(smem_u32(&bar_accfree[b]), 128u);
-            mbar_init(smem_u32(&bar_drain[b]), 1u);
         }
+        mbar_init(smem_u32(&bar_drain), 1u);
         s_abort = 0;
         s_red[0] = s_red[1] = s_red[2] = s_red[3] = 0.0;
         fence_mbar_init();
@@ -456,7 +531,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                         (((img + sl) * a.Yp + (size_t)(u.y0 + hy)) * a.Xp + u.x0) * 8;
                     const uint32_t soff = (uint32_t)sl * a_slice + (uint32_t)(hy * a.HX) * 16u;
                     for (int tt = 0; tt < a.terms; ++tt)
-                        bulk_g2s(sA + (uint32_t)tt * a_part + soff, a.a_t[tt] + goff,
+                        bulk_g2s(sA + (uint32_t)tt * a_part + soff, a.img[tt] + goff,
                                  (uint32_t)a.HX * 16u, smem_u32(&bar_afull));
                 }
                 for (int run = lo; run < hi && ok; ++run) {
@@ -468,14 +543,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                     }
                     if (lane == 0) {
                         const uint32_t bar = smem_u32(&bar_full[stage]);
-                        const uint32_t dst = sB + (uint32_t)stage * stage_total;
+                        const uint32_t dst = sW + (uint32_t)stage * stage_total;
                         const uint32_t bytes = (uint32_t)nt * hd.y;
                         const size_t src = ((size_t)hd.x * 16 + (size_t)d0 * hd.y) / 2;  // elements
                         mbar_expect_tx(bar, bytes * (uint32_t)a.terms);
-                        if (bytes)
-                            for (int tt = 0; tt < a.terms; ++tt)
-                                bulk_g2s(dst + (uint32_t)tt * a.stage_bytes, a.b_t[tt] + src,
-                                         bytes, bar);
+                        for (int tt = 0; tt < a.terms; ++tt)
+                            bulk_g2s(dst + (uint32_t)tt * a.stage_bytes, a.w[tt] + src, bytes,
+                                     bar);
                     }
                     fills[stage]++;
                     __syncwarp();
@@ -501,138 +575,110 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                 !mbar_wait(smem_u32(&bar_afull), (uint32_t)(a_fills - 1) & 1u, &never))
                 atomicExch(a.err, 2);
         }
-    } else if (warp == 1 || warp == kIssuer2Warp) {
-        // ------------------------------ MMA issuers ---------------------------
-        // Issuer j (warp 1, and warp 6 when NI = 2) walks every unit and
-        // group and runs as a converged warp (waits and table reads are
-        // warp-wide, descriptors warp-uniform); it takes every NI-th run of
-        // taps (one stage of the ring) of this CTA, and its elected lane issues
-        // all (pair, tap) products of those stages into the issuer's
-        // accumulator sets of the unit's buffer: j RA (main) and j RA + RA - 1
-        // (corrections).  A lone lane running the whole loop by itself was
-        // measured an order of magnitude slower per MMA.
-        const int j = warp == 1 ? 0 : 1;
-        if (j < a.NI) {
-            const bool leader = elect_one();
-            const uint64_t lbo_a16 = (uint64_t)(a_slice >> 4), sbo_a16 = (uint64_t)(a.HX);
-            // descriptor constant parts: LBO, SBO and the fixed bits 46-48
-            const uint64_t adesc_c = (lbo_a16 << 16) | (sbo_a16 << 32) | ((uint64_t)1 << 46);
-            const uint64_t bdesc_c = ((uint64_t)(128u >> 4) << 32) | ((uint64_t)1 << 46);
-            const uint64_t alo16 = (uint64_t)(a_part >> 4), blo16 = (uint64_t)(a.stage_bytes >> 4);
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                                   (((uint32_t)a.NB >> 3) << 17) | ((128u >> 4) << 24);
-            const uint64_t bdesc = bdesc_c | ((uint64_t)a.NB << 16);  // LBO = N x 16 B
-            const uint32_t pair_b = 2u * (uint32_t)a.NB * 16u;         // B bytes of one pair
-            const int MT = a.MT, NBc = a.NB, terms = a.terms;
-            const uint32_t turn_mask = (uint32_t)a.NI - 1u;
-            const int set_main = j * a.RA, set_corr = j * a.RA + a.RA - 1;
-            int local = 0;  // this CTA's runs so far (ring position and turn)
-            int ag = 0;     // A fills consumed
-            bool ok = true;
-            TcUnit u;
-            for (int k = 0; ok && tc_unit(a, k, u); ++k) {
-                const int buf = a.NBUF == 2 ? (k & 1) : 0;
-                if (k >= a.NBUF) {  // the epilogue has drained this buffer
-                    if (!mbar_wait_warp(smem_u32(&bar_accfree[buf]),
-                                        (uint32_t)(k / a.NBUF - 1) & 1u, &s_abort)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
+    } else if (warp == 1) {
+        // ------------------------------ MMA issuer ----------------------------
+        // The warp walks every unit, group and run as a converged warp (waits
+        // and table reads are warp-wide, descriptors warp-uniform); its elected
+        // lane issues the products of every tap of a stage, from the loop
+        // specialised for this launch's tiles, channel blocks and precision.
+        // The kernel block is the A operand (128 channel rows, K-major: the
+        // two 8-element halves 2048 B apart, 8-row groups 128 B apart); the
+        // halo is the B operand (256 position rows: the two slices one slice
+        // apart, 8-position groups one halo row apart), offset by the tap.
+        const bool leader = elect_one();
+        const uint64_t adesc_c = ((uint64_t)(2048u >> 4) << 16) | ((uint64_t)(128u >> 4) << 32) |
+                                 ((uint64_t)1 << 46);
+        const uint64_t bdesc_c = ((uint64_t)(a_slice >> 4) << 16) | ((uint64_t)a.HX << 32) |
+                                 ((uint64_t)1 << 46);
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                               (((uint32_t)kTilePos >> 3) << 17) | (((uint32_t)kRows >> 4) << 24);
+        const IssueCfg ic{(uint32_t)(a.MB * kBlockBytes), (uint32_t)(a_part >> 4),
+                          (uint32_t)(a.stage_bytes >> 4), idesc};
+        const int kind = issue_kind(a.MT, a.MB, a.terms, a.RA);
+        int local = 0;  // this CTA's runs so far (ring position)
+        int ag = 0;     // halo fills consumed
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        TcUnit u;
+        for (int k = 0; ok && tc_unit(a, k, u); ++k) {
+            const int buf = a.NBUF == 2 ? (k & 1) : 0;
+            if (k >= a.NBUF) {  // the epilogue has drained this buffer
+                if (!mbar_wait_warp(smem_u32(&bar_accfree[buf]), (uint32_t)(k / a.NBUF - 1) & 1u,
+                                    &s_abort)) {
+                    ok = false;
+                    break;
                 }
-                const uint32_t tbuf = tmem + (uint32_t)buf * buf_cols;
-                int rb = 0;  // first run of group g
-                for (int g = 0; g < a.NG && ok; ++g) {
-                    const uint4 hd = s_tab[g];
-                    const int tpr = __shfl_sync(0xffffffffu, (int)hd.z, 0);
-                    const uint32_t tapb = __shfl_sync(0xffffffffu, hd.y, 0);
-                    const int np = __shfl_sync(0xffffffffu, (int)hd.w, 0);
-                    const uint64_t tapb16 = (uint64_t)(tapb >> 4);
-                    const int nr = (kk + tpr - 1) / tpr;
-                    const int lo = max(u.r0, rb), hi = min(u.r1, rb + nr);
-                    const int gb = rb;
-                    rb += nr;
-                    if (lo >= hi) continue;  // no run of this group in the unit
-                    if (ag > 0 && leader) tc_commit(smem_u32(&bar_aempty));
-                    __syncwarp();
-                    if (!mbar_wait_warp(smem_u32(&bar_afull), (uint32_t)ag & 1u, &s_abort)) {
-                        ok = false;
-                        break;
-                    }
-                    ++ag;
-                    tc_fence_after();
-                    for (int run = lo; run < hi; ++run, ++local) {
-                        if (((uint32_t)local & turn_mask) != (uint32_t)j) continue;  // the other issuer's
-                        const int d0 = (run - gb) * tpr;
-                        const int nt = min(tpr, kk - d0);
-                        const int stage = local % a.NS;
-                        const uint32_t phase = (uint32_t)(local / a.NS) & 1u;
-                        if (!mbar_wait_warp(smem_u32(&bar_full[stage]), phase, &s_abort)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t bst = sB + (uint32_t)stage * stage_total;
-                        // A offsets of this stage's taps (16-B units), from the run table
-                        const uint4 ro = s_tab[a.NG + run];
-                        const uint32_t ow[4] = {__shfl_sync(0xffffffffu, ro.x, 0),
-                                                __shfl_sync(0xffffffffu, ro.y, 0),
-                                                __shfl_sync(0xffffffffu, ro.z, 0),
-                                                __shfl_sync(0xffffffffu, ro.w, 0)};
-                        for (int i = 0; i < MT; ++i) {
-                            const uint32_t dt = tbuf + (uint32_t)((set_main * MT + i) * NBc);
-                            const uint32_t dc = tbuf + (uint32_t)((set_corr * MT + i) * NBc);
-                            for (int p = 0; p < np; ++p) {
-                                const uint64_t adp =
-                                    adesc_c |
-                                    (uint64_t)((sA + 2u * (uint32_t)p * a_slice + (uint32_t)i * 128u) >> 4);
-                                const uint64_t bdp = bdesc | (uint64_t)((bst + (uint32_t)p * pair_b) >> 4);
-                                if (leader) {
-#pragma unroll
-                                    for (int t = 0; t < kMaxTapsPerStage; ++t) {
-                                        if (t < nt) {
-                                            const uint64_t ad =
-                                                adp + (uint64_t)((ow[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
-                                            const uint64_t bd = bdp + (uint64_t)t * tapb16;
-                                            tc_mma(dt, ad, bd, idesc, 1u);
-                                            if (terms > 1) {
-                                                tc_mma(dc, ad, bd + blo16, idesc, 1u);
-                                                tc_mma(dc, ad + alo16, bd, idesc, 1u);
-                                            }
-                                        }
-                                    }
-                                }
-                            }
-                        }
-                        __syncwarp();
-                        if (leader) tc_commit(smem_u32(&bar_empty[stage]));
-                        __syncwarp();
-                    }
-                }
-                if (!ok) break;
-                // the unit's accumulators are complete once every MMA issued so far is
-                if (leader) tc_commit(smem_u32(&bar_accfull[buf]));
+                tc_fence_after();
+            }
+            const uint32_t tbuf = tmem + (uint32_t)buf * buf_cols;
+            int rb = 0;  // first run of group g
+            for (int g = 0; g < a.NG && ok; ++g) {
+                const uint4 hd = s_tab[g];
+                const int tpr = __shfl_sync(0xffffffffu, (int)hd.z, 0);
+                const int nr = (kk + tpr - 1) / tpr;
+                const int lo = max(u.r0, rb), hi = min(u.r1, rb + nr);
+                const int gb = rb;
+                rb += nr;
+                if (lo >= hi) continue;  // no run of this group in the unit
+                if (ag > 0 && leader) tc_commit(smem_u32(&bar_aempty));
                 __syncwarp();
+                if (!mbar_wait_warp(smem_u32(&bar_afull), (uint32_t)ag & 1u, &s_abort)) {
+                    ok = false;
+                    break;
+                }
+                ++ag;
+                tc_fence_after();
+                for (int run = lo; run < hi; ++run, ++local) {
+                    const int nt = min(tpr, kk - (run - gb) * tpr);
+                    if (!mbar_wait_warp(smem_u32(&bar_full[stage]), phase, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    // halo offsets of this stage's taps (16-B units), from the run table
+                    const uint4 ro = s_tab[a.NG + (run - gb)];
+                    const uint32_t ow[4] = {__shfl_sync(0xffffffffu, ro.x, 0),
+                                            __shfl_sync(0xffffffffu, ro.y, 0),
+                                            __shfl_sync(0xffffffffu, ro.z, 0),
+                                            __shfl_sync(0xffffffffu, ro.w, 0)};
+                    const uint32_t wst = sW + (uint32_t)stage * stage_total;
+                    if (leader) issue_stage(kind, ic, tbuf, adesc_c | (uint64_t)(wst >> 4),
+                                            bdesc_c | (uint64_t)(sA >> 4), ow, nt);
+                    __syncwarp();
+                    if (leader) tc_commit(smem_u32(&bar_empty[stage]));
+                    __syncwarp();
+                    if (++stage == a.NS) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
             }
-            if (!ok && leader) {
-                s_abort = 1;
-                atomicExch(a.err, 1);
-            }
-            // every MMA of this issuer has completed before TMEM is freed
-            if (leader) tc_commit(smem_u32(&bar_drain[j]));
+            if (!ok) break;
+            // the unit's accumulators are complete once every MMA issued so far is
+            if (leader) tc_commit(smem_u32(&bar_accfull[buf]));
             __syncwarp();
-            volatile int never = 0;
-            if (!mbar_wait_warp(smem_u32(&bar_drain[j]), 0u, &never) && leader) atomicExch(a.err, 2);
         }
-    } else {
+        if (!ok && leader) {
+            s_abort = 1;
+            atomicExch(a.err, 1);
+        }
+        // every MMA of this issuer has completed before TMEM is freed
+        if (leader) tc_commit(smem_u32(&bar_drain));
+        __syncwarp();
+        volatile int never = 0;
+        if (!mbar_wait_warp(smem_u32(&bar_drain), 0u, &never) && leader) atomicExch(a.err, 2);
+    } else if (warp >= 2 && warp <= 5) {
         // ------------------------------ epilogue ------------------------------
+        // Thread li (= 32 q + lane) owns TMEM lane li: channel mb * 128 + li of
+        // every position column.
         const int q = warp & 3;
         const int li = q * 32 + lane;
-        const int yl = li >> 3, xl = li & 7;
         double part = 0.0;
         const uint32_t lanes = (uint32_t)(q * 32) << 16;
-        const size_t unit_floats = (size_t)a.MT * a.NB * 128;
+        const size_t unit_floats = (size_t)a.MB * a.MT * kTilePos * kRows;
         const size_t S = (size_t)a.Y * a.X;
+        const float* __restrict__ ytil = a.ytil;
         TcUnit u;
         for (int k = 0; tc_unit(a, k, u); ++k) {
             const int buf = a.NBUF == 2 ? (k & 1) : 0;
@@ -649,33 +695,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                 }
                 break;  // the same decision in all four warps
             }
-            // the summed accumulator sets of tile ti, columns 16 cb .. 16 cb + 15
-            auto acc16 = [&](int ti, int cb, float (&v)[16]) {
-                tmem_ld16(tbuf + (uint32_t)(ti * a.NB + cb * 16), v);
-                for (int rp = 1; rp < a.RA * a.NI; ++rp) {
+            // the summed accumulator sets of (block mb, tile ti), columns 16 cb .. 16 cb + 15
+            auto acc16 = [&](int mb, int ti, int cb, float (&v)[16]) {
+                tmem_ld16(tbuf + (uint32_t)((mb * a.MT + ti) * kTilePos + cb * 16), v);
+                if (a.RA > 1) {
                     float w[16];
-                    tmem_ld16(tbuf + (uint32_t)((rp * a.MT + ti) * a.NB + cb * 16), w);
+                    tmem_ld16(tbuf + (uint32_t)(((a.MB + mb) * a.MT + ti) * kTilePos + cb * 16), w);
 #pragma unroll
                     for (int e = 0; e < 16; ++e) v[e] += w[e];
                 }
             };
-            auto part_at = [&](int piece, int ti, int cb) -> float* {
+            auto part_at = [&](int piece, int mb, int ti, int cb) -> float* {
                 return a.part + ((size_t)u.ts * a.max_pieces + piece) * unit_floats +
-                       (((size_t)ti * (a.NB / 16) + cb) * 128 + li) * 16;
+                       ((((size_t)mb * a.MT + ti) * (kTilePos / 16) + cb) * kRows + li) * 16;
             };
             bool last = true;
             if (u.pieces > 1) {
                 // publish this unit's partial sums, then the ticket decides who ends
-                for (int ti = 0; ti < a.MT; ++ti)
-                    for (int cb = 0; cb < a.NB / 16; ++cb) {
-                        float v[16];
-                        acc16(ti, cb, v);
-                        float4* dst = reinterpret_cast<float4*>(part_at(u.piece, ti, cb));
+                for (int mb = 0; mb < a.MB; ++mb)
+                    for (int ti = 0; ti < a.MT; ++ti)
+                        for (int cb = 0; cb < kTilePos / 16; ++cb) {
+                            float v[16];
+                            acc16(mb, ti, cb, v);
+                            float4* dst = reinterpret_cast<float4*>(part_at(u.piece, mb, ti, cb));
 #pragma unroll
-                        for (int e4 = 0; e4 < 4; ++e4)
-                            dst[e4] = make_float4(v[4 * e4], v[4 * e4 + 1], v[4 * e4 + 2],
-                                                  v[4 * e4 + 3]);
-                    }
+                            for (int e4 = 0; e4 < 4; ++e4)
+                                dst[e4] = make_float4(v[4 * e4], v[4 * e4 + 1], v[4 * e4 + 2],
+                                                      v[4 * e4 + 3]);
+                        }
                 __threadfence();
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 if (warp == 2 && lane == 0) {
@@ -689,95 +736,109 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
             }
             if (last) {
                 const float cm = a.scale ? a.Cmf[u.m] : 1.f;
-                const int y = u.y0 + yl;
-                for (int ti = 0; ti < a.MT; ++ti) {
-                    const int x = u.x0 + 8 * ti + xl;
-                    const bool valid = (y < a.Y) && (x < a.X);
-                    const size_t pos = (size_t)y * a.X + x;
-                    for (int cb = 0; cb < a.NB / 16; ++cb) {
-                        float v[16];
-                        if (u.pieces <= 2) {
-                            acc16(ti, cb, v);
-                            if (u.pieces == 2) {  // + the other piece's partial sums
-                                const float4* o4 =
-                                    reinterpret_cast<const float4*>(part_at(1 - u.piece, ti, cb));
+                for (int mb = 0; mb < a.MB; ++mb) {
+                    const int ch = mb * kRows + li;
+                    const bool ch_ok = ch < a.rows;
+                    for (int ti = 0; ti < a.MT; ++ti)
+                        for (int cb = 0; cb < kTilePos / 16; ++cb) {
+                            float v[16];
+                            if (u.pieces <= 2) {
+                                acc16(mb, ti, cb, v);
+                                if (u.pieces == 2) {  // + the other piece's partial sums
+                                    const float4* o4 = reinterpret_cast<const float4*>(
+                                        part_at(1 - u.piece, mb, ti, cb));
 #pragma unroll
-                                for (int e4 = 0; e4 < 4; ++e4) {
-                                    const float4 w = __ldcg(o4 + e4);  // written by another SM
-                                    v[4 * e4] += w.x;
-                                    v[4 * e4 + 1] += w.y;
-                                    v[4 * e4 + 2] += w.z;
-                                    v[4 * e4 + 3] += w.w;
+                                    for (int e4 = 0; e4 < 4; ++e4) {
+                                        const float4 w = __ldcg(o4 + e4);  // written by another SM
+                                        v[4 * e4] += w.x;
+                                        v[4 * e4 + 1] += w.y;
+                                        v[4 * e4 + 2] += w.z;
+                                        v[4 * e4 + 3] += w.w;
+                                    }
+                                }
+                            } else {  // every piece's partial sums, in piece order
+#pragma unroll
+                                for (int e = 0; e < 16; ++e) v[e] = 0.f;
+                                for (int pc = 0; pc < u.pieces; ++pc) {
+                                    const float4* o4 =
+                                        reinterpret_cast<const float4*>(part_at(pc, mb, ti, cb));
+#pragma unroll
+                                    for (int e4 = 0; e4 < 4; ++e4) {
+                                        const float4 w = __ldcg(o4 + e4);
+                                        v[4 * e4] += w.x;
+                                        v[4 * e4 + 1] += w.y;
+                                        v[4 * e4 + 2] += w.z;
+                                        v[4 * e4 + 3] += w.w;
+                                    }
                                 }
                             }
-                        } else {  // every piece's partial sums, in piece order
+                            // column 16 cb + e is position (y0 + 2 cb + e / 8, x0 + 8 ti + e % 8);
+                            // the chunk's measurements are loaded together first (the
+                            // stores below would otherwise order every load behind them)
+                            float yv[16];
 #pragma unroll
-                            for (int e = 0; e < 16; ++e) v[e] = 0.f;
-                            for (int pc = 0; pc < u.pieces; ++pc) {
-                                const float4* o4 = reinterpret_cast<const float4*>(part_at(pc, ti, cb));
+                            for (int e = 0; e < 16; ++e) {
+                                const int y = u.y0 + 2 * cb + (e >> 3);
+                                const int x = u.x0 + 8 * ti + (e & 7);
+                                yv[e] = 0.f;
+                                if (ytil && ch_ok && y < a.Y && x < a.X)
+                                    yv[e] = __ldg(ytil + ((size_t)u.m * S + (size_t)y * a.X + x) *
+                                                             a.Twp + ch);
+                            }
 #pragma unroll
-                                for (int e4 = 0; e4 < 4; ++e4) {
-                                    const float4 w = __ldcg(o4 + e4);
-                                    v[4 * e4] += w.x;
-                                    v[4 * e4 + 1] += w.y;
-                                    v[4 * e4 + 2] += w.z;
-                                    v[4 * e4 + 3] += w.w;
+                            for (int e = 0; e < 16; ++e) {
+                                const int y = u.y0 + 2 * cb + (e >> 3);
+                                const int x = u.x0 + 8 * ti + (e & 7);
+                                const bool pos_ok = y < a.Y && x < a.X;  // warp-uniform
+                                if (!pos_ok) continue;
+                                const size_t pos = (size_t)y * a.X + x;
+                                if (a.adj) {
+                                    if (ch_ok) a.out_f[((size_t)u.m * S + pos) * a.Z + ch] = v[e];
+                                    continue;
+                                }
+                                const size_t ub = ((size_t)u.m * S + pos) * a.Twp + ch;
+                                float o = 0.f;
+                                if (ch_ok) {
+                                    if (ytil) {
+                                        o = cm * v[e] - yv[e];
+                                        if (a.partials)
+                                            part += (double)cm * (double)v[e] * v[e] -
+                                                    2.0 * (double)v[e] * yv[e];
+                                    } else {
+                                        o = cm * v[e];
+                                    }
+                                }
+                                if (a.mode == 0) {
+                                    if (ch_ok) a.out_f[ub] = o;
+                                    continue;
+                                }
+                                // the BF16 terms of channels 8 g .. 8 g + 7 (lanes 8 g' ..
+                                // 8 g' + 7 of the warp) gathered into lane 8 g' and written
+                                // as one 16-byte row of the residual image
+                                const __nv_bfloat16 h0 = __float2bfloat16_rn(o);
+                                const float o1 = o - __bfloat162float(h0);
+                                uint32_t w0 = (uint32_t)__bfloat16_as_ushort(h0);
+                                uint32_t w1 = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(o1));
+                                w0 |= __shfl_down_sync(0xffffffffu, w0, 1) << 16;  // even lanes: pairs
+                                w1 |= __shfl_down_sync(0xffffffffu, w1, 1) << 16;
+                                uint4 q0, q1;
+                                q0.x = w0;
+                                q0.y = __shfl_down_sync(0xffffffffu, w0, 2);
+                                q0.z = __shfl_down_sync(0xffffffffu, w0, 4);
+                                q0.w = __shfl_down_sync(0xffffffffu, w0, 6);
+                                q1.x = w1;
+                                q1.y = __shfl_down_sync(0xffffffffu, w1, 2);
+                                q1.z = __shfl_down_sync(0xffffffffu, w1, 4);
+                                q1.w = __shfl_down_sync(0xffffffffu, w1, 6);
+                                if ((lane & 7) == 0 && ch < a.Twp) {
+                                    const size_t ro =
+                                        ((((size_t)u.m * a.KSo + (ch >> 3)) * a.Yp + (y + a.r)) *
+                                             a.Xp + (x + a.r)) * 8;
+                                    *reinterpret_cast<uint4*>(a.out_t[0] + ro) = q0;
+                                    if (a.terms > 1) *reinterpret_cast<uint4*>(a.out_t[1] + ro) = q1;
                                 }
                             }
                         }
-                        if (!valid) continue;
-                        if (a.adj) {
-                            float* out = a.out_f + ((size_t)u.m * S + pos) * a.Z + cb * 16;
-                            const int nz = min(16, a.Z - cb * 16);
-                            if (nz == 16 && (a.Z & 3) == 0) {
-#pragma unroll
-                                for (int e = 0; e < 16; e += 4)
-                                    *reinterpret_cast<float4*>(out + e) =
-                                        make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
-                            } else {
-                                for (int e = 0; e < nz; ++e) out[e] = v[e];
-                            }
-                            continue;
-                        }
-                        const size_t ub = ((size_t)u.m * S + pos) * a.Twp + cb * 16;
-                        float o[16];
-                        if (a.ytil) {
-                            const float4* yt = reinterpret_cast<const float4*>(a.ytil + ub);
-#pragma unroll
-                            for (int e4 = 0; e4 < 4; ++e4) {
-                                const float4 w = yt[e4];
-                                const float wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                                for (int c = 0; c < 4; ++c) {
-                                    const float acc = v[4 * e4 + c];
-                                    o[4 * e4 + c] = cm * acc - wv[c];
-                                    if (a.partials)
-                                        part += (double)cm * (double)acc * acc -
-                                                2.0 * (double)acc * wv[c];
-                                }
-                            }
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < 16; ++e) o[e] = cm * v[e];
-                        }
-                        if (a.mode == 0) {
-                            float4* out = reinterpret_cast<float4*>(a.out_f + ub);
-#pragma unroll
-                            for (int e4 = 0; e4 < 4; ++e4)
-                                out[e4] = make_float4(o[4 * e4], o[4 * e4 + 1], o[4 * e4 + 2],
-                                                      o[4 * e4 + 3]);
-                        } else {
-#pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                const size_t ro = ((((size_t)u.m * a.KSo + 2 * cb + h) * a.Yp +
-                                                    (y + a.r)) * a.Xp + (x + a.r)) * 8;
-                                uint4 parts[kMaxTerms];
-                                split_terms(o + 8 * h, parts, a.terms);
-                                for (int tt = 0; tt < a.terms; ++tt)
-                                    *reinterpret_cast<uint4*>(a.out_t[tt] + ro) = parts[tt];
-                            }
-                        }
-                    }
                 }
             }
             // hand the buffer back zeroed for the unit after next
@@ -938,14 +999,13 @@ uint32_t pow2_cols(int n)
 
 }  // namespace
 
-
 namespace {
 
 void free_dir(TcDir& D)
 {
     for (int tt = 0; tt < kMaxTerms; ++tt) {
-        cudaFree(D.Bt[tt]);
-        D.Bt[tt] = nullptr;
+        cudaFree(D.Wt[tt]);
+        D.Wt[tt] = nullptr;
     }
     cudaFree(D.tab);
     D.tab = nullptr;
@@ -955,83 +1015,115 @@ void free_dir(TcDir& D)
     D.ticket = nullptr;
 }
 
-// Host image of one direction's packed operator.
+// Host image of one direction's configuration and tables (the kernel blocks
+// are packed separately: their layout depends on the slice grouping only).
 struct DirHost {
     TcDir cfg;
-    std::vector<uint16_t> t[kMaxTerms];     // kernel per term
-    std::vector<uint32_t> tab;      // group headers and pair tables (uint4 entries)
+    std::vector<uint32_t> tab;              // group headers and run tables (uint4 entries)
+    int npe = 0;                            // slice pairs holding a nonzero kernel entry
 };
 
-// Builds the banded kernel of one direction for MT tiles per CTA within a
-// shared-memory budget.  Returns false if it does not fit.
-bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int RA, int NI,
-              int NBUF, int skip, int whole, size_t budget, DirHost* out)
+// Kernel value of direction `adj` at channel `row`, contraction index `kidx`, tap d.
+float kernel_value(const swopt_handle* h, bool adj, int row, int kidx, int d)
+{
+    const int kk = h->k * h->k;
+    const int j = adj ? row : kidx, w = adj ? kidx : row;
+    const int tt = h->t0 + w;
+    if (j >= h->Z || w >= h->Twp || tt >= h->T) return 0.f;
+    return (float)h->K64[((size_t)j * kk + d) * h->T + tt];
+}
+
+// The kernel blocks [group][tap][pair][MB][2 halves][128 rows][8], per BF16
+// term, of a configuration's slice grouping.
+void pack_dir(const swopt_handle* h, bool adj, const TcDir& D, int npe,
+              std::vector<uint16_t> (&w)[kMaxTerms])
+{
+    const int kk = h->k * h->k;
+    const int gpairs = D.GA / 2;
+    for (int tt = 0; tt < kMaxTerms; ++tt) {
+        w[tt].clear();
+        w[tt].reserve((size_t)kk * npe * D.MB * kBlockBytes / 2);
+    }
+    for (int g = 0; g < D.NG; ++g) {
+        const int np = std::min(gpairs, npe - g * gpairs);
+        for (int d = 0; d < kk; ++d)
+            for (int p = 0; p < np; ++p) {
+                const int gp = g * gpairs + p;
+                for (int mb = 0; mb < D.MB; ++mb)
+                    for (int half = 0; half < 2; ++half)
+                        for (int row = 0; row < kRows; ++row)
+                            for (int e = 0; e < 8; ++e) {
+                                float rv =
+                                    kernel_value(h, adj, mb * kRows + row, 16 * gp + 8 * half + e, d);
+                                for (int tt = 0; tt < kMaxTerms; ++tt) {
+                                    const uint16_t hb = f2bf(rv);
+                                    w[tt].push_back(hb);
+                                    rv -= bf2f(hb);
+                                }
+                            }
+            }
+    }
+    for (int tt = 0; tt < kMaxTerms; ++tt)
+        if (w[tt].empty()) w[tt].assign(8, 0);
+}
+
+// Builds the kernel blocks of one direction for MT position tiles per CTA
+// within a shared-memory budget.  Returns false if it does not fit.
+bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int RA, int NBUF,
+              int skip, int whole, size_t budget, DirHost* out)
 {
     const int kk = h->k * h->k;
     const int terms = t->terms;
     TcDir D;
     D.MT = MT;
     D.RA = RA;
-    D.NI = NI;
     D.whole = whole;
     D.NBUF = NBUF;
-    D.NB = adj ? t->Zp16 : h->Twp;
-    const int ks_min = adj ? h->Twp / 8 : t->Zp16 / 8;  // both even
+    D.rows = adj ? h->Z : h->Twp;
+    D.MB = (D.rows + kRows - 1) / kRows;
+    if (D.MB > 2) return false;
+    const int ks_min = adj ? h->Twp / 8 : t->Zp16 / 8;  // contracted slices, both even
     const int npairs = ks_min / 2;
     D.HX = 8 * MT + 2 * h->r;
     D.npos = t->HY * D.HX;
-    D.cols = (int)pow2_cols(NBUF * MT * RA * NI * D.NB);
+    D.cols = (int)pow2_cols(NBUF * RA * D.MB * MT * kTilePos);
     if (D.cols > 512) return false;
     D.groupsX = (t->tilesX + MT - 1) / MT;
 
-    // value of the kernel at output column `row` and contraction index `kidx`
-    auto kv = [&](int row, int kidx, int d) -> float {
-        const int j = adj ? row : kidx, w = adj ? kidx : row;
-        const int tt = h->t0 + w;
-        if (j >= h->Z || w >= h->Twp || tt >= h->T) return 0.f;
-        return (float)h->K64[((size_t)j * kk + d) * h->T + tt];
-    };
     // pairs with any nonzero kernel entry; trailing all-zero pairs are dropped
     int npe = 0;
     for (int gp = 0; gp < npairs; ++gp) {
         bool any = false;
         for (int d = 0; d < kk && !any; ++d)
-            for (int row = 0; row < D.NB && !any; ++row)
+            for (int row = 0; row < D.rows && !any; ++row)
                 for (int e = 0; e < 16; ++e)
-                    if (kv(row, 16 * gp + e, d) != 0.f) {
+                    if (kernel_value(h, adj, row, 16 * gp + e, d) != 0.f) {
                         any = true;
                         break;
                     }
         if (any) npe = gp + 1;
     }
     if (npe == 0) npe = 1;
-    const size_t pair_b = 2 * (size_t)D.NB * 16;
-    // smallest number of groups whose A slices and B ring fit the budget (the
-    // `skip`-th next one when skip > 0: more groups leave room for stages of
-    // more taps); prefer stages that hold several taps
+    const size_t pair_b = (size_t)D.MB * kBlockBytes;
+    // one slice pair per group (the issue loop has no loop over pairs); the
+    // largest stage (whole taps, up to kMaxTapsPerStage, at least 3 stages)
+    // that fits the budget with the halo, or with skip > 0 the next smaller
     const size_t mult = (size_t)terms;
     bool found = false;
-    int last_gpairs = 0;
-    for (int ng = 1; ng <= npe && !found; ++ng) {
-        const int gpairs = (npe + ng - 1) / ng;
-        if (gpairs == last_gpairs) continue;
-        last_gpairs = gpairs;
-        const int GA = 2 * gpairs;
-        const int NG = (npe + gpairs - 1) / gpairs;
-        const size_t tapb = (size_t)gpairs * pair_b;
+    {
+        const int GA = 2, NG = npe;
+        const size_t tapb = pair_b;
         const size_t a_bytes = mult * (size_t)GA * D.npos * 16;
-        // group headers plus one entry per run of taps: at least this with
-        // kMaxTapsPerStage taps per run, and 3 stages of at least one tap
-        const size_t tab = ((size_t)NG + (size_t)NG * ((kk + kMaxTapsPerStage - 1) /
-                                                        kMaxTapsPerStage)) * 16;
-        if (a_bytes + tab + 3 * tapb * mult > budget) continue;
-        // largest stage (in whole taps, up to kMaxTapsPerStage) with at least 3 stages
         for (int tps = kMaxTapsPerStage; tps >= 1 && !found; --tps) {
             const size_t stage = tapb * (size_t)std::min(tps, kk);
-            const size_t tabr = ((size_t)NG + (size_t)NG * ((kk + tps - 1) / tps)) * 16;
+            const size_t tabr = ((size_t)NG + (size_t)((kk + tps - 1) / tps)) * 16;
             for (int ns = kMaxStages; ns >= 3; --ns) {
                 const size_t total = a_bytes + (size_t)ns * stage * mult + tabr;
                 if (total <= budget) {
+                    if (skip > 0) {
+                        --skip;
+                        break;  // the next smaller stage
+                    }
                     D.GA = GA;
                     D.NG = NG;
                     // slice stride of the image: at least every slice that the
@@ -1045,10 +1137,6 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
                 }
             }
         }
-        if (found && skip > 0) {
-            --skip;
-            found = false;
-        }
     }
     if (!found) return false;
     // At most 512 / cols CTAs may share an SM's 512 TMEM columns: request
@@ -1057,49 +1145,39 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
     D.smem = std::max(D.smem, (size_t)233472 / (512 / D.cols + 1) + 1024);
     if (D.smem > 225 * 1024) return false;
 
-    // pack [group][tap][pair][2 slices][NB rows][8] and the group headers
+    // group headers (kernel blocks at [group][tap][pair][MB][2][128][8]) and
+    // run tables
     const int gpairs = D.GA / 2;
-    for (int tt = 0; tt < kMaxTerms; ++tt) out->t[tt].clear();
     out->tab.clear();
     std::vector<uint32_t> runtab;
     double macs = 0;
+    size_t base_bytes = 0;
+    // taps per run: what a stage holds of a full group's blocks (every group
+    // uses the same runs, so that one run table serves them all)
+    const uint32_t tpr = std::min<uint32_t>(
+        kMaxTapsPerStage, std::max<uint32_t>(1, D.stage_bytes / (uint32_t)(gpairs * pair_b)));
     for (int g = 0; g < D.NG; ++g) {
         const int np = std::min(gpairs, npe - g * gpairs);
         const uint32_t tapb = (uint32_t)(np * pair_b);
-        const uint32_t base16 = (uint32_t)(out->t[0].size() / 8);
-        const uint32_t tpr = std::min<uint32_t>(
-            kMaxTapsPerStage, std::max<uint32_t>(1, D.stage_bytes / tapb));
+        const uint32_t base16 = (uint32_t)(base_bytes / 16);
+        base_bytes += (size_t)kk * tapb;
         out->tab.insert(out->tab.end(), {base16, tapb, tpr, (uint32_t)np});
         D.runs += (kk + (int)tpr - 1) / (int)tpr;
-        // runs of tpr taps: A offsets (16-B units) of each tap of the run
-        for (int d0 = 0; d0 < kk; d0 += (int)tpr) {
-            uint32_t w[4] = {0, 0, 0, 0};
-            for (int tt = 0; tt < (int)tpr && d0 + tt < kk; ++tt) {
-                const int d = d0 + tt, dy = d / h->k, dx = d - dy * h->k;
-                const int off = adj ? (2 * h->r - dy) * D.HX + (2 * h->r - dx) : dy * D.HX + dx;
-                w[tt >> 1] |= (uint32_t)(off & 0xFFFF) << (16 * (tt & 1));
-            }
-            runtab.insert(runtab.end(), {w[0], w[1], w[2], w[3]});
-        }
-        for (int d = 0; d < kk; ++d)
-            for (int p = 0; p < np; ++p) {
-                const int gp = g * gpairs + p;
-                for (int s2 = 0; s2 < 2; ++s2)
-                    for (int row = 0; row < D.NB; ++row)
-                        for (int e = 0; e < 8; ++e) {
-                            float rv = kv(row, 16 * gp + 8 * s2 + e, d);
-                            for (int tt = 0; tt < kMaxTerms; ++tt) {
-                                const uint16_t hb = f2bf(rv);
-                                out->t[tt].push_back(hb);
-                                rv -= bf2f(hb);
-                            }
-                        }
-                macs += 128.0 * D.NB * 16;
-            }
+        macs += (double)kk * np * D.MB * kRows * kTilePos * 16;
     }
-    for (int tt = 0; tt < kMaxTerms; ++tt)
-        if (out->t[tt].empty()) out->t[tt].assign(8, 0);
+    // runs of tpr taps: halo offsets (16-B units) of each tap of the run
+    for (int d0 = 0; d0 < kk; d0 += (int)tpr) {
+        uint32_t w[4] = {0, 0, 0, 0};
+        for (int tt = 0; tt < (int)tpr && d0 + tt < kk; ++tt) {
+            const int d = d0 + tt, dy = d / h->k, dx = d - dy * h->k;
+            const int off = adj ? (2 * h->r - dy) * D.HX + (2 * h->r - dx) : dy * D.HX + dx;
+            w[tt >> 1] |= (uint32_t)(off & 0xFFFF) << (16 * (tt & 1));
+        }
+        runtab.insert(runtab.end(), {w[0], w[1], w[2], w[3]});
+    }
+    if (base_bytes / 16 > 0xFFFFFFFFull) return false;
     out->tab.insert(out->tab.end(), runtab.begin(), runtab.end());
+    out->npe = npe;
     D.tab_words = (int)out->tab.size();
     const double ctas = (double)D.groupsX * t->tilesY * h->Q;
     D.macs = macs * MT * (terms * (terms + 1) / 2) * ctas;
@@ -1107,24 +1185,54 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
     return true;
 }
 
-swopt_status upload_dir(const DirHost& H, int terms, size_t units, TcDir* D)
+// Packed kernel blocks on the device, one entry per slice grouping (GA).
+struct WCache {
+    int GA = 0;
+    __nv_bfloat16* w[kMaxTerms] = {nullptr, nullptr};
+};
+
+void free_wcache(std::vector<WCache>& c, const __nv_bfloat16* keep)
+{
+    for (auto& e : c)
+        for (int tt = 0; tt < kMaxTerms; ++tt)
+            if (e.w[tt] && e.w[0] != keep) cudaFree(e.w[tt]);
+    c.clear();
+}
+
+// Device copies of a configuration: its tables, and its kernel blocks from
+// the cache (packed and uploaded on the first use of its slice grouping).
+// The kernel arrays stay owned by the cache until the caller keeps them.
+swopt_status upload_dir(const swopt_handle* h, bool adj, const DirHost& H, int terms,
+                        std::vector<WCache>& cache, TcDir* D)
 {
     *D = H.cfg;
-    for (int tt = 0; tt < kMaxTerms; ++tt) D->Bt[tt] = nullptr;
+    for (int tt = 0; tt < kMaxTerms; ++tt) D->Wt[tt] = nullptr;
     D->tab = nullptr;
     D->part = nullptr;
     D->ticket = nullptr;
-    auto up16 = [&](__nv_bfloat16** dst, const std::vector<uint16_t>& v) -> swopt_status {
-        SW_TRY(tc_alloc(dst, v.size()));
-        SW_CUDA(cudaMemcpy(*dst, v.data(), v.size() * 2, cudaMemcpyHostToDevice));
-        return SWOPT_OK;
-    };
-    swopt_status s = SWOPT_OK;
-    for (int tt = 0; tt < terms && s == SWOPT_OK; ++tt) s = up16(&D->Bt[tt], H.t[tt]);
-    if (s == SWOPT_OK) s = tc_upload(&D->tab, H.tab);
-    if (s != SWOPT_OK) free_dir(*D);
-    (void)units;
-    return s;
+    WCache* e = nullptr;
+    for (auto& c : cache)
+        if (c.GA == D->GA) e = &c;
+    if (!e) {
+        std::vector<uint16_t> w[kMaxTerms];
+        pack_dir(h, adj, *D, H.npe, w);
+        cache.push_back(WCache());
+        e = &cache.back();
+        e->GA = D->GA;
+        for (int tt = 0; tt < terms; ++tt) {
+            SW_TRY(tc_alloc(&e->w[tt], w[tt].size()));
+            SW_CUDA(cudaMemcpy(e->w[tt], w[tt].data(), w[tt].size() * 2, cudaMemcpyHostToDevice));
+        }
+    }
+    for (int tt = 0; tt < kMaxTerms; ++tt) D->Wt[tt] = e->w[tt];
+    return tc_upload(&D->tab, H.tab);
+}
+
+// Frees a configuration's own device arrays (not its cached kernel blocks).
+void free_dir_tables(TcDir& D)
+{
+    for (int tt = 0; tt < kMaxTerms; ++tt) D.Wt[tt] = nullptr;
+    free_dir(D);
 }
 
 TcArgs dir_args(const swopt_handle* h, const TcOperator* t, const TcDir& D, bool adj)
@@ -1135,16 +1243,16 @@ TcArgs dir_args(const swopt_handle* h, const TcOperator* t, const TcDir& D, bool
     a.err = t->err;
     a.Y = h->Y; a.X = h->X; a.Yp = t->Yp; a.Xp = t->Xp; a.Z = h->Z; a.k = h->k; a.r = h->r;
     a.HY = t->HY; a.HX = D.HX; a.groupsX = D.groupsX; a.MT = D.MT; a.RA = D.RA;
-    a.NI = D.NI;
+    a.MB = D.MB; a.rows = D.rows;
     a.part = D.part;
     a.ticket = D.ticket;
-    a.KS = D.KS; a.GA = D.GA; a.NG = D.NG; a.NS = D.NS; a.NB = D.NB;
+    a.KS = D.KS; a.GA = D.GA; a.NG = D.NG; a.NS = D.NS;
     a.stage_bytes = D.stage_bytes;
     a.Twp = h->Twp;
     a.KSo = t->A.KS;
     a.terms = t->terms;
     a.adj = adj ? 1 : 0;
-    for (int tt = 0; tt < kMaxTerms; ++tt) a.b_t[tt] = D.Bt[tt];
+    for (int tt = 0; tt < kMaxTerms; ++tt) a.w[tt] = D.Wt[tt];
     a.tab = reinterpret_cast<const uint4*>(D.tab);
     a.tab_n = D.tab_words / 4;
     a.tcols = (uint32_t)D.cols;
@@ -1154,7 +1262,7 @@ TcArgs dir_args(const swopt_handle* h, const TcOperator* t, const TcDir& D, bool
     a.quantum = D.quantum;
     a.wq = D.wq;
     a.max_pieces = D.max_pieces;
-    for (int tt = 0; tt < kMaxTerms; ++tt) a.a_t[tt] = adj ? t->rpad[tt] : t->bpad[tt];
+    for (int tt = 0; tt < kMaxTerms; ++tt) a.img[tt] = adj ? t->rpad[tt] : t->bpad[tt];
     a.gate = h->gate;
     a.want = h->gate_want;
     return a;
@@ -1214,7 +1322,7 @@ swopt_status set_grid(swopt_handle* h, TcDir* D)
         most = std::max(most, owner(ts * R + R - 1) - owner(ts * R) + 1);
     D->max_pieces = (int)most;
     if (most > 1) {
-        const size_t unit_floats = (size_t)D->MT * D->NB * 128;
+        const size_t unit_floats = (size_t)D->MB * D->MT * kTilePos * kRows;
         SW_TRY(tc_alloc(&D->part, (size_t)units_ts * most * unit_floats));
         SW_TRY(tc_alloc(&D->ticket, (size_t)units_ts));
         SW_CUDA(cudaMemset(D->ticket, 0, (size_t)units_ts * sizeof(int)));
@@ -1222,14 +1330,13 @@ swopt_status set_grid(swopt_handle* h, TcDir* D)
     return SWOPT_OK;
 }
 
-// Candidate configurations: tiles per CTA and the shared-memory budget (two
-// CTAs per SM, or one).
+// Candidate configurations: position tiles per CTA and the shared-memory
+// budget (two CTAs per SM, or one).
 struct Cand {
     int MT;
     size_t budget;
 };
-const Cand kCands[] = {{1, 110 * 1024}, {2, 110 * 1024}, {1, 220 * 1024}, {2, 220 * 1024},
-                       {4, 220 * 1024}};
+const Cand kCands[] = {{1, 110 * 1024}, {1, 220 * 1024}, {2, 220 * 1024}};
 
 }  // namespace
 
@@ -1253,12 +1360,13 @@ void tc_release(swopt_handle* h)
 // tiles per CTA, `force_ctas` CTAs per SM, `force_ra` accumulators per tile,
 // `force_split` (1: whole tile-states, 2: stream-K) and `force_nbuf`
 // accumulator buffers, each 0 for free.  The padded images must already be
-// sized for max_ks slices.
+// sized for the largest slice count.
 static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_ctas,
                              int force_ra, int force_split, int force_nbuf, TcDir* best)
 {
     TcOperator* t = h->tc;
     std::vector<DirHost> plans;
+    std::vector<WCache> cache;
     // The split precisions keep their correction products in an accumulator
     // of their own where TMEM holds it: they are about 2^-8 of the main sum,
     // so the FP32 rounding of each accumulation step into it is 2^-8 finer.
@@ -1268,9 +1376,8 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
         for (const Cand& c : kCands) {
             if (force_mt > 0 && c.MT != force_mt) continue;
             if (force_ctas > 0 && (force_ctas == 2) != (c.budget < 200 * 1024)) continue;
-            // two MMA-issuing warps where TMEM holds their accumulators; the
-            // fewest slice groups that fit, and the next split (larger stages);
-            // CTAs taking whole tile-states, or equal shares of all runs
+            // the fewest slice groups that fit, and the next split (larger
+            // stages); CTAs taking whole tile-states, or equal shares of all runs
             for (int skip = 0; skip < 2; ++skip)
                 for (int whole = 1; whole >= 0; --whole) {
                     if (force_split > 0 && whole != (force_split == 1 ? 1 : 0)) continue;
@@ -1279,8 +1386,7 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
                     for (int nbuf = 2; nbuf >= 1; --nbuf) {
                         if (force_nbuf > 0 && nbuf != force_nbuf) continue;
                         DirHost H;
-                        if (plan_dir(h, t, adj, c.MT, ra, 2, nbuf, skip, whole, c.budget, &H) ||
-                            plan_dir(h, t, adj, c.MT, ra, 1, nbuf, skip, whole, c.budget, &H))
+                        if (plan_dir(h, t, adj, c.MT, ra, nbuf, skip, whole, c.budget, &H))
                             plans.push_back(std::move(H));
                     }
                 }
@@ -1299,18 +1405,34 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
         float best_ms = 1e30f;
         for (size_t i = 0; i < plans.size(); ++i) {
             TcDir D;
-            SW_TRY(upload_dir(plans[i], t->terms,
-                              (size_t)plans[i].cfg.groupsX * t->tilesY * h->Q, &D));
+            if (swopt_status su = upload_dir(h, adj, plans[i], t->terms, cache, &D);
+                su != SWOPT_OK) {
+                free_dir_tables(D);
+                free_wcache(cache, nullptr);
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return su;
+            }
             if (swopt_status sg = set_grid(h, &D); sg != SWOPT_OK) {
-                free_dir(D);
+                free_dir_tables(D);
+                free_wcache(cache, nullptr);
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
                 return sg;
             }
             TcArgs a = dir_args(h, t, D, adj);
             a.gate = nullptr;  // tuning launches always run
-            a.out_f = adj ? h->g : h->u;
-            a.mode = 0;
+            if (adj) {
+                a.out_f = h->g;
+                a.mode = 0;
+            } else {
+                // as in the solve: the scaled residual from measurements (h->u
+                // stands in for them) into the residual images
+                a.mode = 1;
+                a.scale = 1;
+                a.ytil = h->u;
+                for (int tt = 0; tt < kMaxTerms; ++tt) a.out_t[tt] = t->rpad[tt];
+            }
             swopt_status s = launch_conv(h, D, a, 0);  // warm-up
             float ms = 0.f;
             if (s == SWOPT_OK) {
@@ -1320,8 +1442,9 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
                 if (cudaEventSynchronize(e1) != cudaSuccess) s = SWOPT_ERR_CUDA;
                 cudaEventElapsedTime(&ms, e0, e1);
             }
-            free_dir(D);
+            free_dir_tables(D);
             if (s != SWOPT_OK) {
+                free_wcache(cache, nullptr);
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
                 return s;
@@ -1334,12 +1457,17 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (tc_error_word(h) != 0) {
+            free_wcache(cache, nullptr);
             set_error("a tensor-core kernel gave up a bounded wait while tuning");
             return SWOPT_ERR_TIMEOUT;
         }
     }
-    SW_TRY(upload_dir(plans[best_i], t->terms,
-                      (size_t)plans[best_i].cfg.groupsX * t->tilesY * h->Q, best));
+    swopt_status s = upload_dir(h, adj, plans[best_i], t->terms, cache, best);
+    free_wcache(cache, s == SWOPT_OK ? best->Wt[0] : nullptr);  // the chosen blocks stay
+    if (s != SWOPT_OK) {
+        free_dir_tables(*best);
+        return s;
+    }
     if (swopt_status sg = set_grid(h, best); sg != SWOPT_OK) {
         free_dir(*best);
         return sg;
@@ -1351,19 +1479,17 @@ swopt_status tc_prepare(swopt_handle* h)
 {
     const int terms = h->precision == SWOPT_PREC_BF16X3 ? 2 : 1;
     if (h->tc && h->tc->terms == terms) return SWOPT_OK;
-    const int keep_f = h->tc ? h->tc->F.MT : 0;
-    (void)keep_f;
     tc_release(h);
     TcOperator* t = new TcOperator();
     t->terms = terms;
     t->tilesX = (h->X + 7) / 8;
-    t->tilesY = (h->Y + 15) / 16;
-    t->Xp = ((t->tilesX + 3) / 4) * 32 + 2 * h->r;  // room for up to 4 tiles per CTA
-    t->Yp = t->tilesY * 16 + 2 * h->r;
-    t->HY = 16 + 2 * h->r;
+    t->tilesY = (h->Y + kTileY - 1) / kTileY;
+    t->Xp = ((t->tilesX + 1) / 2) * 16 + 2 * h->r;  // room for up to 2 tiles per CTA
+    t->Yp = t->tilesY * kTileY + 2 * h->r;
+    t->HY = kTileY + 2 * h->r;
     t->Zp16 = ((h->Z + 15) / 16) * 16;
     h->tc = t;
-    if (h->Twp > 256 || t->Zp16 > 256) {
+    if (h->Twp > 2 * kRows || t->Zp16 > 2 * kRows) {
         set_error("tensor-core path supports a time window and a depth count up to 256 "
                   "(window %d, depths %d)", h->Twp, h->Z);
         tc_release(h);
@@ -1436,8 +1562,9 @@ swopt_status tc_states(swopt_handle* h, const float* c, cudaStream_t st)
         set_error("internal: state images beyond the kernel's limits");
         return SWOPT_ERR_UNSUPPORTED;
     }
-    int grid = grid_for(n, 256);
-    if (grid > 152 * 16) grid = 152 * 16;
+    int sms = 0;
+    SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    const int grid = (int)std::min<size_t>((size_t)grid_for(n, 256), (size_t)sms * 16);
     TermPtrs out{{t->bpad[0], t->bpad[1]}};
     // 16-byte loads when every run of 8 depths starts on a 16-byte boundary
     const int vec = (h->Z % 4) == 0 && ((uintptr_t)c & 15u) == 0;
@@ -1452,8 +1579,9 @@ swopt_status tc_pack_u(swopt_handle* h, cudaStream_t st)
 {
     TcOperator* t = h->tc;
     const size_t n = (size_t)h->Q * (h->Twp / 8) * h->Y * h->X;
-    int grid = grid_for(n, 256);
-    if (grid > 152 * 16) grid = 152 * 16;
+    int sms = 0;
+    SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    const int grid = (int)std::min<size_t>((size_t)grid_for(n, 256), (size_t)sms * 16);
     TermPtrs out{{t->rpad[0], t->rpad[1]}};
     tc_pack_kernel<<<grid, 256, 0, st>>>(h->u, out, t->terms, h->Q, h->Y, h->X, h->Twp, t->A.KS,
                                          t->Yp, t->Xp, h->r);
