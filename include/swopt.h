@@ -81,11 +81,23 @@ typedef struct {
  *                    accumulation with the two correction products in an
  *                    accumulator of their own: measured relative error of
  *                    the operator 4e-6 (A) and 1e-5 (A^T) at 64^3 x 256 with
- *                    15 x 15 support, against 1e-6 for SWOPT_PREC_FP32. */
+ *                    15 x 15 support, against 1e-6 for SWOPT_PREC_FP32.
+ *  SWOPT_PREC_FP8  : tcgen05 tensor cores on FP8 E4M3 operands (3 mantissa
+ *                    bits), FP32 accumulation, with per-channel
+ *                    equilibration: the kernel is stored as K_j / s_j and the
+ *                    image as b_j s_j sigma (s_j per depth for A and per
+ *                    window sample for A^T, from the kernel; sigma per call,
+ *                    from the image's largest scaled entry), so that each
+ *                    product equals K_j b_j sigma in real arithmetic and both
+ *                    operands use the format's range; the output is divided
+ *                    by sigma.  An experiment: its operator error (a few
+ *                    percent) is reported against the FP64 reference.  Not
+ *                    a resync precision of the refined solve. */
 typedef enum {
     SWOPT_PREC_FP32 = 0,
     SWOPT_PREC_BF16 = 1,
-    SWOPT_PREC_BF16X3 = 2
+    SWOPT_PREC_BF16X3 = 2,
+    SWOPT_PREC_FP8 = 3
 } swopt_precision;
 
 /* Momentum of Algorithms 1 and 2: Beck-Teboulle (t_k - 1)/t_{k+1}, the

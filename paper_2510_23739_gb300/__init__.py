@@ -25,7 +25,7 @@ from . import build as _build
 __all__ = ["lib", "Operator", "SolveParams", "SwoptError", "PRECISION", "MOMENTUM",
            "HFunction", "Batch", "REFINED_DEFAULTS"]
 
-PRECISION = {"fp32": 0, "bf16": 1, "bf16x3": 2}
+PRECISION = {"fp32": 0, "bf16": 1, "bf16x3": 2, "fp8": 3}
 MOMENTUM = {"beck_teboulle": 0, "paper_printed": 1, "none": 2}
 # The refined solve's recommended schedule for BF16 contractions: an exact
 # (two-term BF16) gradient every 25 iterations, and sooner whenever the

@@ -833,7 +833,7 @@ swopt_status swopt_set_precision(swopt_handle* h, int precision)
 {
     clear_error();
     SW_TRY(check_handle(h));
-    if (precision < SWOPT_PREC_FP32 || precision > SWOPT_PREC_BF16X3) {
+    if (precision < SWOPT_PREC_FP32 || precision > SWOPT_PREC_FP8) {
         set_error("unknown precision %d", precision);
         return SWOPT_ERR_INVALID_ARG;
     }

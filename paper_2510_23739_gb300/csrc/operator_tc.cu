@@ -47,8 +47,16 @@
 // v - v0) with the 3 products v0 w0, v0 w1, v1 w0 (the dropped v1 w1 is
 // below 2^-16 of |v w|) accumulated in FP32; the 2 correction products go to
 // an accumulator of their own where TMEM holds it, so that the tensor core's
-// FP32 accumulation rounds them on their own (2^-8 smaller) scale.
+// FP32 accumulation rounds them on their own (2^-8 smaller) scale.  Or FP8
+// E4M3 operands (kind::f8f6f4, K = 32 per MMA in the same 32 bytes of a row)
+// with FP32 accumulation and per-channel equilibration of the contracted
+// dimension: the kernel is stored as K_j / s_j and the image as b_j s_j sigma,
+// so every product is K_j b_j sigma exactly in real arithmetic; s_j (static,
+// from the kernel) puts each depth's (A) or sample's (A^T) largest kernel
+// entry at 256, and sigma (per launch, from the largest scaled image entry)
+// does the same for the image; the epilogue divides by sigma.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cmath>
@@ -96,8 +104,14 @@ struct TcDir {
 
 struct TcOperator {
     int terms = 1;                // BF16 terms per operand (1 or 2)
+    bool fp8 = false;             // E4M3 operands (one term)
+    int esl = 8;                  // contracted-dimension elements per 16-byte slice (8 or 16)
     int tilesX = 0, tilesY = 0, Yp = 0, Xp = 0, HY = 0;
-    int Zp16 = 0;
+    int Zp16 = 0;                 // depths padded to a whole slice pair (16 BF16 or 32 FP8)
+    float* s_dep = nullptr;       // FP8: [Zp16] depth scales s_j of the forward
+    float* s_tim = nullptr;       // FP8: [Twp] sample scales s_t of the adjoint
+    unsigned* words = nullptr;    // FP8: [2] largest scaled image / residual entry (float bits)
+    std::vector<double> s_dep_h, s_tim_h;  // FP8: host copies of the scales
     TcDir F, A;
     __nv_bfloat16* bpad[kMaxTerms] = {nullptr, nullptr};  // [Q][F.KS][Yp][Xp][8] per term
     __nv_bfloat16* rpad[kMaxTerms] = {nullptr, nullptr};  // [Q][A.KS][Yp][Xp][8] per term
@@ -224,6 +238,17 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
+// D[tmem] (+)= A * B^T, kind::f8f6f4 with E4M3 A and B (K = 32), FP32 accumulate.
+__device__ __forceinline__ void tc_mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 {
     uint32_t r[16];
@@ -304,6 +329,10 @@ struct TcArgs {
     int max_pieces;             // partial-sum slots per tile-state
     const int* gate;            // launch runs only if *gate == want (null: always)
     int want;
+    int fp8;                    // E4M3 operands: kind::f8f6f4, output divided by sigma
+    const unsigned* in_word;    // FP8: the largest scaled entry of the input images (sigma = 256 / it)
+    unsigned* max_word;         // FP8 forward mode 0: atomic max of |out| s_t (the residual's scale)
+    const float* s_out;         // FP8 forward: the adjoint's sample scales s_t
 };
 
 // ---------------------------------------------------------------------------
@@ -367,7 +396,8 @@ struct IssueCfg {
 
 // The products of every tap of a stage, specialised at compile time: MT
 // tiles, MB channel blocks, and MODE 0 (one BF16 term), 1 (two terms, the
-// corrections in accumulator set 1) or 2 (two terms, one accumulator set).
+// corrections in accumulator set 1), 2 (two terms, one accumulator set) or 3
+// (one E4M3 term, kind::f8f6f4).
 // Accumulator of (set, block, tile): columns ((set MB + block) MT + tile) 256.
 template <int MT, int MB, int MODE>
 __device__ __forceinline__ void issue_taps(const IssueCfg& c, uint32_t tbuf, uint64_t a0,
@@ -385,6 +415,10 @@ __device__ __forceinline__ void issue_taps(const IssueCfg& c, uint32_t tbuf, uin
             for (int i = 0; i < MT; ++i) {
                 const uint64_t bi = bt + (uint64_t)(i * 8);  // the next tile: 8 positions x 16 B
                 const uint32_t dm = tbuf + (uint32_t)((mb * MT + i) * kTilePos);
+                if (MODE == 3) {
+                    tc_mma_f8(dm, am, bi, c.idesc, 1u);
+                    continue;
+                }
                 tc_mma(dm, am, bi, c.idesc, 1u);
                 if (MODE != 0) {
                     const uint32_t dc =
@@ -397,8 +431,9 @@ __device__ __forceinline__ void issue_taps(const IssueCfg& c, uint32_t tbuf, uin
     }
 }
 
-__host__ __device__ __forceinline__ int issue_kind(int MT, int MB, int terms, int RA)
+__host__ __device__ __forceinline__ int issue_kind(int MT, int MB, int terms, int RA, int fp8)
 {
+    if (fp8) return 12 + (MT - 1) * 2 + (MB - 1);
     const int mode = terms == 1 ? 0 : (RA == 2 ? 1 : 2);
     return ((MT - 1) * 2 + (MB - 1)) * 3 + mode;
 }
@@ -419,7 +454,11 @@ __device__ __forceinline__ void issue_stage(int kind, const IssueCfg& c, uint32_
     case 8: issue_taps<2, 1, 2>(c, tbuf, a0, b0, ow, nt); break;
     case 9: issue_taps<2, 2, 0>(c, tbuf, a0, b0, ow, nt); break;
     case 10: issue_taps<2, 2, 1>(c, tbuf, a0, b0, ow, nt); break;
-    default: issue_taps<2, 2, 2>(c, tbuf, a0, b0, ow, nt); break;
+    case 11: issue_taps<2, 2, 2>(c, tbuf, a0, b0, ow, nt); break;
+    case 12: issue_taps<1, 1, 3>(c, tbuf, a0, b0, ow, nt); break;
+    case 13: issue_taps<1, 2, 3>(c, tbuf, a0, b0, ow, nt); break;
+    case 14: issue_taps<2, 1, 3>(c, tbuf, a0, b0, ow, nt); break;
+    default: issue_taps<2, 2, 3>(c, tbuf, a0, b0, ow, nt); break;
     }
 }
 
@@ -590,11 +629,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                                  ((uint64_t)1 << 46);
         const uint64_t bdesc_c = ((uint64_t)(a_slice >> 4) << 16) | ((uint64_t)a.HX << 32) |
                                  ((uint64_t)1 << 46);
-        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+        // FP32 accumulator; BF16 (format 1) or E4M3 (format 0) A and B, K-major
+        const uint32_t ab_fmt = a.fp8 ? 0u : ((1u << 7) | (1u << 10));
+        const uint32_t idesc = (1u << 4) | ab_fmt |
                                (((uint32_t)kTilePos >> 3) << 17) | (((uint32_t)kRows >> 4) << 24);
         const IssueCfg ic{(uint32_t)(a.MB * kBlockBytes), (uint32_t)(a_part >> 4),
                           (uint32_t)(a.stage_bytes >> 4), idesc};
-        const int kind = issue_kind(a.MT, a.MB, a.terms, a.RA);
+        const int kind = issue_kind(a.MT, a.MB, a.terms, a.RA, a.fp8);
         int local = 0;  // this CTA's runs so far (ring position)
         int ag = 0;     // halo fills consumed
         int stage = 0;
@@ -679,6 +720,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         const size_t unit_floats = (size_t)a.MB * a.MT * kTilePos * kRows;
         const size_t S = (size_t)a.Y * a.X;
         const float* __restrict__ ytil = a.ytil;
+        // FP8: the accumulators hold sigma (sum of products); sigma = 256 / (largest
+        // scaled input entry), so the output is the accumulator times that / 256
+        const float inv_sigma = a.fp8 ? __uint_as_float(*a.in_word) * (1.0f / 256.0f) : 1.0f;
+        float rmax = 0.f;  // FP8 forward: largest |output| s_t of this thread
         TcUnit u;
         for (int k = 0; tc_unit(a, k, u); ++k) {
             const int buf = a.NBUF == 2 ? (k & 1) : 0;
@@ -772,6 +817,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                                     }
                                 }
                             }
+                            if (a.fp8) {
+#pragma unroll
+                                for (int e = 0; e < 16; ++e) v[e] *= inv_sigma;
+                            }
                             // column 16 cb + e is position (y0 + 2 cb + e / 8, x0 + 8 ti + e % 8);
                             // the chunk's measurements are loaded together first (the
                             // stores below would otherwise order every load behind them)
@@ -809,7 +858,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                                     }
                                 }
                                 if (a.mode == 0) {
-                                    if (ch_ok) a.out_f[ub] = o;
+                                    if (ch_ok) {
+                                        a.out_f[ub] = o;
+                                        if (a.max_word) rmax = fmaxf(rmax, fabsf(o) * a.s_out[ch]);
+                                    }
                                     continue;
                                 }
                                 // the BF16 terms of channels 8 g .. 8 g + 7 (lanes 8 g' ..
@@ -852,6 +904,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
             if (lane == 0) s_red[q] = part;
+        }
+        if (a.max_word) {
+            // non-negative floats order as their bit patterns
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+                rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
+            if (lane == 0) atomicMax(a.max_word, __float_as_uint(rmax));
         }
     }
 
@@ -950,6 +1009,135 @@ __global__ void tc_pack_kernel(const float* __restrict__ u, TermPtrs out, int te
 }
 
 // ---------------------------------------------------------------------------
+// FP8 (E4M3) images.  Pass 0 of tc_states_f8_kernel finds the largest
+// |b_j| s_j of the state images (atomic max of its float bits in *word; the
+// caller zeroes it first); pass 1 writes b_j s_j sigma, sigma = 256 / *word,
+// as E4M3, 16 depths per 16-byte slice row.  tc_pack_f8_kernel does the same
+// for the residual u (FP32 [Q][S][Twp]) with the sample scales s_t;
+// u_max_f8_kernel is its pass 0 when u did not come from the forward epilogue.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d)
+{
+    return (uint32_t)__nv_cvt_float_to_fp8(a, __NV_SATFINITE, __NV_E4M3) |
+           ((uint32_t)__nv_cvt_float_to_fp8(b, __NV_SATFINITE, __NV_E4M3) << 8) |
+           ((uint32_t)__nv_cvt_float_to_fp8(c, __NV_SATFINITE, __NV_E4M3) << 16) |
+           ((uint32_t)__nv_cvt_float_to_fp8(d, __NV_SATFINITE, __NV_E4M3) << 24);
+}
+
+__device__ __forceinline__ uint4 pack_e4m3x16(const float (&v)[16], float scale)
+{
+    return make_uint4(pack_e4m3x4(v[0] * scale, v[1] * scale, v[2] * scale, v[3] * scale),
+                      pack_e4m3x4(v[4] * scale, v[5] * scale, v[6] * scale, v[7] * scale),
+                      pack_e4m3x4(v[8] * scale, v[9] * scale, v[10] * scale, v[11] * scale),
+                      pack_e4m3x4(v[12] * scale, v[13] * scale, v[14] * scale, v[15] * scale));
+}
+
+__device__ __forceinline__ void warp_max_to(unsigned* word, float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(word, __float_as_uint(v));
+}
+
+__global__ void tc_states_f8_kernel(const float* __restrict__ c, const float* __restrict__ Sm,
+                                    const float* __restrict__ s_dep, uint8_t* __restrict__ out,
+                                    unsigned* word, int pass, int Q, int P, int Y, int X, int Z,
+                                    int slices, int KS, int Yp, int Xp, int r, const int* gate,
+                                    int want)
+{
+    if (gated_off(gate, want)) return;
+    const unsigned n = (unsigned)slices * Y * X;
+    const size_t SZ = (size_t)Y * X * Z;
+    const float sigma = pass == 1 ? 256.0f / fmaxf(__uint_as_float(*word), 1e-30f) : 0.f;
+    float lmax = 0.f;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < ((n + 31u) & ~31u);
+         i += gridDim.x * blockDim.x) {
+        if (i < n) {
+            const int x = (int)(i % (unsigned)X);
+            const int y = (int)((i / (unsigned)X) % (unsigned)Y);
+            const int s16 = (int)(i / ((unsigned)X * Y));
+            const int j0 = 16 * s16;
+            float cv[kMaxSpecies][16];
+#pragma unroll
+            for (int p = 0; p < kMaxSpecies; ++p) {
+                if (p >= P) break;
+                const float* src = c + p * SZ + ((size_t)y * X + x) * Z + j0;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) cv[p][e] = j0 + e < Z ? src[e] : 0.f;
+            }
+            for (int m = 0; m < Q; ++m) {
+                float v[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int j = j0 + e;
+                    float acc = 0.f;
+                    if (j < Z) {
+#pragma unroll
+                        for (int p = 0; p < kMaxSpecies; ++p) {
+                            if (p >= P) break;
+                            acc = fmaf(Sm[(m * P + p) * Z + j], cv[p][e], acc);
+                        }
+                        acc *= s_dep[j];
+                    }
+                    v[e] = acc;
+                }
+                if (pass == 0) {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) lmax = fmaxf(lmax, fabsf(v[e]));
+                } else {
+                    const size_t o = ((((size_t)m * KS + s16) * Yp + (y + r)) * Xp + (x + r)) * 16;
+                    *reinterpret_cast<uint4*>(out + o) = pack_e4m3x16(v, sigma);
+                }
+            }
+        }
+        if (pass == 0) warp_max_to(word, lmax);
+        lmax = 0.f;
+    }
+}
+
+__global__ void u_max_f8_kernel(const float* __restrict__ u, const float* __restrict__ s_tim,
+                                unsigned* word, size_t n, int Twp, const int* gate, int want)
+{
+    if (gated_off(gate, want)) return;
+    float lmax = 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        lmax = fmaxf(lmax, fabsf(u[i]) * s_tim[i % (size_t)Twp]);
+    warp_max_to(word, lmax);
+}
+
+__global__ void tc_pack_f8_kernel(const float* __restrict__ u, const float* __restrict__ s_tim,
+                                  const unsigned* word, uint8_t* __restrict__ out, int Q, int Y,
+                                  int X, int Twp, int KS, int Yp, int Xp, int r, const int* gate,
+                                  int want)
+{
+    if (gated_off(gate, want)) return;
+    const int slices = Twp / 16;
+    const size_t n = (size_t)Q * slices * Y * X;
+    const float sigma = 256.0f / fmaxf(__uint_as_float(*word), 1e-30f);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % X);
+        const int y = (int)((i / X) % Y);
+        const int s16 = (int)((i / ((size_t)X * Y)) % slices);
+        const int m = (int)(i / ((size_t)X * Y * slices));
+        const float4* src = reinterpret_cast<const float4*>(
+            u + (((size_t)m * Y + y) * X + x) * Twp + 16 * s16);
+        float v[16];
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+            const float4 w = src[q4];
+            v[4 * q4] = w.x * s_tim[16 * s16 + 4 * q4];
+            v[4 * q4 + 1] = w.y * s_tim[16 * s16 + 4 * q4 + 1];
+            v[4 * q4 + 2] = w.z * s_tim[16 * s16 + 4 * q4 + 2];
+            v[4 * q4 + 3] = w.w * s_tim[16 * s16 + 4 * q4 + 3];
+        }
+        const size_t o = ((((size_t)m * KS + s16) * Yp + (y + r)) * Xp + (x + r)) * 16;
+        *reinterpret_cast<uint4*>(out + o) = pack_e4m3x16(v, sigma);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host helpers
 // ---------------------------------------------------------------------------
 uint16_t f2bf(float f)
@@ -967,6 +1155,33 @@ float bf2f(uint16_t b)
     float f;
     std::memcpy(&f, &u, 4);
     return f;
+}
+
+// IEEE-style E4M3 (the OCP 8-bit format: 1 sign, 4 exponent bits with bias
+// 7, 3 mantissa bits, subnormals below 2^-6, largest finite 448, no
+// infinity): round to nearest even, saturating at +-448.
+uint8_t f2e4m3(float f)
+{
+    const uint8_t sign = std::signbit(f) ? 0x80 : 0x00;
+    const double a = std::fabs((double)f);
+    if (!(a == a)) return 0x7F;                 // NaN
+    if (a >= 448.0) return sign | 0x7E;         // saturate
+    int e2 = 0;
+    const double fr = std::frexp(a, &e2);       // a = fr 2^e2, fr in [0.5, 1)
+    int e = e2 - 1;                             // a = (2 fr) 2^e
+    if (a == 0.0 || e < -6) {
+        // subnormal: a / 2^-9 rounded to an integer 0..8 (8 is the smallest normal)
+        const double q = a * 512.0;
+        double m = std::nearbyint(q);           // round half to even (default mode)
+        return sign | (uint8_t)m;               // 8 encodes exponent 1, mantissa 0
+    }
+    double m = std::nearbyint((2.0 * fr - 1.0) * 8.0);  // 0..8
+    if (m == 8.0) {
+        m = 0.0;
+        ++e;
+    }
+    if (e > 8 || (e == 8 && m > 6.0)) return sign | 0x7E;
+    return sign | (uint8_t)(((e + 7) << 3) | (int)m);
 }
 
 template <typename T>
@@ -1033,13 +1248,53 @@ float kernel_value(const swopt_handle* h, bool adj, int row, int kidx, int d)
     return (float)h->K64[((size_t)j * kk + d) * h->T + tt];
 }
 
-// The kernel blocks [group][tap][pair][MB][2 halves][128 rows][8], per BF16
-// term, of a configuration's slice grouping.
-void pack_dir(const swopt_handle* h, bool adj, const TcDir& D, int npe,
+// FP8 scale of contraction index kidx: the depth scale s_j for A, the sample
+// scale s_t for A^T (1 for the BF16 precisions).
+double fp8_scale(const swopt_handle* h, const std::vector<double>& s_dep,
+                 const std::vector<double>& s_tim, bool adj, int kidx)
+{
+    (void)h;
+    const std::vector<double>& sv = adj ? s_tim : s_dep;
+    return kidx < (int)sv.size() ? sv[kidx] : 0.0;
+}
+
+// The kernel blocks [group][tap][pair][MB][2 halves][128 rows][16 bytes], per
+// BF16 term (8 values a row), or for FP8 the E4M3 codes of K / s (16 values a
+// row, two to a 16-bit slot), of a configuration's slice grouping.
+void pack_dir(const swopt_handle* h, const TcOperator* t, bool adj, const TcDir& D, int npe,
+              const std::vector<double>& s_dep, const std::vector<double>& s_tim,
               std::vector<uint16_t> (&w)[kMaxTerms])
 {
     const int kk = h->k * h->k;
     const int gpairs = D.GA / 2;
+    if (t->fp8) {
+        for (int tt = 0; tt < kMaxTerms; ++tt) w[tt].clear();
+        w[0].reserve((size_t)kk * npe * D.MB * kBlockBytes / 2);
+        for (int g = 0; g < D.NG; ++g) {
+            const int np = std::min(gpairs, npe - g * gpairs);
+            for (int d = 0; d < kk; ++d)
+                for (int p = 0; p < np; ++p) {
+                    const int gp = g * gpairs + p;
+                    for (int mb = 0; mb < D.MB; ++mb)
+                        for (int half = 0; half < 2; ++half)
+                            for (int row = 0; row < kRows; ++row)
+                                for (int e = 0; e < 16; e += 2) {
+                                    uint16_t pair = 0;
+                                    for (int b = 0; b < 2; ++b) {
+                                        const int kidx = 32 * gp + 16 * half + e + b;
+                                        const double sc = fp8_scale(h, s_dep, s_tim, adj, kidx);
+                                        const double v =
+                                            sc > 0 ? kernel_value(h, adj, mb * kRows + row, kidx, d) / sc
+                                                   : 0.0;
+                                        pair |= (uint16_t)f2e4m3((float)v) << (8 * b);
+                                    }
+                                    w[0].push_back(pair);
+                                }
+                }
+        }
+        if (w[0].empty()) w[0].assign(8, 0);
+        return;
+    }
     for (int tt = 0; tt < kMaxTerms; ++tt) {
         w[tt].clear();
         w[tt].reserve((size_t)kk * npe * D.MB * kBlockBytes / 2);
@@ -1082,8 +1337,10 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
     D.rows = adj ? h->Z : h->Twp;
     D.MB = (D.rows + kRows - 1) / kRows;
     if (D.MB > 2) return false;
-    const int ks_min = adj ? h->Twp / 8 : t->Zp16 / 8;  // contracted slices, both even
+    // contracted slices (both even): 16-byte rows of 8 BF16 or 16 FP8 values
+    const int ks_min = adj ? h->Twp / t->esl : t->Zp16 / t->esl;
     const int npairs = ks_min / 2;
+    const int pair_elems = 2 * t->esl;
     D.HX = 8 * MT + 2 * h->r;
     D.npos = t->HY * D.HX;
     D.cols = (int)pow2_cols(NBUF * RA * D.MB * MT * kTilePos);
@@ -1096,8 +1353,8 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
         bool any = false;
         for (int d = 0; d < kk && !any; ++d)
             for (int row = 0; row < D.rows && !any; ++row)
-                for (int e = 0; e < 16; ++e)
-                    if (kernel_value(h, adj, row, 16 * gp + e, d) != 0.f) {
+                for (int e = 0; e < pair_elems; ++e)
+                    if (kernel_value(h, adj, row, pair_elems * gp + e, d) != 0.f) {
                         any = true;
                         break;
                     }
@@ -1163,7 +1420,7 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
         base_bytes += (size_t)kk * tapb;
         out->tab.insert(out->tab.end(), {base16, tapb, tpr, (uint32_t)np});
         D.runs += (kk + (int)tpr - 1) / (int)tpr;
-        macs += (double)kk * np * D.MB * kRows * kTilePos * 16;
+        macs += (double)kk * np * D.MB * kRows * kTilePos * pair_elems;
     }
     // runs of tpr taps: halo offsets (16-B units) of each tap of the run
     for (int d0 = 0; d0 < kk; d0 += (int)tpr) {
@@ -1215,7 +1472,7 @@ swopt_status upload_dir(const swopt_handle* h, bool adj, const DirHost& H, int t
         if (c.GA == D->GA) e = &c;
     if (!e) {
         std::vector<uint16_t> w[kMaxTerms];
-        pack_dir(h, adj, *D, H.npe, w);
+        pack_dir(h, h->tc, adj, *D, H.npe, h->tc->s_dep_h, h->tc->s_tim_h, w);
         cache.push_back(WCache());
         e = &cache.back();
         e->GA = D->GA;
@@ -1265,6 +1522,11 @@ TcArgs dir_args(const swopt_handle* h, const TcOperator* t, const TcDir& D, bool
     for (int tt = 0; tt < kMaxTerms; ++tt) a.img[tt] = adj ? t->rpad[tt] : t->bpad[tt];
     a.gate = h->gate;
     a.want = h->gate_want;
+    a.fp8 = t->fp8 ? 1 : 0;
+    if (t->fp8) {
+        a.in_word = adj ? t->words + 1 : t->words;
+        a.s_out = t->s_tim;
+    }
     return a;
 }
 
@@ -1351,6 +1613,9 @@ void tc_release(swopt_handle* h)
         cudaFree(t->rpad[tt]);
     }
     cudaFree(t->err);
+    cudaFree(t->s_dep);
+    cudaFree(t->s_tim);
+    cudaFree(t->words);
     delete t;
     h->tc = nullptr;
 }
@@ -1425,6 +1690,11 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
             if (adj) {
                 a.out_f = h->g;
                 a.mode = 0;
+            } else if (t->fp8) {
+                // as in the solve: FP32 output with the residual's scale taken
+                a.out_f = h->u;
+                a.mode = 0;
+                a.max_word = t->words + 1;
             } else {
                 // as in the solve: the scaled residual from measurements (h->u
                 // stands in for them) into the residual images
@@ -1478,16 +1748,19 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
 swopt_status tc_prepare(swopt_handle* h)
 {
     const int terms = h->precision == SWOPT_PREC_BF16X3 ? 2 : 1;
-    if (h->tc && h->tc->terms == terms) return SWOPT_OK;
+    const bool fp8 = h->precision == SWOPT_PREC_FP8;
+    if (h->tc && h->tc->terms == terms && h->tc->fp8 == fp8) return SWOPT_OK;
     tc_release(h);
     TcOperator* t = new TcOperator();
     t->terms = terms;
+    t->fp8 = fp8;
+    t->esl = fp8 ? 16 : 8;
     t->tilesX = (h->X + 7) / 8;
     t->tilesY = (h->Y + kTileY - 1) / kTileY;
     t->Xp = ((t->tilesX + 1) / 2) * 16 + 2 * h->r;  // room for up to 2 tiles per CTA
     t->Yp = t->tilesY * kTileY + 2 * h->r;
     t->HY = kTileY + 2 * h->r;
-    t->Zp16 = ((h->Z + 15) / 16) * 16;
+    t->Zp16 = ((h->Z + 2 * t->esl - 1) / (2 * t->esl)) * (2 * t->esl);
     h->tc = t;
     if (h->Twp > 2 * kRows || t->Zp16 > 2 * kRows) {
         set_error("tensor-core path supports a time window and a depth count up to 256 "
@@ -1497,7 +1770,7 @@ swopt_status tc_prepare(swopt_handle* h)
     }
     // padded images sized for the largest slice count any candidate may use
     // (NG groups of 2 ceil(pairs / NG) slices never exceed twice the pairs' slices)
-    const int ksf_max = 2 * (t->Zp16 / 8), ksa_max = 2 * (h->Twp / 8);
+    const int ksf_max = 2 * (t->Zp16 / t->esl), ksa_max = 2 * (h->Twp / t->esl);
     const size_t plane = (size_t)t->Yp * t->Xp * 8;
     const size_t nb = (size_t)h->Q * ksf_max * plane, nr = (size_t)h->Q * ksa_max * plane;
     swopt_status s = SWOPT_OK;
@@ -1519,6 +1792,34 @@ swopt_status tc_prepare(swopt_handle* h)
         zero(t->rpad[tt], nr * 2);
     }
     zero(t->err, sizeof(int));
+    if (fp8 && s == SWOPT_OK) {
+        // FP8 equilibration: per depth (A) and per window sample (A^T), the
+        // largest kernel entry maps to 256; a channel whose kernel is zero
+        // (padding) gets scale 0, so that it takes no part in the image's
+        // largest scaled entry and its image values are 0
+        const int kk = h->k * h->k;
+        t->s_dep_h.assign(t->Zp16, 0.0);
+        t->s_tim_h.assign(h->Twp, 0.0);
+        std::vector<double> mt(h->Twp, 0.0);
+        for (int j = 0; j < h->Z; ++j) {
+            double mj = 0.0;
+            for (int d = 0; d < kk; ++d)
+                for (int w = 0; w < h->Twp && h->t0 + w < h->T; ++w) {
+                    const double v = std::fabs(h->K64[((size_t)j * kk + d) * h->T + h->t0 + w]);
+                    mj = std::max(mj, v);
+                    mt[w] = std::max(mt[w], v);
+                }
+            if (mj > 0) t->s_dep_h[j] = mj / 256.0;
+        }
+        for (int w = 0; w < h->Twp; ++w)
+            if (mt[w] > 0) t->s_tim_h[w] = mt[w] / 256.0;
+        std::vector<float> sd(t->s_dep_h.begin(), t->s_dep_h.end());
+        std::vector<float> st(t->s_tim_h.begin(), t->s_tim_h.end());
+        step(tc_upload(&t->s_dep, sd));
+        step(tc_upload(&t->s_tim, st));
+        step(tc_alloc(&t->words, 4));
+        zero(t->words, 4 * sizeof(unsigned));
+    }
     // the adjoint's slice count fixes the layout the forward epilogue writes
     if (s == SWOPT_OK)
         s = tune_dir(h, true, h->tc_force_mt[1], h->tc_force_ctas[1], h->tc_force_ra[1],
@@ -1556,6 +1857,26 @@ int tc_forward_blocks(const swopt_handle* h)
 swopt_status tc_states(swopt_handle* h, const float* c, cudaStream_t st)
 {
     TcOperator* t = h->tc;
+    if (t->fp8) {
+        const int slices = (h->Z + 15) / 16;
+        const size_t n = (size_t)slices * h->Y * h->X;
+        if (h->P > kMaxSpecies || n > 0x7FFFFFFFull) {
+            set_error("internal: state images beyond the kernel's limits");
+            return SWOPT_ERR_UNSUPPORTED;
+        }
+        int sms = 0;
+        SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+        const int grid = (int)std::min<size_t>((size_t)grid_for(n, 256), (size_t)sms * 16);
+        uint8_t* out = reinterpret_cast<uint8_t*>(t->bpad[0]);
+        SW_CUDA(cudaMemsetAsync(t->words, 0, sizeof(unsigned), st));
+        for (int pass = 0; pass < 2; ++pass) {
+            tc_states_f8_kernel<<<grid, 256, 0, st>>>(c, h->Sm, t->s_dep, out, t->words, pass, h->Q,
+                                                      h->P, h->Y, h->X, h->Z, slices, t->F.KS,
+                                                      t->Yp, t->Xp, h->r, h->gate, h->gate_want);
+            SW_LAUNCHED(h);
+        }
+        return SWOPT_OK;
+    }
     const int slices = (h->Z + 7) / 8;
     const size_t n = (size_t)slices * h->Y * h->X;
     if (h->P > kMaxSpecies || n > 0x7FFFFFFFull) {
@@ -1575,9 +1896,34 @@ swopt_status tc_states(swopt_handle* h, const float* c, cudaStream_t st)
     return SWOPT_OK;
 }
 
+// FP8: u (FP32 [Q][S][Twp]) into the E4M3 residual images with the scale in
+// words[1] (taken by the forward epilogue, or first here when take_max).
+static swopt_status pack_f8(swopt_handle* h, bool take_max, cudaStream_t st)
+{
+    TcOperator* t = h->tc;
+    int sms = 0;
+    SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    if (take_max) {
+        SW_CUDA(cudaMemsetAsync(t->words + 1, 0, sizeof(unsigned), st));
+        const size_t nu = nu_of(h);
+        u_max_f8_kernel<<<(int)std::min<size_t>((size_t)grid_for(nu, 256), (size_t)sms * 8), 256, 0,
+                          st>>>(h->u, t->s_tim, t->words + 1, nu, h->Twp, h->gate, h->gate_want);
+        SW_LAUNCHED(h);
+    }
+    const size_t n = (size_t)h->Q * (h->Twp / 16) * h->Y * h->X;
+    const int grid = (int)std::min<size_t>((size_t)grid_for(n, 256), (size_t)sms * 16);
+    tc_pack_f8_kernel<<<grid, 256, 0, st>>>(h->u, t->s_tim, t->words + 1,
+                                            reinterpret_cast<uint8_t*>(t->rpad[0]), h->Q, h->Y,
+                                            h->X, h->Twp, t->A.KS, t->Yp, t->Xp, h->r, h->gate,
+                                            h->gate_want);
+    SW_LAUNCHED(h);
+    return SWOPT_OK;
+}
+
 swopt_status tc_pack_u(swopt_handle* h, cudaStream_t st)
 {
     TcOperator* t = h->tc;
+    if (t->fp8) return pack_f8(h, true, st);
     const size_t n = (size_t)h->Q * (h->Twp / 8) * h->Y * h->X;
     int sms = 0;
     SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
@@ -1597,13 +1943,21 @@ swopt_status tc_forward(swopt_handle* h, bool to_r, const float* ytil, double* p
     a.scale = scale;
     a.ytil = ytil;
     a.partials = partials;
-    a.mode = to_r ? 1 : 0;
-    a.out_f = to_r ? nullptr : h->u;
-    for (int tt = 0; tt < kMaxTerms; ++tt) a.out_t[tt] = to_r ? t->rpad[tt] : nullptr;
+    // FP8: the residual goes through FP32 u, whose largest scaled entry the
+    // epilogue takes, into the E4M3 images by a pack pass
+    const bool direct = to_r && !t->fp8;
+    a.mode = direct ? 1 : 0;
+    a.out_f = direct ? nullptr : h->u;
+    for (int tt = 0; tt < kMaxTerms; ++tt) a.out_t[tt] = direct ? t->rpad[tt] : nullptr;
+    if (t->fp8 && to_r) {
+        a.max_word = t->words + 1;
+        SW_CUDA(cudaMemsetAsync(t->words + 1, 0, sizeof(unsigned), st));
+    }
     ProfileRec rec;
     prof_begin(h, 0, st, &rec);
     SW_TRY(launch_conv(h, t->F, a, st));
     prof_end(h, &rec, st);
+    if (t->fp8 && to_r) return pack_f8(h, false, st);
     return SWOPT_OK;
 }
 
