@@ -464,9 +464,13 @@ def run_two_step(args, device):
 
 def run_prox_joint(args, device):
     """The prox of the full R3 with its lambda_3 term (swopt_prox_joint) on
-    the workload's volume and pulses: time per call of `inner` dual
-    iterations, CUDA events over `steps` calls after `warmup`, inputs larger
-    than L2."""
+    the workload's volume and switching states: time per call of `inner` dual
+    iterations, CUDA events over `steps` calls after `warmup`.  Per dual
+    iteration (one dual per switching state, nd = 4 P + 3 Q volumes): L^T
+    reads the momentum duals and z and writes w (nd + 2 P volumes); the update
+    reads w, reads and writes u and r (4 nd + P volumes).  The duals of the
+    large workload (P = 3, Q = 10) are 42 volumes of 6.3 MB, twice L2 per
+    array."""
     import torch
     import paper_2510_23739_gb300 as sw
 
@@ -476,13 +480,15 @@ def run_prox_joint(args, device):
     op = sw.Operator(g, K, prob.sw)
     z = torch.tensor(synth.gaussian(g.c_shape(), 5), dtype=torch.float32, device=device) + 0.5
     lam_tv, lam_l1, lam_b, alpha, inner = prob.lam_tv, prob.lam_l1, prob.lam_tv, 0.5, prob.inner
-    # a dual step below 1/||L||^2 (|S| <= 2 here); the time does not depend on it
-    step2 = 1.0 / (12 * lam_tv ** 2 + lam_l1 ** 2 + 12 * lam_b ** 2 * g.N * 4.0)
+    step2 = 1.0 / op.prox_joint_step_bound(lam_tv, lam_l1, lam_b)
     out = torch.empty_like(z)
     for _ in range(args.warmup):
         op.prox_joint(z, alpha, lam_tv, lam_l1, lam_b, inner, step2, out=out)
     stream = torch.cuda.current_stream()
+    clocks = ClockSampler(_smi_id(device))
     torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -490,19 +496,28 @@ def run_prox_joint(args, device):
         op.prox_joint(z, alpha, lam_tv, lam_l1, lam_b, inner, step2, out=out)
     e1.record(stream)
     torch.cuda.synchronize()
+    clk = clocks.stop()
+    op.check_device()
+    states = op.info()["states"]
+    op.close()
     ms = e0.elapsed_time(e1) / args.steps
     L = g.Y * g.X * g.Z
-    nu = (4 * g.P + 3 * g.N) * L
-    # per dual iteration: L^T reads the momentum duals and z, writes w; the
-    # update reads w (and neighbours), reads and writes u and r
-    bytes_iter = 4 * (nu + 2 * g.P * L) + 4 * (g.P * L + 4 * nu)
+    nd = 4 * g.P + 3 * states
+    bytes_iter = 4.0 * L * ((nd + 2 * g.P) + (4 * nd + g.P))
+    gbs = bytes_iter * inner / (ms * 1e-3) / 1e9
+    peaks, src = _peaks()
     print(json.dumps({
-        "metric": "joint prox time (full R3, lambda_3 term)", "value": ms, "unit": "ms",
-        "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "metric": "joint prox algorithmic HBM throughput (full R3, lambda_3 term)",
+        "value": gbs, "unit": "GB/s", "higher_is_better": True, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "dtype": "f32", "data": "synthetic (seeded Gaussian input)",
         "config": {"workload": args.workload, "inner_iters": inner, "pulses": g.N,
-                   "species": g.P, "dual_values": nu},
-        "algorithmic_gb_per_s": bytes_iter * inner / (ms * 1e-3) / 1e9}), flush=True)
+                   "species": g.P, "switching_states": states, "dual_volumes": nd,
+                   "l2": "dual arrays about 2x L2 each (no flush)"},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                     "bytes_per_dual_iter": bytes_iter, "peak_source": f"HBM copy ({src})"},
+        "clocks": clk}), flush=True)
 
 
 def run_prox_sweep(args, device):
@@ -563,6 +578,7 @@ def run_prox_sweep(args, device):
                      "avg_launch_ms": tv_ms, "peak_source": f"HBM copy ({src})"},
         "prox_l1": {"ms": l1_ms, "gb_per_s": l1_gbs, "frac": l1_gbs / peaks["hbm_gbs"]},
         "clocks": clk}), flush=True)
+
 
 
 def replace_iters(params, iters):

@@ -108,8 +108,9 @@ typedef enum {
     SWOPT_MOMENTUM_NONE = 2
 } swopt_momentum;
 
-/* Settings of Algorithm 1 (FISTA) on Eq. (one-step) with Eq. (reg-tv-l1-one),
- * lambda_3 = 0: w(c) = lambda_tv sum_p TV(c_p) + lambda_l1 ||c||_1 + indicator(c >= 0). */
+/* Settings of Algorithm 1 (FISTA) on Eq. (one-step) with Eq. (reg-tv-l1-one):
+ * w(c) = lambda_tv sum_p TV(c_p) + lambda_l1 ||c||_1 + lambda_3 sum_n TV((S c)^n)
+ * + indicator(c >= 0). */
 typedef struct {
     double step;        /* alpha_1; <= 0 means 1/L with L from swopt_lipschitz */
     double lambda_l1;   /* >= 0 */
@@ -147,6 +148,15 @@ typedef struct {
      * synchronisation): both branches are launched, and the one not taken
      * returns at once.  0: off (resync every refine_every iterations only). */
     double refine_budget;
+    /* lambda_3 of Eq. (reg-tv-l1-one), >= 0: TV of every pulse image (S c)^n.
+     * 0 keeps the composite prox of the other two terms (TV prox, then the
+     * l1 prox).  > 0 takes the prox of all three terms with the nonnegativity
+     * constraint by Algorithm 2 on the stacked operator (swopt_prox_joint),
+     * inner_iters dual iterations with inner_momentum; joint_step2 is its
+     * dual step (<= 0: 1 / the bound of eig_max(L L^T) that
+     * swopt_prox_joint_step_bound returns). */
+    double lambda_3;
+    double joint_step2;
 } swopt_solve_params;
 
 typedef struct {
@@ -265,20 +275,32 @@ swopt_status swopt_solve(swopt_handle* h, const float* y_dev, float* c_dev,
                          const swopt_solve_params* prm, swopt_solve_stats* stats, void* stream);
 
 /* Proximal map of alpha (R3 + delta_{>=0}) with all three terms of Eq.
- * (reg-tv-l1-one), including lambda_3 sum_n TV((S c)^n) (lambda_b here):
- * Algorithm 2 on the stacked L = [lambda_tv D per species; lambda_l1 I;
- * lambda_b D S per pulse] with dual step step2 (at most 1/eig_max(L L^T);
- * 12 lambda_tv^2 + lambda_l1^2 + 12 lambda_b^2 N max_j ||S_j||^2 bounds it),
- * `iters` dual iterations (Beck-Teboulle momentum) from a zero dual, output
- * max(z - L^T u, 0).  S is the handle's switching model (pulse n takes state
- * n mod pulses_per_cycle).  z_dev, x_dev: device [P][Y][X][Z] (x may equal z).
- * Scratch of (4P + 3N) * 2 + P volumes is taken from the stream-ordered
- * allocator for the call.  Errors: INVALID_ARG (null pointers, negative or
- * non-finite weights, iters < 0, step2 <= 0 with iters > 0), UNSUPPORTED
- * for P > 8, OOM, CUDA.  Asynchronous on the stream. */
+ * (reg-tv-l1-one), including lambda_3 sum_n TV((S c)^n) (lambda_b here), by
+ * Algorithm 2 on the dual of Eq. (prox-dual) for the stacked
+ * L = [lambda_tv D per species; lambda_l1 I; lambda_b D S per pulse]: the
+ * nonnegativity constraint of Eq. (prox) makes the dual
+ * min over |u| <= alpha of 1/2 ||max(z - L^T u, 0)||^2, so every dual step
+ * takes L of the projected point w = max(z - L^T r, 0).  Dual step step2 (at
+ * most 1/eig_max(L L^T); swopt_prox_joint_step_bound gives a bound of that
+ * eigenvalue), `iters` dual iterations (Beck-Teboulle momentum) from a zero
+ * dual, output max(z - L^T u, 0).  S is the handle's switching model (pulse n
+ * takes state n mod pulses_per_cycle); pulses of one state share one dual,
+ * which gives the same iterates as one dual per pulse.  z_dev, x_dev: device
+ * [P][Y][X][Z]; x may equal z.  Scratch ((8 P + 6 Q) volumes, Q the switching
+ * states, plus P) is the handle's, allocated on the first call.  Errors:
+ * INVALID_ARG (null pointers, negative or non-finite weights, iters < 0,
+ * step2 <= 0 with iters > 0), UNSUPPORTED for P > 8, OOM, CUDA.
+ * Asynchronous on the stream. */
 swopt_status swopt_prox_joint(swopt_handle* h, const float* z_dev, float* x_dev, double alpha,
                               double lambda_tv, double lambda_l1, double lambda_b, int iters,
                               double step2, void* stream);
+
+/* An upper bound of eig_max(L L^T) for swopt_prox_joint's stacked L:
+ * 12 lambda_tv^2 + lambda_l1^2 + 12 lambda_b^2 sum_n max_j sum_p S[n][p][j]^2
+ * (||D||^2 <= 12 in 3D; a pulse image's Cauchy-Schwarz bound per voxel).
+ * 0 for a null handle. */
+double swopt_prox_joint_step_bound(swopt_handle* h, double lambda_tv, double lambda_l1,
+                                   double lambda_b);
 
 /* The two-step approach (the paper's "Two-Step Approach", the comparison
  * method of the one-step reconstruction): first the acoustic problem of
@@ -301,11 +323,11 @@ swopt_status swopt_two_step(const swopt_geometry* geom, const double* K_host,
                             const swopt_solve_params* unmixing, void* stream);
 
 /* Objective of Eq. (one-step), in FP64: *F = 1/2||H c - y||^2 + lambda_tv sum_p TV(c_p)
- * + lambda_l1 ||c||_1, *fit = the data-fit term (either may be NULL).  c is not
- * checked for nonnegativity.  Synchronises. */
+ * + lambda_l1 ||c||_1 + lambda_3 sum_n TV((S c)^n), *fit = the data-fit term
+ * (either may be NULL).  c is not checked for nonnegativity.  Synchronises. */
 swopt_status swopt_objective(swopt_handle* h, const float* c_dev, const float* y_dev,
-                             double lambda_l1, double lambda_tv, double* F, double* fit,
-                             void* stream);
+                             double lambda_l1, double lambda_tv, double lambda_3, double* F,
+                             double* fit, void* stream);
 
 /* Gradient of f = 1/2||H c - y||^2 with respect to the switching parameters
  * with c held fixed (Eq. final-H differentiated): dkappa_host[p] = df/dkappa_p

@@ -66,6 +66,7 @@ def lib():
             L.oracle_power.restype = ctypes.c_double
             L.oracle_objective.restype = ctypes.c_double
             L.oracle_tv.restype = ctypes.c_double
+            L.oracle_tv_pulses.restype = ctypes.c_double
             L.oracle_num_threads.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -224,22 +225,47 @@ def prox_joint(geom, sw, z, alpha, lam_tv, lam_l1, lam_b, iters, step2,
     return (x, u) if return_dual else x
 
 
-def objective(geom, sw, K, c, y, lam_l1, lam_tv):
-    """Returns (F(c), data-fit 1/2||Hc - y||^2)."""
+def tv_pulses(geom, sw, c):
+    """sum_n TV((S c)^n), the lambda_3 term of Eq. (reg-tv-l1-one)."""
+    S = switch_matrix(geom, sw)
+    c = _f64(c).reshape(geom.c_shape())
+    return float(lib().oracle_tv_pulses(ctypes.c_int(geom.N), ctypes.c_int(geom.P),
+                                        ctypes.c_int(geom.Y), ctypes.c_int(geom.X),
+                                        ctypes.c_int(geom.Z), _p(S), _p(c)))
+
+
+def objective(geom, sw, K, c, y, lam_l1, lam_tv, lam_3=0.0):
+    """Returns (F(c), data-fit 1/2||Hc - y||^2); F includes lam_3 sum_n TV((S c)^n)."""
     S = switch_matrix(geom, sw)
     fit = ctypes.c_double(0.0)
     F = lib().oracle_objective(*_dims(geom), _p(S), _p(_f64(K)), _p(_f64(c)), _p(_f64(y)),
                                ctypes.c_double(lam_l1), ctypes.c_double(lam_tv),
                                ctypes.byref(fit))
+    if lam_3 != 0.0:
+        F += lam_3 * tv_pulses(geom, sw, c)
     return float(F), float(fit.value)
 
 
 def fista(geom, sw, K, y, alpha, iters, lam_l1, lam_tv, inner,
-          momentum="beck_teboulle", inner_momentum="beck_teboulle", history=False):
-    """Algorithm 1 with a fixed iteration count; returns c (and F per iteration)."""
+          momentum="beck_teboulle", inner_momentum="beck_teboulle", history=False,
+          lam_3=0.0, joint_step2=None):
+    """Algorithm 1 with a fixed iteration count; returns c (and F per iteration).
+    lam_3 > 0 takes the prox of all three terms of R3 (prox_joint, ``inner``
+    dual iterations with dual step ``joint_step2``)."""
     S = switch_matrix(geom, sw)
     c = np.empty(geom.c_shape())
     hist = np.empty(iters) if history else None
+    if lam_3 > 0:
+        if joint_step2 is None:
+            raise ValueError("lam_3 > 0 needs the joint prox's dual step")
+        lib().oracle_fista_joint(*_dims(geom), _p(S), _p(_f64(K)), _p(_f64(y)),
+                                 ctypes.c_double(alpha), ctypes.c_int(iters),
+                                 ctypes.c_double(lam_l1), ctypes.c_double(lam_tv),
+                                 ctypes.c_double(lam_3), ctypes.c_int(inner),
+                                 ctypes.c_double(joint_step2), ctypes.c_int(MOMENTUM[momentum]),
+                                 ctypes.c_int(MOMENTUM[inner_momentum]), _p(c),
+                                 _p(hist) if history else ctypes.c_void_p(0))
+        return (c, hist) if history else c
     lib().oracle_fista(*_dims(geom), _p(S), _p(_f64(K)), _p(_f64(y)),
                        ctypes.c_double(alpha), ctypes.c_int(iters),
                        ctypes.c_double(lam_l1), ctypes.c_double(lam_tv), ctypes.c_int(inner),

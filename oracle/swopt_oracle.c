@@ -366,9 +366,14 @@ void oracle_prox(int P, int Y, int X, int Z, const double* z, double* x,
  * differences (one TV per species and one per pulse image, as R3 sums them).
  * Dual u = [uc (P x 3L) ; ul (P L) ; ub (N x 3L)] in the box |u| <= alpha
  * (Eq. prox-dual; the lambdas live in L), dual step `step2` (at most
- * 1/eig_max(L L^T)), u and its momentum iterate start at zero:
+ * 1/eig_max(L L^T)), u and its momentum iterate start at zero.  The prox of
+ * Eq. (prox) includes the nonnegativity indicator, and Eq. (prox-dual) keeps
+ * the matching constraint z - L^T u >= 0: the dual of the constrained problem
+ * is min over |u| <= alpha of 1/2 ||max(z - L^T u, 0)||^2, whose gradient is
+ * -L max(z - L^T u, 0).  So the projected primal point enters every step
+ * (Algorithm 2 on this dual; the paper prints the clip on the output only):
  *   for i = 1..iters:
- *     w   = z - L^T r
+ *     w   = max(z - L^T r, 0)
  *     u_i = clamp(r + step2 L w, -alpha, alpha)
  *     t_{i+1} = (1 + sqrt(1 + 4 t_i^2)) / 2
  *     r   = u_i + beta_i (u_i - u_{i-1})
@@ -436,7 +441,10 @@ void oracle_prox_joint(int N, int P, int Y, int X, int Z, const double* S, const
     double t = 1.0;
     for (int it = 0; it < iters; ++it) {
         joint_LT(N, P, Y, X, Z, S, lam_tv, lam_l1, lam_b, rr, w, tmp);
-        for (size_t i = 0; i < nc; ++i) w[i] = z[i] - w[i];
+        for (size_t i = 0; i < nc; ++i) {
+            const double v = z[i] - w[i];
+            w[i] = v > 0.0 ? v : 0.0;
+        }
         joint_L(N, P, Y, X, Z, S, lam_tv, lam_l1, lam_b, w, g, tmp);
         for (size_t i = 0; i < nu; ++i) {
             const double v = rr[i] + step2 * g[i];
@@ -522,6 +530,66 @@ void oracle_fista(int N, int P, int Y, int X, int Z, int T, int k,
         t = t1;
         if (history)
             history[it] = oracle_objective(N, P, Y, X, Z, T, k, S, K, c, yv, lam_l1, lam_tv, NULL);
+    }
+    memcpy(c_out, c, sizeof(double) * nc);
+    free(c); free(c_new); free(xi); free(zin); free(grad); free(res);
+}
+
+/* sum_n TV((S c)^n): the lambda_3 term of Eq. (reg-tv-l1-one), TV of every
+ * pulse image (S c)^n[j] = sum_p S[n][p][j] c_p[j]. */
+double oracle_tv_pulses(int N, int P, int Y, int X, int Z, const double* S, const double* c)
+{
+    const size_t L = (size_t)Y * X * Z;
+    double* b = (double*)malloc(sizeof(double) * L);
+    double s = 0.0;
+    for (int n = 0; n < N; ++n) {
+        for (size_t i = 0; i < L; ++i) {
+            const int j = (int)(i % (size_t)Z);
+            double v = 0.0;
+            for (int p = 0; p < P; ++p) v += S[((size_t)n * P + p) * Z + j] * c[(size_t)p * L + i];
+            b[i] = v;
+        }
+        s += oracle_tv(1, Y, X, Z, b);
+    }
+    free(b);
+    return s;
+}
+
+/* Algorithm 1 with all three terms of Eq. (reg-tv-l1-one): as oracle_fista,
+ * with the prox of alpha (R3 + delta_{>=0}) taken by oracle_prox_joint
+ * (inner dual iterations with dual step step2 and inner_momentum).  history
+ * (optional) receives F(c_{k+1}) including lam_3 sum_n TV((S c)^n). */
+void oracle_fista_joint(int N, int P, int Y, int X, int Z, int T, int k,
+                        const double* S, const double* K, const double* yv,
+                        double alpha, int iters, double lam_l1, double lam_tv, double lam_3,
+                        int inner, double step2, int momentum, int inner_momentum,
+                        double* c_out, double* history)
+{
+    size_t ny = (size_t)N * Y * X * T, nc = (size_t)P * Y * X * Z;
+    double* c = (double*)calloc(nc, sizeof(double));
+    double* c_new = (double*)malloc(sizeof(double) * nc);
+    double* xi = (double*)calloc(nc, sizeof(double));
+    double* zin = (double*)malloc(sizeof(double) * nc);
+    double* grad = (double*)malloc(sizeof(double) * nc);
+    double* res = (double*)malloc(sizeof(double) * ny);
+    double t = 1.0;
+    for (int it = 0; it < iters; ++it) {
+        oracle_forward(N, P, Y, X, Z, T, k, S, K, xi, res);
+        for (size_t i = 0; i < ny; ++i) res[i] -= yv[i];
+        oracle_adjoint(N, P, Y, X, Z, T, k, S, K, res, grad);
+        for (size_t i = 0; i < nc; ++i) zin[i] = xi[i] - alpha * grad[i];
+        oracle_prox_joint(N, P, Y, X, Z, S, zin, c_new, alpha, lam_tv, lam_l1, lam_3, inner,
+                          step2, inner_momentum, NULL);
+        double t1 = next_t(t);
+        double beta = momentum_coef(momentum, t, t1);
+        for (size_t i = 0; i < nc; ++i) {
+            xi[i] = c_new[i] + beta * (c_new[i] - c[i]);
+            c[i] = c_new[i];
+        }
+        t = t1;
+        if (history)
+            history[it] = oracle_objective(N, P, Y, X, Z, T, k, S, K, c, yv, lam_l1, lam_tv, NULL) +
+                          lam_3 * oracle_tv_pulses(N, P, Y, X, Z, S, c);
     }
     memcpy(c_out, c, sizeof(double) * nc);
     free(c); free(c_new); free(xi); free(zin); free(grad); free(res);

@@ -66,7 +66,8 @@ class _SolveParams(ctypes.Structure):
                 ("inner_momentum", ctypes.c_int), ("power_iters", ctypes.c_int),
                 ("refine_every", ctypes.c_int), ("refine_precision", ctypes.c_int),
                 ("history_host", ctypes.POINTER(ctypes.c_double)),
-                ("refine_budget", ctypes.c_double)]
+                ("refine_budget", ctypes.c_double), ("lambda_3", ctypes.c_double),
+                ("joint_step2", ctypes.c_double)]
 
 
 class _SolveStats(ctypes.Structure):
@@ -103,7 +104,7 @@ _SIGS = {
                      ctypes.POINTER(_SolveParams), ctypes.POINTER(_SolveStats), ctypes.c_void_p],
                     ctypes.c_int),
     "swopt_objective": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
-                         ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                         ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                          ctypes.POINTER(ctypes.c_double), ctypes.c_void_p], ctypes.c_int),
     "swopt_param_grad": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -134,6 +135,8 @@ _SIGS = {
     "swopt_prox_joint": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                           ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                           ctypes.c_double, ctypes.c_void_p], ctypes.c_int),
+    "swopt_prox_joint_step_bound": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double], ctypes.c_double),
     "swopt_two_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                         ctypes.c_void_p], ctypes.c_int),
@@ -224,7 +227,8 @@ class SolveParams:
 
     def __init__(self, step=0.0, lambda_l1=1e-3, lambda_tv=1e-3, inner_iters=10, max_iters=100,
                  eps1=0.0, eps2=0.0, momentum="beck_teboulle", inner_momentum="beck_teboulle",
-                 power_iters=100, refine_every=0, refine_precision="bf16x3", refine_budget=0.0):
+                 power_iters=100, refine_every=0, refine_precision="bf16x3", refine_budget=0.0,
+                 lambda_3=0.0, joint_step2=0.0):
         self.step = step
         self.lambda_l1 = lambda_l1
         self.lambda_tv = lambda_tv
@@ -238,6 +242,8 @@ class SolveParams:
         self.refine_every = refine_every
         self.refine_precision = refine_precision
         self.refine_budget = refine_budget
+        self.lambda_3 = lambda_3
+        self.joint_step2 = joint_step2
 
     def _c(self, history=None):
         p = _SolveParams()
@@ -259,6 +265,8 @@ class SolveParams:
         p.history_host = (history.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
                           if history is not None else ctypes.POINTER(ctypes.c_double)())
         p.refine_budget = float(self.refine_budget)
+        p.lambda_3 = float(self.lambda_3)
+        p.joint_step2 = float(self.joint_step2)
         return p
 
 
@@ -453,12 +461,17 @@ class Operator:
                                       int(iters), float(step2), _stream(stream)))
         return out
 
-    def objective(self, c, y, lambda_l1, lambda_tv, stream=None):
+    def prox_joint_step_bound(self, lambda_tv, lambda_l1, lambda_b):
+        """An upper bound of eig_max(L L^T) for prox_joint's stacked L."""
+        return float(lib().swopt_prox_joint_step_bound(self._h, float(lambda_tv),
+                                                       float(lambda_l1), float(lambda_b)))
+
+    def objective(self, c, y, lambda_l1, lambda_tv, lambda_3=0.0, stream=None):
         F, fit = ctypes.c_double(), ctypes.c_double()
         _check(lib().swopt_objective(self._h, _ptr(c, self.c_shape, "c"),
                                      _ptr(y, self.y_shape, "y"), float(lambda_l1),
-                                     float(lambda_tv), ctypes.byref(F), ctypes.byref(fit),
-                                     _stream(stream)))
+                                     float(lambda_tv), float(lambda_3), ctypes.byref(F),
+                                     ctypes.byref(fit), _stream(stream)))
         return F.value, fit.value
 
     def param_grad(self, c, y, stream=None):

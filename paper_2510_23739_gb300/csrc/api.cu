@@ -192,7 +192,7 @@ void release_all(swopt_handle* h)
     dfree(h->b); dfree(h->u); dfree(h->g); dfree(h->ytil); dfree(h->red); dfree(h->scal);
     dfree(h->c); dfree(h->xi); dfree(h->zin); dfree(h->tvu); dfree(h->tvr0); dfree(h->tvr1);
     dfree(h->tvx); dfree(h->coop_bar);
-    dfree(h->tmp); dfree(h->G); dfree(h->xprev); dfree(h->sched); dfree(h->rlog);
+    dfree(h->tmp); dfree(h->G); dfree(h->xprev); dfree(h->jw); dfree(h->ju); dfree(h->jr); dfree(h->sched); dfree(h->rlog);
     if (h->scal_host) cudaFreeHost(h->scal_host);
     h->scal_host = nullptr;
     for (auto& r : h->prof) {
@@ -417,7 +417,8 @@ swopt_status validate_params(const swopt_solve_params* p)
         p->inner_iters > 100000 || p->max_iters < 0 || p->momentum < 0 || p->momentum > 2 ||
         p->inner_momentum < 0 || p->inner_momentum > 2 || p->refine_every < 0 ||
         p->refine_precision < SWOPT_PREC_FP32 || p->refine_precision > SWOPT_PREC_BF16X3 ||
-        !is_fin(p->refine_budget) || p->refine_budget < 0 ||
+        !is_fin(p->refine_budget) || p->refine_budget < 0 || !is_fin(p->lambda_3) ||
+        p->lambda_3 < 0 || !is_fin(p->joint_step2) || (p->lambda_3 > 0 && p->inner_iters < 1) ||
         (p->step <= 0 && (p->power_iters < 1 || p->power_iters > 100000))) {
         set_error("invalid solve parameters");
         return SWOPT_ERR_INVALID_ARG;
@@ -489,7 +490,15 @@ swopt_status fista_iteration(swopt_handle* h, int kind, cudaStream_t st)
         SW_TRY(launch_pt(h, h->g, h->xi, alpha, h->zin, 1, st));          // P^T, gradient step
     }
     const float theta = (float)(h->step * h->prm.lambda_l1);
-    if (tv) {
+    if (h->prm.lambda_3 > 0) {
+        // the prox of all three terms of R3 with the constraint (in place on
+        // the prox input), then the momentum scalars and step
+        SW_TRY(joint_prox_on(h, h->zin, h->zin, h->step, h->prm.lambda_tv, h->prm.lambda_l1,
+                             h->prm.lambda_3, h->prm.inner_iters, h->jstep2,
+                             h->prm.inner_momentum, h->jw, h->ju, h->jr, st));
+        SW_TRY(fista_scalars(h, h->prm.momentum, st));
+        SW_TRY(fista_finish(h, h->zin, false, 0.f, refined ? h->tmp : nullptr, st));
+    } else if (tv) {
         // TV prox, momentum scalars, l1 prox and momentum step: one launch
         SW_TRY(fista_prox_finish(h, h->zin, (float)(h->step * h->prm.lambda_tv),
                                  h->prm.inner_iters, h->prm.inner_momentum, theta,
@@ -622,7 +631,7 @@ swopt_status run_iteration(swopt_handle* h, cudaStream_t st)
 
 // F(c) and the data fit on measurements y (FP64; slots SC_A..SC_D).
 swopt_status objective_impl(swopt_handle* h, const float* c, const float* y, double lam_l1,
-                            double lam_tv, double* F, double* fit, cudaStream_t st)
+                            double lam_tv, double lam_3, double* F, double* fit, cudaStream_t st)
 {
     SW_TRY(apply_A(h, c, A_OUT_U, nullptr, nullptr, 0, st));
     SW_TRY(ensure_vectors(h));
@@ -646,11 +655,19 @@ swopt_status objective_impl(swopt_handle* h, const float* c, const float* y, dou
     if (s == SWOPT_OK) s = reduce_abs(h, c, nc_of(h), SC_C, st);
     if (s == SWOPT_OK) s = reduce_tv(h, c, SC_D, st);
     if (s == SWOPT_OK) s = read_scalars(h, st);
+    const double l1 = h->scal_host[SC_C], tvc = h->scal_host[SC_D];
+    double tvs = 0.0;  // sum_n TV((S c)^n) = sum_m Cm TV(S_m c)
+    if (s == SWOPT_OK && lam_3 != 0.0) {
+        s = launch_states(h, c, h->b, st);
+        if (s == SWOPT_OK) s = reduce_tv_states(h, h->b, SC_D, st);
+        if (s == SWOPT_OK) s = read_scalars(h, st);
+        tvs = h->scal_host[SC_D];
+    }
     cudaFree(yt);
     SW_TRY(s);
     const double df = 0.5 * (ysq + cu - 2.0 * uy);
     if (fit) *fit = df;
-    if (F) *F = df + lam_l1 * h->scal_host[SC_C] + lam_tv * h->scal_host[SC_D];
+    if (F) *F = df + lam_l1 * l1 + lam_tv * tvc + lam_3 * tvs;
     return SWOPT_OK;
 }
 
@@ -937,7 +954,17 @@ swopt_status swopt_fista_init(swopt_handle* h, const float* y_dev, const swopt_s
     release_graph(h);
     SW_TRY(ensure_vectors(h));
     SW_TRY(ensure_ytil(h));
-    if (prm->lambda_tv > 0 && prm->inner_iters > 0) SW_TRY(ensure_tv_buffers(h));
+    if (prm->lambda_3 > 0) {
+        if (h->P > 8) {
+            set_error("lambda_3 > 0 supports at most 8 species");
+            return SWOPT_ERR_UNSUPPORTED;
+        }
+        SW_TRY(ensure_joint_buffers(h));
+        const double bound = joint_step_bound(h, prm->lambda_tv, prm->lambda_l1, prm->lambda_3);
+        h->jstep2 = prm->joint_step2 > 0 ? prm->joint_step2 : 1.0 / bound;
+    } else if (prm->lambda_tv > 0 && prm->inner_iters > 0) {
+        SW_TRY(ensure_tv_buffers(h));
+    }
     h->prm = *prm;
     SW_TRY(launch_fold(h, y_dev, h->ytil, st));
     SW_TRY(reduce_sumsq(h, y_dev, (size_t)h->N * h->S * h->T, SC_YSQ, st));
@@ -1033,7 +1060,7 @@ struct FistaStateHeader {
     uint64_t magic;
     int32_t version, P, Y, X, Z, N, refine_every, refined, gated;
     int32_t inner_iters, momentum, inner_momentum, refine_precision;
-    double step, lambda_l1, lambda_tv, refine_budget;
+    double step, lambda_l1, lambda_tv, refine_budget, lambda_3, joint_step2;
     int64_t iter, resyncs;
 };
 constexpr uint64_t kStateMagic = 0x5357'4F50'5446'5354ull;  // "SWOPTFST"
@@ -1072,7 +1099,7 @@ swopt_status swopt_fista_save(swopt_handle* h, void* host_buf, size_t bytes, voi
     const size_t n = nc_of(h);
     FistaStateHeader hd{};
     hd.magic = kStateMagic;
-    hd.version = 1;
+    hd.version = 2;
     hd.P = h->P; hd.Y = h->Y; hd.X = h->X; hd.Z = h->Z; hd.N = h->N;
     hd.refine_every = h->prm.refine_every;
     hd.refined = h->prm.refine_every > 0;
@@ -1085,6 +1112,8 @@ swopt_status swopt_fista_save(swopt_handle* h, void* host_buf, size_t bytes, voi
     hd.lambda_l1 = h->prm.lambda_l1;
     hd.lambda_tv = h->prm.lambda_tv;
     hd.refine_budget = h->prm.refine_budget;
+    hd.lambda_3 = h->prm.lambda_3;
+    hd.joint_step2 = h->prm.lambda_3 > 0 ? h->jstep2 : 0.0;
     hd.iter = h->iter;
     hd.resyncs = h->resyncs;
     uint8_t* p = static_cast<uint8_t*>(host_buf);
@@ -1115,14 +1144,16 @@ swopt_status swopt_fista_restore(swopt_handle* h, const void* host_buf, size_t b
     }
     FistaStateHeader hd;
     std::memcpy(&hd, host_buf, sizeof(hd));
-    if (hd.magic != kStateMagic || hd.version != 1 || hd.P != h->P || hd.Y != h->Y ||
+    if (hd.magic != kStateMagic || hd.version != 2 || hd.P != h->P || hd.Y != h->Y ||
         hd.X != h->X || hd.Z != h->Z || hd.N != h->N ||
         hd.refine_every != h->prm.refine_every || hd.gated != (iteration_kind(h) == 2) ||
         hd.inner_iters != h->prm.inner_iters || hd.momentum != h->prm.momentum ||
         hd.inner_momentum != h->prm.inner_momentum ||
         hd.refine_precision != h->prm.refine_precision || hd.lambda_l1 != h->prm.lambda_l1 ||
         hd.lambda_tv != h->prm.lambda_tv || hd.refine_budget != h->prm.refine_budget ||
-        !(hd.step > 0) || hd.iter < 0) {
+        hd.lambda_3 != h->prm.lambda_3 ||
+        hd.joint_step2 != (h->prm.lambda_3 > 0 ? h->jstep2 : 0.0) || !(hd.step > 0) ||
+        hd.iter < 0) {
         set_error("the saved FISTA state belongs to another geometry or other settings");
         return SWOPT_ERR_INVALID_ARG;
     }
@@ -1178,7 +1209,8 @@ swopt_status swopt_solve(swopt_handle* h, const float* y_dev, float* c_dev,
         if (!tests) continue;
         double F = 0.0;
         if (prm->eps1 > 0 || prm->history_host)
-            SW_TRY(objective_impl(h, h->c, y_dev, prm->lambda_l1, prm->lambda_tv, &F, nullptr, st));
+            SW_TRY(objective_impl(h, h->c, y_dev, prm->lambda_l1, prm->lambda_tv, prm->lambda_3,
+                                  &F, nullptr, st));
         if (prm->history_host) prm->history_host[it] = F;
         bool stop = false;
         if (it >= 1 && prm->eps1 > 0 && std::fabs(F - f_prev) < prm->eps1 * std::fabs(f_prev))
@@ -1203,7 +1235,8 @@ swopt_status swopt_solve(swopt_handle* h, const float* y_dev, float* c_dev,
     if (stats) {
         stats->iters = it;
         stats->step = h->step;
-        SW_TRY(objective_impl(h, h->c, y_dev, prm->lambda_l1, prm->lambda_tv, &stats->objective,
+        SW_TRY(objective_impl(h, h->c, y_dev, prm->lambda_l1, prm->lambda_tv, prm->lambda_3,
+                              &stats->objective,
                               &stats->data_fit, st));
     } else {
         SW_CUDA(cudaStreamSynchronize(st));
@@ -1265,16 +1298,17 @@ swopt_status swopt_two_step(const swopt_geometry* geom, const double* K_host,
 }
 
 swopt_status swopt_objective(swopt_handle* h, const float* c_dev, const float* y_dev,
-                             double lambda_l1, double lambda_tv, double* F, double* fit,
-                             void* stream)
+                             double lambda_l1, double lambda_tv, double lambda_3, double* F,
+                             double* fit, void* stream)
 {
     clear_error();
     SW_TRY(check_handle(h));
-    if (!c_dev || !y_dev || !is_fin(lambda_l1) || !is_fin(lambda_tv)) {
+    if (!c_dev || !y_dev || !is_fin(lambda_l1) || !is_fin(lambda_tv) || !is_fin(lambda_3)) {
         set_error("invalid objective arguments");
         return SWOPT_ERR_INVALID_ARG;
     }
-    return objective_impl(h, c_dev, y_dev, lambda_l1, lambda_tv, F, fit, (cudaStream_t)stream);
+    return objective_impl(h, c_dev, y_dev, lambda_l1, lambda_tv, lambda_3, F, fit,
+                          (cudaStream_t)stream);
 }
 
 swopt_status swopt_param_grad(swopt_handle* h, const float* c_dev, const float* y_dev,

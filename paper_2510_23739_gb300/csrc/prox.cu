@@ -692,6 +692,29 @@ __global__ void red_tv_kernel(const float* __restrict__ x, Vol v, double* parts)
     if (threadIdx.x == 0) parts[blockIdx.x] = s;
 }
 
+// sum over volumes m of w[m] TV(x_m), x = [v.P volumes][Y][X][Z]
+__global__ void red_tv_weighted_kernel(const float* __restrict__ x, Vol v,
+                                       const float* __restrict__ w, double* parts)
+{
+    __shared__ double sh[kRedThreads / 32];
+    const size_t XZ = (size_t)v.X * v.Z, V = XZ * v.Y;
+    double s = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < v.L;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i % v.Z);
+        const int xx = (int)((i / v.Z) % v.X);
+        const int y = (int)((i / XZ) % v.Y);
+        const double c = x[i];
+        double a = 0.0;
+        if (y + 1 < v.Y) a += fabs((double)x[i + XZ] - c);
+        if (xx + 1 < v.X) a += fabs((double)x[i + v.Z] - c);
+        if (j + 1 < v.Z) a += fabs((double)x[i + 1] - c);
+        s += (double)w[i / V] * a;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) parts[blockIdx.x] = s;
+}
+
 __global__ void red_final_kernel(const double* parts, int count, double* out)
 {
     __shared__ double sh[kRedThreads / 32];
@@ -1007,6 +1030,16 @@ swopt_status reduce_abs(swopt_handle* h, const float* x, size_t n, int slot, cud
 swopt_status reduce_tv(swopt_handle* h, const float* x, int slot, cudaStream_t st)
 {
     red_tv_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(x, vol_of(h), h->red);
+    SW_LAUNCHED(h);
+    return finish_reduction(h, kRedBlocks, slot, st);
+}
+
+swopt_status reduce_tv_states(swopt_handle* h, const float* b, int slot, cudaStream_t st)
+{
+    Vol v = vol_of(h);
+    v.P = h->Q;
+    v.L = nb_of(h);
+    red_tv_weighted_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(b, v, h->Cmf, h->red);
     SW_LAUNCHED(h);
     return finish_reduction(h, kRedBlocks, slot, st);
 }

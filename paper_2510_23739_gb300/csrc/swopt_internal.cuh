@@ -145,6 +145,7 @@ struct swopt_handle {
     swopt_solve_params prm{};
     double step = 0.0;
     double y_sq = 0.0;            // ||y||^2 of the bound measurements
+    double jstep2 = 0.0;          // lambda_3 > 0: dual step of the joint prox
     float* c = nullptr;           // [P][Y][X][Z] current c_k
     float* xi = nullptr;          // momentum iterate
     float* zin = nullptr;         // gradient-step output (prox input)
@@ -157,6 +158,9 @@ struct swopt_handle {
     int tile_ty = 0, tile_tx = 0; // shared-memory TV prox tile (0: not chosen, -1: none fits)
     float* tmp = nullptr;         // [P][Y][X][Z] scratch (c_{k+1} - c_k in the refined solve)
     float* G = nullptr;           // [P][Y][X][Z] refined solve: gradient at c_k
+    float* jw = nullptr;          // [P][Y][X][Z] joint prox (lambda_3): projected primal point
+    float* ju = nullptr;          // [(4 P + 3 Q) Y X Z] joint prox dual iterate
+    float* jr = nullptr;          // [(4 P + 3 Q) Y X Z] joint prox momentum iterate
     float* xprev = nullptr;       // [P][Y][X][Z] previous momentum iterate (eps2 test)
     int64_t iter = 0;             // FISTA iterations since swopt_fista_init
     int64_t resyncs = 0;          // exact gradients of the refined solve (host-scheduled)
@@ -301,6 +305,8 @@ swopt_status reduce_dot(swopt_handle* h, const float* x, const float* y, size_t 
                         cudaStream_t st);
 swopt_status reduce_abs(swopt_handle* h, const float* x, size_t n, int slot, cudaStream_t st);
 swopt_status reduce_tv(swopt_handle* h, const float* x, int slot, cudaStream_t st);
+// sum_m Cm[m] TV(b_m) of the Q state images b [Q][Y][X][Z] (= sum_n TV((S c)^n))
+swopt_status reduce_tv_states(swopt_handle* h, const float* b, int slot, cudaStream_t st);
 swopt_status reduce_partials(swopt_handle* h, const double* parts, int count, int slot,
                              cudaStream_t st);
 // Refined solve, device-side schedule: rho = ||d|| / ||c|| (FP64) is added
@@ -314,6 +320,19 @@ swopt_status scale_by_inv_sqrt(swopt_handle* h, const float* in, float* out, siz
 swopt_status fill_counter_random(swopt_handle* h, float* x, size_t n, uint64_t seed,
                                  cudaStream_t st);
 swopt_status param_weights(swopt_handle* h, const float* g, const float* c, int slot0,
+                           cudaStream_t st);
+
+// The joint prox of R3 with its lambda_3 term (prox_joint.cu): Algorithm 2 on
+// the stacked operator with one dual per switching state, z and x may alias;
+// scratch w [P L], u and r [joint_dual_floats] (ensure_joint_buffers gives the
+// handle's).  joint_step_bound: an upper bound of eig_max(L L^T).
+size_t joint_dual_floats(const swopt_handle* h);
+double joint_step_bound(const swopt_handle* h, double lambda_tv, double lambda_l1,
+                        double lambda_b);
+swopt_status ensure_joint_buffers(swopt_handle* h);
+swopt_status joint_prox_on(swopt_handle* h, const float* z, float* x, double alpha,
+                           double lambda_tv, double lambda_l1, double lambda_b, int iters,
+                           double step2, int momentum, float* w, float* u, float* r,
                            cudaStream_t st);
 
 // Handle-free launchers of one FGP iteration / the primal recovery on

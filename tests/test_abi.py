@@ -16,7 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     text = open(os.path.join(ROOT, "include", "swopt.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|swopt_status)\s+(swopt_\w+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|swopt_status|double)\s+(swopt_\w+)\s*\(",
                                  text, re.M)))
 
 
@@ -98,6 +98,7 @@ def test_null_handle_calls_fail_cleanly():
     assert L.swopt_tc_schedule_info(None, 0, *[ctypes.byref(i)] * 4) == 1
     assert L.swopt_two_step(None, None, None, None, None, None, None, None, None) == 1
     assert L.swopt_prox_joint(None, None, None, 1.0, 0.1, 0.1, 0.1, 1, 0.1, None) == 1
+    assert L.swopt_prox_joint_step_bound(None, 0.1, 0.1, 0.1) == 0.0
     assert b"null" in L.swopt_last_error()
     assert L.swopt_version().decode().count(".") == 2
 

@@ -702,30 +702,94 @@ def test_two_step_matches_oracle():
     assert rel(host(c), c_or) <= 1e-4
 
 
-@pytest.mark.parametrize("lams", [(0.3, 0.1, 0.2), (0.0, 0.0, 0.4), (0.25, 0.15, 0.0)])
-def test_prox_joint_matches_oracle(lams):
+def _joint_step2(g, s, lam_tv, lam_l1, lam_b):
+    """1 / a bound of eig_max(L L^T): 12 lam_tv^2 + lam_l1^2 + 12 lam_b^2 sum_n
+    max_j sum_p S[n][p][j]^2 (the oracle's S)."""
+    S = oracle.switch_matrix(g, s)
+    return 1.0 / (12 * lam_tv ** 2 + lam_l1 ** 2 +
+                  12 * lam_b ** 2 * float(np.sum(np.max(np.sum(S ** 2, axis=1), axis=1))))
+
+
+@pytest.mark.parametrize("lams,shift,inplace", [((0.3, 0.1, 0.2), 0.5, False),
+                                                ((0.0, 0.0, 0.4), 0.5, False),
+                                                ((0.25, 0.15, 0.0), 0.5, False),
+                                                ((0.2, 0.05, 0.5), -0.2, False),
+                                                ((0.2, 0.05, 0.5), -0.2, True)])
+def test_prox_joint_matches_oracle(lams, shift, inplace):
     """The prox of the full R3 with its lambda_3 term (TV of every pulse
-    image), Algorithm 2 on the stacked L with a fixed iteration count, against
-    the oracle's iterates (pulses fold onto 3 switching states; some outputs
-    clip at zero)."""
+    image) and the nonnegativity constraint, Algorithm 2 on the constrained
+    dual with a fixed iteration count, against the oracle's iterates: pulses
+    fold onto 3 switching states on the GPU (one dual per state) and keep one
+    dual each in the oracle; outputs clip at zero (many of them with the
+    negative shift); in place (x = z) gives the same result."""
     g = Geometry(X=7, Y=5, Z=6, T=8, N=5, P=2, k=3, pulses_per_cycle=3)
     s = Switching((0.2, 0.0), (1.0, 0.0), (0.05, 1.0), 3.0)
     K = np.random.default_rng(60).standard_normal(g.k_shape())
     lam_tv, lam_l1, lam_b = lams
-    S = oracle.switch_matrix(g, s)
-    bound = 12 * lam_tv ** 2 + lam_l1 ** 2 + 12 * lam_b ** 2 * g.N * max(
-        np.linalg.norm(S[:, :, j], 2) ** 2 for j in range(g.Z))
-    step2 = 1.0 / bound
-    z = np.random.default_rng(61).standard_normal(g.c_shape()) + 0.5
+    step2 = _joint_step2(g, s, lam_tv, lam_l1, lam_b)
+    z = np.random.default_rng(61).standard_normal(g.c_shape()) + shift
     op = sw.Operator(g, K, s)
     try:
-        got = host(op.prox_joint(dev(z), 0.6, lam_tv, lam_l1, lam_b, 40, step2))
+        assert op.prox_joint_step_bound(lam_tv, lam_l1, lam_b) == pytest.approx(1 / step2,
+                                                                                 rel=1e-12)
+        zt = dev(z)
+        got = op.prox_joint(zt, 0.6, lam_tv, lam_l1, lam_b, 40, step2,
+                            out=zt if inplace else None)
+        if inplace:
+            assert got.data_ptr() == zt.data_ptr()
+        got = host(got)
         op.check_device()
     finally:
         op.close()
     want = oracle.prox_joint(g, s, z, 0.6, lam_tv, lam_l1, lam_b, 40, step2)
     assert (want == 0).any() and (want > 0).any()
+    if shift < 0:
+        assert (want == 0).mean() > 0.3
     assert rel(got, want) <= 1e-5
+
+
+@pytest.mark.parametrize("mode", ["fp32", "refined_bf16"])
+def test_fista_with_lambda3_matches_oracle(cases, mode):
+    """Algorithm 1 with all three terms of R3 on the tiny workload: 20
+    iterations, lambda_3 = 2e-3 with the workload's other weights, the joint
+    prox with the workload's inner iteration count, the same alpha and dual
+    step on both sides; FP32, and the refined BF16 schedule."""
+    g, s, K, _ = cases["tiny"]
+    y = _tiny_measurements(g, s, K)
+    L = oracle.power(g, s, K, synth.gaussian(g.c_shape(), 1), 100)
+    alpha = 1.0 / L
+    lam_3 = 2e-3
+    step2 = _joint_step2(g, s, TINY.lam_tv, TINY.lam_l1, lam_3)
+    extra = sw.REFINED_DEFAULTS if mode == "refined_bf16" else {}
+    op = sw.Operator(g, K, s, precision="bf16" if mode == "refined_bf16" else "fp32")
+    try:
+        params = sw.SolveParams(step=alpha, lambda_l1=TINY.lam_l1, lambda_tv=TINY.lam_tv,
+                                inner_iters=TINY.inner, max_iters=TINY.iters, lambda_3=lam_3,
+                                joint_step2=step2, **extra)
+        got, stats = op.solve(dev(y), params)
+        op.check_device()
+    finally:
+        op.close()
+    ref = oracle.fista(g, s, K, y, alpha, TINY.iters, TINY.lam_l1, TINY.lam_tv, TINY.inner,
+                       lam_3=lam_3, joint_step2=step2)
+    assert stats["iters"] == TINY.iters
+    assert rel(host(got), ref) <= 1e-4
+    F_ref, _ = oracle.objective(g, s, K, ref, y, TINY.lam_l1, TINY.lam_tv, lam_3)
+    assert stats["objective"] == pytest.approx(F_ref, rel=1e-4)
+    # the lambda_3 term matters at this weight
+    plain = oracle.fista(g, s, K, y, alpha, TINY.iters, TINY.lam_l1, TINY.lam_tv, TINY.inner)
+    assert rel(plain, ref) > 1e-3
+
+
+def test_objective_with_lambda3_matches_oracle(cases):
+    g, s, K, op = cases["tiny"]
+    rng = np.random.default_rng(62)
+    c = np.maximum(rng.standard_normal(g.c_shape()), 0)
+    y = rng.standard_normal(g.y_shape())
+    F, fit = op.objective(dev(c), dev(y), 0.05, 0.07, 0.09)
+    F_ref, fit_ref = oracle.objective(g, s, K, c, y, 0.05, 0.07, 0.09)
+    assert F == pytest.approx(F_ref, rel=1e-5)
+    assert fit == pytest.approx(fit_ref, rel=1e-5)
 
 
 def test_tensor_core_accumulators_option(tc_cases):

@@ -755,6 +755,41 @@ def test_joint_prox_matches_the_dual_solution(lams):
     np.testing.assert_allclose(got.ravel(), want, atol=1e-5)
 
 
+def _constrained_dual_prox(Lmat, z, alpha):
+    """argmin over x >= 0 of 1/2||x - z||^2 + alpha ||L x||_1 through its dual:
+    for fixed u the inner minimum over x >= 0 is at x = max(z - L^T u, 0), and
+    the dual is min over |u| <= alpha of 1/2 ||max(z - L^T u, 0)||^2 (gradient
+    -L max(z - L^T u, 0)), solved by scipy's L-BFGS-B."""
+    def fun(u):
+        w = np.maximum(z - Lmat.T @ u, 0.0)
+        return 0.5 * w @ w, -(Lmat @ w)
+    res = scipy.optimize.minimize(fun, np.zeros(Lmat.shape[0]), jac=True, method="L-BFGS-B",
+                                  bounds=[(-alpha, alpha)] * Lmat.shape[0],
+                                  options={"maxiter": 50000, "ftol": 1e-16, "gtol": 1e-13})
+    return np.maximum(z - Lmat.T @ res.x, 0.0)
+
+
+def test_joint_prox_with_an_active_clip_is_the_constrained_prox():
+    """Inputs with negative parts, the lambda_3 term coupling the species:
+    the joint prox is the prox of R3 plus the nonnegativity indicator (Eq.
+    prox), checked against its constrained dual solved by L-BFGS-B, and it
+    differs from clipping the unconstrained prox (which the printed form of
+    Algorithm 2 would give) by far more than the solvers' tolerance."""
+    g, sw = _joint_case()
+    lam_tv, lam_l1, lam_b = 0.2, 0.05, 0.5
+    rng = np.random.default_rng(34)
+    z = rng.standard_normal(g.c_shape()) * 1.5 - 0.2
+    alpha = 0.7
+    Lmat = _stacked_L(g, sw, lam_tv, lam_l1, lam_b)
+    want = _constrained_dual_prox(Lmat, z.ravel(), alpha)
+    assert (want == 0).sum() > 3  # the constraint is active
+    step2 = 1.0 / np.linalg.norm(Lmat, 2) ** 2
+    got = oracle.prox_joint(g, sw, z, alpha, lam_tv, lam_l1, lam_b, 40000, step2)
+    np.testing.assert_allclose(got.ravel(), want, atol=1e-5)
+    clipped = np.maximum(_box_dual_prox(Lmat, z.ravel(), alpha), 0.0)
+    assert np.abs(clipped - want).max() > 1e-2
+
+
 def test_joint_prox_without_lambda3_is_the_composite_prox():
     """With lambda_3 = 0 the joint dual gives max(prox_TV(z) - alpha lambda_l1, 0),
     the composition the solver uses (reading O8)."""
@@ -832,3 +867,61 @@ def test_unrolled_solve_tangent_matches_central_differences(which):
     fd = (at(h) - at(-h)) / (2 * h)
     assert 0 < (c > 0).mean() < 1 and np.abs(dc).max() > 1e-2   # some outputs clipped, some not
     assert np.linalg.norm(dc - fd) <= 1e-5 * np.linalg.norm(fd)
+
+
+def test_pulse_image_tv_is_the_dense_sum():
+    """sum_n TV((S c)^n) against ||D S_n c||_1 with explicit matrices, and
+    N TV(c) when every pulse image is c itself."""
+    g, sw = _joint_case(N=4, P=2)
+    rng = np.random.default_rng(35)
+    c = rng.standard_normal(g.c_shape())
+    D = _diff_matrix(g.Y, g.X, g.Z)
+    S = oracle.switch_matrix(g, sw)
+    depth = np.tile(np.arange(g.Z), g.Y * g.X)
+    want = 0.0
+    for n in range(g.N):
+        Sn = np.concatenate([np.diag(S[n, p, depth]) for p in range(g.P)], axis=1)
+        want += np.abs(D @ Sn @ c.ravel()).sum()
+    assert oracle.tv_pulses(g, sw, c) == pytest.approx(want, rel=1e-13)
+    g1 = _geom(X=3, Y=2, Z=4, T=4, N=3, P=1, k=1, pulses_per_cycle=3)
+    sw1 = Switching(kappa=(0.0,), eps_bar=(0.0,), eps_off=(1.0,), mu_per_mm=0.0)
+    c1 = rng.standard_normal(g1.c_shape())
+    assert oracle.tv_pulses(g1, sw1, c1) == pytest.approx(g1.N * oracle.tv(c1), rel=1e-13)
+    F0, _ = oracle.objective(g1, sw1, np.ones(g1.k_shape()), c1, np.zeros(g1.y_shape()), 0, 0)
+    F3, _ = oracle.objective(g1, sw1, np.ones(g1.k_shape()), c1, np.zeros(g1.y_shape()), 0, 0,
+                             lam_3=0.3)
+    assert F3 - F0 == pytest.approx(0.3 * g1.N * oracle.tv(c1), rel=1e-12)
+
+
+def test_fista_with_lambda3_reaches_a_fixed_point_of_the_exact_prox_gradient_map():
+    """Algorithm 1 with all three terms of R3: after enough iterations c is a
+    fixed point of c -> prox(c - alpha H^T (H c - y)), the prox computed from
+    its constrained dual by L-BFGS-B with the explicit H and L matrices, and
+    no feasible perturbation lowers F (with the lambda_3 term)."""
+    g, sw, K, y = _small_problem()
+    H = _dense_H(g, sw, K)
+    lam_l1, lam_tv, lam_3 = 0.02, 0.03, 0.04
+    alpha = 1.0 / np.linalg.eigvalsh(H.T @ H)[-1]
+    Lmat = _stacked_L(g, sw, lam_tv, lam_l1, lam_3)
+    step2 = 1.0 / np.linalg.norm(Lmat, 2) ** 2
+    c, hist = oracle.fista(g, sw, K, y, alpha, 1500, lam_l1, lam_tv, 300, lam_3=lam_3,
+                           joint_step2=step2, history=True)
+    cf = c.ravel()
+    zf = cf - alpha * (H.T @ (H @ cf - y.ravel()))
+    fixed = _constrained_dual_prox(Lmat, zf, alpha)
+    assert np.linalg.norm(fixed - cf) <= 1e-5 * np.linalg.norm(cf)
+
+    def F(v):
+        r = H @ v - y.ravel()
+        return 0.5 * r @ r + np.abs(Lmat @ v).sum()
+
+    assert F(cf) == pytest.approx(hist[-1], rel=1e-12)
+    assert hist[-1] == pytest.approx(oracle.objective(g, sw, K, c, y, lam_l1, lam_tv, lam_3)[0],
+                                     rel=1e-12)
+    rng = np.random.default_rng(36)
+    for _ in range(50):
+        d = 1e-3 * rng.standard_normal(cf.size)
+        assert F(np.maximum(cf + d, 0.0)) >= F(cf) - 1e-10
+    # the lambda_3 term changes the solution
+    c0 = oracle.fista(g, sw, K, y, alpha, 300, lam_l1, lam_tv, 300)
+    assert np.linalg.norm(c0 - c) > 1e-3 * np.linalg.norm(c)
