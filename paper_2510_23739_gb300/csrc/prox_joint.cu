@@ -20,7 +20,15 @@
 //
 // Two voxel-parallel kernels per iteration (memory-bound stencils): L^T of
 // the momentum iterate with the projection, then L of the result with the
-// clamp and the momentum step fused.  Scratch (w, u, r) is the handle's.
+// clamp and the momentum step fused, the second split over a grid dimension
+// into the species entries and groups of kStateChunk switching states.  Per
+// dual iteration they move (nd + 2 P) + (4 nd + P) volumes, nd = 4 P + 3 Q.
+// Both are templated on P so that the per-species values stay in registers,
+// and issue the loads of a group of states before their arithmetic (a thread
+// keeps several loads in flight; measured on GB300 at 128 x 128 x 96, P = 3,
+// Q = 10: 0.26 of the HBM copy rate one state at a time, 0.78 like this).
+// The first iteration reads no dual (r = u = 0).  Scratch (w, u, r) is the
+// handle's.
 #include <cmath>
 
 #include "swopt_internal.cuh"
@@ -30,6 +38,7 @@ namespace {
 
 constexpr int kJointBlock = 256;
 constexpr int kJointMaxSpecies = 8;
+constexpr int kStateChunk = 4;  // switching states whose loads are issued together
 
 struct JointArgs {
     int P, Q, Y, X, Z;
@@ -38,126 +47,231 @@ struct JointArgs {
     float lam_tv, lam_l1, lam_b;
 };
 
-// (D^T g)[i] for one field g[3][Y][X][Z] (components y, x, z)
-__device__ __forceinline__ float transpose_diff(const float* g, size_t L, size_t i, int y, int x,
-                                                int j, int Y, int X, int Z)
+// Voxel i = (y X + x) Z + j of a volume with fewer than 2^31 voxels.
+struct Vox {
+    int y, x, j;
+    __device__ __forceinline__ Vox(unsigned i, const JointArgs& a)
+    {
+        const unsigned t = i / (unsigned)a.Z;
+        j = (int)(i - t * (unsigned)a.Z);
+        y = (int)(t / (unsigned)a.X);
+        x = (int)(t - (unsigned)y * (unsigned)a.X);
+    }
+};
+
+// The six terms of (D^T g)[i] for one field g[3][L] (components y, x, z),
+// 0 where the difference does not exist; D^T g = v1 - v0 + v3 - v2 + v5 - v4.
+__device__ __forceinline__ void load_dt(const float* g, size_t L, size_t i, size_t sy, size_t sx,
+                                        const Vox& p, const JointArgs& a, float (&v)[6])
 {
-    const size_t sy = (size_t)X * Z, sx = (size_t)Z;
-    float acc = 0.f;
-    if (y + 1 < Y) acc -= g[i];
-    if (y > 0) acc += g[i - sy];
-    if (x + 1 < X) acc -= g[L + i];
-    if (x > 0) acc += g[L + i - sx];
-    if (j + 1 < Z) acc -= g[2 * L + i];
-    if (j > 0) acc += g[2 * L + i - 1];
-    return acc;
+    v[0] = p.y + 1 < a.Y ? g[i] : 0.f;
+    v[1] = p.y > 0 ? g[i - sy] : 0.f;
+    v[2] = p.x + 1 < a.X ? g[L + i] : 0.f;
+    v[3] = p.x > 0 ? g[L + i - sx] : 0.f;
+    v[4] = p.j + 1 < a.Z ? g[2 * L + i] : 0.f;
+    v[5] = p.j > 0 ? g[2 * L + i - 1] : 0.f;
 }
 
-// out = max(z - L^T r, 0), one thread per voxel, all species.  z and out may
-// be the same array: each thread reads z at its voxel before writing there.
-__global__ void joint_lt_kernel(const JointArgs a, const float* z, const float* __restrict__ r,
-                                float* out)
+__device__ __forceinline__ float dt_value(const float (&v)[6])
 {
-    const size_t L = (size_t)a.Y * a.X * a.Z;
-    const float* rc = r;
-    const float* rl = r + (size_t)a.P * 3 * L;
-    const float* rb = rl + (size_t)a.P * L;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < L;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(i % (size_t)a.Z);
-        const int x = (int)((i / (size_t)a.Z) % (size_t)a.X);
-        const int y = (int)(i / ((size_t)a.Z * a.X));
-        float acc[kJointMaxSpecies];
+    return ((v[1] - v[0]) + (v[3] - v[2])) + (v[5] - v[4]);
+}
+
+// out = max(z - L^T r, 0), one thread per voxel, all NP species (r null:
+// r = 0).  z and out may be the same array: each thread reads z at its voxel
+// before writing there.  The loads of kStateChunk states are issued before
+// their arithmetic, so that a thread keeps several of them in flight.
+template <int NP>
+__global__ void __launch_bounds__(kJointBlock, NP <= 4 ? 4 : 3)
+    joint_lt_kernel(const JointArgs a, const float* z, const float* __restrict__ r, float* out)
+{
+    const unsigned L = (unsigned)a.Y * a.X * a.Z;
+    const size_t Ls = L, sy = (size_t)a.X * a.Z, sx = (size_t)a.Z;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) {
+        const Vox q(i, a);
+        float acc[NP];
 #pragma unroll
-        for (int p = 0; p < kJointMaxSpecies; ++p) {
-            if (p >= a.P) break;
-            acc[p] = a.lam_tv * transpose_diff(rc + (size_t)p * 3 * L, L, i, y, x, j, a.Y, a.X, a.Z) +
-                     a.lam_l1 * rl[(size_t)p * L + i];
-        }
-        for (int m = 0; m < a.Q; ++m) {
-            const float d = a.Cmf[m] * a.lam_b *
-                            transpose_diff(rb + (size_t)m * 3 * L, L, i, y, x, j, a.Y, a.X, a.Z);
-            const float* s = a.Sm + (size_t)m * a.P * a.Z + j;
+        for (int p = 0; p < NP; ++p) acc[p] = 0.f;
+        if (r) {
+            const float* rl = r + (size_t)NP * 3 * Ls;
+            const float* rb = rl + (size_t)NP * Ls;
 #pragma unroll
-            for (int p = 0; p < kJointMaxSpecies; ++p) {
-                if (p >= a.P) break;
-                acc[p] = fmaf(s[(size_t)p * a.Z], d, acc[p]);
+            for (int p = 0; p < NP; ++p) {
+                float v[6];
+                load_dt(r + (size_t)p * 3 * Ls, Ls, i, sy, sx, q, a, v);
+                acc[p] = a.lam_tv * dt_value(v) + a.lam_l1 * rl[(size_t)p * Ls + i];
+            }
+            for (int m0 = 0; m0 < a.Q; m0 += kStateChunk) {
+                float v[kStateChunk][6];
+#pragma unroll
+                for (int c = 0; c < kStateChunk; ++c) {
+                    if (m0 + c < a.Q) {
+                        load_dt(rb + (size_t)(m0 + c) * 3 * Ls, Ls, i, sy, sx, q, a, v[c]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 6; ++e) v[c][e] = 0.f;
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < kStateChunk; ++c) {
+                    const int m = m0 + c;
+                    if (m < a.Q) {
+                        const float d = a.Cmf[m] * a.lam_b * dt_value(v[c]);
+                        const float* s = a.Sm + (size_t)m * NP * a.Z + q.j;
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) acc[p] = fmaf(s[(size_t)p * a.Z], d, acc[p]);
+                    }
+                }
             }
         }
-        float v[kJointMaxSpecies];
+        float v[NP];
 #pragma unroll
-        for (int p = 0; p < kJointMaxSpecies; ++p) {
-            if (p >= a.P) break;
-            v[p] = fmaxf(z[(size_t)p * L + i] - acc[p], 0.f);
-        }
+        for (int p = 0; p < NP; ++p) v[p] = fmaxf(z[(size_t)p * Ls + i] - acc[p], 0.f);
 #pragma unroll
-        for (int p = 0; p < kJointMaxSpecies; ++p) {
-            if (p >= a.P) break;
-            out[(size_t)p * L + i] = v[p];
-        }
+        for (int p = 0; p < NP; ++p) out[(size_t)p * Ls + i] = v[p];
     }
 }
 
-// u_new = clamp(r + step2 (L w)_e, -alpha, alpha); r = u_new + beta (u_new - u); u = u_new
-__device__ __forceinline__ void dual_step(float* r, float* u, size_t e, float lw, float step2,
-                                          float alpha, float beta)
+// u_new = clamp(r + step2 lw, -alpha, alpha); r_new = u_new + beta (u_new - u)
+__device__ __forceinline__ void dual_update(float& rv, float& uv, float lw, float step2,
+                                            float alpha, float beta)
 {
-    float v = fmaf(step2, lw, r[e]);
+    float v = fmaf(step2, lw, rv);
     v = fminf(fmaxf(v, -alpha), alpha);
-    r[e] = fmaf(beta, v - u[e], v);
-    u[e] = v;
+    rv = fmaf(beta, v - uv, v);
+    uv = v;
 }
 
-// the dual update for every entry of voxel i, one thread per voxel
-__global__ void joint_dual_kernel(const JointArgs a, const float* __restrict__ w,
-                                  float* __restrict__ r, float* __restrict__ u, float step2,
-                                  float alpha, float beta)
+// The dual update, one thread per voxel and entry group: blockIdx.y = 0 takes
+// the species entries (3 TV components and the l1 entry of each species),
+// blockIdx.y = g >= 1 the pulse-image TV entries of the switching states
+// [(g - 1) kStateChunk, g kStateChunk).  first: the previous r and u are
+// zero and are not read.
+template <int NP>
+__global__ void __launch_bounds__(kJointBlock, NP <= 4 ? 4 : 3)
+    joint_dual_kernel(const JointArgs a, const float* __restrict__ w, float* __restrict__ r,
+                      float* __restrict__ u, float step2, float alpha, float beta, int first)
 {
-    const size_t L = (size_t)a.Y * a.X * a.Z;
-    const size_t sy = (size_t)a.X * a.Z, sx = (size_t)a.Z;
-    const size_t ol = (size_t)a.P * 3 * L, ob = ol + (size_t)a.P * L;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < L;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(i % (size_t)a.Z);
-        const int x = (int)((i / (size_t)a.Z) % (size_t)a.X);
-        const int y = (int)(i / ((size_t)a.Z * a.X));
-        const bool hy = y + 1 < a.Y, hx = x + 1 < a.X, hz = j + 1 < a.Z;
+    const unsigned L = (unsigned)a.Y * a.X * a.Z;
+    const size_t Ls = L, sy = (size_t)a.X * a.Z, sx = (size_t)a.Z;
+    const size_t ol = (size_t)NP * 3 * Ls, ob = ol + (size_t)NP * Ls;
+    const int group = blockIdx.y;
+    const int m0 = (group - 1) * kStateChunk;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) {
+        const Vox q(i, a);
+        const bool hy = q.y + 1 < a.Y, hx = q.x + 1 < a.X, hz = q.j + 1 < a.Z;
         // w at the voxel and its three forward neighbours (0 past the far faces)
-        float w0[kJointMaxSpecies], wy[kJointMaxSpecies], wx[kJointMaxSpecies],
-            wz[kJointMaxSpecies];
+        float w0[NP], wy[NP], wx[NP], wz[NP];
 #pragma unroll
-        for (int p = 0; p < kJointMaxSpecies; ++p) {
-            if (p >= a.P) break;
-            const float* wp = w + (size_t)p * L;
+        for (int p = 0; p < NP; ++p) {
+            const float* wp = w + (size_t)p * Ls;
             w0[p] = wp[i];
             wy[p] = hy ? wp[i + sy] : 0.f;
             wx[p] = hx ? wp[i + sx] : 0.f;
             wz[p] = hz ? wp[i + 1] : 0.f;
-            const size_t e = (size_t)p * 3 * L + i;
-            dual_step(r, u, e, hy ? a.lam_tv * (wy[p] - w0[p]) : 0.f, step2, alpha, beta);
-            dual_step(r, u, e + L, hx ? a.lam_tv * (wx[p] - w0[p]) : 0.f, step2, alpha, beta);
-            dual_step(r, u, e + 2 * L, hz ? a.lam_tv * (wz[p] - w0[p]) : 0.f, step2, alpha,
-                      beta);
-            dual_step(r, u, ol + (size_t)p * L + i, a.lam_l1 * w0[p], step2, alpha, beta);
         }
-        for (int m = 0; m < a.Q; ++m) {
-            const float* s = a.Sm + (size_t)m * a.P * a.Z;
-            float b0 = 0.f, by = 0.f, bx = 0.f, bz = 0.f;
+        if (group == 0) {
 #pragma unroll
-            for (int p = 0; p < kJointMaxSpecies; ++p) {
-                if (p >= a.P) break;
-                const float sj = s[(size_t)p * a.Z + j];
-                b0 = fmaf(sj, w0[p], b0);
-                by = fmaf(sj, wy[p], by);
-                bx = fmaf(sj, wx[p], bx);
-                if (hz) bz = fmaf(s[(size_t)p * a.Z + j + 1], wz[p], bz);
+            for (int p = 0; p < NP; ++p) {
+                const size_t e[4] = {(size_t)p * 3 * Ls + i, (size_t)p * 3 * Ls + Ls + i,
+                                     (size_t)p * 3 * Ls + 2 * Ls + i, ol + (size_t)p * Ls + i};
+                float rv[4], uv[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    rv[c] = first ? 0.f : r[e[c]];
+                    uv[c] = first ? 0.f : u[e[c]];
+                }
+                const float lw[4] = {hy ? a.lam_tv * (wy[p] - w0[p]) : 0.f,
+                                     hx ? a.lam_tv * (wx[p] - w0[p]) : 0.f,
+                                     hz ? a.lam_tv * (wz[p] - w0[p]) : 0.f, a.lam_l1 * w0[p]};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    dual_update(rv[c], uv[c], lw[c], step2, alpha, beta);
+                    r[e[c]] = rv[c];
+                    u[e[c]] = uv[c];
+                }
             }
-            const size_t e = ob + (size_t)m * 3 * L + i;
-            dual_step(r, u, e, hy ? a.lam_b * (by - b0) : 0.f, step2, alpha, beta);
-            dual_step(r, u, e + L, hx ? a.lam_b * (bx - b0) : 0.f, step2, alpha, beta);
-            dual_step(r, u, e + 2 * L, hz ? a.lam_b * (bz - b0) : 0.f, step2, alpha, beta);
+            continue;
+        }
+        float rv[kStateChunk][3], uv[kStateChunk][3];
+#pragma unroll
+        for (int c = 0; c < kStateChunk; ++c) {
+            const size_t e = ob + (size_t)(m0 + c) * 3 * Ls + i;
+            const bool ld = !first && m0 + c < a.Q;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                rv[c][k] = ld ? r[e + k * Ls] : 0.f;
+                uv[c][k] = ld ? u[e + k * Ls] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kStateChunk; ++c) {
+            const int m = m0 + c;
+            if (m < a.Q) {
+                const float* s = a.Sm + (size_t)m * NP * a.Z;
+                float b0 = 0.f, by = 0.f, bx = 0.f, bz = 0.f;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const float sj = s[(size_t)p * a.Z + q.j];
+                    b0 = fmaf(sj, w0[p], b0);
+                    by = fmaf(sj, wy[p], by);
+                    bx = fmaf(sj, wx[p], bx);
+                    if (hz) bz = fmaf(s[(size_t)p * a.Z + q.j + 1], wz[p], bz);
+                }
+                const float lw[3] = {hy ? a.lam_b * (by - b0) : 0.f,
+                                     hx ? a.lam_b * (bx - b0) : 0.f,
+                                     hz ? a.lam_b * (bz - b0) : 0.f};
+                const size_t e = ob + (size_t)m * 3 * Ls + i;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    dual_update(rv[c][k], uv[c][k], lw[k], step2, alpha, beta);
+                    r[e + k * Ls] = rv[c][k];
+                    u[e + k * Ls] = uv[c][k];
+                }
+            }
         }
     }
+}
+
+template <int NP>
+swopt_status launch_joint_iteration(swopt_handle* h, const JointArgs& a, const float* z,
+                                    const float* rin, float* out, float* w, float* r, float* u,
+                                    float step2, float alpha, float beta, int first, bool dual,
+                                    int grid, cudaStream_t st)
+{
+    joint_lt_kernel<NP><<<grid, kJointBlock, 0, st>>>(a, z, rin, dual ? w : out);
+    SW_LAUNCHED(h);
+    if (!dual) return SWOPT_OK;
+    const dim3 g2(grid, 1 + (a.Q + kStateChunk - 1) / kStateChunk);
+    joint_dual_kernel<NP><<<g2, kJointBlock, 0, st>>>(a, w, r, u, step2, alpha, beta, first);
+    SW_LAUNCHED(h);
+    return SWOPT_OK;
+}
+
+// One dual iteration (dual = true: L^T of rin into w, then the dual update)
+// or the primal recovery (dual = false: out = max(z - L^T rin, 0)).
+swopt_status joint_iteration(swopt_handle* h, const JointArgs& a, const float* z,
+                             const float* rin, float* out, float* w, float* r, float* u,
+                             float step2, float alpha, float beta, int first, bool dual, int grid,
+                             cudaStream_t st)
+{
+    switch (a.P) {
+#define SWOPT_JOINT_CASE(n)                                                                   \
+    case n:                                                                                   \
+        return launch_joint_iteration<n>(h, a, z, rin, out, w, r, u, step2, alpha, beta, first, \
+                                         dual, grid, st);
+        SWOPT_JOINT_CASE(1)
+        SWOPT_JOINT_CASE(2)
+        SWOPT_JOINT_CASE(3)
+        SWOPT_JOINT_CASE(4)
+        SWOPT_JOINT_CASE(5)
+        SWOPT_JOINT_CASE(6)
+        SWOPT_JOINT_CASE(7)
+        SWOPT_JOINT_CASE(8)
+#undef SWOPT_JOINT_CASE
+    }
+    set_error("the joint prox supports 1 to %d species", kJointMaxSpecies);
+    return SWOPT_ERR_UNSUPPORTED;
 }
 
 }  // namespace
@@ -201,7 +315,10 @@ swopt_status joint_prox_on(swopt_handle* h, const float* z, float* x, double alp
         return SWOPT_ERR_UNSUPPORTED;
     }
     const size_t L = (size_t)h->Y * h->X * h->Z;
-    const size_t nu = joint_dual_floats(h);
+    if (L >= (1ull << 31)) {
+        set_error("the joint prox supports volumes below 2^31 voxels");
+        return SWOPT_ERR_UNSUPPORTED;
+    }
     JointArgs a;
     a.P = h->P;
     a.Q = h->Q;
@@ -216,24 +333,19 @@ swopt_status joint_prox_on(swopt_handle* h, const float* z, float* x, double alp
     int sms = 0;
     SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     const int grid = (int)std::min<size_t>((size_t)grid_for(L, kJointBlock), (size_t)sms * 16);
-    SW_CUDA(cudaMemsetAsync(u, 0, sizeof(float) * nu, st));
-    SW_CUDA(cudaMemsetAsync(r, 0, sizeof(float) * nu, st));
+    // the first iteration starts from r = u = 0 without reading them
     double t = 1.0;
     for (int it = 0; it < iters; ++it) {
         const double t1 = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
         const double b = momentum == SWOPT_MOMENTUM_BECK_TEBOULLE ? (t - 1.0) / t1
                          : momentum == SWOPT_MOMENTUM_PAPER_PRINTED ? (t - 1.0) / (t + 1.0)
                                                                     : 0.0;
-        const float beta = (float)b;
         t = t1;
-        joint_lt_kernel<<<grid, kJointBlock, 0, st>>>(a, z, r, w);
-        SW_LAUNCHED(h);
-        joint_dual_kernel<<<grid, kJointBlock, 0, st>>>(a, w, r, u, (float)step2, (float)alpha,
-                                                        beta);
-        SW_LAUNCHED(h);
+        SW_TRY(joint_iteration(h, a, z, it == 0 ? nullptr : r, nullptr, w, r, u, (float)step2,
+                               (float)alpha, (float)b, it == 0 ? 1 : 0, true, grid, st));
     }
-    joint_lt_kernel<<<grid, kJointBlock, 0, st>>>(a, z, u, x);
-    SW_LAUNCHED(h);
+    SW_TRY(joint_iteration(h, a, z, iters > 0 ? u : nullptr, x, w, r, u, 0.f, 0.f, 0.f, 0,
+                           false, grid, st));
     return SWOPT_OK;
 }
 
