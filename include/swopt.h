@@ -268,6 +268,42 @@ swopt_status swopt_fista_restore(swopt_handle* h, const void* host_buf, size_t b
  * the defaults.  Synchronises. */
 swopt_status swopt_debug_barrier(swopt_handle* h, int phantom_arrivals, unsigned poll_limit);
 
+/* Sharding over switching states (pulses of one state together: the
+ * measurement operator is block diagonal over pulses, Eq.
+ * (acoustic-full-forward), and Eq. (final-H) makes pulses of one state share
+ * their images).  A shard is a handle whose pulses are those of the states
+ * [m0, m1) of the whole train, in cycle-major order (pulses_per_cycle =
+ * m1 - m0, N = their count), with swopt_set_state_offset(h, m0) so that its
+ * local state q is pulse-in-cycle m0 + q.  Every shard keeps a replica of the
+ * iterate; one FISTA iteration is
+ *   g_r = swopt_fista_gradient(shard r)     (its states' part of H^T (H xi - y))
+ *   g   = sum over shards of g_r            (the caller's collective)
+ *   swopt_fista_step_external(shard r, g)   (gradient step, prox, momentum)
+ * Plain solves only (refine_every = 0). */
+
+/* Sets the first state of the handle's pulses (default 0): pulse n sits
+ * offset + (n mod pulses_per_cycle) pulses into its cycle in Eq. (final-H).
+ * Errors: INVALID_ARG for offset < 0.  Synchronises. */
+swopt_status swopt_set_state_offset(swopt_handle* h, int offset);
+
+/* The data-fit gradient H^T (H xi - y) at the FISTA state's momentum iterate
+ * (after swopt_fista_init; refine_every must be 0), into g_dev [P][Y][X][Z]:
+ * per element, the P^T sum over the handle's states continues from
+ * carry_dev (a previous shard's output, or NULL for 0) with one FMA per state
+ * in state order.  Shards taken one after another, each continuing from the
+ * last, give the bits of the unsharded gradient whenever each state's A^T
+ * output has the same bits in both (FP32 operators; tensor-core operators
+ * with whole tile-states per CTA, swopt_tc_schedule split 1, and the same
+ * configuration).  Asynchronous on the stream. */
+swopt_status swopt_fista_gradient(swopt_handle* h, const float* carry_dev, float* g_dev,
+                                  void* stream);
+
+/* One FISTA iteration with the data-fit gradient at the momentum iterate
+ * supplied (g_dev, e.g. summed over shards): z = xi - alpha g, the prox of
+ * the solve's regulariser, then the momentum step, exactly as
+ * swopt_fista_step's plain iteration.  Asynchronous on the stream. */
+swopt_status swopt_fista_step_external(swopt_handle* h, const float* g_dev, void* stream);
+
 /* Complete solve (Algorithm 1): init, up to max_iters iterations with the
  * eps1/eps2 stopping tests and the optional history, then c_dev <- c_K and
  * the statistics (stats may be NULL).  Synchronises. */

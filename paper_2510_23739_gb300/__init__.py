@@ -135,6 +135,11 @@ _SIGS = {
     "swopt_prox_joint": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                           ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                           ctypes.c_double, ctypes.c_void_p], ctypes.c_int),
+    "swopt_set_state_offset": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "swopt_fista_gradient": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p], ctypes.c_int),
+    "swopt_fista_step_external": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+                                  ctypes.c_int),
     "swopt_prox_joint_step_bound": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double], ctypes.c_double),
     "swopt_two_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -407,6 +412,26 @@ class Operator:
             out = torch.empty(self.c_shape, device="cuda", dtype=torch.float32)
         _check(lib().swopt_fista_get(self._h, _ptr(out, self.c_shape, "c"), _stream(stream)))
         return out
+
+    def set_state_offset(self, offset):
+        """First switching state of this handle's pulses (see swopt_set_state_offset)."""
+        _check(lib().swopt_set_state_offset(self._h, int(offset)))
+
+    def fista_gradient(self, carry=None, out=None, stream=None):
+        """H^T (H xi - y) at the momentum iterate, the P^T sum continued from
+        ``carry`` (see swopt_fista_gradient)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.c_shape, device="cuda", dtype=torch.float32)
+        _check(lib().swopt_fista_gradient(
+            self._h, _ptr(carry, self.c_shape, "carry") if carry is not None else None,
+            _ptr(out, self.c_shape, "g"), _stream(stream)))
+        return out
+
+    def fista_step_external(self, g, stream=None):
+        """One FISTA iteration with the supplied data-fit gradient."""
+        _check(lib().swopt_fista_step_external(self._h, _ptr(g, self.c_shape, "g"),
+                                               _stream(stream)))
 
     def refine_stats(self, stream=None):
         """(iterations, exact gradients) of the refined solve since fista_init."""

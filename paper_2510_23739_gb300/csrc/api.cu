@@ -346,7 +346,8 @@ void switching_states(swopt_handle* h)
             for (int j = 0; j < h->Z; ++j) {
                 const double ph = h->phi[j];
                 h->Sm64[((size_t)m * h->P + p) * h->Z + j] =
-                    ph * (h->eps_bar[p] * std::exp(-h->kappa[p] * ph * m) + h->eps_off[p]);
+                    ph * (h->eps_bar[p] * std::exp(-h->kappa[p] * ph * (m + h->state_offset)) +
+                          h->eps_off[p]);
             }
 }
 
@@ -376,12 +377,13 @@ void switching_chain_rule(const swopt_handle* h, const std::vector<double>& W, d
 {
     double dm = 0.0;
     for (int p = 0; p < h->P; ++p) dkappa[p] = 0.0;
-    for (int m = 0; m < h->Q; ++m)
+    for (int q = 0; q < h->Q; ++q)
         for (int p = 0; p < h->P; ++p)
             for (int j = 0; j < h->Z; ++j) {
                 const double ph = h->phi[j];
+                const int m = q + h->state_offset;  // pulses into the cycle
                 const double e = std::exp(-h->kappa[p] * ph * m);
-                const double w = W[((size_t)m * h->P + p) * h->Z + j];
+                const double w = W[((size_t)q * h->P + p) * h->Z + j];
                 const double dS_dk = ph * h->eps_bar[p] * e * (-ph * m);
                 const double dS_dphi =
                     h->eps_bar[p] * e + h->eps_off[p] + ph * h->eps_bar[p] * e * (-h->kappa[p] * m);
@@ -479,16 +481,11 @@ struct GateScope {
 //   from c_{k+1} at the resync precision (kind 1).  The gradient step at
 //   xi_{k+1} then follows by linearity.  In exact arithmetic both variants
 //   give the iterates of Algorithm 1.
-swopt_status fista_iteration(swopt_handle* h, int kind, cudaStream_t st)
+// The prox of the prox input h->zin and the momentum step (Algorithm 1 after
+// the gradient step); refined: c_{k+1} - c_k also goes to h->tmp.
+swopt_status fista_prox_momentum(swopt_handle* h, bool refined, cudaStream_t st)
 {
-    const float alpha = (float)h->step;
     const bool tv = h->prm.lambda_tv > 0 && h->prm.inner_iters > 0;
-    const bool refined = h->prm.refine_every > 0;
-    if (!refined) {
-        SW_TRY(apply_A(h, h->xi, A_OUT_R, h->ytil, nullptr, 1, st));     // P, A, folded residual
-        SW_TRY(apply_AT(h, false, st));                                   // A^T
-        SW_TRY(launch_pt(h, h->g, h->xi, alpha, h->zin, 1, st));          // P^T, gradient step
-    }
     const float theta = (float)(h->step * h->prm.lambda_l1);
     if (h->prm.lambda_3 > 0) {
         // the prox of all three terms of R3 with the constraint (in place on
@@ -507,6 +504,19 @@ swopt_status fista_iteration(swopt_handle* h, int kind, cudaStream_t st)
         SW_TRY(fista_scalars(h, h->prm.momentum, st));
         SW_TRY(fista_finish(h, h->zin, false, theta, refined ? h->tmp : nullptr, st));
     }
+    return SWOPT_OK;
+}
+
+swopt_status fista_iteration(swopt_handle* h, int kind, cudaStream_t st)
+{
+    const float alpha = (float)h->step;
+    const bool refined = h->prm.refine_every > 0;
+    if (!refined) {
+        SW_TRY(apply_A(h, h->xi, A_OUT_R, h->ytil, nullptr, 1, st));     // P, A, folded residual
+        SW_TRY(apply_AT(h, false, st));                                   // A^T
+        SW_TRY(launch_pt(h, h->g, h->xi, alpha, h->zin, 1, st));          // P^T, gradient step
+    }
+    SW_TRY(fista_prox_momentum(h, refined, st));
     if (!refined) return SWOPT_OK;
     if (kind == 1) return exact_gradient(h, st);
     if (kind == 2) {
@@ -1029,6 +1039,52 @@ swopt_status swopt_fista_get(swopt_handle* h, float* c_dev, void* stream)
     }
     SW_CUDA(cudaMemcpyAsync(c_dev, h->c, nc_of(h) * sizeof(float), cudaMemcpyDeviceToDevice,
                             (cudaStream_t)stream));
+    return SWOPT_OK;
+}
+
+swopt_status swopt_fista_gradient(swopt_handle* h, const float* carry_dev, float* g_dev,
+                                  void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!g_dev || !h->fista_ready || h->prm.refine_every > 0) {
+        set_error("null gradient output, no FISTA state, or a refined solve");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    SW_TRY(apply_A(h, h->xi, A_OUT_R, h->ytil, nullptr, 1, st));
+    SW_TRY(apply_AT(h, false, st));
+    return launch_pt_carry(h, h->g, carry_dev, g_dev, st);
+}
+
+swopt_status swopt_fista_step_external(swopt_handle* h, const float* g_dev, void* stream)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (!g_dev || !h->fista_ready || h->prm.refine_every > 0) {
+        set_error("null gradient, no FISTA state, or a refined solve");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    SW_TRY(launch_grad_step(h, g_dev, h->xi, (float)h->step, h->zin, st));
+    SW_TRY(fista_prox_momentum(h, false, st));
+    ++h->iter;
+    return SWOPT_OK;
+}
+
+swopt_status swopt_set_state_offset(swopt_handle* h, int offset)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (offset < 0) {
+        set_error("negative state offset");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    SW_CUDA(cudaDeviceSynchronize());
+    h->state_offset = offset;
+    switching_states(h);
+    std::vector<float> Smf(h->Sm64.begin(), h->Sm64.end());
+    SW_CUDA(cudaMemcpy(h->Sm, Smf.data(), Smf.size() * sizeof(float), cudaMemcpyHostToDevice));
     return SWOPT_OK;
 }
 

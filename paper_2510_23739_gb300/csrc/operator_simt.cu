@@ -308,7 +308,7 @@ __global__ void fold_kernel(const float* __restrict__ y, float* __restrict__ yti
 // mode 1: out = xi - alpha * (that)
 __global__ void pt_kernel(const float* __restrict__ g, const float* __restrict__ Sm,
                           const float* __restrict__ xi, float alpha, float* __restrict__ out,
-                          int Q, int P, int S, int Z, int mode)
+                          int Q, int P, int S, int Z, int mode, const float* carry)
 {
     const size_t SZ = (size_t)S * Z;
     const size_t n = (size_t)P * SZ;
@@ -317,7 +317,7 @@ __global__ void pt_kernel(const float* __restrict__ g, const float* __restrict__
         const int j = (int)(i % Z);
         const size_t sj = i % SZ;
         const int p = (int)(i / SZ);
-        float acc = 0.f;
+        float acc = carry ? carry[i] : 0.f;
         for (int m = 0; m < Q; ++m) acc = fmaf(Sm[(m * P + p) * Z + j], g[(size_t)m * SZ + sj], acc);
         out[i] = mode ? fmaf(-alpha, acc, xi[i]) : acc;
     }
@@ -453,7 +453,34 @@ swopt_status launch_pt(swopt_handle* h, const float* g, const float* xi, float a
 {
     const size_t n = nc_of(h);
     pt_kernel<<<grid_for(n, 256), 256, 0, st>>>(g, h->Sm, xi, alpha, out, h->Q, h->P, h->S, h->Z,
-                                                 mode);
+                                                 mode, nullptr);
+    SW_LAUNCHED(h);
+    return SWOPT_OK;
+}
+
+swopt_status launch_pt_carry(swopt_handle* h, const float* g, const float* carry, float* out,
+                             cudaStream_t st)
+{
+    const size_t n = nc_of(h);
+    pt_kernel<<<grid_for(n, 256), 256, 0, st>>>(g, h->Sm, nullptr, 0.f, out, h->Q, h->P, h->S,
+                                                 h->Z, 0, carry);
+    SW_LAUNCHED(h);
+    return SWOPT_OK;
+}
+
+__global__ void grad_step_kernel(const float* __restrict__ g, const float* __restrict__ xi,
+                                 float alpha, float* __restrict__ out, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = fmaf(-alpha, g[i], xi[i]);
+}
+
+swopt_status launch_grad_step(swopt_handle* h, const float* g, const float* xi, float alpha,
+                              float* out, cudaStream_t st)
+{
+    const size_t n = nc_of(h);
+    grad_step_kernel<<<grid_for(n, 256), 256, 0, st>>>(g, xi, alpha, out, n);
     SW_LAUNCHED(h);
     return SWOPT_OK;
 }

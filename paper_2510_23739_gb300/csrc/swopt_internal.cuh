@@ -107,6 +107,7 @@ struct swopt_handle {
     std::vector<double> kappa, eps_bar, eps_off;
     int S;       // X * Y
     int Q;       // distinct switching states min(N, ncyc)
+    int state_offset = 0;  // pulse n sits state_offset + (n mod ncyc) pulses into its cycle
     int t0;      // first sample of the time window
     int tw;      // nonzero extent of the window (t0 + tw - 1 = last nonzero sample)
     int Twp;     // padded window length, multiple of TCHUNK
@@ -275,6 +276,13 @@ swopt_status launch_fold(swopt_handle* h, const float* y, float* ytil, cudaStrea
 // out = sum_m Sm[m][p][j] g[m] (mode 0); out = xi - alpha * that (mode 1)
 swopt_status launch_pt(swopt_handle* h, const float* g, const float* xi, float alpha,
                        float* out, int mode, cudaStream_t st);
+// out = carry + sum_m Sm[m][p][j] g[m], the sum continued from carry (or 0) in
+// the order of the states, one FMA per state
+swopt_status launch_pt_carry(swopt_handle* h, const float* g, const float* carry, float* out,
+                             cudaStream_t st);
+// out = xi - alpha g
+swopt_status launch_grad_step(swopt_handle* h, const float* g, const float* xi, float alpha,
+                              float* out, cudaStream_t st);
 // Refined solve: d = sum_m Sm[m][p][j] g[m]; Gn = (add ? G : 0) + d;
 // out = xi - alpha ((1 + beta) Gn - beta G) with beta = scal[1]; G = Gn.
 swopt_status launch_pt_refine(swopt_handle* h, const float* g, const float* xi, float alpha,
