@@ -380,6 +380,23 @@ swopt_status swopt_param_grad(swopt_handle* h, const float* c_dev, const float* 
 swopt_status swopt_param_vjp(swopt_handle* h, const float* c_dev, const float* w_dev,
                              double* dkappa_host, double* dmu, void* stream);
 
+/* Reverse-mode derivative of the unrolled solve: with y, prm and the handle's
+ * precision as in swopt_solve (explicit step > 0, max_iters >= 1 FISTA
+ * iterations, refine_every = 0, lambda_3 = 0, no stopping tests), the
+ * gradient of <w, c_K> with respect to kappa_p (dkappa_host[P]) and mu
+ * (*dmu) of Eq. (final-H), c_K the output of Algorithm 1 (Algorithm 2 as the
+ * TV prox, clamp masks and the l1/nonnegativity clip taken as fixed where
+ * they are, the step, weights and counts held fixed).  The forward pass
+ * keeps the K momentum iterates on the device (K volumes); the backward pass
+ * recomputes each iteration, records Algorithm 2's masks and applies the
+ * transposed steps, with the parameter derivatives of H taken as in
+ * swopt_param_vjp.  c_dev (optional) receives c_K.  w_dev: [P][Y][X][Z].
+ * Errors: INVALID_ARG, OOM, CUDA.  Synchronises; leaves the handle's FISTA
+ * state at c_K. */
+swopt_status swopt_unrolled_vjp(swopt_handle* h, const float* y_dev,
+                                const swopt_solve_params* prm, const float* w_dev, float* c_dev,
+                                double* dkappa_host, double* dmu, void* stream);
+
 /* Replaces the switching parameters of Eq. (final-H) (kappa, eps_bar, eps_off
  * per species and mu, validated as in swopt_create); the geometry, kernel and
  * precision stay.  Captured FISTA iterations keep working (they read the

@@ -135,6 +135,9 @@ _SIGS = {
     "swopt_prox_joint": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                           ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                           ctypes.c_double, ctypes.c_void_p], ctypes.c_int),
+    "swopt_unrolled_vjp": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_SolveParams),
+                            ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double), ctypes.c_void_p], ctypes.c_int),
     "swopt_set_state_offset": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "swopt_fista_gradient": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_void_p], ctypes.c_int),
@@ -412,6 +415,20 @@ class Operator:
             out = torch.empty(self.c_shape, device="cuda", dtype=torch.float32)
         _check(lib().swopt_fista_get(self._h, _ptr(out, self.c_shape, "c"), _stream(stream)))
         return out
+
+    def unrolled_vjp(self, y, params: SolveParams, w, stream=None):
+        """Gradient of <w, c_K> with respect to (kappa, mu) through the
+        unrolled solve (see swopt_unrolled_vjp).  Returns (c_K, dkappa, dmu)."""
+        import torch
+        c = torch.empty(self.c_shape, device=y.device, dtype=torch.float32)
+        dk = np.zeros(self.geom.P)
+        dm = ctypes.c_double()
+        p = params._c()
+        _check(lib().swopt_unrolled_vjp(self._h, _ptr(y, self.y_shape, "y"), ctypes.byref(p),
+                                        _ptr(w, self.c_shape, "w"), _ptr(c, self.c_shape, "c"),
+                                        dk.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        ctypes.byref(dm), _stream(stream)))
+        return c, dk, dm.value
 
     def set_state_offset(self, offset):
         """First switching state of this handle's pulses (see swopt_set_state_offset)."""

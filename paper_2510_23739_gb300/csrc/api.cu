@@ -958,8 +958,36 @@ swopt_status swopt_fista_init(swopt_handle* h, const float* y_dev, const swopt_s
         set_error("null y");
         return SWOPT_ERR_INVALID_ARG;
     }
+    return fista_init_impl(h, y_dev, prm, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace swopt {
+
+// Helpers of the unrolled derivative (unrolled.cu).
+swopt_status fista_iterate_once(swopt_handle* h, cudaStream_t st) { return run_iteration(h, st); }
+
+swopt_status apply_forward_residual(swopt_handle* h, const float* v, const float* ytil,
+                                    cudaStream_t st)
+{
+    return apply_A(h, v, A_OUT_R, ytil, nullptr, 1, st);
+}
+
+swopt_status apply_adjoint_folded(swopt_handle* h, cudaStream_t st)
+{
+    return apply_AT(h, false, st);
+}
+
+void chain_rule(const swopt_handle* h, const std::vector<double>& W, double* dkappa, double* dmu)
+{
+    switching_chain_rule(h, W, dkappa, dmu);
+}
+
+swopt_status fista_init_impl(swopt_handle* h, const float* y_dev, const swopt_solve_params* prm,
+                             cudaStream_t st)
+{
     SW_TRY(validate_params(prm));
-    cudaStream_t st = (cudaStream_t)stream;
     h->fista_ready = false;
     release_graph(h);
     SW_TRY(ensure_vectors(h));
@@ -1011,6 +1039,10 @@ swopt_status swopt_fista_init(swopt_handle* h, const float* y_dev, const swopt_s
     h->fista_ready = true;
     return SWOPT_OK;
 }
+
+}  // namespace swopt
+
+extern "C" {
 
 swopt_status swopt_fista_step(swopt_handle* h, int iters, void* stream)
 {

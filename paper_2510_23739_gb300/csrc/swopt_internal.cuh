@@ -330,6 +330,10 @@ swopt_status fill_counter_random(swopt_handle* h, float* x, size_t n, uint64_t s
 swopt_status param_weights(swopt_handle* h, const float* g, const float* c, int slot0,
                            cudaStream_t st);
 
+// FISTA set-up on measurements y (api.cu; swopt_fista_init after its checks).
+swopt_status fista_init_impl(swopt_handle* h, const float* y, const swopt_solve_params* prm,
+                             cudaStream_t st);
+
 // The joint prox of R3 with its lambda_3 term (prox_joint.cu): Algorithm 2 on
 // the stacked operator with one dual per switching state, z and x may alias;
 // scratch w [P L], u and r [joint_dual_floats] (ensure_joint_buffers gives the
