@@ -68,6 +68,7 @@ def lib():
             L.oracle_tv.restype = ctypes.c_double
             L.oracle_tv_pulses.restype = ctypes.c_double
             L.oracle_num_threads.restype = ctypes.c_int
+            L.oracle_diffusion_system.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -102,9 +103,37 @@ def fluence(geom, sw):
     return out
 
 
-def switch_matrix(geom, sw):
-    """S[n][p][j] of Eq. (final-H)."""
-    phi = fluence(geom, sw)
+def diffusion_system(Y, X, Z, dx, dz, mu_a, mu_s, g, src_top, lateral_robin=True):
+    """The finite-volume system of Eqs. (de)/(bc) (see oracle_diffusion_system):
+    a scipy CSR matrix and the right-hand side, unknowns Phi[Y][X][Z]."""
+    import scipy.sparse as sp
+    n = Y * X * Z
+    mu_a = np.ascontiguousarray(np.broadcast_to(mu_a, (Y, X, Z)), dtype=np.float64)
+    mu_s = np.ascontiguousarray(np.broadcast_to(mu_s, (Y, X, Z)), dtype=np.float64)
+    src = np.ascontiguousarray(np.broadcast_to(src_top, (Y, X)), dtype=np.float64)
+    rows = np.empty(7 * n, dtype=np.int32)
+    cols = np.empty(7 * n, dtype=np.int32)
+    vals = np.empty(7 * n)
+    rhs = np.empty(n)
+    cnt = lib().oracle_diffusion_system(
+        ctypes.c_int(Y), ctypes.c_int(X), ctypes.c_int(Z), ctypes.c_double(dx),
+        ctypes.c_double(dz), _p(mu_a), _p(mu_s), ctypes.c_double(g), _p(src),
+        ctypes.c_int(1 if lateral_robin else 0), _p(rows), _p(cols), _p(vals), _p(rhs))
+    A = sp.csr_matrix((vals[:cnt], (rows[:cnt], cols[:cnt])), shape=(n, n))
+    return A, rhs
+
+
+def diffusion_fluence(Y, X, Z, dx, dz, mu_a, mu_s, g, src_top, lateral_robin=True):
+    """Phi[Y][X][Z] solving the finite-volume system of Eqs. (de)/(bc)
+    (scipy's sparse direct solver)."""
+    import scipy.sparse.linalg as spla
+    A, rhs = diffusion_system(Y, X, Z, dx, dz, mu_a, mu_s, g, src_top, lateral_robin)
+    return spla.spsolve(A.tocsc(), rhs).reshape(Y, X, Z)
+
+
+def switch_matrix(geom, sw, phi=None):
+    """S[n][p][j] of Eq. (final-H); phi (optional, [Z]) replaces exp(-mu j dz)."""
+    phi = fluence(geom, sw) if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
     kap = _f64(sw.kappa)
     eb = _f64(sw.eps_bar)
     eo = _f64(sw.eps_off)

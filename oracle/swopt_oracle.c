@@ -595,6 +595,63 @@ void oracle_fista_joint(int N, int P, int Y, int X, int Z, int T, int k,
     free(c); free(c_new); free(xi); free(zin); free(grad); free(res);
 }
 
+/* ---------------------------------------------------------------------------
+ * Fluence from the diffusion equation, Eqs. (de), (bc) and
+ * (diffusion-coefficient), by cell-centred finite volumes on the voxel grid
+ * (lateral pitch dx, depth pitch dz, voxel i = (y, x, j), j = 0 the
+ * illuminated top face).  Per voxel, divided by its volume:
+ *   mu_a_i Phi_i + sum over its six faces of (outward flux through the face) / h_face = s_i
+ * with D = 1 / (3 (mu_a + (1 - g) mu_s)) per voxel and, across a face of
+ * normal pitch h,
+ *   inner face to voxel k : D_f (Phi_i - Phi_k) / h,   D_f = 2 D_i D_k / (D_i + D_k)
+ *   boundary face         : 2 D_i Phi_i / (4 D_i + h)
+ * the last from the boundary condition taken as Phi + 2 D dPhi/dn = 0 with n
+ * the outward normal (the boundary value Phi_b from D (Phi_i - Phi_b)/(h/2) =
+ * Phi_b / 2, the outgoing flux Phi_b / 2).  Lateral faces are boundary faces
+ * (lateral_robin = 1) or carry no flux (0: a laterally unbounded sample).
+ * The source is the illumination entering the top face, src_top[y][x] (power
+ * per area), in the top layer: s = src_top / dz for j = 0.
+ * Output: the matrix as (row, col, value) triplets (at most 7 per row;
+ * returns their count) and the right-hand side; Phi is [Y][X][Z].
+ * ------------------------------------------------------------------------- */
+int oracle_diffusion_system(int Y, int X, int Z, double dx, double dz, const double* mu_a,
+                            const double* mu_s, double g, const double* src_top,
+                            int lateral_robin, int* rows, int* cols, double* vals, double* rhs)
+{
+    const size_t n = (size_t)Y * X * Z;
+    double* D = (double*)malloc(sizeof(double) * n);
+    for (size_t i = 0; i < n; ++i) D[i] = 1.0 / (3.0 * (mu_a[i] + (1.0 - g) * mu_s[i]));
+    int cnt = 0;
+    for (int y = 0; y < Y; ++y)
+        for (int x = 0; x < X; ++x)
+            for (int j = 0; j < Z; ++j) {
+                const int i = (y * X + x) * Z + j;
+                double diag = mu_a[i];
+                /* the six faces: (axis pitch, neighbour exists, neighbour index, boundary kind) */
+                const int ny[6] = {y - 1, y + 1, y, y, y, y};
+                const int nx[6] = {x, x, x - 1, x + 1, x, x};
+                const int nj[6] = {j, j, j, j, j - 1, j + 1};
+                for (int f = 0; f < 6; ++f) {
+                    const double h = f < 4 ? dx : dz;
+                    const int inside = ny[f] >= 0 && ny[f] < Y && nx[f] >= 0 && nx[f] < X &&
+                                       nj[f] >= 0 && nj[f] < Z;
+                    if (inside) {
+                        const int k = (ny[f] * X + nx[f]) * Z + nj[f];
+                        const double Df = 2.0 * D[i] * D[k] / (D[i] + D[k]);
+                        const double w = Df / (h * h);
+                        diag += w;
+                        rows[cnt] = i; cols[cnt] = k; vals[cnt] = -w; ++cnt;
+                    } else if (f >= 4 || lateral_robin) {
+                        diag += 2.0 * D[i] / (4.0 * D[i] + h) / h;
+                    }
+                }
+                rows[cnt] = i; cols[cnt] = i; vals[cnt] = diag; ++cnt;
+                rhs[i] = j == 0 ? src_top[y * X + x] / dz : 0.0;
+            }
+    free(D);
+    return cnt;
+}
+
 /* Power iteration for eig_max(H^T H): v <- H^T H v / ||H^T H v|| from the
  * given start vector; returns the Rayleigh quotient v^T H^T H v / v^T v. */
 double oracle_power(int N, int P, int Y, int X, int Z, int T, int k,

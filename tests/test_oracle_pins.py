@@ -925,3 +925,85 @@ def test_fista_with_lambda3_reaches_a_fixed_point_of_the_exact_prox_gradient_map
     # the lambda_3 term changes the solution
     c0 = oracle.fista(g, sw, K, y, alpha, 300, lam_l1, lam_tv, 300)
     assert np.linalg.norm(c0 - c) > 1e-3 * np.linalg.norm(c)
+
+
+# --------------------------------------------------------------------------
+# Fluence from the diffusion equation, Eqs. (de)/(bc), finite volumes
+# --------------------------------------------------------------------------
+
+def _slab_closed_form(Z, dz, mu_a, D, q):
+    """The laterally uniform discrete solution phi_j = A r^j + B r^-j of the
+    finite-volume rows (interior: (mu_a + 2w) phi_j = w (phi_{j-1} + phi_{j+1}),
+    w = D/dz^2; the two end rows carry the boundary loss b = 2D/(4D + dz)/dz
+    and the top one the source q/dz), A and B from the end rows."""
+    w = D / dz ** 2
+    b = 2 * D / (4 * D + dz) / dz
+    c = 2 + mu_a / w
+    r = (c - np.sqrt(c * c - 4)) / 2
+    d = mu_a + w + b
+    j = np.arange(Z, dtype=np.float64)
+    M = np.array([[d - w * r, d - w / r],
+                  [d * r ** (Z - 1) - w * r ** (Z - 2), d * r ** -(Z - 1) - w * r ** -(Z - 2)]])
+    A, B = np.linalg.solve(M, [q / dz, 0.0])
+    return A * r ** j + B * r ** -j
+
+
+def test_diffusion_slab_matches_the_closed_form_of_its_recurrence():
+    Y, X, Z, dx, dz = 3, 4, 20, 0.02, 0.05
+    mu_a, mu_s, g, q = 0.5, 10.0, 0.9, 2.0
+    phi = oracle.diffusion_fluence(Y, X, Z, dx, dz, mu_a, mu_s, g, q, lateral_robin=False)
+    D = 1 / (3 * (mu_a + (1 - g) * mu_s))
+    want = _slab_closed_form(Z, dz, mu_a, D, q)
+    for y in range(Y):
+        for x in range(X):
+            np.testing.assert_allclose(phi[y, x], want, rtol=1e-11)
+
+
+def test_diffusion_slab_converges_to_the_continuum_solution():
+    """-D phi'' + mu_a phi = 0 on (0, H) with -D phi'(0) = q - phi(0)/2
+    (illumination in, the Robin loss out) and -D phi'(H) = phi(H)/2: the
+    finite-volume values at the cell centres converge as dz halves."""
+    H, mu_a, mu_s, g, q = 1.0, 0.3, 8.0, 0.9, 1.0
+    D = 1 / (3 * (mu_a + (1 - g) * mu_s))
+    k = np.sqrt(mu_a / D)
+    # phi = a exp(-k z) + b exp(k z); rows: top -D phi'(0) + phi(0)/2 = q,
+    # bottom -D phi'(H) - phi(H)/2 = 0
+    M = np.array([[D * k + 0.5, -D * k + 0.5],
+                  [(D * k - 0.5) * np.exp(-k * H), (-D * k - 0.5) * np.exp(k * H)]])
+    a, b = np.linalg.solve(M, [q, 0.0])
+    errs = []
+    for Z in (20, 40, 80):
+        dz = H / Z
+        z = (np.arange(Z) + 0.5) * dz
+        exact = a * np.exp(-k * z) + b * np.exp(k * z)
+        phi = oracle.diffusion_fluence(1, 1, Z, 0.1, dz, mu_a, mu_s, g, q, lateral_robin=False)
+        errs.append(np.abs(phi[0, 0] - exact).max() / exact.max())
+    assert errs[0] < 0.05
+    assert errs[1] < errs[0] / 1.8 and errs[2] < errs[1] / 1.8
+
+
+def test_diffusion_conserves_power_and_keeps_symmetry():
+    """Summed over all voxels the rows state that the illumination entering
+    the top equals the absorbed power plus the Robin losses; a source and an
+    absorber map symmetric in x give a symmetric, positive fluence."""
+    Y, X, Z, dx, dz, g = 5, 8, 12, 0.05, 0.04, 0.9
+    rng = np.random.default_rng(37)
+    half = 0.05 + rng.random((Y, X // 2, Z))
+    mu_a = np.concatenate([half, half[:, ::-1]], axis=1)
+    mu_s = np.full((Y, X, Z), 6.0)
+    src = np.zeros((Y, X))
+    src[:, 2:6] = 1.5
+    phi = oracle.diffusion_fluence(Y, X, Z, dx, dz, mu_a, mu_s, g, src)
+    assert phi.min() > 0
+    np.testing.assert_allclose(phi, phi[:, ::-1], rtol=1e-10)
+    D = 1 / (3 * (mu_a + (1 - g) * mu_s))
+    area = {"y": dx * dz, "x": dx * dz, "z": dx * dx}
+    pitch = {"y": dx, "x": dx, "z": dz}
+    loss = 0.0
+    for ax, sl in (("y", np.s_[[0, -1], :, :]), ("x", np.s_[:, [0, -1], :]),
+                   ("z", np.s_[:, :, [0, -1]])):
+        h = pitch[ax]
+        loss += area[ax] * np.sum(2 * D[sl] * phi[sl] / (4 * D[sl] + h))
+    absorbed = np.sum(mu_a * phi) * dx * dx * dz
+    entering = np.sum(src) * dx * dx
+    assert absorbed + loss == pytest.approx(entering, rel=1e-10)
