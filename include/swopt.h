@@ -380,6 +380,35 @@ swopt_status swopt_param_grad(swopt_handle* h, const float* c_dev, const float* 
 swopt_status swopt_param_vjp(swopt_handle* h, const float* c_dev, const float* w_dev,
                              double* dkappa_host, double* dmu, void* stream);
 
+/* Fluence from the diffusion equation, Eqs. (de), (bc) and
+ * (diffusion-coefficient), on the GPU: cell-centred finite volumes on a
+ * Y x X x Z voxel grid (lateral pitch dx_mm, depth pitch dz_mm, depth index 0
+ * the illuminated top face), per voxel
+ *   mu_a Phi + sum over faces (outward flux) / h = s,
+ * inner faces D_f (Phi_i - Phi_k) / h with the harmonic mean D_f, boundary
+ * faces 2 D Phi / (4 D + h) from Phi + 2 D dPhi/dn = 0 (n the outward
+ * normal), D = 1 / (3 (mu_a + (1 - g) mu_s)).  Lateral faces are boundary
+ * faces (lateral_robin = 1) or carry no flux (0: a laterally unbounded
+ * sample).  The illumination src_top_host [Y][X] (power per area) enters the
+ * top layer as s = src / dz_mm.  mu_a_host, mu_s_host [Y][X][Z] in 1/mm (>= 0,
+ * mu_a + (1 - g) mu_s > 0), 0 <= g < 1.  Solved by conjugate gradients with a
+ * diagonal preconditioner in FP64 to ||r|| <= tol ||b|| within max_iters
+ * iterations; phi_host [Y][X][Z] receives the solution, iters_out and
+ * rel_residual_out (either may be NULL) the count and the final relative
+ * residual.  Errors: INVALID_ARG, OOM, CUDA, DEVICE_CHECK (not converged; the
+ * last iterate is still written).  Synchronises. */
+swopt_status swopt_diffusion_fluence(int Y, int X, int Z, double dx_mm, double dz_mm,
+                                     const double* mu_a_host, const double* mu_s_host, double g,
+                                     const double* src_top_host, int lateral_robin, double tol,
+                                     int max_iters, double* phi_host, int* iters_out,
+                                     double* rel_residual_out);
+
+/* Replaces exp(-mu j dz) in Eq. (final-H) by the depth profile phi_host [Z]
+ * (e.g. the lateral mean of swopt_diffusion_fluence's solution; finite, >= 0),
+ * or restores it (phi_host NULL).  With a given profile the derivatives with
+ * respect to mu are 0.  Synchronises. */
+swopt_status swopt_set_fluence(swopt_handle* h, const double* phi_host);
+
 /* Reverse-mode derivative of the unrolled solve: with y, prm and the handle's
  * precision as in swopt_solve (explicit step > 0, max_iters >= 1 FISTA
  * iterations, refine_every = 0, lambda_3 = 0, no stopping tests), the

@@ -138,6 +138,12 @@ _SIGS = {
     "swopt_unrolled_vjp": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_SolveParams),
                             ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_double), ctypes.c_void_p], ctypes.c_int),
+    "swopt_diffusion_fluence": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_double, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                 ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "swopt_set_fluence": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "swopt_set_state_offset": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "swopt_fista_gradient": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_void_p], ctypes.c_int),
@@ -185,6 +191,25 @@ def lib():
 
 def library_path() -> str:
     return _build.LIB
+
+
+def diffusion_fluence(Y, X, Z, dx_mm, dz_mm, mu_a, mu_s, g, src_top, lateral_robin=True,
+                      tol=1e-10, max_iters=100000):
+    """Fluence Phi [Y][X][Z] from the diffusion equation (see
+    swopt_diffusion_fluence); mu_a, mu_s broadcast to [Y][X][Z], src_top to
+    [Y][X].  Returns (phi, iterations, relative residual)."""
+    mu_a = np.ascontiguousarray(np.broadcast_to(mu_a, (Y, X, Z)), dtype=np.float64)
+    mu_s = np.ascontiguousarray(np.broadcast_to(mu_s, (Y, X, Z)), dtype=np.float64)
+    src = np.ascontiguousarray(np.broadcast_to(src_top, (Y, X)), dtype=np.float64)
+    phi = np.empty((Y, X, Z))
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    _check(lib().swopt_diffusion_fluence(
+        int(Y), int(X), int(Z), float(dx_mm), float(dz_mm),
+        mu_a.ctypes.data_as(ctypes.c_void_p), mu_s.ctypes.data_as(ctypes.c_void_p), float(g),
+        src.ctypes.data_as(ctypes.c_void_p), 1 if lateral_robin else 0, float(tol),
+        int(max_iters), phi.ctypes.data_as(ctypes.c_void_p), ctypes.byref(it),
+        ctypes.byref(rel)))
+    return phi, it.value, rel.value
 
 
 def semicircle_kernel(Z, k, T, dims, lateral_ratio, focal_depth, focal_sample, eta, eir):
@@ -429,6 +454,17 @@ class Operator:
                                         dk.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                         ctypes.byref(dm), _stream(stream)))
         return c, dk, dm.value
+
+    def set_fluence(self, phi=None):
+        """Depth profile Phi_j [Z] used in Eq. (final-H) instead of
+        exp(-mu j dz) (None restores it); see swopt_set_fluence."""
+        if phi is None:
+            _check(lib().swopt_set_fluence(self._h, None))
+            return
+        phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
+        if phi.shape != (self.geom.Z,):
+            raise ValueError("the fluence profile needs one value per depth")
+        _check(lib().swopt_set_fluence(self._h, phi.ctypes.data_as(ctypes.c_void_p)))
 
     def set_state_offset(self, offset):
         """First switching state of this handle's pulses (see swopt_set_state_offset)."""

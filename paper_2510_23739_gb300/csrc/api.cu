@@ -338,8 +338,10 @@ swopt_status lipschitz_impl(swopt_handle* h, const float* v0, int iters, double*
 // S[m][p][j] = Phi_j (eps_bar_p exp(-kappa_p Phi_j m) + eps_off_p).
 void switching_states(swopt_handle* h)
 {
-    h->phi.resize(h->Z);
-    for (int j = 0; j < h->Z; ++j) h->phi[j] = std::exp(-h->mu * j * h->dz_mm);
+    if (!h->phi_fixed) {
+        h->phi.resize(h->Z);
+        for (int j = 0; j < h->Z; ++j) h->phi[j] = std::exp(-h->mu * j * h->dz_mm);
+    }
     h->Sm64.resize((size_t)h->Q * h->P * h->Z);
     for (int m = 0; m < h->Q; ++m)
         for (int p = 0; p < h->P; ++p)
@@ -387,7 +389,7 @@ void switching_chain_rule(const swopt_handle* h, const std::vector<double>& W, d
                 const double dS_dk = ph * h->eps_bar[p] * e * (-ph * m);
                 const double dS_dphi =
                     h->eps_bar[p] * e + h->eps_off[p] + ph * h->eps_bar[p] * e * (-h->kappa[p] * m);
-                const double dphi_dmu = -(double)j * h->dz_mm * ph;
+                const double dphi_dmu = h->phi_fixed ? 0.0 : -(double)j * h->dz_mm * ph;
                 dkappa[p] += w * dS_dk;
                 dm += w * dS_dphi * dphi_dmu;
             }
@@ -1101,6 +1103,25 @@ swopt_status swopt_fista_step_external(swopt_handle* h, const float* g_dev, void
     SW_TRY(launch_grad_step(h, g_dev, h->xi, (float)h->step, h->zin, st));
     SW_TRY(fista_prox_momentum(h, false, st));
     ++h->iter;
+    return SWOPT_OK;
+}
+
+swopt_status swopt_set_fluence(swopt_handle* h, const double* phi_host)
+{
+    clear_error();
+    SW_TRY(check_handle(h));
+    if (phi_host)
+        for (int j = 0; j < h->Z; ++j)
+            if (!std::isfinite(phi_host[j]) || phi_host[j] < 0) {
+                set_error("the fluence must be finite and >= 0");
+                return SWOPT_ERR_INVALID_ARG;
+            }
+    SW_CUDA(cudaDeviceSynchronize());
+    h->phi_fixed = phi_host != nullptr;
+    if (phi_host) h->phi.assign(phi_host, phi_host + h->Z);
+    switching_states(h);
+    std::vector<float> Smf(h->Sm64.begin(), h->Sm64.end());
+    SW_CUDA(cudaMemcpy(h->Sm, Smf.data(), Smf.size() * sizeof(float), cudaMemcpyHostToDevice));
     return SWOPT_OK;
 }
 

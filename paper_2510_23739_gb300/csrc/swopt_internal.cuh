@@ -117,6 +117,7 @@ struct swopt_handle {
     int64_t nnz; // nonzero kernel entries
     std::vector<double> K64;      // host copy [Z][k][k][T]
     std::vector<double> phi;      // [Z]
+    bool phi_fixed = false;       // phi given (swopt_set_fluence), not exp(-mu j dz)
     std::vector<double> Sm64;     // [Q][P][Z] switching weights of the states
     std::vector<int> Cm;          // [Q] pulses per state
     int precision = SWOPT_PREC_FP32;
