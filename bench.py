@@ -23,7 +23,7 @@ BF16) solve after the same iteration count.
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl swopt|reference]
                        [--workload NAME] [--precision fp32|bf16|bf16x3]
                        [--refine R] [--refine-budget B] [--presolve I]
-                       [--method one-step|two-step|prox-joint|prox-sweep]
+                       [--method one-step|two-step|prox-joint|prox-sweep|prox-tv]
 For N > 1 it is launched by torch.distributed.run, one rank per GPU; each rank
 solves its own independent problem (replicas, weak scaling).
 """
@@ -144,7 +144,7 @@ class ClockSampler:
 
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("operator_simt.cu", "operator_tc.cu", "swopt_internal.cuh"):
+    for name in ("operator_tc.cu", "swopt_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2510_23739_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -491,11 +491,13 @@ def run_prox_joint(args, device):
     time.sleep(0.3)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()
     e0.record(stream)
     for _ in range(args.steps):
         op.prox_joint(z, alpha, lam_tv, lam_l1, lam_b, inner, step2, out=out)
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     clk = clocks.stop()
     op.check_device()
     states = op.info()["states"]
@@ -517,6 +519,62 @@ def run_prox_joint(args, device):
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": gbs / peaks["hbm_gbs"], "traffic": None,
                      "bytes_per_dual_iter": bytes_iter, "peak_source": f"HBM copy ({src})"},
+        "clocks": clk}), flush=True)
+
+
+def run_prox_tv(args, device):
+    """The TV prox (Algorithm 2, the workload's inner iteration count) alone on
+    the workload's volume [P][Y][X][Z] (the large workload: 3 x 128 x 128 x
+    96, 57 MB per dual array, beyond L2 together): time per call, and GB/s of
+    algorithmic traffic at 52 B per element and inner iteration (read z, r and
+    the previous u, three components each; write u and r) against the HBM
+    copy peak.  The kernel also moves x between its two phases (72 B)."""
+    import torch
+    import paper_2510_23739_gb300 as sw
+
+    prob = synth.workload(args.workload)
+    g = synth.small_variant(prob, T=8, k=1).geom
+    K = np.zeros(g.k_shape())
+    K[:, 0, 0, 0] = 1.0
+    op = sw.Operator(g, K, prob.sw)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(7)
+    z = 0.1 * torch.randn(g.c_shape(), generator=gen, device=device, dtype=torch.float32)
+    x = torch.empty_like(z)
+    tau, inner = 0.02, prob.inner
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        op.prox_tv(z, tau, inner, out=x)
+    clocks = ClockSampler(_smi_id(device))
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        op.prox_tv(z, tau, inner, out=x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    clk = clocks.stop()
+    op.check_device()
+    op.close()
+    ms = e0.elapsed_time(e1) / args.steps
+    n = z.numel()
+    gbs = 52.0 * n * inner / (ms * 1e-3) / 1e9
+    peaks, src = _peaks()
+    print(json.dumps({
+        "metric": "TV prox algorithmic HBM throughput", "value": gbs, "unit": "GB/s",
+        "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "dtype": "f32", "data": "synthetic (seeded Gaussian volume)",
+        "config": {"workload": args.workload, "volume": list(g.c_shape()), "inner_iters": inner,
+                   "l2": "dual arrays 3 x 19 MB per component block, 190 MB in all (no flush)"},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                     "moved_gb_per_s": 72.0 * n * inner / (ms * 1e-3) / 1e9,
+                     "peak_source": f"HBM copy ({src})"},
         "clocks": clk}), flush=True)
 
 
@@ -549,6 +607,7 @@ def run_prox_sweep(args, device):
     clocks.start()
     time.sleep(0.3)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.profiler.start()
     ev[0].record(stream)
     for _ in range(args.steps):
         op.prox_tv(z, tau, inner, out=x)
@@ -558,6 +617,7 @@ def run_prox_sweep(args, device):
         op.prox_l1(x, 1e-3)
     ev[3].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     clk = clocks.stop()
     op.check_device()
     op.close()
@@ -827,10 +887,11 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "bf16x3", "fp8"])
     ap.add_argument("--method", default="one-step",
-                    choices=["one-step", "two-step", "prox-joint", "prox-sweep"],
+                    choices=["one-step", "two-step", "prox-joint", "prox-sweep", "prox-tv"],
                     help="two-step: time swopt_two_step against the one-step solve (FP32); "
                          "prox-joint: time the prox of the full R3 (lambda_3 term); "
-                         "prox-sweep: the TV and l1 proxes on a volume 8x larger than L2")
+                         "prox-sweep: the TV and l1 proxes on a volume 8x larger than L2; "
+                         "prox-tv: the TV prox on the workload's volume")
     ap.add_argument("--kernel", default="aperture", choices=["aperture", "semicircle"],
                     help="per-depth kernel: the aperture-point transducer model, or the "
                          "paper-literal SPR on discrete half spheres (matched time grid)")
@@ -895,7 +956,7 @@ def main():
     import paper_2510_23739_gb300 as sw
     sw.lib()
     single = {"prox-joint": run_prox_joint, "two-step": run_two_step,
-              "prox-sweep": run_prox_sweep}
+              "prox-sweep": run_prox_sweep, "prox-tv": run_prox_tv}
     if args.method in single or args.workload == "batch16":
         if rank == 0:
             (run_batch if args.workload == "batch16" else single[args.method])(args, device)

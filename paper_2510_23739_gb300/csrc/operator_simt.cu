@@ -13,6 +13,8 @@
 //  * inside the window the kernel is banded: for each (depth, tap) only a
 //    few 8-sample sub-blocks are nonzero, and the kernels skip the rest
 //    with warp-uniform branches (8-bit masks built at create time).
+#include <algorithm>
+
 #include "swopt_internal.cuh"
 
 namespace swopt {
@@ -422,7 +424,8 @@ swopt_status simt_adjoint(swopt_handle* h, const float* u, float* g, cudaStream_
 swopt_status launch_states(swopt_handle* h, const float* c, float* b, cudaStream_t st)
 {
     const size_t n = nb_of(h);
-    states_kernel<<<grid_for(n, 256), 256, 0, st>>>(c, h->Sm, b, h->Q, h->P, h->S, h->Z, h->gate,
+    states_kernel<<<std::min(grid_for(n, 256), 152 * 8), 256, 0, st>>>(c, h->Sm, b, h->Q, h->P,
+                                                                        h->S, h->Z, h->gate,
                                                     h->gate_want);
     SW_LAUNCHED(h);
     return SWOPT_OK;
@@ -489,7 +492,10 @@ swopt_status launch_pt_refine(swopt_handle* h, const float* g, const float* xi, 
                               float* G, float* out, int add, cudaStream_t st)
 {
     const size_t n = nc_of(h);
-    pt_refine_kernel<<<grid_for(n, 256), 256, 0, st>>>(g, h->Sm, xi, alpha, G, out, h->scal,
+    // grid-stride: a launch behind a closed gate costs its blocks' start-up,
+    // 40 us at one block per 256 elements of the large workload, 5 us like this
+    const int grid = std::min(grid_for(n, 256), 152 * 8);
+    pt_refine_kernel<<<grid, 256, 0, st>>>(g, h->Sm, xi, alpha, G, out, h->scal,
                                                         h->Q, h->P, h->S, h->Z, add, h->gate,
                                                         h->gate_want);
     SW_LAUNCHED(h);

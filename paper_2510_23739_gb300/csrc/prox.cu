@@ -742,13 +742,17 @@ __global__ void red_pair_kernel(const float* __restrict__ d, const float* __rest
                                 size_t n, double* parts)
 {
     __shared__ double sh[kRedThreads / 32];
-    double sd = 0.0, sc = 0.0;
+    // a thread's few terms in FP32 (the ratio only steers the resync
+    // schedule; FP64 arithmetic per element took 46 us on the large volume),
+    // the block's sum in FP64
+    float fd = 0.f, fc = 0.f;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
-        const double a = d[i], b = c[i];
-        sd += a * a;
-        sc += b * b;
+        const float a = d[i], b = c[i];
+        fd = fmaf(a, a, fd);
+        fc = fmaf(b, b, fc);
     }
+    double sd = fd, sc = fc;
     sd = block_sum(sd, sh);
     __syncthreads();  // sh is reused
     sc = block_sum(sc, sh);
