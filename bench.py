@@ -652,10 +652,11 @@ def run_batch(args, device):
     """Sixteen independent problems of uneven size (scan 32^2..128^2, depths
     48-128, T 128-512, 20-80 pulses, 2-3 species, supports 11-31; seeded):
     aggregate FISTA iterations per second of the batched step (one CUDA graph
-    per iteration, a stream per problem) against the same problems stepped
-    one after another at the same precision, and against plain FP32 one after
-    another (a few iterations per problem, the per-iteration cost being
-    constant)."""
+    per iteration, a stream per problem) against the same batch with the
+    contractions as shared persistent launches over all problems' tile-states,
+    the same problems stepped one after another at the same precision, and
+    plain FP32 one after another (a few iterations per problem, the
+    per-iteration cost being constant)."""
     import torch
     import paper_2510_23739_gb300 as sw
 
@@ -683,24 +684,42 @@ def run_batch(args, device):
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
+    torch.cuda.profiler.start()
     e0.record(stream)
     batch.step(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     clk = clocks.stop()
     batch_ms = e0.elapsed_time(e1)
     launches = ops[0].launch_count() - launches0
+    batch.close()
+    # the same batch with the contractions as shared launches over all problems
+    for op, y, prm in zip(ops, ys, params):
+        op.fista_init(y, prm)
+    batch = sw.Batch(ops, shared=True)
+    batch.step(args.warmup)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    batch.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    shared_ms = e0.elapsed_time(e1)
+    shared = batch.shared_in_use()
+    shared_launches = batch.contraction_launches()
     batch.close()
     # the same problems one after another (each handle's own graph)
     for op, y, prm in zip(ops, ys, params):
         op.fista_init(y, prm)
         op.fista_step(args.warmup)
     torch.cuda.synchronize()
+    torch.cuda.profiler.start()
     e0.record(stream)
     for op in ops:
         op.fista_step(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     seq_ms = e0.elapsed_time(e1)
     # plain FP32, one after another
     fp32_ms = 0.0
@@ -733,6 +752,8 @@ def run_batch(args, device):
                    "l2": "working set larger than L2 (no flush)",
                    "problems": [f"{p.geom.X}x{p.geom.Y}x{p.geom.Z} T{p.geom.T} k{p.geom.k} "
                                 f"N{p.geom.N} P{p.geom.P}" for p in probs]},
+        "shared_launch_it_s": n * args.steps / (shared_ms / 1e3) if shared else None,
+        "shared_launch_contractions_per_path": shared_launches,
         "sequential_same_precision_it_s": n * args.steps / (seq_ms / 1e3),
         "sequential_fp32_plain_it_s": n / (fp32_ms / 1e3),
         "speedup_vs_sequential_fp32": value / (n / (fp32_ms / 1e3)),

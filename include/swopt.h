@@ -589,6 +589,29 @@ swopt_status swopt_batch_create(swopt_handle* const* handles, int count, swopt_b
 swopt_status swopt_batch_step(swopt_batch* b, int iters, void* stream);
 swopt_status swopt_batch_destroy(swopt_batch* b);
 
+/* Shared launches (shared_launch = 1; default 0): the batch's graph runs the contractions
+ * of all problems as persistent launches over a work list of every
+ * problem's tile-states (for A, then for A^T, per gradient path), the
+ * other steps per problem (problems whose halos and stage rings do not fit
+ * one CTA's shared memory together go to separate launches); it falls back to
+ * a stream per problem for FP32 or FP8 operators.  shared_launch = 0 takes a
+ * stream per problem.  Measured on 16 uneven problems, the shared launches ran
+ * at 0.55 of the stream-per-problem graph: a shared stage ring is sized for the
+ * largest problem's stages, so problems with small stages keep fewer bytes in
+ * flight than in their own launches.  The sums per problem are the same either way, but for
+ * the order of FP32 addition in a tile-state that the problem's own launch
+ * splits over CTAs (a shared launch takes tile-states whole).
+ * Errors: INVALID_ARG for a null batch. */
+swopt_status swopt_batch_configure(swopt_batch* b, int shared_launch);
+
+/* *shared_launch_in_use = 1 when every iteration graph captured so far uses
+ * shared launches (0 before the first step); *contraction_launches (may be
+ * NULL): the most contraction kernels of one gradient path in a captured
+ * iteration (shared launches: the groups of A plus those of A^T; a stream per
+ * problem: two per problem). */
+swopt_status swopt_batch_query(swopt_batch* b, int* shared_launch_in_use,
+                               int* contraction_launches);
+
 #ifdef __cplusplus
 }
 #endif

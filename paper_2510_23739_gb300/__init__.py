@@ -117,6 +117,9 @@ _SIGS = {
                             ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "swopt_batch_step": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "swopt_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "swopt_batch_configure": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "swopt_batch_query": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "swopt_profile_enable": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "swopt_use_graphs": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "swopt_profile_read": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -654,15 +657,32 @@ def two_step(geom, K, sw, y, acoustic: "SolveParams", unmixing: "SolveParams", b
 
 class Batch:
     """Independent problems stepped together (``swopt_batch_*``): every
-    iteration of all of them is one CUDA graph with a stream per problem.
-    Each operator must have been ``fista_init``-ed (same refine_every)."""
+    iteration of all of them is one CUDA graph with a stream per problem, or
+    (``shared=True``) with the contractions as persistent launches over all
+    problems' tile-states.  Each operator must have been ``fista_init``-ed
+    (same refine_every)."""
 
-    def __init__(self, ops):
+    def __init__(self, ops, shared=False):
         self.ops = list(ops)
         arr = (ctypes.c_void_p * len(self.ops))(*[o._h.value for o in self.ops])
         b = ctypes.c_void_p()
         _check(lib().swopt_batch_create(arr, len(self.ops), ctypes.byref(b)))
         self._b = b
+        if shared:
+            _check(lib().swopt_batch_configure(self._b, 1))
+
+    def shared_in_use(self):
+        """True when every captured iteration graph uses shared launches."""
+        v, n = ctypes.c_int(), ctypes.c_int()
+        _check(lib().swopt_batch_query(self._b, ctypes.byref(v), ctypes.byref(n)))
+        return bool(v.value)
+
+    def contraction_launches(self):
+        """Contraction kernels of one gradient path per iteration (see
+        swopt_batch_query)."""
+        v, n = ctypes.c_int(), ctypes.c_int()
+        _check(lib().swopt_batch_query(self._b, ctypes.byref(v), ctypes.byref(n)))
+        return n.value
 
     def step(self, iters=1, stream=None):
         _check(lib().swopt_batch_step(self._b, int(iters), _stream(stream)))

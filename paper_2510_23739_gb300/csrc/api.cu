@@ -6,6 +6,7 @@
 #include <cstring>
 #include <algorithm>
 #include <cstdio>
+#include <memory>
 #include <vector>
 
 #include "swopt_internal.cuh"
@@ -1690,6 +1691,10 @@ struct swopt_batch {
     std::vector<uint64_t> gen;          // handle graph generations at capture
     int64_t kernels[3] = {0, 0, 0};
     int64_t iter = 0;
+    bool shared = false;                // contractions as shared launches over all problems
+    bool shared_used[3] = {false, false, false};
+    int contraction_launches[3] = {0, 0, 0};  // per iteration of a captured kind
+    std::vector<swopt::TcMulti*> multi; // the shared launches of the captured graphs
 };
 
 namespace {
@@ -1700,6 +1705,152 @@ void batch_release_graphs(swopt_batch* b)
         if (g) cudaGraphExecDestroy(g);
         g = nullptr;
     }
+    for (auto* m : b->multi) tc_multi_destroy(m);
+    b->multi.clear();
+}
+
+// Prepares one shared launch of A (adj false) or A^T over the batch, with every
+// handle inside a gate (want >= 0) and / or at its resync precision (ref).
+swopt_status batch_multi(swopt_batch* b, bool adj, bool ytil, int want, bool ref, TcMulti** out)
+{
+    std::vector<std::unique_ptr<GateScope>> gs;
+    std::vector<std::unique_ptr<RefScope>> rs;
+    for (swopt_handle* h : b->hs) {
+        if (want >= 0) gs.emplace_back(new GateScope(h, want));
+        if (ref) rs.emplace_back(new RefScope(h, h->prm.refine_precision));
+    }
+    const swopt_status s = tc_multi_create(b->hs.data(), (int)b->hs.size(), adj, ytil, out);
+    if (s == SWOPT_OK) b->multi.push_back(*out);
+    return s;
+}
+
+// One FISTA iteration of every problem (kind as iteration_kind) with the
+// contractions of all problems in shared persistent launches (one for A, one
+// for A^T, per gradient path) and the other steps launched per problem, all on
+// st; the same arithmetic as fista_iteration per handle.
+swopt_status batch_iteration_shared(swopt_batch* b, int kind, TcMulti* const* m, cudaStream_t st)
+{
+    const bool refined = b->hs[0]->prm.refine_every > 0;
+    if (!refined) {
+        for (swopt_handle* h : b->hs) SW_TRY(tc_states(h, h->xi, st));
+        SW_TRY(tc_multi_launch(m[0], st));
+        SW_TRY(tc_multi_launch(m[1], st));
+        for (swopt_handle* h : b->hs) SW_TRY(launch_pt(h, h->g, h->xi, (float)h->step, h->zin, 1, st));
+        for (swopt_handle* h : b->hs) SW_TRY(fista_prox_momentum(h, false, st));
+        return SWOPT_OK;
+    }
+    for (swopt_handle* h : b->hs) SW_TRY(fista_prox_momentum(h, true, st));
+    if (kind == 2)
+        for (swopt_handle* h : b->hs)
+            SW_TRY(refine_decide(h, h->tmp, h->c, SC_BUDGET, h->prm.refine_every,
+                                 h->prm.refine_budget, st));
+    if (kind == 0 || kind == 2) {  // the increment
+        const int want = kind == 2 ? 0 : -1;
+        for (swopt_handle* h : b->hs) {
+            std::unique_ptr<GateScope> g(want >= 0 ? new GateScope(h, want) : nullptr);
+            SW_TRY(tc_states(h, h->tmp, st));
+        }
+        SW_TRY(tc_multi_launch(m[0], st));
+        SW_TRY(tc_multi_launch(m[1], st));
+        for (swopt_handle* h : b->hs) {
+            std::unique_ptr<GateScope> g(want >= 0 ? new GateScope(h, want) : nullptr);
+            SW_TRY(launch_pt_refine(h, h->g, h->xi, (float)h->step, h->G, h->zin, 1, st));
+        }
+    }
+    if (kind == 1 || kind == 2) {  // the exact gradient at the resync precision
+        const int want = kind == 2 ? 1 : -1;
+        for (swopt_handle* h : b->hs) {
+            std::unique_ptr<GateScope> g(want >= 0 ? new GateScope(h, want) : nullptr);
+            RefScope r(h, h->prm.refine_precision);
+            SW_TRY(tc_states(h, h->c, st));
+        }
+        SW_TRY(tc_multi_launch(m[2], st));
+        SW_TRY(tc_multi_launch(m[3], st));
+        for (swopt_handle* h : b->hs) {
+            std::unique_ptr<GateScope> g(want >= 0 ? new GateScope(h, want) : nullptr);
+            SW_TRY(launch_pt_refine(h, h->g, h->xi, (float)h->step, h->G, h->zin, 0, st));
+        }
+    }
+    return SWOPT_OK;
+}
+
+// Captures kind `kind` with shared contraction launches; UNSUPPORTED (nothing
+// captured) when the problems cannot share them.
+swopt_status batch_capture_shared(swopt_batch* b, int kind)
+{
+    for (swopt_handle* h : b->hs)
+        if (!use_tc(h) || !h->tc) {
+            set_error("shared launches need tensor-core precisions");
+            return SWOPT_ERR_UNSUPPORTED;
+        }
+    const bool refined = b->hs[0]->prm.refine_every > 0;
+    TcMulti* m[4] = {nullptr, nullptr, nullptr, nullptr};
+    const size_t keep = b->multi.size();
+    auto undo = [&](swopt_status s) {
+        while (b->multi.size() > keep) {
+            tc_multi_destroy(b->multi.back());
+            b->multi.pop_back();
+        }
+        return s;
+    };
+    swopt_status s = SWOPT_OK;
+    if (!refined) {
+        s = batch_multi(b, false, true, -1, false, &m[0]);
+        if (s == SWOPT_OK) s = batch_multi(b, true, false, -1, false, &m[1]);
+    } else {
+        if (kind == 0 || kind == 2) {
+            const int want = kind == 2 ? 0 : -1;
+            s = batch_multi(b, false, false, want, false, &m[0]);
+            if (s == SWOPT_OK) s = batch_multi(b, true, false, want, false, &m[1]);
+        }
+        if (s == SWOPT_OK && (kind == 1 || kind == 2)) {
+            const int want = kind == 2 ? 1 : -1;
+            s = batch_multi(b, false, true, want, true, &m[2]);
+            if (s == SWOPT_OK) s = batch_multi(b, true, false, want, true, &m[3]);
+        }
+    }
+    if (s != SWOPT_OK) return undo(s);
+    const int n = (int)b->hs.size();
+    std::vector<int64_t> l0(n);
+    std::vector<bool> prof(n);
+    for (int i = 0; i < n; ++i) {
+        l0[i] = b->hs[i]->launches;
+        prof[i] = b->hs[i]->profile;
+        b->hs[i]->profile = false;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        s = batch_iteration_shared(b, kind, m, b->cap);
+        e = cudaStreamEndCapture(b->cap, &g);
+    }
+    int64_t kernels = 0;
+    for (int i = 0; i < n; ++i) {
+        kernels += b->hs[i]->launches - l0[i];
+        b->hs[i]->launches = l0[i];
+        b->hs[i]->profile = prof[i];
+    }
+    if (s != SWOPT_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (s == SWOPT_OK) {
+            set_error("batch capture failed: %s", cudaGetErrorString(e));
+            s = SWOPT_ERR_CUDA;
+        }
+        return undo(s == SWOPT_ERR_UNSUPPORTED ? SWOPT_ERR_CUDA : s);
+    }
+    e = cudaGraphInstantiate(&b->gexec[kind], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->gexec[kind] = nullptr;
+        set_error("batch graph instantiation failed: %s", cudaGetErrorString(e));
+        return undo(SWOPT_ERR_CUDA);
+    }
+    b->kernels[kind] = kernels;
+    b->shared_used[kind] = true;
+    b->contraction_launches[kind] = 0;
+    for (TcMulti* x : m)
+        if (x) b->contraction_launches[kind] += tc_multi_groups(x);
+    return SWOPT_OK;
 }
 
 swopt_status batch_capture(swopt_batch* b, int kind)
@@ -1847,7 +1998,13 @@ swopt_status swopt_batch_step(swopt_batch* b, int iters, void* stream)
     for (int it = 0; it < iters; ++it) {
         for (int i = 0; i < n; ++i) SW_TRY(ensure_ref(b->hs[i]));
         const int kind = iteration_kind(b->hs[0]);
-        if (!b->gexec[kind]) SW_TRY(batch_capture(b, kind));
+        if (!b->gexec[kind]) {
+            swopt_status s = SWOPT_ERR_UNSUPPORTED;
+            b->shared_used[kind] = false;
+            if (b->shared) s = batch_capture_shared(b, kind);
+            if (s == SWOPT_ERR_UNSUPPORTED) s = batch_capture(b, kind);
+            SW_TRY(s);
+        }
         SW_CUDA(cudaGraphLaunch(b->gexec[kind], st));
         for (int i = 0; i < n; ++i) {
             if (kind == 1) ++b->hs[i]->resyncs;
@@ -1856,6 +2013,40 @@ swopt_status swopt_batch_step(swopt_batch* b, int iters, void* stream)
         b->hs[0]->launches += b->kernels[kind];  // counted once, on the first handle
         ++b->iter;
     }
+    return SWOPT_OK;
+}
+
+swopt_status swopt_batch_configure(swopt_batch* b, int shared_launch)
+{
+    clear_error();
+    if (!b) {
+        set_error("null batch");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    b->shared = shared_launch != 0;
+    batch_release_graphs(b);
+    return SWOPT_OK;
+}
+
+swopt_status swopt_batch_query(swopt_batch* b, int* shared_launch_in_use,
+                               int* contraction_launches)
+{
+    clear_error();
+    if (!b || !shared_launch_in_use) {
+        set_error("null argument");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    bool any = false, all = true;
+    int most = 0;
+    for (int k = 0; k < 3; ++k)
+        if (b->gexec[k]) {
+            any = true;
+            all = all && b->shared_used[k];
+            most = std::max(most, b->shared_used[k] ? b->contraction_launches[k]
+                                                    : 2 * (int)b->hs.size());
+        }
+    *shared_launch_in_use = any && all ? 1 : 0;
+    if (contraction_launches) *contraction_launches = most;
     return SWOPT_OK;
 }
 

@@ -333,6 +333,8 @@ struct TcArgs {
     const unsigned* in_word;    // FP8: the largest scaled entry of the input images (sigma = 256 / it)
     unsigned* max_word;         // FP8 forward mode 0: atomic max of |out| s_t (the residual's scale)
     const float* s_out;         // FP8 forward: the adjoint's sample scales s_t
+    const int* split_slot;      // shared launches: partial-sum slot of each split tile-state
+                                // (null: the tile-state's own index)
 };
 
 // ---------------------------------------------------------------------------
@@ -351,6 +353,7 @@ struct TcArgs {
 // in piece order) and runs the epilogue.  No CTA waits for another.
 // ---------------------------------------------------------------------------
 struct TcUnit {
+    int p;               // problem (0 for a single-problem launch)
     int ts, r0, r1;      // tile-state (m * tiles + tile) and its runs [r0, r1)
     int m, x0, y0;
     int piece, pieces;   // this CTA's piece of the tile-state, of how many
@@ -462,7 +465,116 @@ __device__ __forceinline__ void issue_stage(int kind, const IssueCfg& c, uint32_
     }
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
+// A launch over several problems: the runs of every problem's tile-states, in
+// problem order, shared out equally over the CTAs (TcMany::unit).  The stage ring, the halo region and
+// the TMEM columns are sized for the largest problem.
+struct TcBatchMeta {
+    long long piece0;  // the problem's first run in the launch's work
+    int tab_off;       // its run table's first entry among the staged tables
+    int pad;
+};
+
+struct TcBatchArgs {
+    const TcArgs* probs;      // [n] in device memory
+    const TcBatchMeta* meta;  // [n]
+    int n;
+    long long W;              // runs of all problems
+    int NS, NBUF;
+    uint32_t halo_region;     // bytes of the largest halo (all terms)
+    uint32_t stage_slot;      // bytes of the largest stage (all terms)
+    uint32_t tcols;           // TMEM columns allocated
+    uint32_t buf_stride;      // TMEM columns between the accumulator buffers
+    const uint4* tab;         // the problems' group / run tables, concatenated
+    int tab_n;
+    int* err;
+};
+
+// The work and arguments of a launch over one problem ...
+struct TcOne {
+    const TcArgs& a;
+    __device__ int NS() const { return a.NS; }
+    __device__ int NBUF() const { return a.NBUF; }
+    __device__ uint32_t halo_region() const
+    {
+        return (uint32_t)(a.GA * a.HY * a.HX) * 16u * (uint32_t)a.terms;
+    }
+    __device__ uint32_t stage_slot() const { return a.stage_bytes * (uint32_t)a.terms; }
+    __device__ uint32_t tcols() const { return a.tcols; }
+    __device__ uint32_t buf_stride() const { return (uint32_t)(a.RA * a.MB * a.MT * kTilePos); }
+    __device__ const uint4* tab() const { return a.tab; }
+    __device__ int tab_n() const { return a.tab_n; }
+    __device__ int* err() const { return a.err; }
+    __device__ double* partials() const { return a.partials; }
+    __device__ unsigned* max_word() const { return a.max_word; }
+    __device__ bool unit(int k, TcUnit& u) const
+    {
+        u.p = 0;
+        return tc_unit(a, k, u);
+    }
+    __device__ const TcArgs& args(int) const { return a; }
+    __device__ int tab_off(int) const { return 0; }
+    __device__ bool skip(const TcArgs&) const { return false; }
+};
+
+// ... and over several (the gate of each problem is read per tile-state).
+struct TcMany {
+    const TcBatchArgs& B;
+    __device__ int NS() const { return B.NS; }
+    __device__ int NBUF() const { return B.NBUF; }
+    __device__ uint32_t halo_region() const { return B.halo_region; }
+    __device__ uint32_t stage_slot() const { return B.stage_slot; }
+    __device__ uint32_t tcols() const { return B.tcols; }
+    __device__ uint32_t buf_stride() const { return B.buf_stride; }
+    __device__ const uint4* tab() const { return B.tab; }
+    __device__ int tab_n() const { return B.tab_n; }
+    __device__ int* err() const { return B.err; }
+    __device__ double* partials() const { return nullptr; }
+    __device__ unsigned* max_word() const { return nullptr; }
+    // CTA b of G takes the b-th of G equal shares of the W runs of all
+    // problems in order, [L, U) with b W <= x G < (b + 1) W, cut at tile-state
+    // boundaries into units; a tile-state cut between CTAs is finished by the
+    // last of them to arrive (the partial-sum path of the epilogue)
+    __device__ static long long ceil_div(long long x, long long d)
+    {
+        return x >= 0 ? (x + d - 1) / d : -((-x) / d);
+    }
+    __device__ bool unit(int k, TcUnit& u) const
+    {
+        const long long G = gridDim.x;
+        const long long L = ceil_div((long long)blockIdx.x * B.W, G);
+        const long long U = ceil_div(((long long)blockIdx.x + 1) * B.W, G);
+        for (int p = 0; p < B.n; ++p) {
+            const TcArgs& a = B.probs[p];
+            const long long R = a.runs, base = B.meta[p].piece0, end = base + a.wq * R;
+            const long long lo = L > base ? L : base, hi = U < end ? U : end;
+            if (lo >= hi) continue;
+            const long long ts0 = (lo - base) / R, ts1 = (hi - 1 - base) / R;
+            if (k <= ts1 - ts0) {
+                const long long ts = ts0 + k, x0 = base + ts * R;
+                u.p = p;
+                u.ts = (int)ts;
+                u.r0 = (int)(lo > x0 ? lo - x0 : 0);
+                u.r1 = (int)(hi - x0 < R ? hi - x0 : R);
+                const int first = (int)(x0 * G / B.W), last = (int)((x0 + R - 1) * G / B.W);
+                u.pieces = last - first + 1;
+                u.piece = (int)blockIdx.x - first;
+                u.m = u.ts / a.ntiles;
+                const int tile = u.ts - u.m * a.ntiles;
+                u.x0 = (tile % a.groupsX) * 8 * a.MT;
+                u.y0 = (tile / a.groupsX) * kTileY;
+                return true;
+            }
+            k -= (int)(ts1 - ts0 + 1);
+        }
+        return false;
+    }
+    __device__ const TcArgs& args(int p) const { return B.probs[p]; }
+    __device__ int tab_off(int p) const { return B.meta[p].tab_off; }
+    __device__ bool skip(const TcArgs& a) const { return gated_off(a.gate, a.want); }
+};
+
+template <class Src>
+__device__ __forceinline__ void tc_body(const Src& src)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t bar_full[kMaxStages];
@@ -474,31 +586,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
     __shared__ double s_red[4];
     __shared__ int s_last;
     __shared__ int s_eok[4];
-    // a closed gate: return before any barrier, TMEM or copy is set up
-    if (gated_off(a.gate, a.want)) return;
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int kk = a.k * a.k;
-    const uint32_t npos = (uint32_t)(a.HY * a.HX);
-    const uint32_t a_slice = npos * 16u;                       // bytes of one image slice
-    const uint32_t a_part = (uint32_t)a.GA * a_slice;          // hi (or lo) halo bytes
+    const int NS = src.NS(), NBUF = src.NBUF();
+    int* const err = src.err();
+    // shared memory: the halo region, the ring of NS stage slots, the tables
     const uint32_t sA = __shfl_sync(0xffffffffu, smem_u32(smem), 0);
-    const uint32_t halo_region = a_part * (uint32_t)a.terms;
-    const uint32_t sW = sA + halo_region;
-    const uint32_t stage_total = a.stage_bytes * (uint32_t)a.terms;
-    const uint32_t tab_region = halo_region + (uint32_t)a.NS * stage_total;
+    const uint32_t sW = sA + src.halo_region();
+    const uint32_t stage_slot = src.stage_slot();
+    const uint32_t tab_region = src.halo_region() + (uint32_t)NS * stage_slot;
     const uint4* s_tab = reinterpret_cast<const uint4*>(smem + tab_region);
-    // TMEM columns of one accumulator buffer: [set][block][tile][256 positions]
-    const uint32_t buf_cols = (uint32_t)(a.RA * a.MB * a.MT * kTilePos);
+    // TMEM columns between the accumulator buffers (a buffer: [set][block][tile][256 positions])
+    const uint32_t buf_stride = src.buf_stride();
 
-    // the group / run table is small: stage it once
-    for (int i = threadIdx.x; i < a.tab_n; i += kTcThreads)
-        reinterpret_cast<uint4*>(smem + tab_region)[i] = a.tab[i];
+    // the group / run tables are small: stage them once
+    for (int i = threadIdx.x; i < src.tab_n(); i += kTcThreads)
+        reinterpret_cast<uint4*>(smem + tab_region)[i] = src.tab()[i];
     if (threadIdx.x == 0) {
         // the issuer commits to the stage-empty, halo-empty and
         // accumulator-full barriers; every epilogue thread arrives on
         // accumulator-free
-        for (int s = 0; s < a.NS; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
             mbar_init(smem_u32(&bar_empty[s]), 1);
         }
@@ -516,7 +623,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&s_tmem)),
-                     "r"(a.tcols)
+                     "r"(src.tcols())
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -529,7 +636,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
     // zero the accumulator columns of every buffer
     if (warp >= 2 && warp <= 5) {
         const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-        for (uint32_t cb = 0; cb < (uint32_t)a.NBUF * buf_cols / 16u; ++cb)
+        for (uint32_t cb = 0; cb < (uint32_t)NBUF * buf_stride / 16u; ++cb)
             tmem_zero16(tmem + lanes + cb * 16u);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
@@ -546,10 +653,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         int a_fills = 0;
         bool ok = true;
         TcUnit u;
-        for (int k = 0; ok && tc_unit(a, k, u); ++k) {
+        for (int k = 0; ok && src.unit(k, u); ++k) {
+            const TcArgs& a = src.args(u.p);
+            if (src.skip(a)) continue;
+            const int kk = a.k * a.k;
+            const uint32_t a_slice = (uint32_t)(a.HY * a.HX) * 16u;  // bytes of one image slice
+            const uint32_t a_part = (uint32_t)a.GA * a_slice;        // hi (or lo) halo bytes
+            const uint4* tb = s_tab + src.tab_off(u.p);
             int rb = 0;  // first run of group g
             for (int g = 0; g < a.NG && ok; ++g) {
-                const uint4 hd = s_tab[g];  // {base16, tap bytes, taps per run, pairs}
+                const uint4 hd = tb[g];  // {base16, tap bytes, taps per run, pairs}
                 const int nr = (kk + (int)hd.z - 1) / (int)hd.z;
                 const int lo = max(u.r0, rb), hi = min(u.r1, rb + nr);
                 rb += nr;
@@ -582,17 +695,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                     }
                     if (lane == 0) {
                         const uint32_t bar = smem_u32(&bar_full[stage]);
-                        const uint32_t dst = sW + (uint32_t)stage * stage_total;
+                        const uint32_t dst = sW + (uint32_t)stage * stage_slot;
                         const uint32_t bytes = (uint32_t)nt * hd.y;
-                        const size_t src = ((size_t)hd.x * 16 + (size_t)d0 * hd.y) / 2;  // elements
+                        const size_t wsrc = ((size_t)hd.x * 16 + (size_t)d0 * hd.y) / 2;  // elements
                         mbar_expect_tx(bar, bytes * (uint32_t)a.terms);
                         for (int tt = 0; tt < a.terms; ++tt)
-                            bulk_g2s(dst + (uint32_t)tt * a.stage_bytes, a.w[tt] + src, bytes,
+                            bulk_g2s(dst + (uint32_t)tt * a.stage_bytes, a.w[tt] + wsrc, bytes,
                                      bar);
                     }
                     fills[stage]++;
                     __syncwarp();
-                    if (++stage == a.NS) {
+                    if (++stage == NS) {
                         stage = 0;
                         phase ^= 1u;
                     }
@@ -601,18 +714,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         }
         if (!ok && lane == 0) {
             s_abort = 1;
-            atomicExch(a.err, 1);
+            atomicExch(err, 1);
         }
         // drain: every copy this warp issued has landed before the CTA exits
         if (lane == 0) {
             volatile int never = 0;
-            for (int s = 0; s < a.NS; ++s)
+            for (int s = 0; s < NS; ++s)
                 if (fills[s] > 0 &&
                     !mbar_wait(smem_u32(&bar_full[s]), (uint32_t)(fills[s] - 1) & 1u, &never))
-                    atomicExch(a.err, 2);
+                    atomicExch(err, 2);
             if (a_fills > 0 &&
                 !mbar_wait(smem_u32(&bar_afull), (uint32_t)(a_fills - 1) & 1u, &never))
-                atomicExch(a.err, 2);
+                atomicExch(err, 2);
         }
     } else if (warp == 1) {
         // ------------------------------ MMA issuer ----------------------------
@@ -627,35 +740,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         const bool leader = elect_one();
         const uint64_t adesc_c = ((uint64_t)(2048u >> 4) << 16) | ((uint64_t)(128u >> 4) << 32) |
                                  ((uint64_t)1 << 46);
-        const uint64_t bdesc_c = ((uint64_t)(a_slice >> 4) << 16) | ((uint64_t)a.HX << 32) |
-                                 ((uint64_t)1 << 46);
-        // FP32 accumulator; BF16 (format 1) or E4M3 (format 0) A and B, K-major
-        const uint32_t ab_fmt = a.fp8 ? 0u : ((1u << 7) | (1u << 10));
-        const uint32_t idesc = (1u << 4) | ab_fmt |
-                               (((uint32_t)kTilePos >> 3) << 17) | (((uint32_t)kRows >> 4) << 24);
-        const IssueCfg ic{(uint32_t)(a.MB * kBlockBytes), (uint32_t)(a_part >> 4),
-                          (uint32_t)(a.stage_bytes >> 4), idesc};
-        const int kind = issue_kind(a.MT, a.MB, a.terms, a.RA, a.fp8);
         int local = 0;  // this CTA's runs so far (ring position)
         int ag = 0;     // halo fills consumed
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
+        int done = 0;   // units taken (the accumulator buffers alternate over them)
         TcUnit u;
-        for (int k = 0; ok && tc_unit(a, k, u); ++k) {
-            const int buf = a.NBUF == 2 ? (k & 1) : 0;
-            if (k >= a.NBUF) {  // the epilogue has drained this buffer
-                if (!mbar_wait_warp(smem_u32(&bar_accfree[buf]), (uint32_t)(k / a.NBUF - 1) & 1u,
+        for (int k = 0; ok && src.unit(k, u); ++k) {
+            const TcArgs& a = src.args(u.p);
+            if (src.skip(a)) continue;
+            const int kb = done++;
+            const int kk = a.k * a.k;
+            const uint32_t a_slice = (uint32_t)(a.HY * a.HX) * 16u;
+            const uint32_t a_part = (uint32_t)a.GA * a_slice;
+            const uint64_t bdesc_c = ((uint64_t)(a_slice >> 4) << 16) | ((uint64_t)a.HX << 32) |
+                                     ((uint64_t)1 << 46);
+            // FP32 accumulator; BF16 (format 1) or E4M3 (format 0) A and B, K-major
+            const uint32_t ab_fmt = a.fp8 ? 0u : ((1u << 7) | (1u << 10));
+            const uint32_t idesc = (1u << 4) | ab_fmt | (((uint32_t)kTilePos >> 3) << 17) |
+                                   (((uint32_t)kRows >> 4) << 24);
+            const IssueCfg ic{(uint32_t)(a.MB * kBlockBytes), (uint32_t)(a_part >> 4),
+                              (uint32_t)(a.stage_bytes >> 4), idesc};
+            const int kind = issue_kind(a.MT, a.MB, a.terms, a.RA, a.fp8);
+            const uint4* tb = s_tab + src.tab_off(u.p);
+            const int buf = NBUF == 2 ? (kb & 1) : 0;
+            if (kb >= NBUF) {  // the epilogue has drained this buffer
+                if (!mbar_wait_warp(smem_u32(&bar_accfree[buf]), (uint32_t)(kb / NBUF - 1) & 1u,
                                     &s_abort)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
             }
-            const uint32_t tbuf = tmem + (uint32_t)buf * buf_cols;
+            const uint32_t tbuf = tmem + (uint32_t)buf * buf_stride;
             int rb = 0;  // first run of group g
             for (int g = 0; g < a.NG && ok; ++g) {
-                const uint4 hd = s_tab[g];
+                const uint4 hd = tb[g];
                 const int tpr = __shfl_sync(0xffffffffu, (int)hd.z, 0);
                 const int nr = (kk + tpr - 1) / tpr;
                 const int lo = max(u.r0, rb), hi = min(u.r1, rb + nr);
@@ -678,18 +799,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                     }
                     tc_fence_after();
                     // halo offsets of this stage's taps (16-B units), from the run table
-                    const uint4 ro = s_tab[a.NG + (run - gb)];
+                    const uint4 ro = tb[a.NG + (run - gb)];
                     const uint32_t ow[4] = {__shfl_sync(0xffffffffu, ro.x, 0),
                                             __shfl_sync(0xffffffffu, ro.y, 0),
                                             __shfl_sync(0xffffffffu, ro.z, 0),
                                             __shfl_sync(0xffffffffu, ro.w, 0)};
-                    const uint32_t wst = sW + (uint32_t)stage * stage_total;
+                    const uint32_t wst = sW + (uint32_t)stage * stage_slot;
                     if (leader) issue_stage(kind, ic, tbuf, adesc_c | (uint64_t)(wst >> 4),
                                             bdesc_c | (uint64_t)(sA >> 4), ow, nt);
                     __syncwarp();
                     if (leader) tc_commit(smem_u32(&bar_empty[stage]));
                     __syncwarp();
-                    if (++stage == a.NS) {
+                    if (++stage == NS) {
                         stage = 0;
                         phase ^= 1u;
                     }
@@ -702,13 +823,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         }
         if (!ok && leader) {
             s_abort = 1;
-            atomicExch(a.err, 1);
+            atomicExch(err, 1);
         }
         // every MMA of this issuer has completed before TMEM is freed
         if (leader) tc_commit(smem_u32(&bar_drain));
         __syncwarp();
         volatile int never = 0;
-        if (!mbar_wait_warp(smem_u32(&bar_drain), 0u, &never) && leader) atomicExch(a.err, 2);
+        if (!mbar_wait_warp(smem_u32(&bar_drain), 0u, &never) && leader) atomicExch(err, 2);
     } else if (warp >= 2 && warp <= 5) {
         // ------------------------------ epilogue ------------------------------
         // Thread li (= 32 q + lane) owns TMEM lane li: channel mb * 128 + li of
@@ -717,26 +838,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
         const int li = q * 32 + lane;
         double part = 0.0;
         const uint32_t lanes = (uint32_t)(q * 32) << 16;
-        const size_t unit_floats = (size_t)a.MB * a.MT * kTilePos * kRows;
-        const size_t S = (size_t)a.Y * a.X;
-        const float* __restrict__ ytil = a.ytil;
-        // FP8: the accumulators hold sigma (sum of products); sigma = 256 / (largest
-        // scaled input entry), so the output is the accumulator times that / 256
-        const float inv_sigma = a.fp8 ? __uint_as_float(*a.in_word) * (1.0f / 256.0f) : 1.0f;
         float rmax = 0.f;  // FP8 forward: largest |output| s_t of this thread
+        int done = 0;
         TcUnit u;
-        for (int k = 0; tc_unit(a, k, u); ++k) {
-            const int buf = a.NBUF == 2 ? (k & 1) : 0;
-            const uint32_t tbuf = tmem + lanes + (uint32_t)buf * buf_cols;
+        for (int k = 0; src.unit(k, u); ++k) {
+            const TcArgs& a = src.args(u.p);
+            if (src.skip(a)) continue;
+            const int kb = done++;
+            const size_t unit_floats = (size_t)a.MB * a.MT * kTilePos * kRows;
+            const uint32_t buf_cols = (uint32_t)(a.RA * a.MB * a.MT * kTilePos);
+            const size_t S = (size_t)a.Y * a.X;
+            const float* __restrict__ ytil = a.ytil;
+            // FP8: the accumulators hold sigma (sum of products); sigma = 256 / (largest
+            // scaled input entry), so the output is the accumulator times that / 256
+            const float inv_sigma = a.fp8 ? __uint_as_float(*a.in_word) * (1.0f / 256.0f) : 1.0f;
+            const int buf = NBUF == 2 ? (kb & 1) : 0;
+            const uint32_t tbuf = tmem + lanes + (uint32_t)buf * buf_stride;
             const bool w_ok =
-                mbar_wait_warp(smem_u32(&bar_accfull[buf]), (uint32_t)(k / a.NBUF) & 1u, &s_abort);
+                mbar_wait_warp(smem_u32(&bar_accfull[buf]), (uint32_t)(kb / NBUF) & 1u, &s_abort);
             tc_fence_after();
             if (lane == 0) s_eok[q] = w_ok ? 1 : 0;
             asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps
             if (!(s_eok[0] && s_eok[1] && s_eok[2] && s_eok[3])) {
                 if (lane == 0) {
                     s_abort = 1;
-                    atomicExch(a.err, 1);
+                    atomicExch(err, 1);
                 }
                 break;  // the same decision in all four warps
             }
@@ -750,8 +876,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
                     for (int e = 0; e < 16; ++e) v[e] += w[e];
                 }
             };
+            const size_t slot = a.split_slot ? (size_t)a.split_slot[u.ts] : (size_t)u.ts;
             auto part_at = [&](int piece, int mb, int ti, int cb) -> float* {
-                return a.part + ((size_t)u.ts * a.max_pieces + piece) * unit_floats +
+                return a.part + (slot * a.max_pieces + piece) * unit_floats +
                        ((((size_t)mb * a.MT + ti) * (kTilePos / 16) + cb) * kRows + li) * 16;
             };
             bool last = true;
@@ -900,30 +1027,44 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
             mbar_arrive(smem_u32(&bar_accfree[buf]));
             asm volatile("bar.sync 1, 128;" ::: "memory");  // s_eok and s_last are reused
         }
-        if (a.partials) {
+        if (src.partials()) {
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
             if (lane == 0) s_red[q] = part;
         }
-        if (a.max_word) {
+        if (src.max_word()) {
             // non-negative floats order as their bit patterns
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1)
                 rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
-            if (lane == 0) atomicMax(a.max_word, __float_as_uint(rmax));
+            if (lane == 0) atomicMax(src.max_word(), __float_as_uint(rmax));
         }
     }
 
     tc_fence_before();
     __syncthreads();
-    if (a.partials && threadIdx.x == 0)
-        a.partials[blockIdx.x] = s_red[0] + s_red[1] + s_red[2] + s_red[3];
+    if (src.partials() && threadIdx.x == 0)
+        src.partials()[blockIdx.x] = s_red[0] + s_red[1] + s_red[2] + s_red[3];
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(a.tcols)
+                     "r"(src.tcols())
                      : "memory");
     }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) tc_conv_kernel(const TcArgs a)
+{
+    // a closed gate: return before any barrier, TMEM or copy is set up
+    if (gated_off(a.gate, a.want)) return;
+    tc_body(TcOne{a});
+}
+
+// Several problems' tile-states in one persistent launch (no FP8, no data-fit
+// partial sums).
+__global__ void __launch_bounds__(kTcThreads, 1) tc_conv_many_kernel(const TcBatchArgs B)
+{
+    tc_body(TcMany{B});
 }
 
 // P into the padded BF16 state images: for each (m, slice, y, x) the 8
@@ -1970,6 +2111,230 @@ swopt_status tc_adjoint(swopt_handle* h, cudaStream_t st)
     prof_begin(h, 1, st, &rec);
     SW_TRY(launch_conv(h, t->A, a, st));
     prof_end(h, &rec, st);
+    return SWOPT_OK;
+}
+
+// A prepared launch of the contraction over several handles: every
+// problem's tile-states, whole, in persistent kernels over a work list.  The
+// problems are packed greedily (largest halo first) into groups whose largest
+// halo, a ring of at least two of their largest stages and their run tables
+// fit one CTA's shared memory; each group is one launch (usually one or two).
+struct TcMultiGroup {
+    TcBatchArgs B{};
+    TcArgs* probs = nullptr;
+    TcBatchMeta* meta = nullptr;
+    uint4* tab = nullptr;
+    std::vector<void*> owned;     // partial sums, tickets and slot tables of split tile-states
+    size_t smem = 0;
+    int grid = 0;
+};
+
+struct TcMulti {
+    std::vector<TcMultiGroup> groups;
+    int dmax = 0;                 // the kernel's dynamic shared-memory limit
+    int64_t* launches = nullptr;  // the first handle's launch counter
+};
+
+void tc_multi_destroy(TcMulti* m)
+{
+    if (!m) return;
+    for (TcMultiGroup& g : m->groups) {
+        if (g.probs) cudaFree(g.probs);
+        if (g.meta) cudaFree(g.meta);
+        if (g.tab) cudaFree(g.tab);
+        for (void* q : g.owned) cudaFree(q);
+    }
+    delete m;
+}
+
+swopt_status tc_multi_create(swopt_handle* const* hs, int n, bool adj, bool use_ytil,
+                             TcMulti** out)
+{
+    *out = nullptr;
+    if (n < 1) {
+        set_error("no problems for a shared launch");
+        return SWOPT_ERR_INVALID_ARG;
+    }
+    std::vector<TcArgs> args(n);
+    std::vector<std::vector<uint4>> tabs(n);
+    std::vector<uint32_t> halo(n), slot(n), cols(n);
+    for (int i = 0; i < n; ++i) {
+        swopt_handle* h = hs[i];
+        TcOperator* t = h->tc;
+        if (!t || t->fp8) {
+            set_error("a shared launch needs BF16 tensor-core operators on every problem");
+            return SWOPT_ERR_UNSUPPORTED;
+        }
+        const TcDir& D = adj ? t->A : t->F;
+        TcArgs a = dir_args(h, t, D, adj);
+        if (adj) {
+            a.out_f = h->g;
+        } else {  // as tc_forward's residual mode: the padded BF16 residual images
+            a.scale = 1;
+            a.ytil = use_ytil ? h->ytil : nullptr;
+            a.mode = 1;
+            for (int tt = 0; tt < kMaxTerms; ++tt) a.out_t[tt] = t->rpad[tt];
+        }
+        // the launch's split decides the partial-sum slots (set per group)
+        a.quantum = 1;
+        a.wq = (long long)a.ntiles * h->Q;  // tile-states
+        a.max_pieces = 1;
+        a.part = nullptr;
+        a.ticket = nullptr;
+        a.split_slot = nullptr;
+        args[i] = a;
+        tabs[i].resize((size_t)a.tab_n);
+        SW_CUDA(cudaMemcpy(tabs[i].data(), a.tab, tabs[i].size() * sizeof(uint4),
+                           cudaMemcpyDeviceToHost));
+        halo[i] = (uint32_t)(a.GA * a.HY * a.HX) * 16u * (uint32_t)a.terms;
+        slot[i] = a.stage_bytes * (uint32_t)a.terms;
+        cols[i] = (uint32_t)(a.RA * a.MB * a.MT * kTilePos);
+    }
+    const int dmax = max_dynamic_smem(hs[0], (const void*)tc_conv_many_kernel);
+    int nsm = 0;
+    SW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, hs[0]->device));
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return halo[x] > halo[y]; });
+    auto need = [&](uint32_t hmax, uint32_t smax, size_t tabn) {
+        return (size_t)hmax + 2 * (size_t)smax + tabn * sizeof(uint4);
+    };
+    TcMulti* m = new TcMulti();
+    m->dmax = dmax;
+    m->launches = &hs[0]->launches;
+    size_t at = 0;
+    while (at < order.size()) {
+        // the group: problems order[at .. end)
+        uint32_t hmax = 0, smax = 0, cmax = 0;
+        size_t tabn = 0, end = at;
+        while (end < order.size()) {
+            const int i = order[end];
+            const uint32_t h2 = std::max(hmax, halo[i]), s2 = std::max(smax, slot[i]);
+            if (dmax <= 0 || need(h2, s2, tabn + tabs[i].size()) > (size_t)dmax) break;
+            hmax = h2;
+            smax = s2;
+            cmax = std::max(cmax, cols[i]);
+            tabn += tabs[i].size();
+            ++end;
+        }
+        if (end == at) {
+            tc_multi_destroy(m);
+            set_error("a problem's halo, stages and tables exceed shared memory");
+            return SWOPT_ERR_UNSUPPORTED;
+        }
+        TcMultiGroup g;
+        TcBatchArgs& B = g.B;
+        std::vector<TcArgs> ga;
+        std::vector<TcBatchMeta> gm;
+        std::vector<uint4> gt;
+        long long W = 0;
+        for (size_t q = at; q < end; ++q) {
+            const int i = order[q];
+            TcBatchMeta mt{};
+            mt.piece0 = W;
+            mt.tab_off = (int)gt.size();
+            W += args[i].wq * args[i].runs;
+            gt.insert(gt.end(), tabs[i].begin(), tabs[i].end());
+            ga.push_back(args[i]);
+            gm.push_back(mt);
+        }
+        const long long G = std::min<long long>(W, nsm);
+        // tile-states cut between CTAs: their partial-sum slots, as the kernel
+        // assigns the runs (CTA of run x: x G / W)
+        swopt_status s = SWOPT_OK;
+        for (size_t q = 0; q < ga.size() && s == SWOPT_OK; ++q) {
+            TcArgs& a = ga[q];
+            const long long R = a.runs, base = gm[q].piece0;
+            std::vector<int> slot((size_t)a.wq, -1);
+            int nsplit = 0, maxp = 1;
+            for (long long ts = 0; ts < a.wq; ++ts) {
+                const long long x0 = base + ts * R;
+                const int pieces = (int)((x0 + R - 1) * G / W - x0 * G / W) + 1;
+                if (pieces > 1) {
+                    slot[(size_t)ts] = nsplit++;
+                    maxp = std::max(maxp, pieces);
+                }
+            }
+            if (!nsplit) continue;
+            const size_t unit_floats = (size_t)a.MB * a.MT * kTilePos * kRows;
+            float* part = nullptr;
+            int* ticket = nullptr;
+            int* sl = nullptr;
+            s = tc_alloc(&part, (size_t)nsplit * maxp * unit_floats);
+            if (s == SWOPT_OK) g.owned.push_back(part);
+            if (s == SWOPT_OK) s = tc_alloc(&ticket, (size_t)a.wq);
+            if (s == SWOPT_OK) {
+                g.owned.push_back(ticket);
+                if (cudaMemset(ticket, 0, sizeof(int) * (size_t)a.wq) != cudaSuccess) {
+                    set_error("cudaMemset failed");
+                    s = SWOPT_ERR_CUDA;
+                }
+            }
+            if (s == SWOPT_OK) s = tc_upload(&sl, slot);
+            if (s == SWOPT_OK) g.owned.push_back(sl);
+            a.part = part;
+            a.ticket = ticket;
+            a.split_slot = sl;
+            a.max_pieces = maxp;
+        }
+        if (s != SWOPT_OK) {
+            for (void* q : g.owned) cudaFree(q);
+            tc_multi_destroy(m);
+            return s;
+        }
+        B.n = (int)ga.size();
+        B.W = W;
+        B.NBUF = 2 * cmax <= 512 ? 2 : 1;
+        B.buf_stride = cmax;
+        B.tcols = pow2_cols((int)(B.NBUF * cmax));
+        B.halo_region = hmax;
+        B.stage_slot = smax;
+        B.tab_n = (int)gt.size();
+        B.err = hs[0]->tc->err;
+        const size_t fixed = (size_t)hmax + gt.size() * sizeof(uint4);
+        B.NS = 2;
+        for (int k = kMaxStages; k > 2; --k)
+            if (fixed + (size_t)k * smax <= (size_t)dmax) {
+                B.NS = k;
+                break;
+            }
+        // at most 512 / tcols CTAs may share an SM's TMEM: ask for enough shared memory
+        g.smem = std::max(fixed + (size_t)B.NS * smax,
+                          std::min((size_t)dmax, (size_t)233472 / (512 / B.tcols + 1) + 1024));
+        g.grid = (int)G;
+        s = tc_upload(&g.probs, ga);
+        if (s == SWOPT_OK) s = tc_upload(&g.meta, gm);
+        if (s == SWOPT_OK) s = tc_upload(&g.tab, gt);
+        B.probs = g.probs;
+        B.meta = g.meta;
+        B.tab = g.tab;
+        m->groups.push_back(g);
+        if (s != SWOPT_OK) {
+            tc_multi_destroy(m);
+            return s;
+        }
+        at = end;
+    }
+    *out = m;
+    return SWOPT_OK;
+}
+
+int tc_multi_groups(const TcMulti* m) { return m ? (int)m->groups.size() : 0; }
+
+swopt_status tc_multi_launch(TcMulti* m, cudaStream_t st)
+{
+    SW_CUDA(cudaFuncSetAttribute(tc_conv_many_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 m->dmax));
+    for (const TcMultiGroup& g : m->groups) {
+        tc_conv_many_kernel<<<g.grid, kTcThreads, g.smem, st>>>(g.B);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_error("shared contraction launch failed: %s", cudaGetErrorString(e));
+            return SWOPT_ERR_CUDA;
+        }
+        ++*m->launches;
+    }
     return SWOPT_OK;
 }
 

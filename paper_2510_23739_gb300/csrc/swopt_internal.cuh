@@ -257,6 +257,19 @@ swopt_status tc_forward(swopt_handle* h, bool to_r, const float* ytil, double* p
                         int scale, cudaStream_t st);
 // h->u (FP32) -> padded BF16 residual images
 swopt_status tc_pack_u(swopt_handle* h, cudaStream_t st);
+// A of several handles (adj false: into the residual images, as tc_forward
+// with to_r, scale 1 and ytil = the handle's folded measurements or none) or
+// A^T, as persistent launches over a work list of their tile-states (whole,
+// one CTA each), the problems packed into as few launches as shared memory
+// allows (tc_multi_groups), each with the handle's current gate and
+// tensor-core operator.  Prepared on the host (never while capturing);
+// UNSUPPORTED for FP8 operators.
+struct TcMulti;
+swopt_status tc_multi_create(swopt_handle* const* hs, int n, bool adj, bool use_ytil,
+                             TcMulti** out);
+swopt_status tc_multi_launch(TcMulti* m, cudaStream_t st);
+int tc_multi_groups(const TcMulti* m);
+void tc_multi_destroy(TcMulti* m);
 // A^T of the padded residual images into h->g (FP32 [Q][S][Z])
 swopt_status tc_adjoint(swopt_handle* h, cudaStream_t st);
 int tc_forward_blocks(const swopt_handle* h);
