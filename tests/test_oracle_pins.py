@@ -112,11 +112,45 @@ def test_adjoint_identity_tiny_workload_kernel():
         assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
 
 
+def _dense_H_definition(g, sw, K):
+    """H entry by entry from Eq. (final-H) and the per-depth lateral
+    correlation (Eq. acoustic-full-forward): row (n, y, x, t), column
+    (p, y', x', j) holds S[n][p][j] K[j][y' - y + r][x' - x + r][t] for
+    |y' - y|, |x' - x| <= r (pulse n's image b^n = sum_p S[n][p] c_p, read at
+    the scan position shifted by the tap), else 0."""
+    S = oracle.switch_matrix(g, sw)
+    r = g.k // 2
+    H = np.zeros((int(np.prod(g.y_shape())), int(np.prod(g.c_shape()))))
+    for n in range(g.N):
+        for y in range(g.Y):
+            for x in range(g.X):
+                for t in range(g.T):
+                    row = ((n * g.Y + y) * g.X + x) * g.T + t
+                    for p in range(g.P):
+                        for yy in range(max(0, y - r), min(g.Y, y + r + 1)):
+                            for xx in range(max(0, x - r), min(g.X, x + r + 1)):
+                                for j in range(g.Z):
+                                    col = ((p * g.Y + yy) * g.X + xx) * g.Z + j
+                                    H[row, col] = S[n, p, j] * K[j, yy - y + r, xx - x + r, t]
+    return H
+
+
+def test_dense_forward_matches_the_entrywise_definition():
+    """The oracle's forward, column by column, equals H assembled entry by
+    entry from its definition (a ragged grid, a support wider than it on one
+    axis, an asymmetric kernel, several pulses on a partial cycle)."""
+    g = _geom(X=4, Y=3, Z=3, T=5, N=4, P=2, k=5, pulses_per_cycle=3)
+    sw = _sw(g.P)
+    K = _rand_kernel(g, 9)
+    np.testing.assert_allclose(_dense_H(g, sw, K), _dense_H_definition(g, sw, K), rtol=0,
+                               atol=1e-13)
+
+
 def test_dense_adjoint_is_transpose():
     g = _geom(X=4, Y=3, Z=3, T=6, N=3, P=2, k=3)
     sw = _sw(g.P)
     K = _rand_kernel(g, 8)
-    H = _dense_H(g, sw, K)
+    H = _dense_H_definition(g, sw, K)
     ny = int(np.prod(g.y_shape()))
     rows = []
     for i in range(ny):
