@@ -902,7 +902,9 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: one resync period of the refined solve, "
+                         "refine_every iterations, else 20)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="swopt", choices=["swopt", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
@@ -945,6 +947,10 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.refine is None:
         args.refine = 25 if args.precision == "bf16" else 0
+    if args.steps is None:
+        # a whole resync period: the timed iterations hold the schedule's average
+        # share of exact gradients
+        args.steps = args.refine if args.refine > 0 and args.method == "one-step" else 20
     if args.refine_budget is None:
         args.refine_budget = 0.1 if args.refine > 0 else 0.0
     if args.presolve is None:
