@@ -99,8 +99,36 @@ def test_null_handle_calls_fail_cleanly():
     assert L.swopt_two_step(None, None, None, None, None, None, None, None, None) == 1
     assert L.swopt_prox_joint(None, None, None, 1.0, 0.1, 0.1, 0.1, 1, 0.1, None) == 1
     assert L.swopt_prox_joint_step_bound(None, 0.1, 0.1, 0.1) == 0.0
+    assert L.swopt_set_state_offset(None, 0) == 1
+    assert L.swopt_fista_gradient(None, None, None, None) == 1
+    assert L.swopt_fista_step_external(None, None, None) == 1
+    assert L.swopt_set_fluence(None, None) == 1
+    assert L.swopt_unrolled_vjp(None, None, None, None, None, None, None, None) == 1
+    i = ctypes.c_int()
+    assert L.swopt_batch_configure(None, 1) == 1
+    assert L.swopt_batch_query(None, ctypes.byref(i), None) == 1
     assert b"null" in L.swopt_last_error()
     assert L.swopt_version().decode().count(".") == 2
+
+
+def test_diffusion_fluence_rejects_bad_arguments_before_gpu_work():
+    L = sw.lib()
+    n = 2 * 2 * 3
+    ok = np.ones(n)
+    src = np.ones(4)
+    out = np.zeros(n)
+    dp = ctypes.c_void_p
+    args = lambda mu_a, g, tol: (2, 2, 3, 0.02, 0.01, mu_a.ctypes.data_as(dp),
+                                 ok.ctypes.data_as(dp), g, src.ctypes.data_as(dp), 1, tol, 100,
+                                 out.ctypes.data_as(dp), None, None)
+    assert L.swopt_diffusion_fluence(*args(ok, 1.0, 1e-8)) == 1       # g must be < 1
+    assert L.swopt_diffusion_fluence(*args(ok, 0.9, 0.0)) == 1        # tol must be > 0
+    bad = ok.copy()
+    bad[3] = -1.0
+    assert L.swopt_diffusion_fluence(*args(bad, 0.9, 1e-8)) == 1      # negative absorption
+    bad[3] = np.nan
+    assert L.swopt_diffusion_fluence(*args(bad, 0.9, 1e-8)) == 1
+    assert b"absorption" in L.swopt_last_error()
 
 
 @pytest.mark.parametrize("dims,rho,kf", [(2, 2.0, 3.5), (3, 2.0, 3.5), (3, 1.0, 4.0)])
