@@ -23,7 +23,7 @@ BF16) solve after the same iteration count.
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl swopt|reference]
                        [--workload NAME] [--precision fp32|bf16|bf16x3]
                        [--refine R] [--refine-budget B] [--presolve I]
-                       [--method one-step|two-step|prox-joint|prox-sweep|prox-tv]
+                       [--method one-step|two-step|prox-joint|prox-sweep|prox-tv|objective-gap]
 For N > 1 it is launched by torch.distributed.run, one rank per GPU; each rank
 solves its own independent problem (replicas, weak scaling).
 """
@@ -641,6 +641,110 @@ def run_prox_sweep(args, device):
 
 
 
+def _gap_trace(op, ev_op, y, params, iters, every, stream):
+    """Step a FISTA solve for `iters` iterations; every `every` iterations
+    read the iterate and evaluate F on the FP32 evaluator handle.  Returns
+    [(iteration, solve ms so far, F)]: the solve time is the CUDA-event time
+    of the FISTA steps alone, the evaluations stay outside it."""
+    import torch
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    op.fista_init(y, params)
+    trace, done, ms = [], 0, 0.0
+    c = None
+    while done < iters:
+        n = min(every, iters - done)
+        torch.cuda.synchronize()
+        s0.record(stream)
+        op.fista_step(n)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms += s0.elapsed_time(s1)
+        done += n
+        c = op.fista_get(c)
+        F, _ = ev_op.objective(c, y, params.lambda_l1, params.lambda_tv)
+        trace.append((done, ms, F))
+    return trace
+
+
+def run_objective_gap(args, device):
+    """Time to a relative objective gap (F(c_k) - F*)/F* of the one-step
+    problem (Eq. one-step, l1 + TV) on the workload: the refined BF16 solve
+    (the bench default), the FP32-class solve (two-term BF16, every gradient
+    exact), plain BF16 and, with `--gap-fp32-iters`, plain FP32 on the CUDA
+    cores.  F is evaluated every `--gap-every` iterations in
+    FP32 (CUDA-core operator, FP64 sums) on a separate handle; F* is the
+    lowest F seen in any run (the FP32-class solve runs `--gap-ref-iters`
+    iterations, twice the compared runs' length by default)."""
+    import torch
+    import paper_2510_23739_gb300 as sw
+
+    prob = workload_problem(args.workload, args.kernel)
+    g = prob.geom
+    op, K, c_true, y = make_problem(prob, seed=0, device=device, kernel=args.kernel)
+    L = op.lipschitz(args.power_iters)
+    alpha = 1.0 / L
+    ev_op = sw.Operator(g, K, prob.sw)  # FP32 evaluator
+    stream = torch.cuda.current_stream()
+    iters, every = args.gap_iters, args.gap_every
+    ref_iters = args.gap_ref_iters or 2 * iters
+    base = dict(step=alpha, lambda_l1=prob.lam_l1, lambda_tv=prob.lam_tv, inner_iters=prob.inner)
+    runs = {}
+    clocks = ClockSampler(_smi_id(device))
+    clocks.start()
+    op.set_precision("bf16")
+    runs["refined_bf16"] = _gap_trace(
+        op, ev_op, y, sw.SolveParams(max_iters=iters, refine_every=25, refine_precision="bf16x3",
+                                     refine_budget=0.1, **base), iters, every, stream)
+    plain = args.gap_plain_iters or iters
+    runs["plain_bf16"] = _gap_trace(op, ev_op, y, sw.SolveParams(max_iters=plain, **base),
+                                    plain, every, stream)
+    if args.gap_fp32_iters:
+        op.set_precision("fp32")
+        runs["plain_fp32"] = _gap_trace(op, ev_op, y,
+                                        sw.SolveParams(max_iters=args.gap_fp32_iters, **base),
+                                        args.gap_fp32_iters, every, stream)
+    op.set_precision("bf16x3")
+    runs["fp32_class_bf16x3"] = _gap_trace(op, ev_op, y, sw.SolveParams(max_iters=ref_iters,
+                                                                        **base),
+                                           ref_iters, every, stream)
+    clk = clocks.stop()
+    op.check_device()
+    op.close()
+    ev_op.close()
+    Fstar = min(F for tr in runs.values() for _, _, F in tr)
+    levels = (1e-3, 1e-4, 1e-5)
+    out = {}
+    for name, tr in runs.items():
+        reach = {}
+        for lv in levels:
+            hit = next(((it, ms) for it, ms, F in tr if (F - Fstar) / abs(Fstar) <= lv), None)
+            reach[f"{lv:g}"] = ({"iterations": hit[0], "seconds": hit[1] / 1e3}
+                                if hit else None)
+        last_it, last_ms, last_F = tr[-1]
+        out[name] = {"reached": reach, "final_gap": (last_F - Fstar) / abs(Fstar),
+                     "iterations": last_it, "ms_per_iteration": last_ms / last_it,
+                     "trace_every_4th": [(it, round(ms, 1), (F - Fstar) / abs(Fstar))
+                                         for it, ms, F in tr[::4]]}
+    me_t = out["refined_bf16"]["reached"]["1e-05"]
+
+    def speedup(name):
+        ref_t = out[name]["reached"]["1e-05"] if name in out else None
+        return (ref_t["seconds"] / me_t["seconds"]) if ref_t and me_t else None
+    print(json.dumps({
+        "metric": "seconds to 1e-5 relative objective gap, refined BF16 solve",
+        "value": me_t["seconds"] if me_t else None, "unit": "s", "higher_is_better": False,
+        "n_gpus": 1, "dtype": "bf16 + refinement (bf16x3 resync)",
+        "data": "synthetic (seeded tube phantom, transducer kernel, 20 dB noise)",
+        "config": {"workload": args.workload, "kernel": args.kernel, "eval_every": every,
+                   "compared_iterations": iters, "reference_iterations": ref_iters,
+                   "plain_bf16_iterations": plain,
+                   "objective_evaluator": "FP32 CUDA-core operator, FP64 sums"},
+        "F_star": Fstar, "speedup_vs_fp32_class_to_1e-5": speedup("fp32_class_bf16x3"),
+        "speedup_vs_plain_fp32_to_1e-5": speedup("plain_fp32"), "runs": out,
+        "clocks": clk}), flush=True)
+
+
 def replace_iters(params, iters):
     import copy
     p = copy.copy(params)
@@ -910,11 +1014,13 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "bf16x3", "fp8"])
     ap.add_argument("--method", default="one-step",
-                    choices=["one-step", "two-step", "prox-joint", "prox-sweep", "prox-tv"],
+                    choices=["one-step", "two-step", "prox-joint", "prox-sweep", "prox-tv",
+                             "objective-gap"],
                     help="two-step: time swopt_two_step against the one-step solve (FP32); "
                          "prox-joint: time the prox of the full R3 (lambda_3 term); "
                          "prox-sweep: the TV and l1 proxes on a volume 8x larger than L2; "
-                         "prox-tv: the TV prox on the workload's volume")
+                         "prox-tv: the TV prox on the workload's volume; "
+                         "objective-gap: time to a relative objective gap per precision")
     ap.add_argument("--kernel", default="aperture", choices=["aperture", "semicircle"],
                     help="per-depth kernel: the aperture-point transducer model, or the "
                          "paper-literal SPR on discrete half spheres (matched time grid)")
@@ -940,6 +1046,17 @@ def main():
                          "0.05%% on the large workload)")
     ap.add_argument("--ref-frac-fwd", type=float, default=None)
     ap.add_argument("--ref-frac-adj", type=float, default=None)
+    ap.add_argument("--gap-iters", type=int, default=3000,
+                    help="objective-gap: iterations of the compared solves")
+    ap.add_argument("--gap-every", type=int, default=50,
+                    help="objective-gap: iterations between objective evaluations")
+    ap.add_argument("--gap-ref-iters", type=int, default=0,
+                    help="objective-gap: iterations of the FP32-class solve (default 2x)")
+    ap.add_argument("--gap-fp32-iters", type=int, default=0,
+                    help="objective-gap: iterations of a plain FP32 (CUDA-core) solve (0: none)")
+    ap.add_argument("--gap-plain-iters", type=int, default=0,
+                    help="objective-gap: iterations of the plain BF16 solve (default: "
+                         "--gap-iters)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
     args = ap.parse_args()
@@ -983,7 +1100,8 @@ def main():
     import paper_2510_23739_gb300 as sw
     sw.lib()
     single = {"prox-joint": run_prox_joint, "two-step": run_two_step,
-              "prox-sweep": run_prox_sweep, "prox-tv": run_prox_tv}
+              "prox-sweep": run_prox_sweep, "prox-tv": run_prox_tv,
+              "objective-gap": run_objective_gap}
     if args.method in single or args.workload == "batch16":
         if rank == 0:
             (run_batch if args.workload == "batch16" else single[args.method])(args, device)
