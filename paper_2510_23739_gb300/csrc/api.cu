@@ -192,7 +192,7 @@ void release_all(swopt_handle* h)
     dfree(h->Kf); dfree(h->Ka); dfree(h->fmask); dfree(h->amask); dfree(h->Sm); dfree(h->Cmf);
     dfree(h->b); dfree(h->u); dfree(h->g); dfree(h->ytil); dfree(h->red); dfree(h->scal);
     dfree(h->c); dfree(h->xi); dfree(h->zin); dfree(h->tvu); dfree(h->tvr0); dfree(h->tvr1);
-    dfree(h->tvx); dfree(h->coop_bar);
+    dfree(h->coop_bar);
     dfree(h->tmp); dfree(h->G); dfree(h->xprev); dfree(h->jw); dfree(h->ju); dfree(h->jr); dfree(h->sched); dfree(h->rlog);
     if (h->scal_host) cudaFreeHost(h->scal_host);
     h->scal_host = nullptr;
@@ -211,7 +211,6 @@ swopt_status ensure_tv_buffers(swopt_handle* h)
     if (!h->tvu) SW_TRY(dalloc(&h->tvu, 3 * n));
     if (!h->tvr0) SW_TRY(dalloc(&h->tvr0, 3 * n));
     if (!h->tvr1) SW_TRY(dalloc(&h->tvr1, 3 * n));
-    if (!h->tvx) SW_TRY(dalloc(&h->tvx, n));
     SW_TRY(coop_prepare(h));
     return SWOPT_OK;
 }

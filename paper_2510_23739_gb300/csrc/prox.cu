@@ -176,22 +176,39 @@ __global__ void __launch_bounds__(256) fista_finish_kernel(const float* __restri
 
 // ---------------------------------------------------------------------------
 // The whole TV prox in one cooperative launch: every block of a grid sized to
-// be co-resident loops over the volume, and the phases of Algorithm 2 are
-// separated by a grid-wide barrier.  Per inner iteration i:
-//   phase A:  x = z - D^T r_{i-1}            (skipped for i = 1, where r = 0)
-//   phase B:  u_i = clamp(r_{i-1} + D x / 12, -tau, tau)
-//             r_i = u_i + beta_i (u_i - u_{i-1})
-// and after the last: x = z - D^T u_K written out (mode 0), or the end of the
-// FISTA iteration with the momentum scalars updated here (mode 1, as
+// be co-resident loops over the volume, one grid-wide barrier per inner
+// iteration i of Algorithm 2.  The volume is cut into tiles of 8 x 8 columns
+// x 32 depths; per tile a block
+//   1. computes x = z - D^T r_{i-1} (x = z for i = 1, where r = 0) on the
+//      tile and on the points its forward differences reach (its +y and +x
+//      faces and its +z cap), into shared memory, keeping the tile's r_{i-1};
+//   2. takes u_i = clamp(r_{i-1} + D x / 12, -tau, tau) and
+//      r_i = u_i + beta_i (u_i - u_{i-1}) on the tile (r ping-pongs between
+//      two arrays, u is updated in place).
+// After the last iteration: x = z - D^T u_K written out (mode 0), or the end
+// of the FISTA iteration with the momentum scalars updated here (mode 1, as
 // fista_finish_kernel).  The inner coefficients beta_i follow Algorithm 2's
-// t recursion in FP64 in every thread.  Phase B issues all its loads of an
-// entry before its stores and the grid holds every block that fits (40
-// registers: 6 per SM); on GB300 these took a 2 x 1024 x 512 x 256 volume
-// from 2.95 to 4.35 TB/s of algorithmic traffic (52 B per entry and
-// iteration; 72 B move, x going through memory between the phases).
-// Updating r in place instead of ping-ponging was slower (3.9 TB/s).
+// t recursion in FP64.  HBM traffic per entry and iteration is the 52
+// algorithmic bytes (read z, r and the previous u, three components each;
+// write u and r) plus the halo columns' share of z and r, which mostly hit L2
+// because neighbouring tiles run at the same time.  Each warp loads
+// kStBatch work units (32 points each) before it uses any of them.  On a
+// GB300 this runs the 2 x 1024 x 512 x 256 sweep volume at 4.51 TB/s of
+// algorithmic traffic and the 3 x 128 x 128 x 96 volume at 4.15 TB/s.  The
+// same arithmetic in two phases per iteration (x through memory, 72 B moved,
+// two barriers) ran at 4.35 / 3.56 TB/s.  One unit per warp at a time was
+// latency-bound at 1.13 TB/s, and five blocks per SM with three units each
+// ran at 4.09 TB/s.
 // ---------------------------------------------------------------------------
 constexpr int kCoopThreads = 256;
+// Tiles of the single-barrier iteration: kStTY x kStTX columns x kStZC depths.
+// x is computed on the tile and on the points its forward differences reach
+// (the +y and +x faces, kStBoxCols columns with the tile's own, and the +z
+// cap, kStTY * kStTX points in whole warps).
+constexpr int kStTY = 8, kStTX = 8, kStZC = 32;
+constexpr int kStBoxCols = kStTY * kStTX + kStTY + kStTX;
+constexpr int kStUnits = kStBoxCols + (kStTY * kStTX + 31) / 32;
+constexpr int kStBatch = 4;  // units a warp loads before it computes
 constexpr uint32_t kBarrierPolls = 1u << 25;  // x 32 ns back-off: about a second
 
 // Grid barrier over all blocks of a cooperative launch.  bar[0] counts
@@ -282,7 +299,6 @@ __device__ __forceinline__ void cp_async_wait()
 
 struct FgpCoop {
     const float* z;  // prox input
-    float* xb;       // x scratch
     float* u;        // dual iterate [3][L]
     float* r0;       // extrapolated duals (ping-pong) [3][L]
     float* r1;
@@ -327,7 +343,7 @@ __device__ __forceinline__ void for_rows(const Vol& v, F body)
     }
 }
 
-__global__ void __launch_bounds__(kCoopThreads) fgp_coop_kernel(const FgpCoop a)
+__global__ void __launch_bounds__(kCoopThreads, 4) fgp_coop_kernel(const FgpCoop a)
 {
     const Vol v = a.v;
     const size_t L = v.L, XZ = (size_t)v.X * v.Z;
@@ -346,6 +362,12 @@ __global__ void __launch_bounds__(kCoopThreads) fgp_coop_kernel(const FgpCoop a)
     // arithmetic is scarce on this GPU) and reaches the block through shared
     // memory
     __shared__ float s_beta;
+    __shared__ float xs[kStTY + 1][kStTX + 1][kStZC + 1];
+    __shared__ float rs[3][kStTY * kStTX][kStZC];
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int tY = (v.Y + kStTY - 1) / kStTY, tX = (v.X + kStTX - 1) / kStTX;
+    const int tZ = (v.Z + kStZC - 1) / kStZC;
+    const long long ntiles = (long long)v.P * tY * tX * tZ;
     double t = 1.0;
     for (int it = 0; it < a.iters; ++it) {
         if (threadIdx.x == 0) {
@@ -355,43 +377,122 @@ __global__ void __launch_bounds__(kCoopThreads) fgp_coop_kernel(const FgpCoop a)
         }
         __syncthreads();
         const float beta = s_beta;
-        if (it > 0) {
-            for_rows(v, [&](int y, int x, size_t base) {
-                for (int j = lane; j < v.Z; j += 32) {
-                    const size_t e = base + j;
-                    a.xb[e] = a.z[e] - dtq(rin, v, e, y, x, j);
-                }
-            });
-            grid_sync(a.bar, nb);
-        }
-        const float* xs = it == 0 ? a.z : a.xb;
-        const float* ri = rin;
-        float* ro = rout;
-        // Every load of a depth is issued before its stores (which could
-        // alias later loads for the compiler): a warp keeps the round trips of
-        // x, r and u in flight together.
-        for_rows(v, [&](int y, int x, size_t base) {
-            const bool hy = y + 1 < v.Y, hx = x + 1 < v.X;
-            for (int j = lane; j < v.Z; j += 32) {
-                const size_t e = base + j;
-                const float xc = xs[e];
-                const float d[3] = {hy ? xs[e + XZ] - xc : 0.f, hx ? xs[e + v.Z] - xc : 0.f,
-                                    j + 1 < v.Z ? xs[e + 1] - xc : 0.f};
-                float ra[3], up[3];
+        for (long long tile = blockIdx.x; tile < ntiles; tile += nb) {
+            long long q = tile;
+            const int z0 = (int)(q % tZ) * kStZC;
+            q /= tZ;
+            const int x0 = (int)(q % tX) * kStTX;
+            q /= tX;
+            const int y0 = (int)(q % tY) * kStTY;
+            const size_t pbase = (size_t)(q / tY) * v.Y * XZ;
+            // x = z - D^T r_{i-1} on the tile, on its +y and +x faces and on
+            // its +z cap (the points the forward differences reach), into
+            // shared memory; the tile's r_{i-1} is kept there too
+            // (kStBatch units per warp at a time, every load issued before any use)
+            for (int u0 = warp; u0 < kStUnits; u0 += nwarps * kStBatch) {
+                float zv[kStBatch], c0[kStBatch], c1[kStBatch], c2[kStBatch];
+                float b0[kStBatch], b1[kStBatch], b2[kStBatch];
+                int pos[kStBatch];  // yy | xx << 8 | zz << 16, or -1
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    ra[c] = it == 0 ? 0.f : ri[(size_t)c * L + e];
-                    up[c] = it == 0 ? 0.f : a.u[(size_t)c * L + e];
+                for (int k = 0; k < kStBatch; ++k) {
+                    const int unit = u0 + k * nwarps;
+                    int yy = 0, xx = 0, zz = lane;
+                    bool ok = unit < kStUnits;
+                    if (unit < kStTY * kStTX) {
+                        yy = unit / kStTX;
+                        xx = unit % kStTX;
+                    } else if (unit < kStTY * kStTX + kStTX) {
+                        yy = kStTY;
+                        xx = unit - kStTY * kStTX;
+                    } else if (unit < kStBoxCols) {
+                        yy = unit - kStTY * kStTX - kStTX;
+                        xx = kStTX;
+                    } else {
+                        const int col = (unit - kStBoxCols) * 32 + lane;
+                        ok = ok && col < kStTY * kStTX;
+                        yy = col / kStTX;
+                        xx = col % kStTX;
+                        zz = kStZC;
+                    }
+                    const int y = y0 + yy, x = x0 + xx, j = z0 + zz;
+                    ok = ok && y < v.Y && x < v.X && j < v.Z;
+                    pos[k] = ok ? (yy | xx << 8 | zz << 16) : -1;
+                    zv[k] = c0[k] = c1[k] = c2[k] = b0[k] = b1[k] = b2[k] = 0.f;
+                    if (!ok) continue;
+                    const size_t e = pbase + ((size_t)y * v.X + x) * v.Z + j;
+                    zv[k] = a.z[e];
+                    if (it > 0) {
+                        c0[k] = rin[e];
+                        c1[k] = rin[L + e];
+                        c2[k] = rin[2 * L + e];
+                        if (y > 0) b0[k] = rin[e - XZ];
+                        if (x > 0) b1[k] = rin[L + e - v.Z];
+                        if (j > 0) b2[k] = rin[2 * L + e - 1];
+                    }
                 }
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const size_t ia = (size_t)c * L + e;
-                    const float un = clampf(fmaf(d[c], 1.0f / 12.0f, ra[c]), -a.tau, a.tau);
-                    a.u[ia] = un;
-                    ro[ia] = fmaf(beta, un - up[c], un);
+                for (int k = 0; k < kStBatch; ++k) {
+                    if (pos[k] < 0) continue;
+                    const int yy = pos[k] & 0xFF, xx = (pos[k] >> 8) & 0xFF, zz = pos[k] >> 16;
+                    const int y = y0 + yy, x = x0 + xx, j = z0 + zz;
+                    float xv = zv[k];
+                    if (it > 0) {
+                        // D^T r_{i-1}, in the order of dtq
+                        float acc = 0.f;
+                        if (y + 1 < v.Y) acc -= c0[k];
+                        if (y > 0) acc += b0[k];
+                        if (x + 1 < v.X) acc -= c1[k];
+                        if (x > 0) acc += b1[k];
+                        if (j + 1 < v.Z) acc -= c2[k];
+                        if (j > 0) acc += b2[k];
+                        xv -= acc;
+                    }
+                    if (yy < kStTY && xx < kStTX && zz < kStZC) {
+                        const int col = yy * kStTX + xx;
+                        rs[0][col][zz] = c0[k];
+                        rs[1][col][zz] = c1[k];
+                        rs[2][col][zz] = c2[k];
+                    }
+                    xs[yy][xx][zz] = xv;
                 }
             }
-        });
+            __syncthreads();
+            // u_i = clamp(r_{i-1} + D x / 12), r_i = u_i + beta_i (u_i - u_{i-1})
+            for (int k0 = warp; k0 < kStTY * kStTX; k0 += nwarps * kStBatch) {
+                float up[kStBatch][3];
+#pragma unroll
+                for (int k = 0; k < kStBatch; ++k) {
+                    const int col = k0 + k * nwarps;
+                    const int y = y0 + col / kStTX, x = x0 + col % kStTX, j = z0 + lane;
+                    const bool ok = col < kStTY * kStTX && y < v.Y && x < v.X && j < v.Z;
+                    const size_t e = pbase + ((size_t)y * v.X + x) * v.Z + j;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        up[k][c] = ok && it > 0 ? a.u[(size_t)c * L + e] : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < kStBatch; ++k) {
+                    const int col = k0 + k * nwarps;
+                    const int yy = col / kStTX, xx = col % kStTX;
+                    const int y = y0 + yy, x = x0 + xx, j = z0 + lane;
+                    if (col >= kStTY * kStTX || y >= v.Y || x >= v.X || j >= v.Z) continue;
+                    const size_t e = pbase + ((size_t)y * v.X + x) * v.Z + j;
+                    const float xc = xs[yy][xx][lane];
+                    const float d[3] = {y + 1 < v.Y ? xs[yy + 1][xx][lane] - xc : 0.f,
+                                        x + 1 < v.X ? xs[yy][xx + 1][lane] - xc : 0.f,
+                                        j + 1 < v.Z ? xs[yy][xx][lane + 1] - xc : 0.f};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const size_t ia = (size_t)c * L + e;
+                        const float un =
+                            clampf(fmaf(d[c], 1.0f / 12.0f, rs[c][col][lane]), -a.tau, a.tau);
+                        a.u[ia] = un;
+                        rout[ia] = fmaf(beta, un - up[k][c], un);
+                    }
+                }
+            }
+            __syncthreads();
+        }
         grid_sync(a.bar, nb);  // also orders s_beta's next write after every read
         const float* tmp = rin;
         rin = rout;
@@ -953,7 +1054,7 @@ swopt_status prox_tv_coop(swopt_handle* h, const float* z, float tau, int iters,
                           int inner_momentum, float* out, cudaStream_t st)
 {
     FgpCoop a{};
-    a.z = z; a.xb = h->tvx; a.u = h->tvu; a.r0 = h->tvr0; a.r1 = h->tvr1;
+    a.z = z; a.u = h->tvu; a.r0 = h->tvr0; a.r1 = h->tvr1;
     a.v = vol_of(h); a.tau = tau; a.iters = iters; a.inner_momentum = inner_momentum;
     a.mode = 0; a.out = out;
     return launch_coop(h, a, st);
@@ -963,7 +1064,7 @@ swopt_status fista_prox_finish(swopt_handle* h, const float* z, float tau, int i
                                int inner_momentum, float theta, float* delta, cudaStream_t st)
 {
     FgpCoop a{};
-    a.z = z; a.xb = h->tvx; a.u = h->tvu; a.r0 = h->tvr0; a.r1 = h->tvr1;
+    a.z = z; a.u = h->tvu; a.r0 = h->tvr0; a.r1 = h->tvr1;
     a.v = vol_of(h); a.tau = tau; a.iters = iters; a.inner_momentum = inner_momentum;
     a.mode = 1; a.c = h->c; a.xi = h->xi; a.delta = delta; a.scal = h->scal;
     a.momentum = h->prm.momentum; a.theta = theta;

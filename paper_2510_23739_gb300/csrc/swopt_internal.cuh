@@ -154,7 +154,6 @@ struct swopt_handle {
     float* tvu = nullptr;         // [3][P][Y][X][Z] dual iterate
     float* tvr0 = nullptr;        // [3][..] extrapolated dual (ping)
     float* tvr1 = nullptr;        // [3][..] (pong)
-    float* tvx = nullptr;         // [P][Y][X][Z] x = z - D^T r of the current inner iteration
     unsigned* coop_bar = nullptr; // grid barrier of the cooperative TV prox: count, generation, error
     int coop_blocks = 0;          // its grid size (0: not yet sized)
     int tile_ty = 0, tile_tx = 0; // shared-memory TV prox tile (0: not chosen, -1: none fits)
