@@ -21,7 +21,7 @@ the plain FP32 solve's speed, and the difference from an FP32-class (two-term
 BF16) solve after the same iteration count.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl swopt|reference]
-                       [--workload NAME] [--precision fp32|bf16|bf16x3]
+                       [--workload NAME] [--precision fp32|bf16|bf16x3|bf16x6|fp8]
                        [--refine R] [--refine-budget B] [--presolve I]
                        [--method one-step|two-step|prox-joint|prox-sweep|prox-tv|objective-gap]
 For N > 1 it is launched by torch.distributed.run, one rank per GPU; each rank
@@ -1012,7 +1012,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="swopt", choices=["swopt", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "bf16x3", "fp8"])
+    ap.add_argument("--precision", default="bf16",
+                    choices=["fp32", "bf16", "bf16x3", "bf16x6", "fp8"])
     ap.add_argument("--method", default="one-step",
                     choices=["one-step", "two-step", "prox-joint", "prox-sweep", "prox-tv",
                              "objective-gap"],
@@ -1027,7 +1028,7 @@ def main():
     ap.add_argument("--refine", type=int, default=None,
                     help="refined solve: exact gradient at least every R iterations (0: off; "
                          "default 25 for bf16, else 0)")
-    ap.add_argument("--refine-precision", default="bf16x3", choices=["fp32", "bf16x3"])
+    ap.add_argument("--refine-precision", default="bf16x3", choices=["fp32", "bf16x3", "bf16x6"])
     ap.add_argument("--refine-budget", type=float, default=None,
                     help="refined solve: also resync when the relative steps since the last "
                          "exact gradient add up to this (0: off; default 0.1)")
@@ -1134,6 +1135,10 @@ def main():
             # the measured BF16 burst times the nominal FP8 / BF16 ratio (4.5 / 2.25)
             peak = peaks["bf16_tflops"] * 2
             bound, peak_note = "tensor", f"bf16 dense burst x 2, nominal fp8 ratio ({peak_src})"
+        elif prec_dom == "bf16x6":
+            # each useful multiply-add costs 6 BF16 multiply-adds (three-term split)
+            peak = peaks["bf16_tflops"] / 6
+            bound, peak_note = "tensor", f"bf16 dense burst / 6 products ({peak_src})"
         else:
             # each useful multiply-add costs 3 BF16 multiply-adds (two-term split)
             peak = peaks["bf16_tflops"] / 3
@@ -1151,6 +1156,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3 (2-term split)",
+                      "bf16x6": "bf16x6 (3-term split)",
                       "fp8": "fp8 e4m3 (per-depth equilibration)"}[args.precision] + (f" + refinement (exact {args.refine_precision} gradient at "
                                    f"least every {args.refine} iterations, budget "
                                    f"{args.refine_budget:g})" if refine else ""),
@@ -1171,7 +1177,10 @@ def main():
                                                           / peaks["bf16_tflops"])
                          if bound == "tensor" else None,
                          "issued_tflops": issued_tflops,
-                         "issued_frac_of_peak": (issued_tflops / peak if issued_tflops else None),
+                         # every executed MMA against the BF16 (FP8: 2x) dense rate
+                         "issued_frac_of_peak": (issued_tflops / (peaks["bf16_tflops"] *
+                                                                  (2 if prec_dom == "fp8" else 1))
+                                                 if issued_tflops else None),
                          "kernel_avg_ms": {"A": res["avg_ms"][0], "AT": res["avg_ms"][1],
                                            "A_resync": res["avg_ms"][2],
                                            "AT_resync": res["avg_ms"][3]},

@@ -82,6 +82,12 @@ typedef struct {
  *                    accumulator of their own: measured relative error of
  *                    the operator 4e-6 (A) and 1e-5 (A^T) at 64^3 x 256 with
  *                    15 x 15 support, against 1e-6 for SWOPT_PREC_FP32.
+ *  SWOPT_PREC_BF16X6: tcgen05 tensor cores on a three-term BF16 split of both
+ *                    operands (v = v0 + v1 + v2) with the six products of
+ *                    total order up to 2, the five corrections in an
+ *                    accumulator of their own: each product is kept to about
+ *                    2^-24, so the operator meets the FP32 bound; twice the
+ *                    MMAs of SWOPT_PREC_BF16X3.
  *  SWOPT_PREC_FP8  : tcgen05 tensor cores on FP8 E4M3 operands (3 mantissa
  *                    bits), FP32 accumulation, with per-channel
  *                    equilibration: the kernel is stored as K_j / s_j and the
@@ -97,7 +103,8 @@ typedef enum {
     SWOPT_PREC_FP32 = 0,
     SWOPT_PREC_BF16 = 1,
     SWOPT_PREC_BF16X3 = 2,
-    SWOPT_PREC_FP8 = 3
+    SWOPT_PREC_FP8 = 3,
+    SWOPT_PREC_BF16X6 = 4
 } swopt_precision;
 
 /* Momentum of Algorithms 1 and 2: Beck-Teboulle (t_k - 1)/t_{k+1}, the

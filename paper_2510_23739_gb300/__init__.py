@@ -25,7 +25,7 @@ from . import build as _build
 __all__ = ["lib", "Operator", "SolveParams", "SwoptError", "PRECISION", "MOMENTUM",
            "HFunction", "Batch", "REFINED_DEFAULTS"]
 
-PRECISION = {"fp32": 0, "bf16": 1, "bf16x3": 2, "fp8": 3}
+PRECISION = {"fp32": 0, "bf16": 1, "bf16x3": 2, "fp8": 3, "bf16x6": 4}
 MOMENTUM = {"beck_teboulle": 0, "paper_printed": 1, "none": 2}
 # The refined solve's recommended schedule for BF16 contractions: an exact
 # (two-term BF16) gradient every 25 iterations, and sooner whenever the
@@ -329,8 +329,13 @@ class Operator:
         _check(L.swopt_create(ctypes.byref(g), K.ctypes.data_as(ctypes.c_void_p), ctypes.byref(s),
                               ctypes.byref(h)))
         self._h = h
+        self.precision = "fp32"
         if precision != "fp32":
-            self.set_precision(precision)
+            try:
+                self.set_precision(precision)
+            except SwoptError:
+                self.close()  # a precision the geometry does not support: no handle leaks
+                raise
         self.precision = precision
 
     def _switching_struct(self, kappa, eps_bar, eps_off, mu):

@@ -420,7 +420,8 @@ swopt_status validate_params(const swopt_solve_params* p)
         !is_fin(p->eps2) || p->lambda_l1 < 0 || p->lambda_tv < 0 || p->inner_iters < 0 ||
         p->inner_iters > 100000 || p->max_iters < 0 || p->momentum < 0 || p->momentum > 2 ||
         p->inner_momentum < 0 || p->inner_momentum > 2 || p->refine_every < 0 ||
-        p->refine_precision < SWOPT_PREC_FP32 || p->refine_precision > SWOPT_PREC_BF16X3 ||
+        p->refine_precision < SWOPT_PREC_FP32 || p->refine_precision > SWOPT_PREC_BF16X6 ||
+        p->refine_precision == SWOPT_PREC_FP8 ||
         !is_fin(p->refine_budget) || p->refine_budget < 0 || !is_fin(p->lambda_3) ||
         p->lambda_3 < 0 || !is_fin(p->joint_step2) || (p->lambda_3 > 0 && p->inner_iters < 1) ||
         (p->step <= 0 && (p->power_iters < 1 || p->power_iters > 100000))) {
@@ -862,7 +863,7 @@ swopt_status swopt_set_precision(swopt_handle* h, int precision)
 {
     clear_error();
     SW_TRY(check_handle(h));
-    if (precision < SWOPT_PREC_FP32 || precision > SWOPT_PREC_FP8) {
+    if (precision < SWOPT_PREC_FP32 || precision > SWOPT_PREC_BF16X6) {
         set_error("unknown precision %d", precision);
         return SWOPT_ERR_INVALID_ARG;
     }

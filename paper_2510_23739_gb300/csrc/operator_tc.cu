@@ -47,7 +47,11 @@
 // v - v0) with the 3 products v0 w0, v0 w1, v1 w0 (the dropped v1 w1 is
 // below 2^-16 of |v w|) accumulated in FP32; the 2 correction products go to
 // an accumulator of their own where TMEM holds it, so that the tensor core's
-// FP32 accumulation rounds them on their own (2^-8 smaller) scale.  Or FP8
+// FP32 accumulation rounds them on their own (2^-8 smaller) scale.  Or 3
+// BF16 terms (v2 the BF16 rounding of v - v0 - v1) with the 6 products of
+// total order up to 2 (v0 w0; v0 w1, v1 w0; v0 w2, v1 w1, v2 w0), the
+// representation and the dropped products below about 2^-24 of |v w|, the
+// 5 corrections in the correction accumulator.  Or FP8
 // E4M3 operands (kind::f8f6f4, K = 32 per MMA in the same 32 bytes of a row)
 // with FP32 accumulation and per-channel equilibration of the contracted
 // dimension: the kernel is stored as K_j / s_j and the image as b_j s_j sigma,
@@ -66,7 +70,7 @@
 
 namespace swopt {
 
-constexpr int kMaxTerms = 2;    // BF16 terms per operand of the split precision
+constexpr int kMaxTerms = 3;    // BF16 terms per operand of the split precisions
 constexpr int kMaxSpecies = 8;  // the geometry's limit on P
 constexpr int kRows = 128;      // MMA M: output channels per block
 constexpr int kTileY = 32;      // scan rows of a position tile
@@ -95,7 +99,7 @@ struct TcDir {
     int cols = 0;                 // TMEM columns allocated
     size_t smem = 0;              // dynamic shared memory requested
     int groupsX = 0;              // CTAs along x
-    __nv_bfloat16* Wt[kMaxTerms] = {nullptr, nullptr};  // kernel per term,
+    __nv_bfloat16* Wt[kMaxTerms] = {};  // kernel per term,
                                   // [group][tap][pair][MB][2][128][8]
     uint32_t* tab = nullptr;      // per group: header + run table (see TcArgs)
     int tab_words = 0;
@@ -103,7 +107,7 @@ struct TcDir {
 };
 
 struct TcOperator {
-    int terms = 1;                // BF16 terms per operand (1 or 2)
+    int terms = 1;                // BF16 terms per operand (1, 2 or 3)
     bool fp8 = false;             // E4M3 operands (one term)
     int esl = 8;                  // contracted-dimension elements per 16-byte slice (8 or 16)
     int tilesX = 0, tilesY = 0, Yp = 0, Xp = 0, HY = 0;
@@ -113,8 +117,8 @@ struct TcOperator {
     unsigned* words = nullptr;    // FP8: [2] largest scaled image / residual entry (float bits)
     std::vector<double> s_dep_h, s_tim_h;  // FP8: host copies of the scales
     TcDir F, A;
-    __nv_bfloat16* bpad[kMaxTerms] = {nullptr, nullptr};  // [Q][F.KS][Yp][Xp][8] per term
-    __nv_bfloat16* rpad[kMaxTerms] = {nullptr, nullptr};  // [Q][A.KS][Yp][Xp][8] per term
+    __nv_bfloat16* bpad[kMaxTerms] = {};  // [Q][F.KS][Yp][Xp][8] per term
+    __nv_bfloat16* rpad[kMaxTerms] = {};  // [Q][A.KS][Yp][Xp][8] per term
     int* err = nullptr;
 };
 
@@ -280,8 +284,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// The BF16 terms of 8 values: t0 = bf16(v), then t1 = bf16(v - t0) when
-// `terms` is 2, each packed as one uint4.
+// The BF16 terms of 8 values: t0 = bf16(v), then t1 = bf16(v - t0) and
+// t2 = bf16(v - t0 - t1) as `terms` asks, each packed as one uint4.
 __device__ __forceinline__ void split_terms(const float* v, uint4* out, int terms)
 {
     float r[8];
@@ -392,15 +396,16 @@ __device__ __forceinline__ bool tc_unit(const TcArgs& a, int k, TcUnit& u)
 // terms of the halo and of the stage.
 struct IssueCfg {
     uint32_t tap_bytes;     // the MB channel blocks of one tap (kBlockBytes apart)
-    uint32_t halo_lo16;     // halo of the second term
-    uint32_t stage_lo16;    // kernel blocks of the second term
+    uint32_t halo_lo16;     // halo of the second term (the third follows at twice this)
+    uint32_t stage_lo16;    // kernel blocks of the second term (likewise)
     uint32_t idesc;
 };
 
 // The products of every tap of a stage, specialised at compile time: MT
 // tiles, MB channel blocks, and MODE 0 (one BF16 term), 1 (two terms, the
-// corrections in accumulator set 1), 2 (two terms, one accumulator set) or 3
-// (one E4M3 term, kind::f8f6f4).
+// corrections in accumulator set 1), 2 (two terms, one accumulator set), 3
+// (one E4M3 term, kind::f8f6f4), 4 (three terms, the corrections in set 1)
+// or 5 (three terms, one accumulator set).
 // Accumulator of (set, block, tile): columns ((set MB + block) MT + tile) 256.
 template <int MT, int MB, int MODE>
 __device__ __forceinline__ void issue_taps(const IssueCfg& c, uint32_t tbuf, uint64_t a0,
@@ -424,10 +429,16 @@ __device__ __forceinline__ void issue_taps(const IssueCfg& c, uint32_t tbuf, uin
                 }
                 tc_mma(dm, am, bi, c.idesc, 1u);
                 if (MODE != 0) {
-                    const uint32_t dc =
-                        MODE == 1 ? tbuf + (uint32_t)(((MB + mb) * MT + i) * kTilePos) : dm;
+                    const uint32_t dc = MODE == 1 || MODE == 4
+                                            ? tbuf + (uint32_t)(((MB + mb) * MT + i) * kTilePos)
+                                            : dm;
                     tc_mma(dc, am + c.stage_lo16, bi, c.idesc, 1u);
                     tc_mma(dc, am, bi + c.halo_lo16, c.idesc, 1u);
+                    if (MODE >= 4) {
+                        tc_mma(dc, am + 2 * (uint64_t)c.stage_lo16, bi, c.idesc, 1u);
+                        tc_mma(dc, am + c.stage_lo16, bi + c.halo_lo16, c.idesc, 1u);
+                        tc_mma(dc, am, bi + 2 * (uint64_t)c.halo_lo16, c.idesc, 1u);
+                    }
                 }
             }
         }
@@ -437,6 +448,7 @@ __device__ __forceinline__ void issue_taps(const IssueCfg& c, uint32_t tbuf, uin
 __host__ __device__ __forceinline__ int issue_kind(int MT, int MB, int terms, int RA, int fp8)
 {
     if (fp8) return 12 + (MT - 1) * 2 + (MB - 1);
+    if (terms == 3) return 16 + ((MT - 1) * 2 + (MB - 1)) * 2 + (RA == 2 ? 0 : 1);
     const int mode = terms == 1 ? 0 : (RA == 2 ? 1 : 2);
     return ((MT - 1) * 2 + (MB - 1)) * 3 + mode;
 }
@@ -461,7 +473,15 @@ __device__ __forceinline__ void issue_stage(int kind, const IssueCfg& c, uint32_
     case 12: issue_taps<1, 1, 3>(c, tbuf, a0, b0, ow, nt); break;
     case 13: issue_taps<1, 2, 3>(c, tbuf, a0, b0, ow, nt); break;
     case 14: issue_taps<2, 1, 3>(c, tbuf, a0, b0, ow, nt); break;
-    default: issue_taps<2, 2, 3>(c, tbuf, a0, b0, ow, nt); break;
+    case 15: issue_taps<2, 2, 3>(c, tbuf, a0, b0, ow, nt); break;
+    case 16: issue_taps<1, 1, 4>(c, tbuf, a0, b0, ow, nt); break;
+    case 17: issue_taps<1, 1, 5>(c, tbuf, a0, b0, ow, nt); break;
+    case 18: issue_taps<1, 2, 4>(c, tbuf, a0, b0, ow, nt); break;
+    case 19: issue_taps<1, 2, 5>(c, tbuf, a0, b0, ow, nt); break;
+    case 20: issue_taps<2, 1, 4>(c, tbuf, a0, b0, ow, nt); break;
+    case 21: issue_taps<2, 1, 5>(c, tbuf, a0, b0, ow, nt); break;
+    case 22: issue_taps<2, 2, 4>(c, tbuf, a0, b0, ow, nt); break;
+    default: issue_taps<2, 2, 5>(c, tbuf, a0, b0, ow, nt); break;
     }
 }
 
@@ -996,11 +1016,13 @@ __device__ __forceinline__ void tc_body(const Src& src)
                                 // as one 16-byte row of the residual image
                                 const __nv_bfloat16 h0 = __float2bfloat16_rn(o);
                                 const float o1 = o - __bfloat162float(h0);
+                                const __nv_bfloat16 h1 = __float2bfloat16_rn(o1);
+                                const float o2 = o1 - __bfloat162float(h1);
                                 uint32_t w0 = (uint32_t)__bfloat16_as_ushort(h0);
-                                uint32_t w1 = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(o1));
+                                uint32_t w1 = (uint32_t)__bfloat16_as_ushort(h1);
                                 w0 |= __shfl_down_sync(0xffffffffu, w0, 1) << 16;  // even lanes: pairs
                                 w1 |= __shfl_down_sync(0xffffffffu, w1, 1) << 16;
-                                uint4 q0, q1;
+                                uint4 q0, q1, q2 = make_uint4(0u, 0u, 0u, 0u);
                                 q0.x = w0;
                                 q0.y = __shfl_down_sync(0xffffffffu, w0, 2);
                                 q0.z = __shfl_down_sync(0xffffffffu, w0, 4);
@@ -1009,12 +1031,22 @@ __device__ __forceinline__ void tc_body(const Src& src)
                                 q1.y = __shfl_down_sync(0xffffffffu, w1, 2);
                                 q1.z = __shfl_down_sync(0xffffffffu, w1, 4);
                                 q1.w = __shfl_down_sync(0xffffffffu, w1, 6);
+                                if (a.terms > 2) {  // warp-uniform
+                                    uint32_t w2 =
+                                        (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(o2));
+                                    w2 |= __shfl_down_sync(0xffffffffu, w2, 1) << 16;
+                                    q2.x = w2;
+                                    q2.y = __shfl_down_sync(0xffffffffu, w2, 2);
+                                    q2.z = __shfl_down_sync(0xffffffffu, w2, 4);
+                                    q2.w = __shfl_down_sync(0xffffffffu, w2, 6);
+                                }
                                 if ((lane & 7) == 0 && ch < a.Twp) {
                                     const size_t ro =
                                         ((((size_t)u.m * a.KSo + (ch >> 3)) * a.Yp + (y + a.r)) *
                                              a.Xp + (x + a.r)) * 8;
                                     *reinterpret_cast<uint4*>(a.out_t[0] + ro) = q0;
                                     if (a.terms > 1) *reinterpret_cast<uint4*>(a.out_t[1] + ro) = q1;
+                                    if (a.terms > 2) *reinterpret_cast<uint4*>(a.out_t[2] + ro) = q2;
                                 }
                             }
                         }
@@ -1586,7 +1618,7 @@ bool plan_dir(const swopt_handle* h, const TcOperator* t, bool adj, int MT, int 
 // Packed kernel blocks on the device, one entry per slice grouping (GA).
 struct WCache {
     int GA = 0;
-    __nv_bfloat16* w[kMaxTerms] = {nullptr, nullptr};
+    __nv_bfloat16* w[kMaxTerms] = {};
 };
 
 void free_wcache(std::vector<WCache>& c, const __nv_bfloat16* keep)
@@ -1888,7 +1920,8 @@ static swopt_status tune_dir(swopt_handle* h, bool adj, int force_mt, int force_
 
 swopt_status tc_prepare(swopt_handle* h)
 {
-    const int terms = h->precision == SWOPT_PREC_BF16X3 ? 2 : 1;
+    const int terms =
+        h->precision == SWOPT_PREC_BF16X6 ? 3 : (h->precision == SWOPT_PREC_BF16X3 ? 2 : 1);
     const bool fp8 = h->precision == SWOPT_PREC_FP8;
     if (h->tc && h->tc->terms == terms && h->tc->fp8 == fp8) return SWOPT_OK;
     tc_release(h);
@@ -2027,7 +2060,7 @@ swopt_status tc_states(swopt_handle* h, const float* c, cudaStream_t st)
     int sms = 0;
     SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     const int grid = (int)std::min<size_t>((size_t)grid_for(n, 256), (size_t)sms * 16);
-    TermPtrs out{{t->bpad[0], t->bpad[1]}};
+    TermPtrs out{{t->bpad[0], t->bpad[1], t->bpad[2]}};
     // 16-byte loads when every run of 8 depths starts on a 16-byte boundary
     const int vec = (h->Z % 4) == 0 && ((uintptr_t)c & 15u) == 0;
     tc_states_kernel<<<grid, 256, 0, st>>>(c, h->Sm, out, t->terms, h->Q, h->P, h->Y, h->X, h->Z,
@@ -2069,7 +2102,7 @@ swopt_status tc_pack_u(swopt_handle* h, cudaStream_t st)
     int sms = 0;
     SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     const int grid = (int)std::min<size_t>((size_t)grid_for(n, 256), (size_t)sms * 16);
-    TermPtrs out{{t->rpad[0], t->rpad[1]}};
+    TermPtrs out{{t->rpad[0], t->rpad[1], t->rpad[2]}};
     tc_pack_kernel<<<grid, 256, 0, st>>>(h->u, out, t->terms, h->Q, h->Y, h->X, h->Twp, t->A.KS,
                                          t->Yp, t->Xp, h->r);
     SW_LAUNCHED(h);

@@ -357,12 +357,14 @@ def test_medium_adjoint_identity_and_descent(medium):
 # accumulates hi*hi + hi*lo + lo*hi in FP32, so each product carries at most
 # about 3 * 2^-16 = 4.6e-5 relative error (two representation errors and the
 # dropped lo*lo, each <= 2^-16): held to 4e-5 (measured 0.4-1.0e-5 with the
-# corrections accumulated apart).  Plain BF16: two roundings of <= 2^-8 per
+# corrections accumulated apart).  The three-term split keeps each product to
+# about 3 * 2^-24; the FP32 accumulation is then what is left, as on the CUDA
+# cores: held to the FP32 operator bound, 1e-5.  Plain BF16: two roundings of <= 2^-8 per
 # product (7.8e-3 worst, about 0.9-3.3e-3 measured): held to 5e-3.  FP8 E4M3
 # (3 mantissa bits, u = 2^-4) with per-channel equilibration: two roundings
 # of <= 2^-4 per product (0.125 worst): held to 0.1 (measured 0.8-4e-2).
 # ---------------------------------------------------------------------------
-TC_TOL = {"bf16x3": 4e-5, "bf16": 5e-3, "fp8": 1e-1}
+TC_TOL = {"bf16x6": 1e-5, "bf16x3": 4e-5, "bf16": 5e-3, "fp8": 1e-1}
 
 
 @pytest.fixture(scope="module")
@@ -376,11 +378,17 @@ def tc_cases():
     return out
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "fp8"])
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16x3", "bf16", "fp8"])
 @pytest.mark.parametrize("name", ["tiny", "ragged", "k1_one_pulse", "pulses_below_cycle",
                                   "single_column", "support_wider_than_grid", "support_31"])
 def test_tensor_core_operator_matches_oracle(tc_cases, name, prec):
     g, s, K = tc_cases[name]
+    if prec == "bf16x6" and g.k > 27:
+        # three image terms of a 31-wide halo leave no shared memory for the
+        # kernel stages: refused on the host, before any GPU work
+        with pytest.raises(sw.SwoptError, match="no tensor-core configuration fits"):
+            sw.Operator(g, K, s, precision=prec)
+        return
     op = sw.Operator(g, K, s, precision=prec)
     c = np.random.default_rng(30).standard_normal(g.c_shape())
     yv = np.random.default_rng(31).standard_normal(g.y_shape())
@@ -392,7 +400,7 @@ def test_tensor_core_operator_matches_oracle(tc_cases, name, prec):
     op.close()
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16x3", "bf16"])
 def test_tensor_core_medium_sampled(medium, prec):
     g, s, K, op = medium
     op.set_precision(prec)

@@ -10,6 +10,8 @@ Tolerances (relative L2), from the arithmetic:
 - two-term BF16: each operand kept to 2^-16, products to about 3 2^-16; the
   tensor core's FP32 accumulation over the ~10^5 terms of an output of the
   31 x 31 support adds about sqrt(10^5) 2^-24 = 2e-5: held to 1e-4.
+- three-term BF16 does not fit the 31 x 31 support (three image terms of its
+  halo leave no shared memory for the kernel stages) and is refused there.
 - BF16: two roundings of <= 2^-8 per product: held to 5e-3.
 - FP8 E4M3: two roundings of <= 2^-4 per product (0.125 worst case, about 0.07
   rms): held to 0.1.
@@ -25,7 +27,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 LARGE = synth.workload("large_128x128x96_T512_k31_N60_P3")
-TOL = {"fp32": 1e-5, "bf16x3": 1e-4, "bf16": 5e-3, "fp8": 1e-1}
+TOL = {"fp32": 1e-5, "bf16x6": 1e-5, "bf16x3": 1e-4, "bf16": 5e-3, "fp8": 1e-1}
 
 
 def rel(a, b):
@@ -119,6 +121,12 @@ def large_full():
     f_ref = oracle.forward_at(g, s, K, c, nyx)
     a_ref = oracle.adjoint_at(g, s, K, w, pyxj)
     return g, s, K, c, w, nyx, pyxj, f_ref, a_ref
+
+
+def test_three_term_split_is_refused_on_the_31_wide_support(scaled):
+    prob, g, s, K, c, w, f_ref, a_ref = scaled
+    with pytest.raises(sw.SwoptError, match="no tensor-core configuration fits"):
+        sw.Operator(g, K, s, precision="bf16x6")
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16", "fp8"])
