@@ -37,6 +37,17 @@ def test_every_declared_symbol_is_exported():
     assert set(names) <= set(sw._SIGS)
 
 
+def test_binding_enums_match_the_header():
+    """The binding's precision and momentum names carry the header's values."""
+    text = open(os.path.join(ROOT, "include", "swopt.h")).read()
+    prec = {m.group(1).lower(): int(m.group(2))
+            for m in re.finditer(r"SWOPT_PREC_(\w+)\s*=\s*(\d+)", text)}
+    assert prec == sw.PRECISION
+    mom = {m.group(1).lower(): int(m.group(2))
+           for m in re.finditer(r"SWOPT_MOMENTUM_(\w+)\s*=\s*(\d+)", text)}
+    assert mom == sw.MOMENTUM
+
+
 def _geom(**kw):
     g = sw._Geometry(8, 8, 4, 16, 4, 2, 3, 2, 0.01)
     for k, v in kw.items():
